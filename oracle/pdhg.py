@@ -1,0 +1,388 @@
+"""Oracle PDHG for  min c^T x  s.t.  l_c <= A x <= u_c,  l_x <= x <= u_x  (eq. (1)).
+
+TEST INFRASTRUCTURE ONLY (see the package header).  FP64 throughout.
+
+The paper (Sec. 1 and Sec. 4.2) names the solver it times -- a restarted PDHG
+method in the PDLP / cuPDLP / cuPDLPx family -- but does not print its update,
+restart rule, step size, weights or termination formula.  This module writes
+those steps out from the LP and its optimality conditions (eq. (1), eq. (2))
+and from the published PDHG method the paper cites; every constant is a field
+of :class:`Opts`, the same fields the C ABI's ``lp_solve_opts`` carries.
+Readings (choices where the paper is silent) are marked READING.
+
+Pins (tests/test_oracle_pdhg.py): the planted optimum of every generator is a
+fixed point of the operator T for any step sizes; vertex enumeration and
+``scipy.optimize.linprog(method="highs")`` fix the optimal objective of tiny
+and small LPs; with rho = 0 and no anchor the iteration reproduces a textbook
+equality-form PDHG written independently; a 1 x 1 LP has a closed-form
+solution; rel-KKT takes hand-computed values on 1-D examples; the power
+iteration matches numpy's 2-norm; scaling leaves a signed permutation matrix
+unchanged.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+# termination codes (same numbering as the C ABI)
+OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL = 0, 1, 2, 3
+
+
+@dataclass
+class Opts:
+    eps_rel: float = 1e-6
+    max_iter: int = 200_000
+    time_limit_s: float = math.inf
+    check_every: int = 64  # K, READING: restart/termination checks every 64 iterations
+    rho: float = 1.0  # reflection, READING: 1 (r2HPDHG); rho = 0 is plain Halpern
+    beta_suff: float = 0.2  # READING: PDLP's restart constants
+    beta_nec: float = 0.8
+    beta_art: float = 0.36
+    theta: float = 0.5  # primal-weight smoothing
+    ruiz_iters: int = 10
+    pock_chambolle: bool = True
+    power_iters: int = 100
+    halpern: bool = True  # False: plain PDHG z <- (1+rho)T(z) - rho z (no anchor)
+    restarts: bool = True
+
+
+@dataclass
+class Result:
+    status: int
+    x: np.ndarray  # T(z) at termination, unscaled
+    y: np.ndarray
+    z: np.ndarray  # c - A^T y, unscaled (reduced costs of the returned y)
+    x_iter: np.ndarray  # current iterate z^t, unscaled
+    y_iter: np.ndarray
+    iterations: int
+    restarts: int
+    kkt: dict
+    eta: float
+    omega: float
+    omega0: float
+    iterates: list = field(default_factory=list)
+    checks: list = field(default_factory=list)
+
+
+# ----------------------------------------------------------------------------
+# problem access
+
+
+def csr_of(lp) -> sp.csr_matrix:
+    return sp.csr_matrix(
+        (np.asarray(lp.val, dtype=np.float64), np.asarray(lp.col_idx, dtype=np.int64),
+         np.asarray(lp.row_ptr, dtype=np.int64)), shape=(lp.m, lp.n))
+
+
+def box(v, lo, hi):
+    """Euclidean projection onto [lo, hi] (componentwise, infinite ends allowed)."""
+    return np.minimum(np.maximum(v, lo), hi)
+
+
+# ----------------------------------------------------------------------------
+# optimality measure (eq. (2))
+
+
+def dual_cone_project(g, col_lo, col_hi):
+    """Project g onto Lambda = prod_j Lambda_j, the sign set that eq. (2) allows
+    for z_j: {0} for a free column, [0, inf) if only the lower bound is finite,
+    (-inf, 0] if only the upper bound is finite, R if both are finite."""
+    lf = np.isfinite(col_lo)
+    uf = np.isfinite(col_hi)
+    lam = np.array(g, dtype=np.float64, copy=True)
+    lam[~lf & ~uf] = 0.0
+    only_l = lf & ~uf
+    only_u = ~lf & uf
+    lam[only_l] = np.maximum(lam[only_l], 0.0)
+    lam[only_u] = np.minimum(lam[only_u], 0.0)
+    return lam
+
+
+def dual_row_project(y, row_lo, row_hi):
+    """Sign domain of y_i from eq. (2): y_i <= 0 if row_lo_i = -inf,
+    y_i >= 0 if row_hi_i = +inf (so 0 if both are infinite)."""
+    out = np.array(y, dtype=np.float64, copy=True)
+    lf = np.isfinite(row_lo)
+    uf = np.isfinite(row_hi)
+    out[~lf] = np.minimum(out[~lf], 0.0)
+    out[~uf] = np.maximum(out[~uf], 0.0)
+    return out
+
+
+def _support(v, lo, hi):
+    """sum_i (v_i^+ lo_i - v_i^- hi_i) with 0 * inf := 0."""
+    pos = v > 0
+    neg = v < 0
+    s = 0.0
+    if pos.any():
+        s += float(np.sum(v[pos] * lo[pos]))
+    if neg.any():
+        s += float(np.sum(v[neg] * hi[neg]))
+    return s
+
+
+def bhat_norm(row_lo, row_hi):
+    """2-norm of the finite entries of row_lo and row_hi, equality rows once."""
+    lf = np.isfinite(row_lo)
+    uf = np.isfinite(row_hi) & ~(lf & (row_lo == row_hi))
+    return float(math.sqrt(np.sum(row_lo[lf] ** 2) + np.sum(row_hi[uf] ** 2)))
+
+
+def rel_kkt(lp, x, y, A=None):
+    """Relative KKT error of (x, y) for eq. (1), from the conditions of eq. (2).
+
+    READING (the paper fixes only eps_rel, not the formula): PDLP-style relative
+    measure
+      r_p   = || A x - proj_[l_c,u_c](A x) ||_2
+      lam   = proj_Lambda(c - A^T y)                      (sign rules of eq. (2))
+      r_d   = || (c - A^T y - lam,  y - proj_Y(y)) ||_2    (y outside its sign
+              domain counts as dual infeasibility; it never is for PDHG output)
+      p     = c^T x + off
+      d     = sum_i (yp_i^+ l_ci - yp_i^- u_ci) + sum_j (lam_j^+ l_xj - lam_j^- u_xj) + off,
+              yp = proj_Y(y), 0 * inf := 0
+      relKKT = max(r_p / (1 + ||bhat||), r_d / (1 + ||c||), |p - d| / (1 + |p| + |d|)).
+    x is taken as given (PDHG output lies in the column bounds).
+    """
+    if A is None:
+        A = csr_of(lp)
+    c = np.asarray(lp.c, dtype=np.float64)
+    lo, hi = np.asarray(lp.row_lo, np.float64), np.asarray(lp.row_hi, np.float64)
+    lx, ux = np.asarray(lp.col_lo, np.float64), np.asarray(lp.col_hi, np.float64)
+    ax = A @ x
+    rp_vec = ax - box(ax, lo, hi)
+    g = c - A.T @ y
+    lam = dual_cone_project(g, lx, ux)
+    yp = dual_row_project(y, lo, hi)
+    r_p = float(np.linalg.norm(rp_vec))
+    r_d = float(math.sqrt(np.sum((g - lam) ** 2) + np.sum((y - yp) ** 2)))
+    p = float(c @ x) + float(lp.obj_offset)
+    d = _support(yp, lo, hi) + _support(lam, lx, ux) + float(lp.obj_offset)
+    nb = bhat_norm(lo, hi)
+    nc = float(np.linalg.norm(c))
+    rel_p = r_p / (1.0 + nb)
+    rel_d = r_d / (1.0 + nc)
+    gap = abs(p - d)
+    rel_gap = gap / (1.0 + abs(p) + abs(d))
+    return {"r_p": r_p, "r_d": r_d, "gap": gap, "p": p, "d": d, "rel_p": rel_p,
+            "rel_d": rel_d, "rel_gap": rel_gap, "rel_kkt": max(rel_p, rel_d, rel_gap),
+            "bhat_norm": nb, "c_norm": nc}
+
+
+# ----------------------------------------------------------------------------
+# preconditioning and step size (READING: the paper is silent)
+
+
+def ruiz_pc_scaling(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool = True):
+    """Diagonal scalings D_r, D_c with scaled matrix D_r A D_c.
+
+    READING: ``ruiz_iters`` Ruiz equilibration passes, each dividing every row
+    and column of the current scaled matrix by the square root of its largest
+    absolute entry (both computed from the same current matrix; empty rows and
+    columns keep factor 1), then one Pock-Chambolle pass with alpha = 1
+    dividing by the square root of the absolute row and column sums.
+    """
+    m, n = A.shape
+    dr = np.ones(m)
+    dc = np.ones(n)
+    absA = abs(A).tocsr()
+    for _ in range(ruiz_iters):
+        S = sp.diags(dr) @ absA @ sp.diags(dc)
+        rmax = np.asarray(S.max(axis=1).todense()).ravel()
+        cmax = np.asarray(S.max(axis=0).todense()).ravel()
+        rmax = np.where(rmax > 0, rmax, 1.0)
+        cmax = np.where(cmax > 0, cmax, 1.0)
+        dr = dr / np.sqrt(rmax)
+        dc = dc / np.sqrt(cmax)
+    if pock_chambolle:
+        S = sp.diags(dr) @ absA @ sp.diags(dc)
+        rsum = np.asarray(S.sum(axis=1)).ravel()
+        csum = np.asarray(S.sum(axis=0)).ravel()
+        rsum = np.where(rsum > 0, rsum, 1.0)
+        csum = np.where(csum > 0, csum, 1.0)
+        dr = dr / np.sqrt(rsum)
+        dc = dc / np.sqrt(csum)
+    return dr, dc
+
+
+def power_norm(A: sp.spmatrix, iters: int = 100) -> float:
+    """Estimate ||A||_2 by power iteration on A^T A.
+
+    READING: start vector all-ones / sqrt(n); each step v <- A^T (A v) / ||.||;
+    the estimate is ||A v||_2 for the final unit vector v.
+    """
+    m, n = A.shape
+    if n == 0 or m == 0:
+        return 0.0
+    v = np.full(n, 1.0 / math.sqrt(n))
+    for _ in range(iters):
+        w = A.T @ (A @ v)
+        nw = float(np.linalg.norm(w))
+        if nw == 0.0:
+            return 0.0
+        v = w / nw
+    return float(np.linalg.norm(A @ v))
+
+
+# ----------------------------------------------------------------------------
+# the PDHG operator and the restarted Halpern iteration
+
+
+def pdhg_operator(A, c, lx, ux, lc, uc, x, y, tau, sigma):
+    """One PDHG step T(x, y) for the saddle problem of eq. (1):
+      xh = proj_[lx,ux](x - tau (c - A^T y))
+      xb = 2 xh - x
+      v  = y - sigma A xb
+      yh = v + sigma proj_[lc,uc](-v / sigma)   (prox of the row-bound conjugate)
+    """
+    xh = box(x - tau * (c - A.T @ y), lx, ux)
+    xb = 2.0 * xh - x
+    v = y - sigma * (A @ xb)
+    yh = v + sigma * box(-v / sigma, lc, uc)
+    return xh, yh
+
+
+class Scaled:
+    """The problem after scaling: A~ = D_r A D_c, c~ = D_c c, row bounds D_r l,
+    column bounds l / D_c."""
+
+    def __init__(self, lp, opts: Opts):
+        A = csr_of(lp)
+        self.A0 = A
+        self.dr, self.dc = ruiz_pc_scaling(A, opts.ruiz_iters, opts.pock_chambolle)
+        self.A = (sp.diags(self.dr) @ A @ sp.diags(self.dc)).tocsr()
+        self.c = self.dc * np.asarray(lp.c, np.float64)
+        self.lc = self.dr * np.asarray(lp.row_lo, np.float64)
+        self.uc = self.dr * np.asarray(lp.row_hi, np.float64)
+        self.lx = np.asarray(lp.col_lo, np.float64) / self.dc
+        self.ux = np.asarray(lp.col_hi, np.float64) / self.dc
+
+
+def default_omega(sc: Scaled) -> float:
+    """READING: omega_0 = ||c~||_2 / ||bhat~||_2, 1 if either is 0."""
+    nc = float(np.linalg.norm(sc.c))
+    nb = bhat_norm(sc.lc, sc.uc)
+    if nc > 0 and nb > 0:
+        return nc / nb
+    return 1.0
+
+
+def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
+               omega0: float | None = None, x_init=None, y_init=None,
+               record_iterates: int = 0, record_checks: bool = False) -> Result:
+    """Restarted reflected Halpern PDHG (READING of the solver the paper times).
+
+    State z = (x, y) in the scaled space, anchor z0, Halpern counter k.
+    Iteration t = 0, 1, ...:
+      1. (xh, yh) = T(z)                                   (pdhg_operator)
+      2. if t % K == 0 (a check):
+         a. stop if relKKT(unscaled xh, yh) <= eps_rel (return T(z)), or on
+            non-finite values, or past the time limit;
+         b. r = ||z - T(z)||_omega,  ||(a, b)||_omega^2 = omega ||a||^2 + ||b||^2 / omega;
+         c. k == 0 (t = 0): r0 = r_prev = r;
+            else restart if (i) r <= beta_suff r0, or (ii) r <= beta_nec r0 and
+            r > r_prev, or (iii) k >= beta_art t.  On restart: new anchor
+            z0' = T(z); primal weight omega <- exp(theta log(dy/dx) +
+            (1 - theta) log omega) with dx = ||x0' - x0||, dy = ||y0' - y0||
+            when both exceed 1e-10; z = z0 = T(z); k = 0; r0 = r_prev = r;
+            skip step 3.  Otherwise r_prev = r.
+      3. z <- lam_k ((1 + rho) T(z) - rho z) + (1 - lam_k) z0,  lam_k = (k+1)/(k+2);
+         k <- k + 1.   (halpern=False: z <- (1 + rho) T(z) - rho z.)
+    tau = eta / omega, sigma = eta * omega; eta = 0.998 / ||A~||_2 unless given.
+    Initial point (READING): x = proj_[lx~,ux~](0), y = 0, or the given warm start.
+    """
+    opts = opts or Opts()
+    sc = Scaled(lp, opts)
+    A = sc.A
+    m, n = A.shape
+    if eta is None:
+        nrm = power_norm(A, opts.power_iters)
+        eta = 0.998 / nrm if nrm > 0 else 1.0
+    if omega0 is None:
+        omega0 = default_omega(sc)
+    omega = float(omega0)
+    if x_init is None:
+        x = box(np.zeros(n), sc.lx, sc.ux)
+    else:
+        x = np.asarray(x_init, np.float64) / sc.dc
+    y = np.zeros(m) if y_init is None else np.asarray(y_init, np.float64) / sc.dr
+    x0, y0 = x.copy(), y.copy()
+    K = max(int(opts.check_every), 1)
+    k = 0
+    t = 0
+    restarts = 0
+    r0 = r_prev = None
+    status = ITER_LIMIT
+    kkt = None
+    xh = x
+    yh = y
+    iterates = []
+    checks = []
+    start = time.perf_counter()
+    if record_iterates:
+        iterates.append((sc.dc * x, sc.dr * y))
+    while t < opts.max_iter:
+        tau = eta / omega
+        sigma = eta * omega
+        xh, yh = pdhg_operator(A, sc.c, sc.lx, sc.ux, sc.lc, sc.uc, x, y, tau, sigma)
+        if t % K == 0:
+            kkt = rel_kkt(lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
+            if record_checks:
+                checks.append({"t": t, "rel_kkt": kkt["rel_kkt"], "omega": omega, "k": k})
+            if not (np.all(np.isfinite(xh)) and np.all(np.isfinite(yh))
+                    and math.isfinite(kkt["rel_kkt"])):
+                status = NUMERICAL
+            elif kkt["rel_kkt"] <= opts.eps_rel:
+                status = OPTIMAL
+            elif time.perf_counter() - start > opts.time_limit_s:
+                status = TIME_LIMIT
+            if status != ITER_LIMIT:
+                t += 1  # count this evaluation of T
+                break
+            r = math.sqrt(omega * float(np.sum((x - xh) ** 2))
+                          + float(np.sum((y - yh) ** 2)) / omega)
+            if k == 0:
+                r0 = r_prev = r
+            elif opts.restarts and (
+                r <= opts.beta_suff * r0
+                or (r <= opts.beta_nec * r0 and r > r_prev)
+                or k >= opts.beta_art * t
+            ):
+                dx = float(np.linalg.norm(xh - x0))
+                dy = float(np.linalg.norm(yh - y0))
+                if dx > 1e-10 and dy > 1e-10:
+                    omega = math.exp(opts.theta * math.log(dy / dx)
+                                     + (1.0 - opts.theta) * math.log(omega))
+                x, y = xh.copy(), yh.copy()
+                x0, y0 = xh.copy(), yh.copy()
+                k = 0
+                r0 = r_prev = r
+                restarts += 1
+                t += 1
+                if record_iterates and t <= record_iterates:
+                    iterates.append((sc.dc * x, sc.dr * y))
+                continue
+            else:
+                r_prev = r
+        if opts.halpern:
+            lam = (k + 1.0) / (k + 2.0)
+            x = lam * ((1.0 + opts.rho) * xh - opts.rho * x) + (1.0 - lam) * x0
+            y = lam * ((1.0 + opts.rho) * yh - opts.rho * y) + (1.0 - lam) * y0
+        else:
+            x = (1.0 + opts.rho) * xh - opts.rho * x
+            y = (1.0 + opts.rho) * yh - opts.rho * y
+        k += 1
+        t += 1
+        if record_iterates and t <= record_iterates:
+            iterates.append((sc.dc * x, sc.dr * y))
+    if kkt is None or status == ITER_LIMIT:
+        kkt = rel_kkt(lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
+    xs = sc.dc * xh
+    ys = sc.dr * yh
+    zs = np.asarray(lp.c, np.float64) - sc.A0.T @ ys
+    return Result(status=status, x=xs, y=ys, z=zs, x_iter=sc.dc * x, y_iter=sc.dr * y,
+                  iterations=t, restarts=restarts, kkt=kkt, eta=float(eta), omega=omega,
+                  omega0=float(omega0), iterates=iterates, checks=checks)

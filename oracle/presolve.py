@@ -1,0 +1,510 @@
+"""Oracle presolve / postsolve for eq. (1): the simple rules of Sec. 2-3.
+
+TEST INFRASTRUCTURE ONLY (see the package header).  Plain Python loops over
+dict-of-dicts row and column storage; slow, meant for small and medium LPs.
+
+A reduction is a presolve transformation plus a postsolve transformation
+(Sec. 2.1).  The explorers used here are the fast ones of Table 1 (empty rows
+and columns, fixed columns, singleton rows, redundant rows / dominated row
+sides from activity bounds, doubleton equality rows, free or implied-free
+column singletons in equality rows), run in rounds that re-examine only what
+the previous round touched (Sec. 3.2).
+
+Schedule (READING): each round runs the passes
+    empty rows -> empty cols -> fixed cols -> singleton rows
+    -> redundant rows / dominated sides -> doubleton equalities
+    -> free column singletons,
+each pass scanning its candidates in increasing index order.  Round 1 scans
+every row and column; later rounds scan the rows and columns marked dirty in
+the previous round.  Stop after a round with no reduction or after 20 rounds.
+
+Dirty marking: removing, adding or changing an entry (i, j) dirties row i and
+column j; changing row bounds dirties the row; changing column bounds dirties
+the column and every row holding it; changing c_j dirties column j.
+
+Tolerances (READING): infeasibility is declared when a lower bound exceeds an
+upper bound by more than 1e-9; coefficients below 1e-12 in magnitude after an
+update are dropped.  Activity sums run over a row's entries in increasing
+column order; comparisons of activities with row bounds are exact.
+
+Postsolve replays the records in reverse order and keeps eq. (2)'s dual
+feasibility c - A^T y - z = 0 of every intermediate problem:
+  empty row / redundant row      y_i = 0
+  dropped row side               nothing (y keeps a sign valid for the old row)
+  fixed / empty column (value v) x_j = v,  z_j = c_j - sum_i a_ij y_i
+                                 (the fix-variable postsolve of Sec. 2.1)
+  singleton row a x_j in [l, u]  if z_j > 0 and the lower bound of x_j came
+                                 from the row, or z_j < 0 and the upper bound
+                                 did: y_i = z_j / a, z_j = 0; else y_i = 0
+  doubleton a_j x_j + a_k x_k = b   x_j = (b - a_k x_k) / a_j,
+                                 D_j = c_j - sum_{r != i} a_rj y_r;
+                                 if the active bound of x_k (sign of z_k) was
+                                 transferred from x_j: y_i = (z_k + (a_k/a_j) D_j)/a_k,
+                                 z_j = D_j - a_j y_i, z_k = 0;
+                                 else y_i = D_j / a_j, z_j = 0 (z_k unchanged)
+  free column singleton          x_j = (b - sum_{r != j} a_ir x_r) / a_ij,
+                                 y_i = c_j / a_ij, z_j = 0
+
+Pins (tests/test_oracle_presolve.py): the worked examples of Sec. 2 (fixing a
+variable; the redundant row x1 >= 1, x2 >= 2, x1 + 2 x2 >= 5; the doubleton
+x1 + x2 = 1, x >= 0); and the invariant that postsolve of an exact solution of
+the reduced problem (HiGHS) is a KKT point of the original problem whose
+objective equals the planted optimum.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FEAS_TOL = 1e-9
+DROP_TOL = 1e-12
+MAX_ROUNDS = 20
+
+REDUCED, INFEASIBLE, UNBOUNDED, SOLVED = 0, 1, 2, 3
+
+INF = math.inf
+
+
+@dataclass
+class PresolveResult:
+    status: int
+    reduced: object  # a plain LP container (same attribute names as the input)
+    row_map: np.ndarray  # reduced row index -> original row
+    col_map: np.ndarray  # reduced col index -> original col
+    records: list
+    rounds: int
+    counts: dict = field(default_factory=dict)
+    m0: int = 0
+    n0: int = 0
+    seconds: float = 0.0
+
+
+class _LP:
+    def __init__(self, m, n, row_ptr, col_idx, val, c, off, lo, hi, lx, ux):
+        self.m, self.n = m, n
+        self.row_ptr, self.col_idx, self.val = row_ptr, col_idx, val
+        self.c, self.obj_offset = c, off
+        self.row_lo, self.row_hi, self.col_lo, self.col_hi = lo, hi, lx, ux
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
+class Presolver:
+    def __init__(self, lp):
+        self.m, self.n = int(lp.m), int(lp.n)
+        self.rows = [dict() for _ in range(self.m)]
+        self.cols = [dict() for _ in range(self.n)]
+        rp = np.asarray(lp.row_ptr, np.int64)
+        ci = np.asarray(lp.col_idx, np.int64)
+        va = np.asarray(lp.val, np.float64)
+        for i in range(self.m):
+            for k in range(int(rp[i]), int(rp[i + 1])):
+                j = int(ci[k])
+                v = float(va[k])
+                if v != 0.0:
+                    self.rows[i][j] = v
+                    self.cols[j][i] = v
+        self.c = [float(v) for v in lp.c]
+        self.off = float(lp.obj_offset)
+        self.lo = [float(v) for v in lp.row_lo]
+        self.hi = [float(v) for v in lp.row_hi]
+        self.lx = [float(v) for v in lp.col_lo]
+        self.ux = [float(v) for v in lp.col_hi]
+        self.row_on = [True] * self.m
+        self.col_on = [True] * self.n
+        self.records = []
+        self.dirty_r = set()
+        self.dirty_c = set()
+        self.changed = False
+        self.status = REDUCED
+        self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
+                                      "redundant_row", "dropped_side", "doubleton",
+                                      "free_col_singleton")}
+
+    # -- primitive edits with dirty marking --------------------------------
+    def _mark_col_bounds(self, j):
+        self.dirty_c.add(j)
+        for i in self.cols[j]:
+            self.dirty_r.add(i)
+
+    def _remove_entry(self, i, j):
+        del self.rows[i][j]
+        del self.cols[j][i]
+        self.dirty_r.add(i)
+        self.dirty_c.add(j)
+
+    def _set_entry(self, i, j, v):
+        if abs(v) < DROP_TOL:
+            if j in self.rows[i]:
+                self._remove_entry(i, j)
+            return
+        self.rows[i][j] = v
+        self.cols[j][i] = v
+        self.dirty_r.add(i)
+        self.dirty_c.add(j)
+
+    def _remove_row(self, i):
+        for j in list(self.rows[i].keys()):
+            self._remove_entry(i, j)
+        self.row_on[i] = False
+
+    def _remove_col(self, j):
+        for i in list(self.cols[j].keys()):
+            self._remove_entry(i, j)
+        self.col_on[j] = False
+
+    def _activity(self, i, skip=-1):
+        """(min, max) of sum_j a_ij x_j over the column bounds, ascending j."""
+        lo_s = 0.0
+        hi_s = 0.0
+        lo_inf = 0
+        hi_inf = 0
+        for j in sorted(self.rows[i]):
+            if j == skip:
+                continue
+            a = self.rows[i][j]
+            if a > 0:
+                bl, bu = self.lx[j], self.ux[j]
+            else:
+                bl, bu = self.ux[j], self.lx[j]
+            if math.isinf(bl):
+                lo_inf += 1
+            else:
+                lo_s += a * bl
+            if math.isinf(bu):
+                hi_inf += 1
+            else:
+                hi_s += a * bu
+        return (-INF if lo_inf else lo_s), (INF if hi_inf else hi_s)
+
+    # -- rules ---------------------------------------------------------------
+    def empty_row(self, i):
+        if self.lo[i] > FEAS_TOL or self.hi[i] < -FEAS_TOL:
+            self.status = INFEASIBLE
+            return
+        self.records.append(("empty_row", i))
+        self.row_on[i] = False
+        self.counts["empty_row"] += 1
+        self.changed = True
+
+    def empty_col(self, j):
+        cj = self.c[j]
+        if cj > 0:
+            v = self.lx[j]
+        elif cj < 0:
+            v = self.ux[j]
+        else:
+            v = min(max(0.0, self.lx[j]), self.ux[j])
+        if math.isinf(v):
+            self.status = UNBOUNDED
+            return
+        self.off += cj * v
+        self.records.append(("fix_col", j, v, cj, []))
+        self.col_on[j] = False
+        self.dirty_c.add(j)
+        self.counts["empty_col"] += 1
+        self.changed = True
+
+    def fixed_col(self, j):
+        v = self.lx[j]
+        entries = sorted(self.cols[j].items())
+        for i, a in entries:
+            if not math.isinf(self.lo[i]):
+                self.lo[i] -= a * v
+            if not math.isinf(self.hi[i]):
+                self.hi[i] -= a * v
+            self.dirty_r.add(i)
+        self.off += self.c[j] * v
+        self.records.append(("fix_col", j, v, self.c[j], entries))
+        self._remove_col(j)
+        self.counts["fixed_col"] += 1
+        self.changed = True
+
+    def singleton_row(self, i):
+        (j, a), = self.rows[i].items()
+        if a > 0:
+            ilo = self.lo[i] / a if not math.isinf(self.lo[i]) else -INF
+            ihi = self.hi[i] / a if not math.isinf(self.hi[i]) else INF
+        else:
+            ilo = self.hi[i] / a if not math.isinf(self.hi[i]) else -INF
+            ihi = self.lo[i] / a if not math.isinf(self.lo[i]) else INF
+        lo_from = ilo > self.lx[j]
+        hi_from = ihi < self.ux[j]
+        nl = ilo if lo_from else self.lx[j]
+        nu = ihi if hi_from else self.ux[j]
+        if nl > nu + FEAS_TOL:
+            self.status = INFEASIBLE
+            return
+        if nl > nu:
+            nl = nu = 0.5 * (nl + nu)
+        self.records.append(("singleton_row", i, j, a, lo_from, hi_from))
+        self._remove_row(i)
+        if nl != self.lx[j] or nu != self.ux[j]:
+            self.lx[j] = nl
+            self.ux[j] = nu
+            self._mark_col_bounds(j)
+        self.counts["singleton_row"] += 1
+        self.changed = True
+
+    def redundant_row(self, i):
+        lo, hi = self.lo[i], self.hi[i]
+        if lo == hi:
+            return
+        amin, amax = self._activity(i)
+        lo_imp = math.isinf(lo) or amin >= lo
+        hi_imp = math.isinf(hi) or amax <= hi
+        if lo_imp and hi_imp:
+            self.records.append(("redundant_row", i))
+            self._remove_row(i)
+            self.counts["redundant_row"] += 1
+            self.changed = True
+        elif lo_imp and not math.isinf(lo):
+            self.records.append(("drop_side", i, 0, lo))
+            self.lo[i] = -INF
+            self.dirty_r.add(i)
+            self.counts["dropped_side"] += 1
+            self.changed = True
+        elif hi_imp and not math.isinf(hi):
+            self.records.append(("drop_side", i, 1, hi))
+            self.hi[i] = INF
+            self.dirty_r.add(i)
+            self.counts["dropped_side"] += 1
+            self.changed = True
+
+    def doubleton(self, i):
+        (p, ap), (q, aq) = sorted(self.rows[i].items())
+        b = self.lo[i]
+        # eliminate the larger |a| (so |a_k / a_j| <= 1); ties: fewer column
+        # entries, then lower index
+        if abs(ap) > abs(aq):
+            j, aj, k, ak = p, ap, q, aq
+        elif abs(aq) > abs(ap):
+            j, aj, k, ak = q, aq, p, ap
+        elif len(self.cols[q]) < len(self.cols[p]):
+            j, aj, k, ak = q, aq, p, ap
+        else:
+            j, aj, k, ak = p, ap, q, aq
+        r = ak / aj
+        s = b / aj
+        # l_j <= s - r x_k <= u_j  ->  r x_k in [s - u_j, s - l_j]
+        t_lo = s - self.ux[j] if not math.isinf(self.ux[j]) else -INF
+        t_hi = s - self.lx[j] if not math.isinf(self.lx[j]) else INF
+        if r > 0:
+            ilo = t_lo / r if not math.isinf(t_lo) else -INF
+            ihi = t_hi / r if not math.isinf(t_hi) else INF
+        else:
+            ilo = t_hi / r if not math.isinf(t_hi) else -INF
+            ihi = t_lo / r if not math.isinf(t_lo) else INF
+        lo_from = ilo > self.lx[k]
+        hi_from = ihi < self.ux[k]
+        nl = ilo if lo_from else self.lx[k]
+        nu = ihi if hi_from else self.ux[k]
+        if nl > nu + FEAS_TOL:
+            self.status = INFEASIBLE
+            return
+        if nl > nu:
+            nl = nu = 0.5 * (nl + nu)
+        colj = sorted((rr, a) for rr, a in self.cols[j].items() if rr != i)
+        cj = self.c[j]
+        self.records.append(("doubleton", i, j, k, aj, ak, b, cj, lo_from, hi_from, colj))
+        # objective: c_j x_j = c_j s - c_j r x_k
+        self.off += cj * s
+        if cj != 0.0:
+            self.c[k] -= cj * r
+            self.dirty_c.add(k)
+        # substitute into the other rows of column j
+        for rr, a in colj:
+            if not math.isinf(self.lo[rr]):
+                self.lo[rr] -= a * s
+            if not math.isinf(self.hi[rr]):
+                self.hi[rr] -= a * s
+            old = self.rows[rr].get(k, 0.0)
+            self._remove_entry(rr, j)
+            self._set_entry(rr, k, old - a * r)
+        self._remove_row(i)
+        self._remove_col(j)
+        if nl != self.lx[k] or nu != self.ux[k]:
+            self.lx[k] = nl
+            self.ux[k] = nu
+            self._mark_col_bounds(k)
+        self.counts["doubleton"] += 1
+        self.changed = True
+
+    def free_col_singleton(self, j):
+        (i, a), = self.cols[j].items()
+        if not self.row_on[i] or self.lo[i] != self.hi[i] or len(self.rows[i]) < 2:
+            return
+        b = self.lo[i]
+        free = math.isinf(self.lx[j]) and math.isinf(self.ux[j])
+        if not free:
+            amin, amax = self._activity(i, skip=j)
+            if a > 0:
+                ilo, ihi = (b - amax) / a, (b - amin) / a
+            else:
+                ilo, ihi = (b - amin) / a, (b - amax) / a
+            if not (ilo >= self.lx[j] and ihi <= self.ux[j]):
+                return
+        cj = self.c[j]
+        others = sorted((r, v) for r, v in self.rows[i].items() if r != j)
+        self.records.append(("free_col_singleton", i, j, a, b, cj, others))
+        self.off += cj * b / a
+        if cj != 0.0:
+            for r, v in others:
+                self.c[r] -= cj * v / a
+                self.dirty_c.add(r)
+        self._remove_row(i)
+        self._remove_col(j)
+        self.counts["free_col_singleton"] += 1
+        self.changed = True
+
+    # -- driver ----------------------------------------------------------------
+    def run(self, max_rounds=MAX_ROUNDS):
+        rows_c = list(range(self.m))
+        cols_c = list(range(self.n))
+        rounds = 0
+        for rnd in range(max_rounds):
+            rounds = rnd + 1
+            self.dirty_r = set()
+            self.dirty_c = set()
+            self.changed = False
+            for i in rows_c:
+                if self.row_on[i] and not self.rows[i]:
+                    self.empty_row(i)
+                    if self.status != REDUCED:
+                        return rounds
+            for j in cols_c:
+                if self.col_on[j] and not self.cols[j]:
+                    self.empty_col(j)
+                    if self.status != REDUCED:
+                        return rounds
+            for j in cols_c:
+                if self.col_on[j] and self.lx[j] == self.ux[j]:
+                    self.fixed_col(j)
+            for i in rows_c:
+                if self.row_on[i] and len(self.rows[i]) == 1:
+                    self.singleton_row(i)
+                    if self.status != REDUCED:
+                        return rounds
+            for i in rows_c:
+                if self.row_on[i] and len(self.rows[i]) >= 1:
+                    self.redundant_row(i)
+            for i in rows_c:
+                if (self.row_on[i] and len(self.rows[i]) == 2
+                        and self.lo[i] == self.hi[i]):
+                    self.doubleton(i)
+                    if self.status != REDUCED:
+                        return rounds
+            for j in cols_c:
+                if self.col_on[j] and len(self.cols[j]) == 1:
+                    self.free_col_singleton(j)
+            if not self.changed:
+                break
+            rows_c = sorted(i for i in self.dirty_r if self.row_on[i])
+            cols_c = sorted(j for j in self.dirty_c if self.col_on[j])
+        return rounds
+
+    def reduced(self):
+        rmap = np.array([i for i in range(self.m) if self.row_on[i]], dtype=np.int64)
+        cmap = np.array([j for j in range(self.n) if self.col_on[j]], dtype=np.int64)
+        cpos = -np.ones(self.n, dtype=np.int64)
+        cpos[cmap] = np.arange(cmap.shape[0])
+        rp = [0]
+        ci = []
+        va = []
+        for i in rmap:
+            for j in sorted(self.rows[i]):
+                ci.append(cpos[j])
+                va.append(self.rows[i][j])
+            rp.append(len(ci))
+        lp = _LP(int(rmap.shape[0]), int(cmap.shape[0]), np.array(rp, dtype=np.int64),
+                 np.array(ci, dtype=np.int32), np.array(va, dtype=np.float64),
+                 np.array([self.c[j] for j in cmap], dtype=np.float64), self.off,
+                 np.array([self.lo[i] for i in rmap], dtype=np.float64),
+                 np.array([self.hi[i] for i in rmap], dtype=np.float64),
+                 np.array([self.lx[j] for j in cmap], dtype=np.float64),
+                 np.array([self.ux[j] for j in cmap], dtype=np.float64))
+        return lp, rmap, cmap
+
+
+def presolve(lp, max_rounds: int = MAX_ROUNDS) -> PresolveResult:
+    t0 = time.perf_counter()
+    ps = Presolver(lp)
+    rounds = ps.run(max_rounds)
+    red, rmap, cmap = ps.reduced()
+    status = ps.status
+    if status == REDUCED and red.m == 0 and red.n == 0:
+        status = SOLVED
+    return PresolveResult(status=status, reduced=red, row_map=rmap, col_map=cmap,
+                          records=ps.records, rounds=rounds, counts=ps.counts,
+                          m0=ps.m, n0=ps.n, seconds=time.perf_counter() - t0)
+
+
+def postsolve(res: PresolveResult, x_red, y_red, z_red=None):
+    """Map a (approximate) solution of the reduced LP to (x, y, z) of the
+    original LP by replaying the postsolve records in reverse."""
+    x = np.zeros(res.n0)
+    y = np.zeros(res.m0)
+    z = np.zeros(res.n0)
+    red = res.reduced
+    x[res.col_map] = x_red
+    y[res.row_map] = y_red
+    if z_red is None:
+        A = _csr(red)
+        z_red = np.asarray(red.c, np.float64) - A.T @ np.asarray(y_red, np.float64)
+    z[res.col_map] = z_red
+    for rec in reversed(res.records):
+        kind = rec[0]
+        if kind in ("empty_row", "redundant_row"):
+            y[rec[1]] = 0.0
+        elif kind == "drop_side":
+            pass
+        elif kind == "fix_col":
+            _, j, v, cj, entries = rec
+            x[j] = v
+            s = cj
+            for i, a in entries:
+                s -= a * y[i]
+            z[j] = s
+        elif kind == "singleton_row":
+            _, i, j, a, lo_from, hi_from = rec
+            if (z[j] > 0 and lo_from) or (z[j] < 0 and hi_from):
+                y[i] = z[j] / a
+                z[j] = 0.0
+            else:
+                y[i] = 0.0
+        elif kind == "doubleton":
+            _, i, j, k, aj, ak, b, cj, lo_from, hi_from, colj = rec
+            x[j] = (b - ak * x[k]) / aj
+            dj = cj
+            for rr, a in colj:
+                dj -= a * y[rr]
+            if (z[k] > 0 and lo_from) or (z[k] < 0 and hi_from):
+                y[i] = (z[k] + (ak / aj) * dj) / ak
+                z[j] = dj - aj * y[i]
+                z[k] = 0.0
+            else:
+                y[i] = dj / aj
+                z[j] = 0.0
+        elif kind == "free_col_singleton":
+            _, i, j, a, b, cj, others = rec
+            s = b
+            for r, v in others:
+                s -= v * x[r]
+            x[j] = s / a
+            y[i] = cj / a
+            z[j] = 0.0
+        else:  # pragma: no cover
+            raise ValueError(kind)
+    return x, y, z
+
+
+def _csr(lp):
+    import scipy.sparse as sp
+
+    return sp.csr_matrix((np.asarray(lp.val, np.float64), np.asarray(lp.col_idx, np.int64),
+                          np.asarray(lp.row_ptr, np.int64)), shape=(lp.m, lp.n))

@@ -1,0 +1,288 @@
+"""Pins for the oracle PDHG (CPU only).
+
+Each pin ties the oracle to something other than itself: the planted optimum
+(fixed by construction through eq. (2)), vertex enumeration, scipy's HiGHS,
+hand-computed values, numpy's matrix 2-norm, or a textbook equality-form PDHG
+written here independently of the oracle's general prox form.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+from oracle import pdhg as P
+from oracle.vertex import vertex_optimum
+from lp_helpers import SimpleLP, highs_solve
+
+
+def rel_obj_err(p, q):
+    return abs(p - q) / (1.0 + abs(q))
+
+
+# ---------------------------------------------------------------------------
+# the planted optimum is a fixed point of T for any step sizes
+
+
+@pytest.mark.parametrize("make", [
+    lambda: lpgen.c1_small(),
+    lambda: lpgen.general_structure(300, 700, 11, nnz_target=4000, one_sided=0.3),
+    lambda: lpgen.c3_powerlaw(seed=5, m=400, n=1000, row_nnz_target=6000, n_dense=5,
+                              dense_len=60),
+    lambda: lpgen.tiny_box(4, 6, 3),
+])
+def test_planted_point_is_fixed_point(make):
+    lp = make()
+    sc = P.Scaled(lp, P.Opts())
+    xs, ys = lp.x_star / sc.dc, lp.y_star / sc.dr
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        tau, sigma = rng.uniform(0.01, 2.0, size=2)
+        xh, yh = P.pdhg_operator(sc.A, sc.c, sc.lx, sc.ux, sc.lc, sc.uc, xs, ys, tau, sigma)
+        assert np.max(np.abs(xh - xs)) <= 1e-9 * (1 + np.max(np.abs(xs)))
+        assert np.max(np.abs(yh - ys)) <= 1e-9 * (1 + np.max(np.abs(ys)))
+    k = oracle.rel_kkt(lp, lp.x_star, lp.y_star)
+    assert k["rel_kkt"] <= 1e-12
+
+
+def test_planted_point_moves_when_perturbed():
+    # a non-optimal point is not a fixed point (guards against a T that is the identity)
+    lp = lpgen.c1_small()
+    sc = P.Scaled(lp, P.Opts())
+    xs, ys = lp.x_star / sc.dc + 0.01, lp.y_star / sc.dr
+    xh, yh = P.pdhg_operator(sc.A, sc.c, sc.lx, sc.ux, sc.lc, sc.uc, xs, ys, 0.5, 0.5)
+    assert np.max(np.abs(xh - xs)) + np.max(np.abs(yh - ys)) > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# vertex enumeration and HiGHS fix the objective
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_vertex_enumeration_agrees_with_highs_and_plant(seed):
+    lp = lpgen.tiny_box(4, 5, seed)
+    pv, _ = vertex_optimum(lp)
+    ph, _, _ = highs_solve(lp)
+    assert abs(pv - ph) <= 1e-9 * (1 + abs(ph))
+    assert abs(pv - lp.p_star) <= 1e-9 * (1 + abs(pv))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_pdhg_reaches_vertex_optimum(seed):
+    lp = lpgen.tiny_box(4, 5, seed)
+    pv, _ = vertex_optimum(lp)
+    r = oracle.pdhg_solve(lp, P.Opts(eps_rel=1e-8))
+    assert r.status == P.OPTIMAL
+    assert r.kkt["rel_kkt"] <= 1e-8
+    assert rel_obj_err(r.kkt["p"], pv) <= 1e-6
+
+
+def test_c1_converges_to_planted_optimum():
+    lp = lpgen.c1_small()
+    ph, _, _ = highs_solve(lp)
+    assert rel_obj_err(ph, lp.p_star) <= 1e-9
+    r = oracle.pdhg_solve(lp)
+    assert r.status == P.OPTIMAL
+    assert r.kkt["rel_kkt"] <= 1e-6
+    assert rel_obj_err(r.kkt["p"], lp.p_star) <= 1e-6
+    assert r.restarts >= 1
+
+
+def test_small_presolvable_structure_converges():
+    lp = lpgen.general_structure(400, 1000, 21, nnz_target=8000, one_sided=0.2)
+    ph, _, _ = highs_solve(lp)
+    assert rel_obj_err(ph, lp.p_star) <= 1e-8
+    r = oracle.pdhg_solve(lp)
+    assert r.status == P.OPTIMAL
+    assert rel_obj_err(r.kkt["p"], lp.p_star) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# special cases that reduce to a textbook method
+
+
+def _textbook_equality_pdhg(A, b, c, tau, sigma, iters, halpern, rho):
+    """Textbook PDHG for min c^T x, A x = b, x >= 0 (dense, no scaling):
+    x+ = max(0, x - tau (c - A^T y)),  y+ = y + sigma (b - A (2 x+ - x));
+    optionally reflected (rho) and Halpern-anchored at the start point."""
+    m, n = A.shape
+    x = np.zeros(n)
+    y = np.zeros(m)
+    x0, y0 = x.copy(), y.copy()
+    out = []
+    for k in range(iters):
+        xp = np.maximum(0.0, x - tau * (c - A.T @ y))
+        yp = y + sigma * (b - A @ (2 * xp - x))
+        rx, ry = (1 + rho) * xp - rho * x, (1 + rho) * yp - rho * y
+        if halpern:
+            w = (k + 1) / (k + 2)
+            x, y = w * rx + (1 - w) * x0, w * ry + (1 - w) * y0
+        else:
+            x, y = rx, ry
+        out.append((x.copy(), y.copy()))
+    return out
+
+
+@pytest.mark.parametrize("halpern,rho", [(False, 0.0), (True, 0.0), (True, 1.0), (True, 0.5)])
+def test_matches_textbook_equality_pdhg(halpern, rho):
+    lp = lpgen.equality_nonneg(30, 60, 5, 3, 8)
+    A = lp.csr().toarray()
+    b = lp.row_lo.copy()
+    opts = P.Opts(max_iter=40, check_every=10_000, ruiz_iters=0, pock_chambolle=False,
+                  halpern=halpern, rho=rho, restarts=False)
+    eta, omega = 0.9 / np.linalg.norm(A, 2), 1.7
+    r = oracle.pdhg_solve(lp, opts, eta=eta, omega0=omega, record_iterates=40)
+    ref = _textbook_equality_pdhg(A, b, lp.c, eta / omega, eta * omega, 40, halpern, rho)
+    for k in range(40):
+        xo, yo = r.iterates[k + 1]
+        xr, yr = ref[k]
+        assert np.allclose(xo, xr, rtol=1e-12, atol=1e-12)
+        assert np.allclose(yo, yr, rtol=1e-12, atol=1e-12)
+
+
+def test_matches_textbook_inequality_pdhg():
+    # A x >= b, x >= 0: textbook y+ = max(0, y + sigma (b - A xbar))
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((12, 20))
+    b = rng.standard_normal(12)
+    c = np.abs(rng.standard_normal(20))
+    lp = SimpleLP(A, c, b, np.full(12, np.inf), np.zeros(20), np.full(20, np.inf))
+    opts = P.Opts(max_iter=30, check_every=10_000, ruiz_iters=0, pock_chambolle=False,
+                  halpern=False, rho=0.0, restarts=False)
+    tau, sigma = 0.05, 0.08
+    eta, omega = math.sqrt(tau * sigma), math.sqrt(sigma / tau)
+    r = oracle.pdhg_solve(lp, opts, eta=eta, omega0=omega, record_iterates=30)
+    x = np.zeros(20)
+    y = np.zeros(12)
+    for k in range(30):
+        xp = np.maximum(0, x - tau * (c - A.T @ y))
+        y = np.maximum(0, y + sigma * (b - A @ (2 * xp - x)))
+        x = xp
+        xo, yo = r.iterates[k + 1]
+        assert np.allclose(xo, x, atol=1e-11)
+        assert np.allclose(yo, y, atol=1e-11)
+
+
+def test_one_by_one_closed_form():
+    # min -3 x  s.t. 1 <= 2 x <= 5, 0 <= x <= 2: optimum x = min(2, 5/2) = 2, p = -6;
+    # the row is inactive at x = 2 (2x = 4 < 5) so y = 0 and z = c = -3 (upper bound).
+    lp = SimpleLP([[2.0]], [-3.0], [1.0], [5.0], [0.0], [2.0])
+    r = oracle.pdhg_solve(lp, P.Opts(eps_rel=1e-10))
+    assert r.status == P.OPTIMAL
+    assert abs(r.x[0] - 2.0) <= 1e-8
+    assert abs(r.kkt["p"] + 6.0) <= 1e-8
+    # tighten the row: 2 x <= 3 -> x = 1.5, y = c / a = -1.5, z = 0
+    lp = SimpleLP([[2.0]], [-3.0], [1.0], [3.0], [0.0], [2.0])
+    r = oracle.pdhg_solve(lp, P.Opts(eps_rel=1e-10))
+    assert abs(r.x[0] - 1.5) <= 1e-8 and abs(r.y[0] + 1.5) <= 1e-8
+    assert abs(r.kkt["p"] + 4.5) <= 1e-8
+
+
+def test_first_check_restarts_and_resets_to_T():
+    # criterion (iii) holds at the first check after t = 0 (k = t); after 65
+    # evaluations of T the state is T(z^64), i.e. the anchor
+    lp = lpgen.c1_small()
+    r = oracle.pdhg_solve(lp, P.Opts(max_iter=65, eps_rel=0.0))
+    assert r.restarts == 1
+    r64 = oracle.pdhg_solve(lp, P.Opts(max_iter=65, eps_rel=0.0, restarts=False))
+    # T(z^64) is the returned x of the no-restart run (last T evaluated)
+    assert np.allclose(r.x_iter, r64.x, atol=1e-13)
+    assert np.allclose(r.y_iter, r64.y, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# rel-KKT on hand-computed examples
+
+
+def test_rel_kkt_hand_values():
+    # min 2x  s.t. 1 <= x <= 3, 0 <= x <= 10, at x = 0.5, y = 1:
+    # Ax = 0.5 -> r_p = 0.5; c - A^T y = 1, column boxed -> lam = 1, r_d = 0;
+    # p = 1, d = y*1 + lam*0 = 1; ||bhat|| = sqrt(1 + 9).
+    lp = SimpleLP([[1.0]], [2.0], [1.0], [3.0], [0.0], [10.0])
+    k = oracle.rel_kkt(lp, np.array([0.5]), np.array([1.0]))
+    assert k["r_p"] == 0.5 and k["r_d"] == 0.0
+    assert k["p"] == 1.0 and k["d"] == 1.0
+    assert abs(k["rel_p"] - 0.12012653667602105) < 1e-15
+    assert abs(k["rel_kkt"] - 0.12012653667602105) < 1e-15
+    # free column: lam = 0, r_d = |c - a y| = |2 - 3| = 1; y = 3 on a row with
+    # l = 1: d = 3, p = 2 * 2 = 4 at x = 2 (feasible), gap 1 / (1 + 4 + 3)
+    lp = SimpleLP([[1.0]], [2.0], [1.0], [3.0], [-np.inf], [np.inf])
+    k = oracle.rel_kkt(lp, np.array([2.0]), np.array([3.0]))
+    assert k["r_p"] == 0.0 and k["r_d"] == 1.0
+    assert k["p"] == 4.0 and k["d"] == 3.0
+    assert abs(k["rel_d"] - 1.0 / 3.0) < 1e-15
+    assert abs(k["rel_gap"] - 0.125) < 1e-15
+    # row with only a lower side: y must be >= 0; y = -2 is out of its domain
+    # (counts 2 in r_d, and yp = 0 in d); x >= 0 column: c - A^T y = 1 - (-2) = 3 >= 0
+    lp = SimpleLP([[1.0]], [1.0], [1.0], [np.inf], [0.0], [np.inf])
+    k = oracle.rel_kkt(lp, np.array([1.0]), np.array([-2.0]))
+    assert k["r_d"] == 2.0
+    assert k["d"] == 0.0 and k["p"] == 1.0
+
+
+# ---------------------------------------------------------------------------
+# step size and scaling
+
+
+def test_power_norm_matches_numpy():
+    rng = np.random.default_rng(1)
+    Q1, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    s = np.concatenate([[7.0, 2.0, 1.5], np.linspace(1.0, 0.1, 27)])
+    M = Q1[:, :30] @ np.diag(s) @ Q2.T
+    est = P.power_norm(sp.csr_matrix(M), 100)
+    assert abs(est - np.linalg.norm(M, 2)) <= 1e-12 * 7
+    A = lpgen.c1_small().csr()
+    est = P.power_norm(A, 100)
+    true = np.linalg.norm(A.toarray(), 2)
+    assert est <= true * (1 + 1e-12)
+    assert est >= true * 0.98
+
+
+def test_scaling_leaves_signed_permutation_unchanged():
+    rng = np.random.default_rng(2)
+    p = rng.permutation(25)
+    M = sp.csr_matrix((np.where(rng.random(25) < 0.5, -1.0, 1.0), (np.arange(25), p)),
+                      shape=(25, 25))
+    dr, dc = P.ruiz_pc_scaling(M, 10, True)
+    assert np.all(dr == 1.0) and np.all(dc == 1.0)
+
+
+def test_ruiz_equilibrates():
+    A = lpgen.general_structure(200, 500, 3, nnz_target=3000).csr()
+    dr, dc = P.ruiz_pc_scaling(A, 40, False)
+    S = abs(sp.diags(dr) @ A @ sp.diags(dc)).tocsr()
+    rmax = np.asarray(S.max(axis=1).todense()).ravel()
+    cmax = np.asarray(S.max(axis=0).todense()).ravel()
+    rmax = rmax[np.diff(A.indptr) > 0]
+    cmax = cmax[np.diff(A.tocsc().indptr) > 0]
+    assert np.all(np.abs(rmax - 1) < 1e-3) and np.all(np.abs(cmax - 1) < 1e-3)
+
+
+def test_artificial_restart_schedule_hand_derived():
+    # with criteria (i) and (ii) disabled, restarts happen at the checks
+    # t = 64 j where the Halpern count k since the last restart satisfies
+    # k >= 0.36 t: t = 64 (k = 64), 128 (63 >= 46.08), 256 (127 >= 92.16),
+    # 448 (191 >= 161.28), 704 (255 >= 253.44)
+    lp = lpgen.c1_small()
+    opts = P.Opts(max_iter=1000, eps_rel=0.0, beta_suff=0.0, beta_nec=0.0)
+    r = oracle.pdhg_solve(lp, opts, record_checks=True)
+    ks = {c["t"]: c["k"] for c in r.checks}
+    restarted = [t for t in sorted(ks) if t + 64 in ks and ks[t + 64] == 63]
+    assert restarted == [64, 128, 256, 448, 704]
+    assert r.restarts == 5
+
+
+def test_scaling_closed_form_one_row():
+    # A = [1, 3], one Ruiz pass then Pock-Chambolle (alpha = 1), by hand:
+    # Ruiz: row max 3 -> dr = 1/sqrt(3); column maxes 1, 3 -> dc = (1, 1/sqrt(3));
+    # scaled row (1/sqrt(3), 1); PC: row sum 1 + 1/sqrt(3), column sums
+    # 1/sqrt(3) and 1 -> dr /= sqrt(1 + 1/sqrt(3)), dc = (3^(1/4), 1/sqrt(3)).
+    A = sp.csr_matrix(np.array([[1.0, 3.0]]))
+    dr, dc = P.ruiz_pc_scaling(A, 1, True)
+    s3 = math.sqrt(3.0)
+    assert abs(dr[0] - (1 / s3) / math.sqrt(1 + 1 / s3)) <= 1e-15
+    assert abs(dc[0] - 3.0 ** 0.25) <= 1e-15
+    assert abs(dc[1] - 1 / s3) <= 1e-15

@@ -1,0 +1,172 @@
+"""Pins for the oracle presolve/postsolve (CPU only).
+
+The worked examples of Sec. 2 (fix a variable, the redundant row
+x1 >= 1, x2 >= 2, x1 + 2 x2 >= 5, the doubleton x1 + x2 = 1 with x >= 0) and
+the invariant that postsolve(exact solution of presolve(LP)) is a KKT point of
+the original LP with the planted optimal objective.  Exact reduced solutions
+come from scipy's HiGHS, independent of the oracle's PDHG.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import presolve as PS
+from lp_helpers import SimpleLP, highs_solve
+
+INF = np.inf
+
+
+def solve_via_presolve(lp):
+    res = PS.presolve(lp)
+    assert res.status in (PS.REDUCED, PS.SOLVED)
+    red = res.reduced
+    if red.m == 0 and red.n == 0:
+        xr, yr = np.zeros(0), np.zeros(0)
+    elif red.m == 0:
+        # no rows left: each column at the bound its cost points to
+        xr = np.where(red.c > 0, red.col_lo, np.where(red.c < 0, red.col_hi,
+                                                      np.clip(0.0, red.col_lo, red.col_hi)))
+        yr = np.zeros(0)
+    else:
+        _, xr, yr = highs_solve(red)
+    x, y, z = PS.postsolve(res, xr, yr)
+    return res, x, y, z
+
+
+def test_fix_variable_postsolve_sets_reduced_cost():
+    # Sec. 2.1: x_k fixed at xhat; postsolve x_k = xhat, y unchanged,
+    # z_k = c_k - a_k^T y
+    A = [[1.0, 2.0, 1.0], [3.0, 1.0, -1.0]]
+    lp = SimpleLP(A, [1.0, 2.0, -1.0], [2.0, 1.0], [INF, INF], [0.0, 0.5, 0.0],
+                  [10.0, 0.5, 10.0])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["fixed_col"] == 1
+    assert x[1] == 0.5
+    assert abs(z[1] - (2.0 - (2.0 * y[0] + 1.0 * y[1]))) <= 1e-12
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+
+
+def test_redundant_row_worked_example():
+    # x1 >= 1, x2 >= 2 imply x1 + 2 x2 >= 5: the row is removed
+    lp = SimpleLP([[1.0, 2.0]], [1.0, 1.0], [5.0], [INF], [1.0, 2.0], [INF, INF])
+    res = PS.presolve(lp)
+    assert res.counts["redundant_row"] == 1
+    assert res.reduced.m == 0
+    _, x, y, _ = solve_via_presolve(lp)
+    assert y[0] == 0.0 and list(x) == [1.0, 2.0]
+
+
+def test_doubleton_worked_example():
+    # x1 + x2 = 1, x >= 0: x1's bound x1 >= 0 moves to x2 <= 1, x1 = 1 - x2,
+    # row and x1 removed; a reduced x2 = a maps back to (1 - a, a)
+    lp = SimpleLP([[1.0, 1.0]], [2.0, 3.0], [1.0], [1.0], [0.0, 0.0], [INF, INF])
+    ps = PS.Presolver(lp)
+    ps.doubleton(0)
+    assert ps.records[0][0] == "doubleton" and ps.records[0][2] == 0  # x1 eliminated
+    assert ps.lx[1] == 0.0 and ps.ux[1] == 1.0
+    assert not ps.row_on[0] and not ps.col_on[0]
+    red, rmap, cmap = ps.reduced()
+    res = PS.PresolveResult(PS.REDUCED, red, rmap, cmap, ps.records, 1, m0=1, n0=2)
+    for a in (0.0, 0.25, 1.0):
+        x, _, _ = PS.postsolve(res, np.array([a]), np.zeros(0))
+        assert x[0] == 1.0 - a and x[1] == a
+    # objective 2 x1 + 3 x2 = 2 + x2 -> min at x2 = 0, x = (1, 0), p = 2
+    _, x, y, z = solve_via_presolve(lp)
+    assert np.allclose(x, [1.0, 0.0])
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-12 and abs(k["p"] - 2.0) <= 1e-12
+
+
+@pytest.mark.parametrize("a,lo,hi,c", [
+    (2.0, 1.0, 3.0, 1.0), (2.0, 1.0, 3.0, -1.0), (-2.0, 1.0, 3.0, 1.0),
+    (-2.0, 1.0, 3.0, -1.0), (0.5, -INF, 1.0, -1.0), (-0.5, -1.0, INF, -1.0),
+])
+def test_singleton_row_duals_both_signs(a, lo, hi, c):
+    # one singleton row tightening a boxed variable, plus a second row so the
+    # LP is not trivial
+    A = [[a, 0.0], [1.0, 1.0]]
+    lp = SimpleLP(A, [c, 0.5], [lo, 0.0], [hi, 4.0], [-5.0, 0.0], [5.0, 3.0])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["singleton_row"] >= 1
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+
+
+@pytest.mark.parametrize("c0,c1", [(2.0, 3.0), (3.0, 2.0), (-1.0, 1.0), (1.0, -4.0)])
+def test_doubleton_postsolve_both_branches(c0, c1):
+    # x0 + 2 x1 = 2 with boxes; a third column linking another row so the
+    # eliminated column has an entry elsewhere (substitution + fill-in)
+    A = [[1.0, 2.0, 0.0], [1.0, 0.0, 1.0]]
+    lp = SimpleLP(A, [c0, c1, 0.3], [2.0, 0.5], [2.0, 3.0], [0.0, 0.0, -1.0],
+                  [1.5, 5.0, 2.0])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["doubleton"] >= 1
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+
+
+def test_free_column_singleton():
+    # x2 is free and appears only in the equality row 0
+    A = [[1.0, 1.0, 2.0], [1.0, -1.0, 0.0]]
+    lp = SimpleLP(A, [1.0, 2.0, -1.0], [4.0, -1.0], [4.0, 3.0], [0.0, 0.0, -INF],
+                  [5.0, 5.0, INF])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["free_col_singleton"] == 1
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+
+
+def test_infeasible_and_unbounded_detection():
+    lp = SimpleLP(np.zeros((1, 1)), [1.0], [1.0], [2.0], [0.0], [1.0])  # empty row 1 <= 0
+    assert PS.presolve(lp).status == PS.INFEASIBLE
+    lp = SimpleLP([[1.0, 0.0], [1.0, 0.0]], [1.0, 0.0], [3.0, -INF], [INF, 1.0],
+                  [0.0, 0.0], [INF, 1.0])  # x0 >= 3 and x0 <= 1
+    assert PS.presolve(lp).status == PS.INFEASIBLE
+    lp = SimpleLP([[1.0, 0.0]], [1.0, -1.0], [1.0], [2.0], [0.0, 0.0], [INF, INF])
+    assert PS.presolve(lp).status == PS.UNBOUNDED  # empty col with c < 0, u = inf
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33])
+def test_postsolve_of_exact_reduced_solution_is_kkt(seed):
+    lp = lpgen.general_structure(600, 1500, seed, nnz_target=9000, one_sided=0.2)
+    res, x, y, z = solve_via_presolve(lp)
+    red = res.reduced
+    assert red.m < lp.m and red.n < lp.n
+    assert sum(res.counts.values()) > 0
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+    # dual feasibility is exact by construction of every postsolve step
+    g = lp.c - lp.csr().T @ y
+    assert np.max(np.abs(g - z)) <= 1e-8 * (1 + np.max(np.abs(lp.c)))
+
+
+def test_presolve_scaled_c2_structure():
+    lp = lpgen.c2_presolvable(scale=0.005)
+    res, x, y, z = solve_via_presolve(lp)
+    for key in ("empty_row", "fixed_col", "singleton_row", "doubleton"):
+        assert res.counts[key] > 0, key
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+
+
+def test_pdhg_on_reduced_then_postsolve():
+    lp = lpgen.general_structure(500, 1200, 41, nnz_target=7000)
+    res = PS.presolve(lp)
+    r = oracle.pdhg_solve(res.reduced, oracle.Opts(eps_rel=1e-8))
+    assert r.status == 0
+    x, y, z = PS.postsolve(res, r.x, r.y, r.z)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-6
+    assert abs(k["p"] - lp.p_star) <= 1e-6 * (1 + abs(lp.p_star))
