@@ -1,0 +1,251 @@
+/*
+ * lp.h -- C ABI of the GB300 restarted-PDHG LP library.
+ *
+ * Problem (eq. (1), Sec. 2):   minimize  c^T x + obj_offset
+ *                              subject to row_lo <= A x <= row_hi
+ *                                         col_lo <= x  <= col_hi
+ * A is m x n, given in CSR.  Infinite bounds are IEEE +-INFINITY; an equality
+ * row has row_lo[i] == row_hi[i].  A solution is (x, y, z) satisfying the
+ * optimality conditions of eq. (2): primal feasibility, c - A^T y - z = 0 and
+ * the sign / complementarity rules for y and z.
+ *
+ * Pipeline (Sec. 1, Sec. 3.3): lp_create -> lp_presolve (host, the simple
+ * rules of Sec. 2-3, keeps a postsolve record) -> lp_solve (GPU restarted
+ * reflected Halpern PDHG on the reduced LP) -> lp_postsolve (host, maps the
+ * reduced solution back to an (x, y, z) of the original LP).  The presolve
+ * interface follows the minimal pointer-in / same-form-out design of Sec. 3.3.
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers passed in are HOST pointers unless stated otherwise.  Input
+ *     arrays are copied; the caller keeps ownership and may free them once
+ *     the call returns.  Output arrays are caller-allocated host buffers.
+ *   - Return codes: LP_OK (0) on success, LP_PENDING (1) from lp_batch_poll
+ *     while a request is in flight, a negative LP_ERR_* code on failure.
+ *     lp_last_error() returns a message for the last failure on the calling
+ *     thread.  No C++ exception and no abort crosses this boundary.
+ *   - Device work runs on the CUDA stream given in lp_device_ctx (NULL = the
+ *     library creates its own non-blocking stream).  Device memory comes from
+ *     the ctx allocator callbacks when given, else from cudaMallocAsync.
+ *   - Sizes: m, n < 2^31; nnz < 2^31 on the device (checked at upload).
+ */
+#ifndef GB300_LP_H
+#define GB300_LP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define LP_OK 0
+#define LP_PENDING 1
+#define LP_ERR_INVALID (-1) /* malformed input (NaN, bad CSR, lo > hi, ...)   */
+#define LP_ERR_OOM (-2)     /* host or device allocation failed              */
+#define LP_ERR_CUDA (-3)    /* a CUDA runtime call failed                    */
+#define LP_ERR_STATE (-4)   /* call not valid in the object's current state  */
+#define LP_ERR_BUDGET (-5)  /* request larger than the server's HBM budget   */
+#define LP_ERR_TIMEOUT (-6) /* a bounded wait ran out                        */
+
+/* ---- termination codes (lp_result.termination) ------------------------ */
+#define LP_OPTIMAL 0    /* relative KKT error <= eps_rel                     */
+#define LP_ITER_LIMIT 1 /* max_iter iterations done                          */
+#define LP_TIME_LIMIT 2 /* time_limit_s elapsed                              */
+#define LP_NUMERICAL 3  /* a non-finite value appeared                       */
+#define LP_INFEASIBLE 4 /* presolve proved the LP infeasible                 */
+#define LP_UNBOUNDED 5  /* presolve proved the LP unbounded                  */
+#define LP_CANCELLED 6  /* batch request cancelled                           */
+
+/* ---- presolve status (lp_presolve_info.status) ------------------------- */
+#define LP_PRESOLVE_REDUCED 0
+#define LP_PRESOLVE_INFEASIBLE 1
+#define LP_PRESOLVE_UNBOUNDED 2
+#define LP_PRESOLVE_SOLVED 3 /* every row and column was removed            */
+
+/* ---- precision (lp_solve_opts.precision) ------------------------------- */
+#define LP_FP64 0  /* FP64 matrix, FP64 SpMV, FP64 everything               */
+#define LP_MIXED 1 /* FP32 matrix values and SpMV with FP32 accumulation;    */
+                   /* iterates, anchor, reductions, restarts stay FP64       */
+
+typedef struct lp_problem lp_problem; /* opaque: host copy + device buffers */
+typedef struct lp_server lp_server;   /* opaque: continuous-batching server  */
+
+/* Device context.  alloc(bytes, user) returns device memory or NULL; free
+ * releases it.  Both NULL: the library uses cudaMallocAsync / cudaFreeAsync
+ * on `stream`.  `stream` is a cudaStream_t (NULL: the library creates one).
+ * The callbacks are only invoked from the thread that calls into the library
+ * (a server calls alloc once, at lp_server_create). */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *user);
+  void (*free)(void *ptr, void *user);
+  void *user;
+  void *stream;
+  int32_t device;
+} lp_device_ctx;
+
+typedef struct {
+  int32_t max_rounds; /* 20: stop after this many rounds                     */
+  int32_t enable;     /* bit mask of rules, LP_RULE_ALL by default           */
+} lp_presolve_opts;
+
+#define LP_RULE_EMPTY_ROW 1
+#define LP_RULE_EMPTY_COL 2
+#define LP_RULE_FIXED_COL 4
+#define LP_RULE_SINGLETON_ROW 8
+#define LP_RULE_REDUNDANT_ROW 16
+#define LP_RULE_DOUBLETON 32
+#define LP_RULE_FREE_COL_SINGLETON 64
+#define LP_RULE_ALL 127
+
+typedef struct {
+  int32_t status;          /* LP_PRESOLVE_*                                 */
+  int32_t rounds;
+  int32_t m, n;            /* reduced sizes                                 */
+  int64_t nnz;
+  int32_t m0, n0;          /* original sizes                                */
+  int64_t nnz0;
+  int64_t counts[8];       /* reductions per rule: empty_row, empty_col,
+                              fixed_col, singleton_row, redundant_row,
+                              dropped_side, doubleton, free_col_singleton   */
+  double seconds;
+} lp_presolve_info;
+
+typedef struct {
+  double eps_rel;        /* 1e-6: stop when relative KKT error <= eps_rel   */
+  int64_t max_iter;      /* 200000                                          */
+  double time_limit_s;   /* 3600                                            */
+  int32_t precision;     /* LP_FP64 | LP_MIXED                              */
+  int32_t check_every;   /* 64: restart/termination check period K          */
+  double rho;            /* 1.0: reflection weight (0 = plain Halpern)      */
+  double beta_suff;      /* 0.2  restart if r <= beta_suff r0               */
+  double beta_nec;       /* 0.8  ... or r <= beta_nec r0 and r > r_prev     */
+  double beta_art;       /* 0.36 ... or k >= beta_art t                     */
+  double theta;          /* 0.5  primal-weight smoothing                    */
+  int32_t ruiz_iters;    /* 10                                              */
+  int32_t pock_chambolle;/* 1                                               */
+  int32_t power_iters;   /* 100                                             */
+  int32_t halpern;       /* 1: Halpern anchoring; 0: (1+rho)T(z) - rho z    */
+  int32_t restarts;      /* 1: restarts enabled                             */
+  int32_t use_graph;     /* 1: replay a CUDA graph of check_every iterations */
+  double step_size;      /* 0 = auto: 0.998 / ||A~||_2 by power iteration   */
+  double primal_weight;  /* 0 = auto: ||c~|| / ||bhat~||                    */
+  const double *x_init;  /* NULL or n doubles (current LP): warm start x    */
+  const double *y_init;  /* NULL or m doubles: warm start y                 */
+  int32_t tile_items;    /* 0 = auto: target nonzeros per lane in SpMV      */
+  int32_t verbose;
+} lp_solve_opts;
+
+typedef struct {
+  int32_t termination;   /* LP_OPTIMAL ...                                   */
+  int32_t restarts;
+  int64_t iterations;    /* evaluations of the PDHG operator T              */
+  double rel_kkt, rel_p, rel_d, rel_gap;
+  double r_p, r_d, gap;
+  double primal_obj, dual_obj;
+  double eta, omega;
+  double t_setup_s;      /* scaling + step size (device)                    */
+  double t_solve_s;      /* PDHG iterations (device)                        */
+  double t_total_s;      /* wall time of the call                           */
+  int64_t kernel_launches; /* kernels launched by this call                 */
+} lp_result;
+
+/* Defaults above; always call before filling in a field. */
+void lp_solve_opts_default(lp_solve_opts *opts);
+void lp_presolve_opts_default(lp_presolve_opts *opts);
+
+/* Thread-local message for the last failing call on this thread. */
+const char *lp_last_error(void);
+
+/* Create a problem from CSR (row_ptr: m+1 int64, col_idx: nnz int32 strictly
+ * increasing within each row, val: nnz doubles), c (n), bounds.  dev may be
+ * NULL (host-only: presolve/postsolve work, lp_solve fails LP_ERR_STATE).
+ * Fails LP_ERR_INVALID on NaN, a decreasing row_ptr, an out-of-range or
+ * repeated column index in a row, lo > hi, +inf lower or -inf upper bound. */
+int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+              const int32_t *col_idx, const double *val, const double *c,
+              double obj_offset, const double *row_lo, const double *row_hi,
+              const double *col_lo, const double *col_hi,
+              const lp_device_ctx *dev, lp_problem **out);
+
+/* Presolve in place (Sec. 2-3): the problem becomes the reduced LP; the
+ * postsolve record is kept inside.  Host only.  May be called once. */
+int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *info);
+
+/* Copy the current (reduced) LP to the device and build its layout (row
+ * binning and the stored transpose).  lp_solve calls it when needed. */
+int lp_upload(lp_problem *lp);
+
+/* Solve the current (reduced) LP on the GPU.  May be called repeatedly;
+ * every call starts from the initial (or warm-start) point. */
+int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res);
+
+/* Solution of the current (reduced) LP: x (n), y (m), z = c - A^T y (n).
+ * Any pointer may be NULL. */
+int lp_get_solution(const lp_problem *lp, double *x, double *y, double *z);
+
+/* The PDHG iterate z^t = (x, y) after the last lp_solve (unscaled). */
+int lp_get_iterate(const lp_problem *lp, double *x, double *y);
+
+/* Map the reduced solution back to the original LP (Sec. 2.1, Sec. 3.3):
+ * x (n0), y (m0), z (n0), any may be NULL.  Without a presolve it copies. */
+int lp_postsolve(lp_problem *lp, double *x, double *y, double *z);
+
+/* Postsolve an externally supplied reduced solution (xr: n, yr: m, zr: n or
+ * NULL for c - A^T yr) into original-size x, y, z. */
+int lp_postsolve_from(lp_problem *lp, const double *xr, const double *yr,
+                      const double *zr, double *x, double *y, double *z);
+
+/* Current LP data (after presolve: the reduced LP).  Arrays may be NULL. */
+int lp_get_dims(const lp_problem *lp, int32_t *m, int32_t *n, int64_t *nnz,
+                int32_t *m0, int32_t *n0);
+int lp_get_data(const lp_problem *lp, int64_t *row_ptr, int32_t *col_idx,
+                double *val, double *c, double *obj_offset, double *row_lo,
+                double *row_hi, double *col_lo, double *col_hi);
+
+/* Relative KKT error (rel-KKT of the termination test) of a host point (x,
+ * y) for the current LP, computed on the host in FP64. out: rel_kkt, rel_p,
+ * rel_d, rel_gap, primal_obj, dual_obj (6 doubles). */
+int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, double *out);
+
+void lp_destroy(lp_problem *lp);
+
+/* ---- batched solving and continuous-batching server ------------------ */
+
+/* A server holds up to hbm_budget_bytes of device memory (allocated once),
+ * packs admitted problems into slots of a persistent segmented batch and
+ * runs them with one launch per period; finished slots are refilled from the
+ * queue.  `opts` applies to every request (precision, eps_rel, ...).
+ * worker: 1 = a background host thread drives the device loop; 0 = the
+ * caller drives it through lp_server_pump. */
+int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
+                     const lp_solve_opts *opts, int32_t worker, lp_server **out);
+
+/* Queue a problem (its current, possibly presolved LP).  The server borrows
+ * `lp` until its result has been polled.  Fails LP_ERR_BUDGET if the
+ * problem alone exceeds the budget. */
+int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket);
+
+/* LP_PENDING while in flight; LP_OK once done: res, x (n), y (m) of the
+ * current LP are filled (pointers may be NULL) and the ticket is released. */
+int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, double *y);
+
+/* Drive the device loop for at most `periods` launch periods (worker = 0).
+ * Returns the number of requests still queued or running. */
+int lp_server_pump(lp_server *srv, int32_t periods);
+
+/* Cancel a queued or running request: its poll returns LP_OK with
+ * termination LP_CANCELLED. */
+int lp_batch_cancel(lp_server *srv, uint64_t ticket);
+
+/* Statistics: out[0] admitted, out[1] finished, out[2] periods launched,
+ * out[3] peak resident bytes, out[4] kernel launches, out[5] queue length. */
+int lp_server_stats(const lp_server *srv, int64_t *out);
+
+void lp_server_destroy(lp_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LP_H */

@@ -1,0 +1,20 @@
+"""GB300-native restarted-PDHG LP solver with host presolve/postsolve.
+
+The compute path is the native library built from ``csrc/`` (CUDA for
+sm_103a + host C++), reached through the C ABI of ``include/lp.h``.  This
+package only marshals arguments (``capi``); PyTorch supplies device memory
+and streams.
+"""
+from .capi import (  # noqa: F401
+    LP_FP64,
+    LP_MIXED,
+    LP_OPTIMAL,
+    LP_ITER_LIMIT,
+    LP_TIME_LIMIT,
+    LP_NUMERICAL,
+    LPError,
+    Problem,
+    TorchDevice,
+    load,
+    solve_opts,
+)

@@ -1,0 +1,649 @@
+// Host presolve / postsolve for eq. (1): the simple ("fast") explorers of
+// Table 1 applied through the reductions of Sec. 2.1, in rounds (Sec. 3.2),
+// with A stored both row-wise and column-wise with per-row / per-column
+// slack for fill-in (Sec. 3.2).
+//
+// Rules, schedule and postsolve formulas:
+//   round = empty rows -> empty cols -> fixed cols -> singleton rows ->
+//           redundant rows / dominated sides -> doubleton equalities ->
+//           free (or implied-free) column singletons in equality rows;
+//   each pass scans candidates in increasing index order; round 1 scans
+//   everything, later rounds what the previous round dirtied; stop after a
+//   round without reductions or after max_rounds.
+//   Infeasibility when a lower bound exceeds an upper one by more than 1e-9;
+//   coefficients below 1e-12 in magnitude after an update are dropped;
+//   activities sum a row's entries in increasing column order, compared with
+//   the row bounds exactly.  Arithmetic is plain IEEE double (the library is
+//   built with -ffp-contract=off), so the decisions are reproducible.
+//
+// Postsolve keeps c - A^T y - z = 0 (second line of eq. (2)) for every
+// intermediate problem:
+//   empty / redundant row:   y_i = 0
+//   dropped row side:        nothing
+//   fixed / empty column v:  x_j = v, z_j = c_j - sum_i a_ij y_i   (Sec. 2.1)
+//   singleton row a x_j:     y_i = z_j / a, z_j = 0 when z_j's sign points at
+//                            a bound that came from the row, else y_i = 0
+//   doubleton a_j x_j + a_k x_k = b:  x_j = (b - a_k x_k) / a_j;
+//                            D_j = c_j - sum_{r != i} a_rj y_r;
+//                            bound of x_k active and transferred from x_j:
+//                              y_i = (z_k + (a_k / a_j) D_j) / a_k,
+//                              z_j = D_j - a_j y_i, z_k = 0;
+//                            otherwise y_i = D_j / a_j, z_j = 0
+//   free column singleton:   x_j = (b - sum_{r != j} a_ir x_r) / a_ij,
+//                            y_i = c_j / a_ij, z_j = 0
+#include <algorithm>
+#include <cmath>
+#include <limits>
+#include <vector>
+
+#include "lp_internal.h"
+
+namespace gb300lp {
+namespace {
+
+constexpr double kFeasTol = 1e-9;
+constexpr double kDropTol = 1e-12;
+constexpr double kInf = std::numeric_limits<double>::infinity();
+
+enum RecKind {
+  REC_EMPTY_ROW = 0,
+  REC_REDUNDANT_ROW = 1,
+  REC_DROP_SIDE = 2,
+  REC_FIX_COL = 3,
+  REC_SINGLETON_ROW = 4,
+  REC_DOUBLETON = 5,
+  REC_FREE_COL = 6,
+};
+
+enum CountIdx {
+  C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
+  C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL,
+};
+
+// Sorted sparse vectors in one pool, each with spare capacity.  A vector that
+// outgrows its capacity moves to the end of the pool with twice the room.
+struct SlackStore {
+  std::vector<int64_t> start;
+  std::vector<int32_t> len, cap;
+  std::vector<int32_t> idx;
+  std::vector<double> val;
+
+  void init(int32_t count, const std::vector<int32_t> &lens) {
+    start.assign(count, 0);
+    len.assign(count, 0);
+    cap.assign(count, 0);
+    int64_t total = 0;
+    for (int32_t r = 0; r < count; ++r) {
+      start[r] = total;
+      cap[r] = lens[r] + 2 + lens[r] / 4;
+      total += cap[r];
+    }
+    idx.assign(total, 0);
+    val.assign(total, 0.0);
+  }
+  // position of key in vector r, or -(insertion point) - 1
+  int32_t find(int32_t r, int32_t key) const {
+    const int32_t *p = idx.data() + start[r];
+    int32_t lo = 0, hi = len[r];
+    while (lo < hi) {
+      int32_t mid = (lo + hi) >> 1;
+      if (p[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo < len[r] && p[lo] == key) return lo;
+    return -lo - 1;
+  }
+  void erase_at(int32_t r, int32_t pos) {
+    int64_t s = start[r];
+    for (int32_t q = pos; q + 1 < len[r]; ++q) {
+      idx[s + q] = idx[s + q + 1];
+      val[s + q] = val[s + q + 1];
+    }
+    --len[r];
+  }
+  void erase(int32_t r, int32_t key) {
+    int32_t p = find(r, key);
+    if (p >= 0) erase_at(r, p);
+  }
+  void grow(int32_t r) {
+    int32_t ncap = std::max(4, cap[r] * 2);
+    int64_t ns = (int64_t)idx.size();
+    idx.resize(ns + ncap);
+    val.resize(ns + ncap);
+    for (int32_t q = 0; q < len[r]; ++q) {
+      idx[ns + q] = idx[start[r] + q];
+      val[ns + q] = val[start[r] + q];
+    }
+    start[r] = ns;
+    cap[r] = ncap;
+  }
+  // insert or overwrite
+  void put(int32_t r, int32_t key, double v) {
+    int32_t p = find(r, key);
+    if (p >= 0) {
+      val[start[r] + p] = v;
+      return;
+    }
+    int32_t ins = -p - 1;
+    if (len[r] == cap[r]) grow(r);
+    int64_t s = start[r];
+    for (int32_t q = len[r]; q > ins; --q) {
+      idx[s + q] = idx[s + q - 1];
+      val[s + q] = val[s + q - 1];
+    }
+    idx[s + ins] = key;
+    val[s + ins] = v;
+    ++len[r];
+  }
+  double get(int32_t r, int32_t key, double dflt) const {
+    int32_t p = find(r, key);
+    return p >= 0 ? val[start[r] + p] : dflt;
+  }
+};
+
+struct Presolver {
+  int32_t m, n;
+  SlackStore rows, cols;
+  std::vector<double> c, lo, hi, lx, ux;
+  double off;
+  std::vector<uint8_t> row_on, col_on;
+  std::vector<uint8_t> dmark_r, dmark_c;
+  std::vector<int32_t> dlist_r, dlist_c;
+  bool changed = false;
+  int32_t status = LP_PRESOLVE_REDUCED;
+  PresolveOutcome *po;
+
+  explicit Presolver(const HostLP &in, PresolveOutcome *out) : po(out) {
+    m = in.m;
+    n = in.n;
+    std::vector<int32_t> rl(m), cl(n, 0);
+    for (int32_t i = 0; i < m; ++i) {
+      int32_t cnt = 0;
+      for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k)
+        if (in.val[k] != 0.0) { ++cnt; ++cl[in.col_idx[k]]; }
+      rl[i] = cnt;
+    }
+    rows.init(m, rl);
+    cols.init(n, cl);
+    for (int32_t i = 0; i < m; ++i) {
+      for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
+        double v = in.val[k];
+        if (v == 0.0) continue;
+        int32_t j = in.col_idx[k];
+        // input rows are sorted by column and rows arrive in order, so these
+        // are appends
+        rows.idx[rows.start[i] + rows.len[i]] = j;
+        rows.val[rows.start[i] + rows.len[i]] = v;
+        ++rows.len[i];
+        cols.idx[cols.start[j] + cols.len[j]] = i;
+        cols.val[cols.start[j] + cols.len[j]] = v;
+        ++cols.len[j];
+      }
+    }
+    c = in.c;
+    off = in.off;
+    lo = in.row_lo;
+    hi = in.row_hi;
+    lx = in.col_lo;
+    ux = in.col_hi;
+    row_on.assign(m, 1);
+    col_on.assign(n, 1);
+    dmark_r.assign(m, 0);
+    dmark_c.assign(n, 0);
+  }
+
+  void dirty_row(int32_t i) {
+    if (!dmark_r[i]) { dmark_r[i] = 1; dlist_r.push_back(i); }
+  }
+  void dirty_col(int32_t j) {
+    if (!dmark_c[j]) { dmark_c[j] = 1; dlist_c.push_back(j); }
+  }
+  void mark_col_bounds(int32_t j) {
+    dirty_col(j);
+    for (int32_t q = 0; q < cols.len[j]; ++q) dirty_row(cols.idx[cols.start[j] + q]);
+  }
+  void remove_entry(int32_t i, int32_t j) {
+    rows.erase(i, j);
+    cols.erase(j, i);
+    dirty_row(i);
+    dirty_col(j);
+  }
+  void set_entry(int32_t i, int32_t j, double v) {
+    if (std::fabs(v) < kDropTol) {
+      if (rows.find(i, j) >= 0) remove_entry(i, j);
+      return;
+    }
+    rows.put(i, j, v);
+    cols.put(j, i, v);
+    dirty_row(i);
+    dirty_col(j);
+  }
+  void remove_row(int32_t i) {
+    while (rows.len[i] > 0) {
+      int32_t j = rows.idx[rows.start[i] + rows.len[i] - 1];
+      remove_entry(i, j);
+    }
+    row_on[i] = 0;
+  }
+  void remove_col(int32_t j) {
+    while (cols.len[j] > 0) {
+      int32_t i = cols.idx[cols.start[j] + cols.len[j] - 1];
+      remove_entry(i, j);
+    }
+    col_on[j] = 0;
+  }
+  void activity(int32_t i, int32_t skip, double &amin, double &amax) const {
+    double lo_s = 0.0, hi_s = 0.0;
+    int lo_inf = 0, hi_inf = 0;
+    int64_t s = rows.start[i];
+    for (int32_t q = 0; q < rows.len[i]; ++q) {
+      int32_t j = rows.idx[s + q];
+      if (j == skip) continue;
+      double a = rows.val[s + q];
+      double bl, bu;
+      if (a > 0) { bl = lx[j]; bu = ux[j]; } else { bl = ux[j]; bu = lx[j]; }
+      if (std::isinf(bl)) ++lo_inf; else lo_s += a * bl;
+      if (std::isinf(bu)) ++hi_inf; else hi_s += a * bu;
+    }
+    amin = lo_inf ? -kInf : lo_s;
+    amax = hi_inf ? kInf : hi_s;
+  }
+  PostsolveRecord &push(int32_t kind) {
+    PostsolveRecord r{};
+    r.kind = kind;
+    r.ent_begin = r.ent_end = (int64_t)po->ent_idx.size();
+    po->records.push_back(r);
+    return po->records.back();
+  }
+  void push_entry(PostsolveRecord &r, int32_t idx, double v) {
+    po->ent_idx.push_back(idx);
+    po->ent_val.push_back(v);
+    r.ent_end = (int64_t)po->ent_idx.size();
+  }
+
+  // ---- rules --------------------------------------------------------------
+  void empty_row(int32_t i) {
+    if (lo[i] > kFeasTol || hi[i] < -kFeasTol) { status = LP_PRESOLVE_INFEASIBLE; return; }
+    PostsolveRecord &r = push(REC_EMPTY_ROW);
+    r.i = i;
+    row_on[i] = 0;
+    po->counts[C_EMPTY_ROW]++;
+    changed = true;
+  }
+  void empty_col(int32_t j) {
+    double cj = c[j], v;
+    if (cj > 0) v = lx[j];
+    else if (cj < 0) v = ux[j];
+    else v = std::min(std::max(0.0, lx[j]), ux[j]);
+    if (std::isinf(v)) { status = LP_PRESOLVE_UNBOUNDED; return; }
+    off += cj * v;
+    PostsolveRecord &r = push(REC_FIX_COL);
+    r.j = j; r.v = v; r.cj = cj;
+    col_on[j] = 0;
+    dirty_col(j);
+    po->counts[C_EMPTY_COL]++;
+    changed = true;
+  }
+  void fixed_col(int32_t j) {
+    double v = lx[j];
+    PostsolveRecord &r = push(REC_FIX_COL);
+    r.j = j; r.v = v; r.cj = c[j];
+    size_t rec = po->records.size() - 1;
+    int64_t s = cols.start[j];
+    for (int32_t q = 0; q < cols.len[j]; ++q) {
+      int32_t i = cols.idx[s + q];
+      double a = cols.val[s + q];
+      if (!std::isinf(lo[i])) lo[i] -= a * v;
+      if (!std::isinf(hi[i])) hi[i] -= a * v;
+      dirty_row(i);
+      push_entry(po->records[rec], i, a);
+    }
+    off += c[j] * v;
+    remove_col(j);
+    po->counts[C_FIXED_COL]++;
+    changed = true;
+  }
+  void singleton_row(int32_t i) {
+    int32_t j = rows.idx[rows.start[i]];
+    double a = rows.val[rows.start[i]];
+    double ilo, ihi;
+    if (a > 0) {
+      ilo = std::isinf(lo[i]) ? -kInf : lo[i] / a;
+      ihi = std::isinf(hi[i]) ? kInf : hi[i] / a;
+    } else {
+      ilo = std::isinf(hi[i]) ? -kInf : hi[i] / a;
+      ihi = std::isinf(lo[i]) ? kInf : lo[i] / a;
+    }
+    bool lo_from = ilo > lx[j];
+    bool hi_from = ihi < ux[j];
+    double nl = lo_from ? ilo : lx[j];
+    double nu = hi_from ? ihi : ux[j];
+    if (nl > nu + kFeasTol) { status = LP_PRESOLVE_INFEASIBLE; return; }
+    if (nl > nu) nl = nu = 0.5 * (nl + nu);
+    PostsolveRecord &r = push(REC_SINGLETON_ROW);
+    r.i = i; r.j = j; r.a = a; r.flags = (lo_from ? 1 : 0) | (hi_from ? 2 : 0);
+    remove_row(i);
+    if (nl != lx[j] || nu != ux[j]) {
+      lx[j] = nl;
+      ux[j] = nu;
+      mark_col_bounds(j);
+    }
+    po->counts[C_SINGLETON_ROW]++;
+    changed = true;
+  }
+  void redundant_row(int32_t i) {
+    double l = lo[i], h = hi[i];
+    if (l == h) return;
+    double amin, amax;
+    activity(i, -1, amin, amax);
+    bool lo_imp = std::isinf(l) || amin >= l;
+    bool hi_imp = std::isinf(h) || amax <= h;
+    if (lo_imp && hi_imp) {
+      PostsolveRecord &r = push(REC_REDUNDANT_ROW);
+      r.i = i;
+      remove_row(i);
+      po->counts[C_REDUNDANT_ROW]++;
+      changed = true;
+    } else if (lo_imp && !std::isinf(l)) {
+      PostsolveRecord &r = push(REC_DROP_SIDE);
+      r.i = i; r.flags = 0; r.v = l;
+      lo[i] = -kInf;
+      dirty_row(i);
+      po->counts[C_DROPPED_SIDE]++;
+      changed = true;
+    } else if (hi_imp && !std::isinf(h)) {
+      PostsolveRecord &r = push(REC_DROP_SIDE);
+      r.i = i; r.flags = 1; r.v = h;
+      hi[i] = kInf;
+      dirty_row(i);
+      po->counts[C_DROPPED_SIDE]++;
+      changed = true;
+    }
+  }
+  void doubleton(int32_t i) {
+    int64_t s = rows.start[i];
+    int32_t p = rows.idx[s], q = rows.idx[s + 1];
+    double ap = rows.val[s], aq = rows.val[s + 1];
+    double b = lo[i];
+    int32_t j, k;
+    double aj, ak;
+    if (std::fabs(ap) > std::fabs(aq)) { j = p; aj = ap; k = q; ak = aq; }
+    else if (std::fabs(aq) > std::fabs(ap)) { j = q; aj = aq; k = p; ak = ap; }
+    else if (cols.len[q] < cols.len[p]) { j = q; aj = aq; k = p; ak = ap; }
+    else { j = p; aj = ap; k = q; ak = aq; }
+    double r = ak / aj;
+    double sv = b / aj;
+    double t_lo = std::isinf(ux[j]) ? -kInf : sv - ux[j];
+    double t_hi = std::isinf(lx[j]) ? kInf : sv - lx[j];
+    double ilo, ihi;
+    if (r > 0) {
+      ilo = std::isinf(t_lo) ? -kInf : t_lo / r;
+      ihi = std::isinf(t_hi) ? kInf : t_hi / r;
+    } else {
+      ilo = std::isinf(t_hi) ? -kInf : t_hi / r;
+      ihi = std::isinf(t_lo) ? kInf : t_lo / r;
+    }
+    bool lo_from = ilo > lx[k];
+    bool hi_from = ihi < ux[k];
+    double nl = lo_from ? ilo : lx[k];
+    double nu = hi_from ? ihi : ux[k];
+    if (nl > nu + kFeasTol) { status = LP_PRESOLVE_INFEASIBLE; return; }
+    if (nl > nu) nl = nu = 0.5 * (nl + nu);
+    double cj = c[j];
+    {
+      PostsolveRecord &rec = push(REC_DOUBLETON);
+      rec.i = i; rec.j = j; rec.k = k; rec.a = aj; rec.ak = ak; rec.b = b; rec.cj = cj;
+      rec.flags = (lo_from ? 1 : 0) | (hi_from ? 2 : 0);
+    }
+    size_t ri = po->records.size() - 1;
+    // snapshot column j without row i (ascending rows)
+    std::vector<int32_t> crow;
+    std::vector<double> cval;
+    int64_t cs = cols.start[j];
+    for (int32_t qq = 0; qq < cols.len[j]; ++qq) {
+      int32_t rr = cols.idx[cs + qq];
+      if (rr == i) continue;
+      crow.push_back(rr);
+      cval.push_back(cols.val[cs + qq]);
+      push_entry(po->records[ri], rr, cols.val[cs + qq]);
+    }
+    off += cj * sv;
+    if (cj != 0.0) {
+      c[k] -= cj * r;
+      dirty_col(k);
+    }
+    for (size_t t = 0; t < crow.size(); ++t) {
+      int32_t rr = crow[t];
+      double a = cval[t];
+      if (!std::isinf(lo[rr])) lo[rr] -= a * sv;
+      if (!std::isinf(hi[rr])) hi[rr] -= a * sv;
+      double old = rows.get(rr, k, 0.0);
+      remove_entry(rr, j);
+      set_entry(rr, k, old - a * r);
+    }
+    remove_row(i);
+    remove_col(j);
+    if (nl != lx[k] || nu != ux[k]) {
+      lx[k] = nl;
+      ux[k] = nu;
+      mark_col_bounds(k);
+    }
+    po->counts[C_DOUBLETON]++;
+    changed = true;
+  }
+  void free_col_singleton(int32_t j) {
+    int32_t i = cols.idx[cols.start[j]];
+    double a = cols.val[cols.start[j]];
+    if (!row_on[i] || lo[i] != hi[i] || rows.len[i] < 2) return;
+    double b = lo[i];
+    bool is_free = std::isinf(lx[j]) && std::isinf(ux[j]);
+    if (!is_free) {
+      double amin, amax, ilo, ihi;
+      activity(i, j, amin, amax);
+      if (a > 0) { ilo = (b - amax) / a; ihi = (b - amin) / a; }
+      else { ilo = (b - amin) / a; ihi = (b - amax) / a; }
+      if (!(ilo >= lx[j] && ihi <= ux[j])) return;
+    }
+    double cj = c[j];
+    {
+      PostsolveRecord &rec = push(REC_FREE_COL);
+      rec.i = i; rec.j = j; rec.a = a; rec.b = b; rec.cj = cj;
+    }
+    size_t ri = po->records.size() - 1;
+    int64_t s = rows.start[i];
+    for (int32_t q = 0; q < rows.len[i]; ++q) {
+      int32_t r = rows.idx[s + q];
+      if (r == j) continue;
+      push_entry(po->records[ri], r, rows.val[s + q]);
+    }
+    off += cj * b / a;
+    if (cj != 0.0) {
+      const PostsolveRecord &rec = po->records[ri];
+      for (int64_t e = rec.ent_begin; e < rec.ent_end; ++e) {
+        int32_t r = po->ent_idx[e];
+        c[r] -= cj * po->ent_val[e] / a;
+        dirty_col(r);
+      }
+    }
+    remove_row(i);
+    remove_col(j);
+    po->counts[C_FREE_COL]++;
+    changed = true;
+  }
+
+  int run(int max_rounds, int mask) {
+    std::vector<int32_t> rc(m), cc(n);
+    for (int32_t i = 0; i < m; ++i) rc[i] = i;
+    for (int32_t j = 0; j < n; ++j) cc[j] = j;
+    int rounds = 0;
+    for (int rnd = 0; rnd < max_rounds; ++rnd) {
+      rounds = rnd + 1;
+      for (int32_t i : dlist_r) dmark_r[i] = 0;
+      for (int32_t j : dlist_c) dmark_c[j] = 0;
+      dlist_r.clear();
+      dlist_c.clear();
+      changed = false;
+      if (mask & LP_RULE_EMPTY_ROW)
+        for (int32_t i : rc)
+          if (row_on[i] && rows.len[i] == 0) {
+            empty_row(i);
+            if (status != LP_PRESOLVE_REDUCED) return rounds;
+          }
+      if (mask & LP_RULE_EMPTY_COL)
+        for (int32_t j : cc)
+          if (col_on[j] && cols.len[j] == 0) {
+            empty_col(j);
+            if (status != LP_PRESOLVE_REDUCED) return rounds;
+          }
+      if (mask & LP_RULE_FIXED_COL)
+        for (int32_t j : cc)
+          if (col_on[j] && lx[j] == ux[j]) fixed_col(j);
+      if (mask & LP_RULE_SINGLETON_ROW)
+        for (int32_t i : rc)
+          if (row_on[i] && rows.len[i] == 1) {
+            singleton_row(i);
+            if (status != LP_PRESOLVE_REDUCED) return rounds;
+          }
+      if (mask & LP_RULE_REDUNDANT_ROW)
+        for (int32_t i : rc)
+          if (row_on[i] && rows.len[i] >= 1) redundant_row(i);
+      if (mask & LP_RULE_DOUBLETON)
+        for (int32_t i : rc)
+          if (row_on[i] && rows.len[i] == 2 && lo[i] == hi[i]) {
+            doubleton(i);
+            if (status != LP_PRESOLVE_REDUCED) return rounds;
+          }
+      if (mask & LP_RULE_FREE_COL_SINGLETON)
+        for (int32_t j : cc)
+          if (col_on[j] && cols.len[j] == 1) free_col_singleton(j);
+      if (!changed) break;
+      rc.clear();
+      cc.clear();
+      for (int32_t i : dlist_r) if (row_on[i]) rc.push_back(i);
+      for (int32_t j : dlist_c) if (col_on[j]) cc.push_back(j);
+      std::sort(rc.begin(), rc.end());
+      std::sort(cc.begin(), cc.end());
+    }
+    return rounds;
+  }
+
+  void build_reduced(HostLP &out) {
+    po->row_map.clear();
+    po->col_map.clear();
+    std::vector<int32_t> cpos(n, -1);
+    for (int32_t j = 0; j < n; ++j)
+      if (col_on[j]) { cpos[j] = (int32_t)po->col_map.size(); po->col_map.push_back(j); }
+    for (int32_t i = 0; i < m; ++i)
+      if (row_on[i]) po->row_map.push_back(i);
+    out = HostLP();
+    out.m = (int32_t)po->row_map.size();
+    out.n = (int32_t)po->col_map.size();
+    out.row_ptr.assign(out.m + 1, 0);
+    for (int32_t r = 0; r < out.m; ++r) {
+      int32_t i = po->row_map[r];
+      int64_t s = rows.start[i];
+      for (int32_t q = 0; q < rows.len[i]; ++q) {
+        out.col_idx.push_back(cpos[rows.idx[s + q]]);
+        out.val.push_back(rows.val[s + q]);
+      }
+      out.row_ptr[r + 1] = (int64_t)out.col_idx.size();
+      out.row_lo.push_back(lo[i]);
+      out.row_hi.push_back(hi[i]);
+    }
+    for (int32_t j : po->col_map) {
+      out.c.push_back(c[j]);
+      out.col_lo.push_back(lx[j]);
+      out.col_hi.push_back(ux[j]);
+    }
+    out.off = off;
+  }
+};
+
+}  // namespace
+
+void presolve_run(const HostLP &in, int max_rounds, int rule_mask, HostLP &out,
+                  PresolveOutcome &po) {
+  po = PresolveOutcome();
+  po.m0 = in.m;
+  po.n0 = in.n;
+  Presolver ps(in, &po);
+  po.rounds = ps.run(max_rounds, rule_mask);
+  po.status = ps.status;
+  ps.build_reduced(out);
+  if (po.status == LP_PRESOLVE_REDUCED && out.m == 0 && out.n == 0)
+    po.status = LP_PRESOLVE_SOLVED;
+}
+
+void postsolve_run(const PresolveOutcome &po, const HostLP &red, const double *xr,
+                   const double *yr, const double *zr, double *x, double *y, double *z) {
+  std::fill(x, x + po.n0, 0.0);
+  std::fill(y, y + po.m0, 0.0);
+  std::fill(z, z + po.n0, 0.0);
+  for (int32_t q = 0; q < red.n; ++q) x[po.col_map[q]] = xr[q];
+  for (int32_t r = 0; r < red.m; ++r) y[po.row_map[r]] = yr[r];
+  if (zr) {
+    for (int32_t q = 0; q < red.n; ++q) z[po.col_map[q]] = zr[q];
+  } else {
+    std::vector<double> g(red.c);
+    for (int32_t r = 0; r < red.m; ++r)
+      for (int64_t e = red.row_ptr[r]; e < red.row_ptr[r + 1]; ++e)
+        g[red.col_idx[e]] -= red.val[e] * yr[r];
+    for (int32_t q = 0; q < red.n; ++q) z[po.col_map[q]] = g[q];
+  }
+  for (size_t t = po.records.size(); t-- > 0;) {
+    const PostsolveRecord &r = po.records[t];
+    switch (r.kind) {
+      case REC_EMPTY_ROW:
+      case REC_REDUNDANT_ROW:
+        y[r.i] = 0.0;
+        break;
+      case REC_DROP_SIDE:
+        break;
+      case REC_FIX_COL: {
+        x[r.j] = r.v;
+        double s = r.cj;
+        for (int64_t e = r.ent_begin; e < r.ent_end; ++e) s -= po.ent_val[e] * y[po.ent_idx[e]];
+        z[r.j] = s;
+        break;
+      }
+      case REC_SINGLETON_ROW: {
+        bool lo_from = r.flags & 1, hi_from = r.flags & 2;
+        if ((z[r.j] > 0 && lo_from) || (z[r.j] < 0 && hi_from)) {
+          y[r.i] = z[r.j] / r.a;
+          z[r.j] = 0.0;
+        } else {
+          y[r.i] = 0.0;
+        }
+        break;
+      }
+      case REC_DOUBLETON: {
+        int32_t i = r.i, j = r.j, k = r.k;
+        double aj = r.a, ak = r.ak;
+        x[j] = (r.b - ak * x[k]) / aj;
+        double dj = r.cj;
+        for (int64_t e = r.ent_begin; e < r.ent_end; ++e) dj -= po.ent_val[e] * y[po.ent_idx[e]];
+        bool lo_from = r.flags & 1, hi_from = r.flags & 2;
+        if ((z[k] > 0 && lo_from) || (z[k] < 0 && hi_from)) {
+          y[i] = (z[k] + (ak / aj) * dj) / ak;
+          z[j] = dj - aj * y[i];
+          z[k] = 0.0;
+        } else {
+          y[i] = dj / aj;
+          z[j] = 0.0;
+        }
+        break;
+      }
+      case REC_FREE_COL: {
+        double s = r.b;
+        for (int64_t e = r.ent_begin; e < r.ent_end; ++e) s -= po.ent_val[e] * x[po.ent_idx[e]];
+        x[r.j] = s / r.a;
+        y[r.i] = r.cj / r.a;
+        z[r.j] = 0.0;
+        break;
+      }
+      default:
+        break;
+    }
+  }
+}
+
+}  // namespace gb300lp

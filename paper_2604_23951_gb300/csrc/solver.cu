@@ -1,0 +1,1246 @@
+// Single-LP GPU path: restarted reflected Halpern PDHG for eq. (1).
+//
+// Data layout in HBM (built once per problem by dev_upload):
+//   * rows of A and rows of A^T (= columns of A) are each sorted by a length
+//     class (stable), so every class is a contiguous index range; the LP is
+//     renumbered with those permutations, so the epilogues of the SpMV
+//     kernels read and write their vectors contiguously;
+//   * A (m rows) and its stored transpose A^T (n rows) in CSR with int32
+//     offsets and column indices; unscaled FP64 values are kept for
+//     re-solves, scaled FP64 values (and FP32 copies in mixed precision) are
+//     what the iteration reads;
+//   * per-row / per-column vectors in FP64.
+//
+// Kernels per PDHG iteration (the operator T and the Halpern step):
+//   K1  g = A~^T y       fused with  xh = proj(x - tau (c~ - g)), xbar = 2 xh - x,
+//                                     x <- lam((1+rho) xh - rho x) + (1-lam) x0
+//   K2  h = A~ xbar      fused with  v = y - sigma h, yh = v + sigma proj(-v / sigma),
+//                                     y <- lam((1+rho) yh - rho y) + (1-lam) y0
+// and every K-th iteration (the check):
+//   K1/K2 also write xh, yh and block partials of ||x - xh||^2, ||xh - x0||^2, ...
+//   K3a h = A~ xh        fused with  primal residual and the y part of the dual objective
+//   K3b g = A~^T yh      fused with  dual residual, lambda part of the dual objective, c^T x
+//   K4  one CTA: fixed-order reduction of the partials, rel-KKT, termination,
+//       restart test and primal-weight update (device state, no host round trip)
+//   K5  on restart: x = x0 = xh, y = y0 = yh
+// A CUDA graph holds one check iteration plus K - 1 plain iterations and the
+// D2H copy of the state word; the host replays it until the state says done.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "device_common.cuh"
+#include "lp_internal.h"
+
+namespace gb300lp {
+
+constexpr int kBlock = 256;
+constexpr int kMaxBins = 8;
+constexpr int kBlockRowLog = 8;  // vlog marking the block-per-row class
+
+struct Bins {
+  int nbins = 0;
+  int ntiles = 0;
+  int tile_begin[kMaxBins + 1] = {0};
+  int row_begin[kMaxBins + 1] = {0};
+  int vlog[kMaxBins] = {0};
+};
+
+constexpr int ST_RUNNING = -1;
+
+struct State {
+  double eta, omega, tau, sigma;
+  double rho, beta_suff, beta_nec, beta_art, theta, eps_rel;
+  double r0, r_prev, last_r;
+  double bnorm, cnorm, off;
+  double rel_kkt, rel_p, rel_d, rel_gap, r_p, r_d, gap, pobj, dobj;
+  long long t;
+  long long iters;
+  int K;
+  int k_base, k_off;
+  int restarts;
+  int status;
+  int restart_flag;
+  int halpern, restarts_on;
+};
+
+enum {
+  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P, Q_CN, Q_BN, Q_PW, NQ
+};
+
+// ---------------------------------------------------------------------------
+// generic binned row loop: each row reduced by a group of V lanes (V = 1..32)
+// or by the whole CTA (block-per-row class); epi.row(r, value) is called once
+// per row by one thread.
+
+template <typename Acc>
+__device__ __forceinline__ Acc group_sum(Acc s, int vlog) {
+  for (int o = (1 << vlog) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  return s;
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc block_sum_bcast0(Acc s, Acc *red) {
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  Acc tot = 0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kBlock / 32; ++w) tot += red[w];
+  }
+  __syncthreads();
+  return tot;
+}
+
+// SpMV row loop: value of row r = sum_k va[k] * vec[ci[k]] in Acc precision
+template <typename T, typename V, typename Acc, class Epi>
+__device__ __forceinline__ void spmv_loop(const int *__restrict__ rp, const int *__restrict__ ci,
+                                          const T *__restrict__ va, const V *__restrict__ vec,
+                                          const Bins &bins, Epi &epi) {
+  __shared__ Acc red[kBlock / 32];
+  for (int t = blockIdx.x; t < bins.ntiles; t += gridDim.x) {
+    int b = 0;
+    while (t >= bins.tile_begin[b + 1]) ++b;
+    const int vlog = bins.vlog[b];
+    if (vlog != kBlockRowLog) {
+      const int rpt = kBlock >> vlog;
+      const int r = bins.row_begin[b] + (t - bins.tile_begin[b]) * rpt + (threadIdx.x >> vlog);
+      const int lane = threadIdx.x & ((1 << vlog) - 1);
+      const bool valid = r < bins.row_begin[b + 1];
+      Acc s = 0;
+      if (valid) {
+        const int e = rp[r + 1];
+        const int step = 1 << vlog;
+#pragma unroll 4
+        for (int k = rp[r] + lane; k < e; k += step) s += (Acc)va[k] * (Acc)vec[ci[k]];
+      }
+      s = group_sum(s, vlog);
+      if (valid && lane == 0) epi.row(r, (double)s);
+    } else {
+      const int r = bins.row_begin[b] + (t - bins.tile_begin[b]);
+      const int e = rp[r + 1];
+      Acc s = 0;
+#pragma unroll 4
+      for (int k = rp[r] + threadIdx.x; k < e; k += kBlock) s += (Acc)va[k] * (Acc)vec[ci[k]];
+      s = block_sum_bcast0(s, red);
+      if (threadIdx.x == 0) epi.row(r, (double)s);
+    }
+  }
+}
+
+// deterministic block reduction of NQL accumulators into partials[q * G + block]
+template <int NQL>
+__device__ __forceinline__ void store_partials(double (&acc)[NQL], const int (&qidx)[NQL],
+                                               double *partials, int G) {
+  __shared__ double sh[NQL][kBlock / 32];
+#pragma unroll
+  for (int q = 0; q < NQL; ++q) {
+    double v = warp_sum(acc[q]);
+    if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQL) {
+    double s = 0;
+    for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
+    partials[qidx[threadIdx.x] * G + blockIdx.x] = s;
+  }
+}
+
+// fixed-order sum of one quantity's partials by a whole CTA; result in all threads
+__device__ double reduce_partials(const double *partials, int q, int G) {
+  __shared__ double sh[kBlock / 32];
+  __shared__ double out;
+  double s = 0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s += partials[q * G + b];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
+    out = t;
+  }
+  __syncthreads();
+  double r = out;
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// scaling (Ruiz passes, then Pock-Chambolle alpha = 1)
+
+// d_new[r] = d_self[r] / sqrt(max or sum over the row of |scaled a|), where the
+// scaled entry is (dr_i |a_ij|) dc_j; for rows of A^T (TRANSPOSED) the row
+// scale is dc and the other one dr.
+template <bool TRANSPOSED, bool SUM>
+__global__ void k_scale_pass(int rows, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ a0, const double *__restrict__ dself,
+                             const double *__restrict__ dother, double *__restrict__ dnew) {
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    double acc = 0.0;
+    const double ds = dself[r];
+    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) {
+      double v = TRANSPOSED ? (dother[ci[k]] * fabs(a0[k])) * ds : (ds * fabs(a0[k])) * dother[ci[k]];
+      acc = SUM ? acc + v : fmax(acc, v);
+    }
+    acc = SUM ? warp_sum(acc) : warp_max(acc);
+    if (lane == 0) dnew[r] = acc > 0.0 ? ds / sqrt(acc) : ds;
+  }
+}
+
+// scaled values (dr_i a_ij) dc_j in FP64 and optionally FP32
+template <bool TRANSPOSED>
+__global__ void k_apply_matrix(int rows, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const double *__restrict__ a0, const double *__restrict__ dself,
+                               const double *__restrict__ dother, double *__restrict__ out,
+                               float *__restrict__ outf) {
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const double ds = dself[r];
+    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) {
+      double v = TRANSPOSED ? (dother[ci[k]] * a0[k]) * ds : (ds * a0[k]) * dother[ci[k]];
+      out[k] = v;
+      if (outf) outf[k] = (float)v;
+    }
+  }
+}
+
+// c~ = dc c, lx~ = lx / dc, ux~ = ux / dc; partial ||c~||^2
+__global__ void k_apply_cols(int n, const double *__restrict__ c0, const double *__restrict__ lx0,
+                             const double *__restrict__ ux0, const double *__restrict__ dc,
+                             double *__restrict__ c, double *__restrict__ lx,
+                             double *__restrict__ ux, double *partials, int G) {
+  double acc[1] = {0.0};
+  const int qi[1] = {Q_CN};
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double d = dc[j];
+    double cj = d * c0[j];
+    c[j] = cj;
+    lx[j] = lx0[j] / d;
+    ux[j] = ux0[j] / d;
+    acc[0] += cj * cj;
+  }
+  store_partials<1>(acc, qi, partials, G);
+}
+
+// lc~ = dr lc, uc~ = dr uc; partial ||bhat~||^2 (finite sides, equality once)
+__global__ void k_apply_rows(int m, const double *__restrict__ lc0, const double *__restrict__ uc0,
+                             const double *__restrict__ dr, double *__restrict__ lc,
+                             double *__restrict__ uc, double *partials, int G) {
+  double acc[1] = {0.0};
+  const int qi[1] = {Q_BN};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double d = dr[i];
+    double l = d * lc0[i], u = d * uc0[i];
+    lc[i] = l;
+    uc[i] = u;
+    bool lf = isfinite(l), uf = isfinite(u);
+    if (lf) acc[0] += l * l;
+    if (uf && !(lf && l == u)) acc[0] += u * u;
+  }
+  store_partials<1>(acc, qi, partials, G);
+}
+
+__global__ void k_fill(double *p, double v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// power iteration on A~^T A~
+
+struct StoreEpi {
+  double *out;
+  __device__ __forceinline__ void row(int r, double s) { out[r] = s; }
+};
+struct StoreSqEpi {
+  double *out;
+  double acc;
+  __device__ __forceinline__ void row(int r, double s) {
+    out[r] = s;
+    acc += s * s;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_spmv_store(const int *__restrict__ rp,
+                                                       const int *__restrict__ ci,
+                                                       const double *__restrict__ va,
+                                                       const double *__restrict__ vec, Bins bins,
+                                                       double *out) {
+  StoreEpi e{out};
+  spmv_loop<double, double, double>(rp, ci, va, vec, bins, e);
+}
+
+__global__ void __launch_bounds__(kBlock) k_spmv_store_sq(const int *__restrict__ rp,
+                                                          const int *__restrict__ ci,
+                                                          const double *__restrict__ va,
+                                                          const double *__restrict__ vec,
+                                                          Bins bins, double *out,
+                                                          double *partials, int G) {
+  StoreSqEpi e{out, 0.0};
+  spmv_loop<double, double, double>(rp, ci, va, vec, bins, e);
+  double acc[1] = {e.acc};
+  const int qi[1] = {Q_PW};
+  store_partials<1>(acc, qi, partials, G);
+}
+
+// v = w / ||w|| (every CTA reduces the partials in the same fixed order)
+__global__ void k_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
+                            const double *partials, int G) {
+  double nw = sqrt(reduce_partials(partials, Q_PW, G));
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    v[j] = nw > 0.0 ? w[j] / nw : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// state set-up
+
+__global__ void k_setup_final(State *st, const double *partials, int G, double eta_given,
+                              double omega_given, int power_done) {
+  double cn = sqrt(reduce_partials(partials, Q_CN, G));
+  double bn = sqrt(reduce_partials(partials, Q_BN, G));
+  double pw = power_done ? sqrt(reduce_partials(partials, Q_PW, G)) : 0.0;
+  if (threadIdx.x == 0) {
+    double eta = eta_given > 0 ? eta_given : (pw > 0 ? 0.998 / pw : 1.0);
+    double om = omega_given > 0 ? omega_given : ((cn > 0 && bn > 0) ? cn / bn : 1.0);
+    st->eta = eta;
+    st->omega = om;
+    st->tau = eta / om;
+    st->sigma = eta * om;
+    st->t = 0;
+    st->iters = 0;
+    st->k_base = 0;
+    st->k_off = 0;
+    st->restarts = 0;
+    st->status = ST_RUNNING;
+    st->restart_flag = 0;
+    st->r0 = st->r_prev = st->last_r = 0.0;
+    st->rel_kkt = INFINITY;
+  }
+}
+
+__global__ void k_init_x(int n, const double *__restrict__ lx, const double *__restrict__ ux,
+                         const double *__restrict__ dc, const double *__restrict__ xinit,
+                         double *x, double *x0) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double v = xinit ? xinit[j] / dc[j] : clampd(0.0, lx[j], ux[j]);
+    x[j] = v;
+    x0[j] = v;
+  }
+}
+
+__global__ void k_init_y(int m, const double *__restrict__ dr, const double *__restrict__ yinit,
+                         double *y, double *y0, float *yf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double v = yinit ? yinit[i] / dr[i] : 0.0;
+    y[i] = v;
+    y0[i] = v;
+    if (yf) yf[i] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the iteration kernels
+
+__device__ __forceinline__ double halpern_weight(const State *st, int j) {
+  if (!st->halpern) return 1.0;
+  int k = (j == 0) ? st->k_base : st->k_off + j;
+  return (k + 1.0) / (k + 2.0);
+}
+
+template <bool CHECK, bool MIXED>
+struct PrimalEpi {
+  const double *c, *lx, *ux;
+  double *x, *x0, *xbar, *xhat;
+  float *xbar_f;
+  double tau, lam, rho;
+  double acc0, acc1;
+  __device__ __forceinline__ void row(int j, double g) {
+    double xk = x[j];
+    double xh = clampd(xk - tau * (c[j] - g), lx[j], ux[j]);
+    double xb = 2.0 * xh - xk;
+    double a0 = x0[j];
+    x[j] = lam * ((1.0 + rho) * xh - rho * xk) + (1.0 - lam) * a0;
+    if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
+    if (CHECK) {
+      xhat[j] = xh;
+      acc0 += (xk - xh) * (xk - xh);
+      acc1 += (xh - a0) * (xh - a0);
+    }
+  }
+};
+
+template <typename T, bool CHECK>
+__global__ void __launch_bounds__(kBlock) k_primal(
+    const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ va, Bins bins,
+    const double *__restrict__ y, const float *__restrict__ yf, const double *__restrict__ c,
+    const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
+    double *xbar, float *xbar_f, double *xhat, const State *__restrict__ st, int j,
+    double *partials, int G) {
+  if (st->status != ST_RUNNING) return;
+  constexpr bool MIXED = sizeof(T) == 4;
+  PrimalEpi<CHECK, MIXED> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau, halpern_weight(st, j),
+                            st->rho, 0.0, 0.0};
+  if (MIXED)
+    spmv_loop<T, float, float>(rp, ci, va, yf, bins, e);
+  else
+    spmv_loop<T, double, double>(rp, ci, va, y, bins, e);
+  if (CHECK) {
+    double acc[2] = {e.acc0, e.acc1};
+    const int qi[2] = {Q_XRES, Q_XD};
+    store_partials<2>(acc, qi, partials, G);
+  }
+}
+
+template <bool CHECK, bool MIXED>
+struct DualEpi {
+  const double *lc, *uc;
+  double *y, *y0, *yhat;
+  float *yf;
+  double sigma, lam, rho;
+  double acc0, acc1;
+  __device__ __forceinline__ void row(int i, double h) {
+    double yk = y[i];
+    double v = yk - sigma * h;
+    double yh = v + sigma * clampd(-v / sigma, lc[i], uc[i]);
+    double a0 = y0[i];
+    double yn = lam * ((1.0 + rho) * yh - rho * yk) + (1.0 - lam) * a0;
+    y[i] = yn;
+    if (MIXED) yf[i] = (float)yn;
+    if (CHECK) {
+      yhat[i] = yh;
+      acc0 += (yk - yh) * (yk - yh);
+      acc1 += (yh - a0) * (yh - a0);
+    }
+  }
+};
+
+template <typename T, bool CHECK>
+__global__ void __launch_bounds__(kBlock) k_dual(
+    const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ va, Bins bins,
+    const double *__restrict__ xbar, const float *__restrict__ xbar_f,
+    const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
+    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int G) {
+  if (st->status != ST_RUNNING) return;
+  constexpr bool MIXED = sizeof(T) == 4;
+  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_weight(st, j), st->rho,
+                          0.0, 0.0};
+  if (MIXED)
+    spmv_loop<T, float, float>(rp, ci, va, xbar_f, bins, e);
+  else
+    spmv_loop<T, double, double>(rp, ci, va, xbar, bins, e);
+  if (CHECK) {
+    double acc[2] = {e.acc0, e.acc1};
+    const int qi[2] = {Q_YRES, Q_YD};
+    store_partials<2>(acc, qi, partials, G);
+  }
+}
+
+// K3a: rows of A: primal residual of the unscaled A x and the y terms
+struct KktRowEpi {
+  const double *dr, *lc0, *uc0, *yhat;
+  double rp2, rdy2, dy;
+  __device__ __forceinline__ void row(int i, double h) {
+    double d = dr[i];
+    double ax = h / d;
+    double lo = lc0[i], hi = uc0[i];
+    double pr = clampd(ax, lo, hi);
+    rp2 += (ax - pr) * (ax - pr);
+    double yv = d * yhat[i];
+    double yp = yv;
+    if (!isfinite(lo)) yp = fmin(yp, 0.0);
+    if (!isfinite(hi)) yp = fmax(yp, 0.0);
+    rdy2 += (yv - yp) * (yv - yp);
+    dy += support_term(yp, lo, hi);
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_kkt_rows(
+    const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ va,
+    Bins bins, const double *__restrict__ xhat, const double *__restrict__ dr,
+    const double *__restrict__ lc0, const double *__restrict__ uc0,
+    const double *__restrict__ yhat, const State *__restrict__ st, int force, double *partials,
+    int G) {
+  if (!force && st->status != ST_RUNNING) return;
+  KktRowEpi e{dr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
+  spmv_loop<double, double, double>(rp, ci, va, xhat, bins, e);
+  double acc[3] = {e.rp2, e.rdy2, e.dy};
+  const int qi[3] = {Q_RP, Q_RDY, Q_DY};
+  store_partials<3>(acc, qi, partials, G);
+}
+
+// K3b: rows of A^T: dual residual, lambda terms and the primal objective
+struct KktColEpi {
+  const double *c, *dc, *c0, *lx0, *ux0, *xhat;
+  double *zbuf;
+  double rd2, dl, p;
+  __device__ __forceinline__ void row(int j, double h) {
+    double d = dc[j];
+    double g = (c[j] - h) / d;
+    double lo = lx0[j], hi = ux0[j];
+    bool lf = isfinite(lo), uf = isfinite(hi);
+    double lam = g;
+    if (!lf && !uf) lam = 0.0;
+    else if (lf && !uf) lam = fmax(lam, 0.0);
+    else if (!lf && uf) lam = fmin(lam, 0.0);
+    rd2 += (g - lam) * (g - lam);
+    dl += support_term(lam, lo, hi);
+    p += c0[j] * (d * xhat[j]);
+    zbuf[j] = g;
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_kkt_cols(
+    const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ va,
+    Bins bins, const double *__restrict__ yhat, const double *__restrict__ c,
+    const double *__restrict__ dc, const double *__restrict__ c0, const double *__restrict__ lx0,
+    const double *__restrict__ ux0, const double *__restrict__ xhat, double *zbuf,
+    const State *__restrict__ st, int force, double *partials, int G) {
+  if (!force && st->status != ST_RUNNING) return;
+  KktColEpi e{c, dc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
+  spmv_loop<double, double, double>(rp, ci, va, yhat, bins, e);
+  double acc[3] = {e.rd2, e.dl, e.p};
+  const int qi[3] = {Q_RD, Q_DL, Q_P};
+  store_partials<3>(acc, qi, partials, G);
+}
+
+// K4: the check.  eval_only: fill in the KKT fields and mark ITER_LIMIT.
+__global__ void k_check(State *st, const double *partials, int G, int eval_only) {
+  if (!eval_only && st->status != ST_RUNNING) return;
+  double q[NQ];
+  for (int i = 0; i < Q_CN; ++i) q[i] = reduce_partials(partials, i, G);
+  if (threadIdx.x != 0) return;
+  double rp = sqrt(q[Q_RP]);
+  double rd = sqrt(q[Q_RD] + q[Q_RDY]);
+  double p = q[Q_P] + st->off;
+  double d = q[Q_DY] + q[Q_DL] + st->off;
+  double relp = rp / (1.0 + st->bnorm);
+  double reld = rd / (1.0 + st->cnorm);
+  double gap = fabs(p - d);
+  double relg = gap / (1.0 + fabs(p) + fabs(d));
+  double rel = fmax(relp, fmax(reld, relg));
+  st->rel_kkt = rel;
+  st->rel_p = relp;
+  st->rel_d = reld;
+  st->rel_gap = relg;
+  st->r_p = rp;
+  st->r_d = rd;
+  st->gap = gap;
+  st->pobj = p;
+  st->dobj = d;
+  if (eval_only) {
+    if (st->status == ST_RUNNING) st->status = 1;  // LP_ITER_LIMIT
+    return;
+  }
+  bool finite = isfinite(rel) && isfinite(q[Q_XRES]) && isfinite(q[Q_YRES]);
+  if (!finite || rel <= st->eps_rel) {
+    st->status = finite ? 0 : 3;  // LP_OPTIMAL : LP_NUMERICAL
+    st->iters = st->t + 1;
+    return;
+  }
+  double om = st->omega;
+  double r = sqrt(om * q[Q_XRES] + q[Q_YRES] / om);
+  st->last_r = r;
+  int kb = st->k_base;
+  int restart = 0;
+  if (kb == 0) {
+    st->r0 = st->r_prev = r;
+  } else if (st->restarts_on &&
+             (r <= st->beta_suff * st->r0 || (r <= st->beta_nec * st->r0 && r > st->r_prev) ||
+              (double)kb >= st->beta_art * (double)st->t)) {
+    double dx = sqrt(q[Q_XD]), dy = sqrt(q[Q_YD]);
+    if (dx > 1e-10 && dy > 1e-10) om = exp(st->theta * log(dy / dx) + (1.0 - st->theta) * log(om));
+    st->omega = om;
+    st->tau = st->eta / om;
+    st->sigma = st->eta * om;
+    st->r0 = st->r_prev = r;
+    st->restarts += 1;
+    restart = 1;
+  } else {
+    st->r_prev = r;
+  }
+  st->restart_flag = restart;
+  st->k_off = restart ? -1 : kb;
+  st->k_base = st->k_off + st->K;
+  st->t += st->K;
+}
+
+// K5: on restart, x = x0 = xh and y = y0 = yh
+__global__ void k_restart(const State *__restrict__ st, int n, int m, double *x, double *x0,
+                          const double *__restrict__ xhat, double *y, double *y0,
+                          const double *__restrict__ yhat, float *yf) {
+  if (st->status != ST_RUNNING || !st->restart_flag) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double v = xhat[j];
+    x[j] = v;
+    x0[j] = v;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double v = yhat[i];
+    y[i] = v;
+    y0[i] = v;
+    if (yf) yf[i] = (float)v;
+  }
+}
+
+// unscaled outputs in the permuted order
+__global__ void k_unscale(int n, int m, const double *__restrict__ dc, const double *__restrict__ dr,
+                          const double *__restrict__ xhat, const double *__restrict__ yhat,
+                          const double *__restrict__ x, const double *__restrict__ y,
+                          double *out_xh, double *out_yh, double *out_x, double *out_y) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    out_xh[j] = dc[j] * xhat[j];
+    out_x[j] = dc[j] * x[j];
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    out_yh[i] = dr[i] * yhat[i];
+    out_y[i] = dr[i] * y[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct DeviceLP {
+  lp_device_ctx ctx{};
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int sm_count = 0;
+  bool uploaded = false;
+  int m = 0, n = 0;
+  long long nnz = 0;
+  std::vector<int> rperm, cperm;  // new -> old
+  Bins binsA, binsT;
+  int G = 1;
+  int *A_rp = nullptr, *A_ci = nullptr, *T_rp = nullptr, *T_ci = nullptr;
+  double *A_v0 = nullptr, *T_v0 = nullptr, *A_v = nullptr, *T_v = nullptr;
+  float *A_vf = nullptr, *T_vf = nullptr;
+  double *c0 = nullptr, *lx0 = nullptr, *ux0 = nullptr, *lc0 = nullptr, *uc0 = nullptr;
+  double *c = nullptr, *lx = nullptr, *ux = nullptr, *lc = nullptr, *uc = nullptr;
+  double *dr = nullptr, *dc = nullptr, *dr2 = nullptr, *dc2 = nullptr;
+  double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
+  double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
+  double *pv = nullptr, *pw = nullptr, *pu = nullptr;
+  double *ox = nullptr, *oy = nullptr, *oxi = nullptr, *oyi = nullptr;
+  float *xbar_f = nullptr, *yf = nullptr;
+  double *partials = nullptr;
+  State *st = nullptr;
+  State *hst = nullptr;
+  double *hbuf = nullptr;  // pinned staging for warm starts
+  double bnorm = 0, cnorm = 0, off = 0;
+  std::vector<void *> allocs;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_K[2] = {0, 0};
+  long long launches = 0;
+
+  void *dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (ctx.alloc) {
+      p = ctx.alloc(bytes, ctx.user);
+      if (!p) throw DeviceOOM("device allocation of " + std::to_string(bytes) + " bytes failed");
+    } else {
+      cudaError_t e = cudaMallocAsync(&p, bytes, s);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        throw DeviceOOM("device allocation of " + std::to_string(bytes) + " bytes failed");
+      }
+      CK(e);
+    }
+    allocs.push_back(p);
+    return p;
+  }
+  template <typename T>
+  T *dalloc_n(size_t n) {
+    return static_cast<T *>(dalloc(n * sizeof(T)));
+  }
+  void release_all() {
+    for (int q = 0; q < 2; ++q)
+      if (graph[q]) {
+        cudaGraphExecDestroy(graph[q]);
+        graph[q] = nullptr;
+      }
+    for (void *p : allocs) {
+      if (ctx.free) ctx.free(p, ctx.user);
+      else cudaFreeAsync(p, s);
+    }
+    allocs.clear();
+    uploaded = false;
+  }
+  int grid_for(long long work) const {
+    long long g = (work + kBlock - 1) / kBlock;
+    g = std::max<long long>(1, std::min<long long>(g, (long long)sm_count * 8));
+    return (int)g;
+  }
+};
+
+static void plan_bins(const std::vector<int64_t> &len, int items, int block_min, Bins &bins,
+                      std::vector<int> &perm) {
+  // class c in 0..5: V = 2^c lanes per row; class 6: whole CTA per row
+  const int nclass = 7;
+  int rows = (int)len.size();
+  std::vector<int> cls(rows);
+  std::vector<int> count(nclass, 0);
+  for (int r = 0; r < rows; ++r) {
+    int64_t L = len[r];
+    int cc;
+    if (L >= block_min) {
+      cc = 6;
+    } else {
+      int64_t need = (L + items - 1) / items;
+      cc = 0;
+      while ((1LL << cc) < need && cc < 5) ++cc;
+    }
+    cls[r] = cc;
+    count[cc]++;
+  }
+  std::vector<int> start(nclass + 1, 0);
+  for (int q = 0; q < nclass; ++q) start[q + 1] = start[q] + count[q];
+  perm.assign(rows, 0);
+  std::vector<int> pos(start.begin(), start.end() - 1);
+  for (int r = 0; r < rows; ++r) perm[pos[cls[r]]++] = r;
+  bins = Bins();
+  int nb = 0, tiles = 0;
+  for (int q = 0; q < nclass; ++q) {
+    if (count[q] == 0) continue;
+    bins.row_begin[nb] = start[q];
+    bins.tile_begin[nb] = tiles;
+    int vlog = q == 6 ? kBlockRowLog : q;
+    bins.vlog[nb] = vlog;
+    int rpt = q == 6 ? 1 : (kBlock >> q);
+    tiles += (count[q] + rpt - 1) / rpt;
+    ++nb;
+  }
+  bins.nbins = nb;
+  bins.ntiles = tiles;
+  bins.row_begin[nb] = rows;
+  bins.tile_begin[nb] = tiles;
+  for (int q = nb + 1; q <= kMaxBins; ++q) {
+    bins.row_begin[q] = rows;
+    bins.tile_begin[q] = tiles;
+  }
+}
+
+DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
+  DeviceLP *d = new DeviceLP();
+  try {
+    if (ctx) d->ctx = *ctx;
+    d->device = d->ctx.device;
+    CK(cudaSetDevice(d->device));
+    CK(cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, d->device));
+    if (d->ctx.stream) {
+      d->s = static_cast<cudaStream_t>(d->ctx.stream);
+    } else {
+      CK(cudaStreamCreateWithFlags(&d->s, cudaStreamNonBlocking));
+      d->own_stream = true;
+    }
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&d->hst), sizeof(State), cudaHostAllocDefault));
+  } catch (const std::exception &e) {
+    err = e.what();
+    delete d;
+    return nullptr;
+  }
+  return d;
+}
+
+bool dev_uploaded(const DeviceLP *d) { return d && d->uploaded; }
+
+void dev_destroy(DeviceLP *d) {
+  if (!d) return;
+  cudaSetDevice(d->device);
+  d->release_all();
+  cudaStreamSynchronize(d->s);
+  if (d->hst) cudaFreeHost(d->hst);
+  if (d->hbuf) cudaFreeHost(d->hbuf);
+  if (d->own_stream) cudaStreamDestroy(d->s);
+  delete d;
+}
+
+int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
+  try {
+    CK(cudaSetDevice(d->device));
+    d->release_all();
+    if (h.nnz() >= (int64_t)INT32_MAX) {
+      err = "nnz must be below 2^31 on the device";
+      return LP_ERR_INVALID;
+    }
+    const int m = h.m, n = h.n;
+    const long long nnz = h.nnz();
+    d->m = m;
+    d->n = n;
+    d->nnz = nnz;
+    const int items = tile_items > 0 ? tile_items : 4;
+    const int block_min = 32 * items * 16;
+    // row classes of A and of A^T
+    std::vector<int64_t> rlen(m), clen(n, 0);
+    for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
+    for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
+    plan_bins(rlen, items, block_min, d->binsA, d->rperm);
+    plan_bins(clen, items, block_min, d->binsT, d->cperm);
+    std::vector<int> rinv(m), cinv(n);
+    for (int i = 0; i < m; ++i) rinv[d->rperm[i]] = i;
+    for (int j = 0; j < n; ++j) cinv[d->cperm[j]] = j;
+    // permuted A
+    std::vector<int> arp(m + 1, 0), aci(nnz);
+    std::vector<double> av(nnz);
+    for (int i = 0; i < m; ++i) {
+      int o = d->rperm[i];
+      arp[i + 1] = arp[i] + (int)rlen[o];
+      int w = arp[i];
+      for (int64_t k = h.row_ptr[o]; k < h.row_ptr[o + 1]; ++k, ++w) {
+        aci[w] = cinv[h.col_idx[k]];
+        av[w] = h.val[k];
+      }
+    }
+    // transpose of the permuted A, rows in new column order, entries by new row
+    std::vector<int> trp(n + 1, 0), tci(nnz);
+    std::vector<double> tv(nnz);
+    for (int j = 0; j < n; ++j) trp[j + 1] = trp[j] + (int)clen[d->cperm[j]];
+    {
+      std::vector<int> cur(trp.begin(), trp.end() - 1);
+      for (int i = 0; i < m; ++i)
+        for (int k = arp[i]; k < arp[i + 1]; ++k) {
+          int j = aci[k];
+          tci[cur[j]] = i;
+          tv[cur[j]] = av[k];
+          ++cur[j];
+        }
+    }
+    std::vector<double> c0(n), lx0(n), ux0(n), lc0(m), uc0(m);
+    for (int j = 0; j < n; ++j) {
+      int o = d->cperm[j];
+      c0[j] = h.c[o];
+      lx0[j] = h.col_lo[o];
+      ux0[j] = h.col_hi[o];
+    }
+    for (int i = 0; i < m; ++i) {
+      int o = d->rperm[i];
+      lc0[i] = h.row_lo[o];
+      uc0[i] = h.row_hi[o];
+    }
+    // norms of the unscaled data for the relative KKT error
+    double bn2 = 0, cn2 = 0;
+    for (int i = 0; i < m; ++i) {
+      bool lf = std::isfinite(lc0[i]), uf = std::isfinite(uc0[i]);
+      if (lf) bn2 += lc0[i] * lc0[i];
+      if (uf && !(lf && lc0[i] == uc0[i])) bn2 += uc0[i] * uc0[i];
+    }
+    for (int j = 0; j < n; ++j) cn2 += c0[j] * c0[j];
+    d->bnorm = std::sqrt(bn2);
+    d->cnorm = std::sqrt(cn2);
+    d->off = h.off;
+    // device buffers
+    d->A_rp = d->dalloc_n<int>(m + 1);
+    d->A_ci = d->dalloc_n<int>(nnz);
+    d->A_v0 = d->dalloc_n<double>(nnz);
+    d->A_v = d->dalloc_n<double>(nnz);
+    d->T_rp = d->dalloc_n<int>(n + 1);
+    d->T_ci = d->dalloc_n<int>(nnz);
+    d->T_v0 = d->dalloc_n<double>(nnz);
+    d->T_v = d->dalloc_n<double>(nnz);
+    d->A_vf = d->dalloc_n<float>(nnz);
+    d->T_vf = d->dalloc_n<float>(nnz);
+    double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
+                        &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv, &d->pw,
+                        &d->ox, &d->oxi};
+    for (double **p : cols_) *p = d->dalloc_n<double>(n);
+    double **rows_[] = {&d->lc0, &d->uc0, &d->lc, &d->uc, &d->dr, &d->dr2, &d->y, &d->y0,
+                        &d->yhat, &d->pu, &d->oy, &d->oyi};
+    for (double **p : rows_) *p = d->dalloc_n<double>(m);
+    d->xbar_f = d->dalloc_n<float>(n);
+    d->yf = d->dalloc_n<float>(m);
+    int tiles = std::max(d->binsA.ntiles, d->binsT.ntiles);
+    d->G = std::max(1, std::min(tiles, d->sm_count * 4));
+    d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
+    d->st = d->dalloc_n<State>(1);
+    CK(cudaMemcpyAsync(d->A_rp, arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_ci, aci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_v0, av.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_rp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_ci, tci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_v0, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->c0, c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->lx0, lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->ux0, ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->lc0, lc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->uc0, uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+    CK(cudaStreamSynchronize(d->s));
+    d->uploaded = true;
+  } catch (const DeviceOOM &e) {
+    err = e.what();
+    return LP_ERR_OOM;
+  } catch (const std::exception &e) {
+    err = e.what();
+    return LP_ERR_CUDA;
+  }
+  return LP_OK;
+}
+
+namespace {
+
+// one PDHG iteration (position j in its chunk); check adds K3, K4, K5
+void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only) {
+  const int gA = std::max(1, std::min(d->binsA.ntiles, d->G));
+  const int gT = std::max(1, std::min(d->binsT.ntiles, d->G));
+  const bool wr = check || hat_only;
+  // the partial-producing kernels must cover all G slots: use G CTAs then
+  const int gT1 = wr ? d->G : gT;
+  const int gA1 = wr ? d->G : gA;
+  if (mixed) {
+    if (wr)
+      k_primal<float, true><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y,
+                                                       d->yf, d->c, d->lx, d->ux, d->x, d->x0,
+                                                       d->xbar, d->xbar_f, d->xhat, d->st, j,
+                                                       d->partials, d->G);
+    else
+      k_primal<float, false><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y,
+                                                        d->yf, d->c, d->lx, d->ux, d->x, d->x0,
+                                                        d->xbar, d->xbar_f, d->xhat, d->st, j,
+                                                        d->partials, d->G);
+    if (wr)
+      k_dual<float, true><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_vf, d->binsA, d->xbar,
+                                                     d->xbar_f, d->lc, d->uc, d->y, d->y0, d->yf,
+                                                     d->yhat, d->st, j, d->partials, d->G);
+    else
+      k_dual<float, false><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_vf, d->binsA,
+                                                      d->xbar, d->xbar_f, d->lc, d->uc, d->y,
+                                                      d->y0, d->yf, d->yhat, d->st, j,
+                                                      d->partials, d->G);
+  } else {
+    if (wr)
+      k_primal<double, true><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->y,
+                                                        d->yf, d->c, d->lx, d->ux, d->x, d->x0,
+                                                        d->xbar, d->xbar_f, d->xhat, d->st, j,
+                                                        d->partials, d->G);
+    else
+      k_primal<double, false><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->y,
+                                                         d->yf, d->c, d->lx, d->ux, d->x, d->x0,
+                                                         d->xbar, d->xbar_f, d->xhat, d->st, j,
+                                                         d->partials, d->G);
+    if (wr)
+      k_dual<double, true><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xbar,
+                                                      d->xbar_f, d->lc, d->uc, d->y, d->y0,
+                                                      nullptr, d->yhat, d->st, j, d->partials,
+                                                      d->G);
+    else
+      k_dual<double, false><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA,
+                                                       d->xbar, d->xbar_f, d->lc, d->uc, d->y,
+                                                       d->y0, nullptr, d->yhat, d->st, j,
+                                                       d->partials, d->G);
+  }
+  d->launches += 2;
+  if (check) {
+    k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat, d->dr,
+                                          d->lc0, d->uc0, d->yhat, d->st, 0, d->partials, d->G);
+    k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat, d->c,
+                                          d->dc, d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st,
+                                          0, d->partials, d->G);
+    k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 0);
+    k_restart<<<d->grid_for(std::max(d->m, d->n)), kBlock, 0, d->s>>>(
+        d->st, d->n, d->m, d->x, d->x0, d->xhat, d->y, d->y0, d->yhat, mixed ? d->yf : nullptr);
+    d->launches += 4;
+  }
+}
+
+void final_eval(DeviceLP *d) {
+  k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat, d->dr,
+                                        d->lc0, d->uc0, d->yhat, d->st, 1, d->partials, d->G);
+  k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat, d->c, d->dc,
+                                        d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st, 1,
+                                        d->partials, d->G);
+  k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 1);
+  d->launches += 3;
+}
+
+void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double *xinit_perm,
+                  const double *yinit_perm) {
+  const int m = d->m, n = d->n;
+  const int gm = d->grid_for(std::max(m, 1)), gn = d->grid_for(std::max(n, 1));
+  const int gwm = d->grid_for((long long)std::max(m, 1) * 32);
+  const int gwn = d->grid_for((long long)std::max(n, 1) * 32);
+  k_fill<<<gm, kBlock, 0, d->s>>>(d->dr, 1.0, m);
+  k_fill<<<gn, kBlock, 0, d->s>>>(d->dc, 1.0, n);
+  d->launches += 2;
+  for (int it = 0; it < o.ruiz_iters; ++it) {
+    k_scale_pass<false, false><<<gwm, kBlock, 0, d->s>>>(m, d->A_rp, d->A_ci, d->A_v0, d->dr,
+                                                         d->dc, d->dr2);
+    k_scale_pass<true, false><<<gwn, kBlock, 0, d->s>>>(n, d->T_rp, d->T_ci, d->T_v0, d->dc,
+                                                        d->dr, d->dc2);
+    std::swap(d->dr, d->dr2);
+    std::swap(d->dc, d->dc2);
+    d->launches += 2;
+  }
+  if (o.pock_chambolle) {
+    k_scale_pass<false, true><<<gwm, kBlock, 0, d->s>>>(m, d->A_rp, d->A_ci, d->A_v0, d->dr,
+                                                        d->dc, d->dr2);
+    k_scale_pass<true, true><<<gwn, kBlock, 0, d->s>>>(n, d->T_rp, d->T_ci, d->T_v0, d->dc,
+                                                       d->dr, d->dc2);
+    std::swap(d->dr, d->dr2);
+    std::swap(d->dc, d->dc2);
+    d->launches += 2;
+  }
+  k_apply_matrix<false><<<gwm, kBlock, 0, d->s>>>(m, d->A_rp, d->A_ci, d->A_v0, d->dr, d->dc,
+                                                  d->A_v, mixed ? d->A_vf : nullptr);
+  k_apply_matrix<true><<<gwn, kBlock, 0, d->s>>>(n, d->T_rp, d->T_ci, d->T_v0, d->dc, d->dr,
+                                                 d->T_v, mixed ? d->T_vf : nullptr);
+  k_apply_cols<<<d->G, kBlock, 0, d->s>>>(n, d->c0, d->lx0, d->ux0, d->dc, d->c, d->lx, d->ux,
+                                          d->partials, d->G);
+  k_apply_rows<<<d->G, kBlock, 0, d->s>>>(m, d->lc0, d->uc0, d->dr, d->lc, d->uc, d->partials,
+                                          d->G);
+  d->launches += 4;
+  bool power = !(o.step_size > 0) && n > 0 && m > 0;
+  if (power) {
+    k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
+    d->launches += 1;
+    for (int it = 0; it < o.power_iters; ++it) {
+      k_spmv_store<<<std::max(1, std::min(d->binsA.ntiles, d->G)), kBlock, 0, d->s>>>(
+          d->A_rp, d->A_ci, d->A_v, d->pv, d->binsA, d->pu);
+      k_spmv_store_sq<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->pu, d->binsT, d->pw,
+                                                 d->partials, d->G);
+      k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->partials, d->G);
+      d->launches += 3;
+    }
+    k_spmv_store_sq<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->pv, d->binsA, d->pu,
+                                               d->partials, d->G);
+    d->launches += 1;
+  }
+  k_init_x<<<gn, kBlock, 0, d->s>>>(n, d->lx, d->ux, d->dc, xinit_perm, d->x, d->x0);
+  k_init_y<<<gm, kBlock, 0, d->s>>>(m, d->dr, yinit_perm, d->y, d->y0, mixed ? d->yf : nullptr);
+  k_setup_final<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, o.step_size, o.primal_weight,
+                                        power ? 1 : 0);
+  d->launches += 3;
+}
+
+}  // namespace
+
+int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *res,
+              DeviceSolution &sol, std::string &err) {
+  auto t_start = std::chrono::steady_clock::now();
+  try {
+    CK(cudaSetDevice(d->device));
+    const bool mixed = o.precision == LP_MIXED;
+    const int m = d->m, n = d->n;
+    const int K = std::max(1, o.check_every);
+    d->launches = 0;
+    // state constants
+    State init{};
+    init.rho = o.rho;
+    init.beta_suff = o.beta_suff;
+    init.beta_nec = o.beta_nec;
+    init.beta_art = o.beta_art;
+    init.theta = o.theta;
+    init.eps_rel = o.eps_rel;
+    init.bnorm = d->bnorm;
+    init.cnorm = d->cnorm;
+    init.off = d->off;
+    init.K = K;
+    init.halpern = o.halpern ? 1 : 0;
+    init.restarts_on = o.restarts ? 1 : 0;
+    init.status = ST_RUNNING;
+    CK(cudaMemcpyAsync(d->st, &init, sizeof(State), cudaMemcpyHostToDevice, d->s));
+    // warm start, permuted to the device order
+    double *xin = nullptr, *yin = nullptr;
+    if (o.x_init || o.y_init) {
+      if (d->hbuf) cudaFreeHost(d->hbuf);
+      CK(cudaHostAlloc(reinterpret_cast<void **>(&d->hbuf), sizeof(double) * (size_t)(n + m + 2),
+                       cudaHostAllocDefault));
+      if (o.x_init) {
+        for (int j = 0; j < n; ++j) d->hbuf[j] = o.x_init[d->cperm[j]];
+        xin = d->ox;
+        CK(cudaMemcpyAsync(xin, d->hbuf, sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+      }
+      if (o.y_init) {
+        for (int i = 0; i < m; ++i) d->hbuf[n + i] = o.y_init[d->rperm[i]];
+        yin = d->oy;
+        CK(cudaMemcpyAsync(yin, d->hbuf + n, sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+      }
+    }
+    cudaEvent_t e0, e1, e2;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventCreate(&e2));
+    CK(cudaEventRecord(e0, d->s));
+    // k_setup_final overwrites the state's running fields; constants stay
+    setup_device(d, o, mixed, xin, yin);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(e1, d->s));
+    // iteration driver
+    const long long max_iter = o.max_iter;
+    long long launched = 0;
+    int pi = mixed ? 1 : 0;
+    bool use_graph = o.use_graph != 0;
+    if (use_graph && (d->graph[pi] == nullptr || d->graph_K[pi] != K)) {
+      if (d->graph[pi]) {
+        cudaGraphExecDestroy(d->graph[pi]);
+        d->graph[pi] = nullptr;
+      }
+      cudaGraph_t g;
+      long long saved = d->launches;
+      CK(cudaStreamBeginCapture(d->s, cudaStreamCaptureModeThreadLocal));
+      for (int j = 0; j < K; ++j) launch_iteration(d, mixed, j, j == 0, false);
+      cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s);
+      CK(cudaStreamEndCapture(d->s, &g));
+      CK(cudaGraphInstantiate(&d->graph[pi], g, 0));
+      CK(cudaGraphDestroy(g));
+      d->graph_K[pi] = K;
+      d->launches = saved;
+    }
+    const long long per_graph = 2LL * K + 4;
+    std::vector<cudaEvent_t> evs;
+    std::vector<cudaEvent_t> pool;
+    auto get_event = [&]() {
+      cudaEvent_t e;
+      if (!pool.empty()) {
+        e = pool.back();
+        pool.pop_back();
+      } else {
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      }
+      return e;
+    };
+    bool done = false;
+    bool timed_out = false;
+    const double tl = o.time_limit_s > 0 ? o.time_limit_s : 1e30;
+    size_t head = 0;
+    while (!done) {
+      // keep up to two chunks in flight
+      while (evs.size() - head < 2 && launched < max_iter) {
+        long long rem = max_iter - launched;
+        if (use_graph && rem > K) {
+          CK(cudaGraphLaunch(d->graph[pi], d->s));
+          d->launches += per_graph;
+          launched += K;
+        } else {
+          long long len = std::min<long long>(rem, K);
+          for (long long j = 0; j < len; ++j) {
+            bool last = (launched + j + 1 == max_iter);
+            launch_iteration(d, mixed, (int)j, j == 0, last && j != 0);
+          }
+          CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+          launched += len;
+        }
+        cudaEvent_t e = get_event();
+        CK(cudaEventRecord(e, d->s));
+        evs.push_back(e);
+      }
+      if (head == evs.size()) break;
+      CK(cudaEventSynchronize(evs[head]));
+      pool.push_back(evs[head]);
+      ++head;
+      volatile int status = d->hst->status;
+      if (status != ST_RUNNING) {
+        done = true;
+        break;
+      }
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      if (el > tl) {
+        timed_out = true;
+        break;
+      }
+    }
+    CK(cudaStreamSynchronize(d->s));
+    for (size_t q = head; q < evs.size(); ++q) pool.push_back(evs[q]);
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
+    int status = d->hst->status;
+    long long iters = d->hst->iters;
+    if (status == ST_RUNNING) {
+      if (timed_out) {
+        status = LP_TIME_LIMIT;
+        iters = std::min(launched, max_iter);
+        State fix = *d->hst;
+        fix.status = LP_TIME_LIMIT;
+        CK(cudaMemcpyAsync(d->st, &fix, sizeof(State), cudaMemcpyHostToDevice, d->s));
+      } else {
+        // max_iter reached: evaluate the last T(z)
+        final_eval(d);
+        status = LP_ITER_LIMIT;
+        iters = max_iter;
+      }
+    } else if (status == LP_ITER_LIMIT) {
+      iters = max_iter;
+    }
+    CK(cudaEventRecord(e2, d->s));
+    // outputs
+    const int gmn = d->grid_for(std::max(std::max(m, n), 1));
+    k_unscale<<<gmn, kBlock, 0, d->s>>>(n, m, d->dc, d->dr, d->xhat, d->yhat, d->x, d->y, d->ox,
+                                        d->oy, d->oxi, d->oyi);
+    d->launches += 1;
+    CK(cudaGetLastError());
+    std::vector<double> hx(n), hy(m), hz(n), hxi(n), hyi(m);
+    if (n) {
+      CK(cudaMemcpyAsync(hx.data(), d->ox, sizeof(double) * n, cudaMemcpyDeviceToHost, d->s));
+      CK(cudaMemcpyAsync(hxi.data(), d->oxi, sizeof(double) * n, cudaMemcpyDeviceToHost, d->s));
+      CK(cudaMemcpyAsync(hz.data(), d->zbuf, sizeof(double) * n, cudaMemcpyDeviceToHost, d->s));
+    }
+    if (m) {
+      CK(cudaMemcpyAsync(hy.data(), d->oy, sizeof(double) * m, cudaMemcpyDeviceToHost, d->s));
+      CK(cudaMemcpyAsync(hyi.data(), d->oyi, sizeof(double) * m, cudaMemcpyDeviceToHost, d->s));
+    }
+    CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+    CK(cudaStreamSynchronize(d->s));
+    float ms_setup = 0, ms_solve = 0;
+    CK(cudaEventElapsedTime(&ms_setup, e0, e1));
+    CK(cudaEventElapsedTime(&ms_solve, e1, e2));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    sol.x.assign(n, 0.0);
+    sol.z.assign(n, 0.0);
+    sol.xi.assign(n, 0.0);
+    sol.y.assign(m, 0.0);
+    sol.yi.assign(m, 0.0);
+    for (int j = 0; j < n; ++j) {
+      int o2 = d->cperm[j];
+      sol.x[o2] = hx[j];
+      sol.xi[o2] = hxi[j];
+      sol.z[o2] = hz[j];
+    }
+    for (int i = 0; i < m; ++i) {
+      int o2 = d->rperm[i];
+      sol.y[o2] = hy[i];
+      sol.yi[o2] = hyi[i];
+    }
+    sol.valid = true;
+    const State &S = *d->hst;
+    if (res) {
+      res->termination = status;
+      res->restarts = S.restarts;
+      res->iterations = iters;
+      res->rel_kkt = S.rel_kkt;
+      res->rel_p = S.rel_p;
+      res->rel_d = S.rel_d;
+      res->rel_gap = S.rel_gap;
+      res->r_p = S.r_p;
+      res->r_d = S.r_d;
+      res->gap = S.gap;
+      res->primal_obj = S.pobj;
+      res->dual_obj = S.dobj;
+      res->eta = S.eta;
+      res->omega = S.omega;
+      res->t_setup_s = ms_setup * 1e-3;
+      res->t_solve_s = ms_solve * 1e-3;
+      res->t_total_s =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      res->kernel_launches = d->launches;
+    }
+  } catch (const DeviceOOM &e) {
+    err = e.what();
+    return LP_ERR_OOM;
+  } catch (const std::exception &e) {
+    err = e.what();
+    return LP_ERR_CUDA;
+  }
+  return LP_OK;
+}
+
+}  // namespace gb300lp

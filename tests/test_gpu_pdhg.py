@@ -1,0 +1,169 @@
+"""GPU PDHG (through the C ABI) against the CPU oracle.
+
+Tolerances: iterates 1e-10 relative to max(1, ||oracle||_inf) (FP64, step and
+weight passed explicitly); final objectives 1e-6 relative; both sides reach
+rel-KKT <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import presolve as PS
+from lp_helpers import SimpleLP
+
+pytestmark = pytest.mark.gpu
+
+INF = np.inf
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2604_23951_gb300 as p
+
+    p.load()
+    return p
+
+
+@pytest.fixture(scope="module")
+def dev(pkg):
+    return pkg.TorchDevice(0)
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b))) if b.size else 0.0
+
+
+def rel_obj(p, q):
+    return abs(p - q) / (1.0 + abs(q))
+
+
+@pytest.mark.parametrize("iters", [1, 2, 5, 17, 50])
+def test_first_iterates_match_oracle_c1(pkg, dev, iters):
+    lp = lpgen.c1_small()
+    eta, om = 0.05, 1.3
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta, omega0=om)
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(max_iter=iters, eps_rel=0.0, step_size=eta, primal_weight=om)
+    assert r.termination == pkg.LP_ITER_LIMIT and r.iterations == iters
+    xi, yi = prob.iterate()
+    assert relerr(xi, ref.x_iter) <= 1e-10
+    assert relerr(yi, ref.y_iter) <= 1e-10
+    # the returned point is the last T(z) evaluated, as in the oracle
+    x, y, _ = prob.solution()
+    assert relerr(x, ref.x) <= 1e-10 and relerr(y, ref.y) <= 1e-10
+    assert abs(r.rel_kkt - ref.kkt["rel_kkt"]) <= 1e-9 * (1 + ref.kkt["rel_kkt"])
+
+
+def test_iterates_powerlaw_all_row_classes(pkg, dev):
+    # row lengths from 1 to thousands: every lanes-per-row class and the
+    # block-per-row class are exercised, with a ragged last tile in each
+    lp = lpgen.c3_powerlaw(seed=7, m=3000, n=8000, row_nnz_target=60000, n_dense=20,
+                           dense_len=2500, kmax=6000)
+    eta, om = 0.02, 0.7
+    for items in (1, 4):
+        ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=40, eps_rel=0.0), eta=eta, omega0=om)
+        prob = pkg.Problem(lp, dev)
+        prob.solve(max_iter=40, eps_rel=0.0, step_size=eta, primal_weight=om, tile_items=items)
+        xi, yi = prob.iterate()
+        assert relerr(xi, ref.x_iter) <= 1e-10
+        assert relerr(yi, ref.y_iter) <= 1e-10
+        prob.close()
+
+
+def test_step_size_and_weight_match_oracle(pkg, dev):
+    lp = lpgen.general_structure(500, 1200, 3, nnz_target=7000, one_sided=0.2)
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=1, eps_rel=0.0))
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(max_iter=1, eps_rel=0.0)
+    assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
+    assert abs(r.omega - ref.omega0) <= 1e-12 * ref.omega0
+
+
+def test_c1_solves_to_tolerance(pkg, dev):
+    lp = lpgen.c1_small()
+    ref = oracle.pdhg_solve(lp)
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve()
+    assert r.termination == pkg.LP_OPTIMAL
+    assert r.rel_kkt <= 1e-6
+    x, y, z = prob.solution()
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-6
+    assert rel_obj(r.primal_obj, ref.kkt["p"]) <= 1e-6
+    assert rel_obj(r.primal_obj, lp.p_star) <= 1e-6
+    # the restart schedule agrees until the trajectories split on a threshold
+    assert r.restarts >= 1
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_graph_and_direct_launches_agree_bitwise(pkg, dev, graph):
+    lp = lpgen.general_structure(400, 1000, 8, nnz_target=6000)
+    prob = pkg.Problem(lp, dev)
+    r1 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=1)
+    x1, y1 = prob.iterate()
+    r2 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=graph)
+    x2, y2 = prob.iterate()
+    assert r1.restarts == r2.restarts
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(y1, y2)
+
+
+def test_presolve_solve_postsolve_is_kkt(pkg, dev):
+    lp = lpgen.general_structure(1500, 3800, 12, nnz_target=30000, one_sided=0.1)
+    prob = pkg.Problem(lp, dev)
+    info = prob.presolve()
+    assert info.m < lp.m
+    r = prob.solve()
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    x, y, z = prob.postsolve()
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-5
+    assert rel_obj(k["p"], lp.p_star) <= 1e-6
+    # the oracle on the same reduced problem reaches the same objective
+    ref = oracle.pdhg_solve(PS.presolve(lp).reduced)
+    assert rel_obj(r.primal_obj, ref.kkt["p"]) <= 1e-6
+
+
+def test_mixed_precision_reaches_tolerance(pkg, dev):
+    lp = lpgen.c1_small()
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(precision=pkg.LP_MIXED)
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    assert rel_obj(r.primal_obj, lp.p_star) <= 1e-5
+
+
+def test_deterministic_reruns(pkg, dev):
+    lp = lpgen.general_structure(600, 1500, 4, nnz_target=9000)
+    prob = pkg.Problem(lp, dev)
+    prob.solve(max_iter=500, eps_rel=0.0)
+    a = prob.iterate()
+    prob.solve(max_iter=500, eps_rel=0.0)
+    b = prob.iterate()
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_degenerate_shapes(pkg, dev):
+    # no rows: each column goes to the bound its cost points to
+    lp = SimpleLP(np.zeros((0, 3)), [1.0, -2.0, 0.0], [], [], [-1.0, 0.0, -3.0],
+                  [4.0, 5.0, 3.0])
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(eps_rel=1e-9)
+    assert r.termination == pkg.LP_OPTIMAL
+    x, _, _ = prob.solution()
+    assert np.allclose(x, [-1.0, 5.0, 0.0], atol=1e-8)
+    # an empty row and an empty column kept (no presolve)
+    lp = SimpleLP([[1.0, 0.0, 1.0], [0.0, 0.0, 0.0]], [1.0, 0.0, 2.0], [1.0, -1.0],
+                  [1.0, 1.0], [0.0, 0.0, 0.0], [INF, 2.0, INF])
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(eps_rel=1e-9)
+    assert r.termination == pkg.LP_OPTIMAL
+    assert abs(r.primal_obj - 1.0) <= 1e-7
+
+
+def test_warm_start_from_solution_converges_at_first_check(pkg, dev):
+    lp = lpgen.c1_small()
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(x_init=lp.x_star, y_init=lp.y_star)
+    assert r.termination == pkg.LP_OPTIMAL and r.iterations == 1

@@ -1,0 +1,135 @@
+"""Host C presolve/postsolve (through the C ABI) against the oracle (CPU only).
+
+Presolve is integer and index work plus deterministic IEEE arithmetic, so the
+reduced problems must agree exactly: same sizes, same kept rows and columns,
+same sparsity pattern, and bit-identical values.  Postsolve outputs agree to
+1e-12 relative (same formulas, summation order may differ).
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import presolve as PS
+from lp_helpers import SimpleLP, highs_solve
+
+pkg = pytest.importorskip("paper_2604_23951_gb300")
+
+INF = np.inf
+
+
+def _lib_or_skip():
+    try:
+        pkg.load()
+    except RuntimeError as e:  # library not built in this checkout
+        pytest.skip(str(e))
+
+
+def _cases():
+    return [
+        ("general_small", lambda: lpgen.general_structure(600, 1500, 31, nnz_target=9000,
+                                                          one_sided=0.2)),
+        ("general_b", lambda: lpgen.general_structure(800, 2000, 77, nnz_target=16000)),
+        ("c2_scaled", lambda: lpgen.c2_presolvable(scale=0.01)),
+        ("c1", lambda: lpgen.c1_small()),
+        ("tiny_box", lambda: lpgen.tiny_box(5, 6, 9)),
+        ("doubleton_chain", lambda: SimpleLP(
+            [[1.0, 1.0, 0.0, 0.0], [0.0, 1.0, -2.0, 0.0], [0.0, 0.0, 1.0, 3.0],
+             [1.0, 0.0, 1.0, 1.0]],
+            [1.0, 2.0, -1.0, 0.5], [1.0, 0.0, 2.0, -INF], [1.0, 0.0, 2.0, 6.0],
+            [0.0, 0.0, -1.0, 0.0], [INF, 5.0, 4.0, INF])),
+    ]
+
+
+@pytest.mark.parametrize("name,make", _cases())
+def test_reduced_problem_identical(name, make):
+    _lib_or_skip()
+    lp = make()
+    ref = PS.presolve(lp)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve()
+    assert info.status == ref.status
+    red = prob.data()
+    r = ref.reduced
+    assert (red.m, red.n) == (r.m, r.n), name
+    assert info.rounds == ref.rounds
+    assert list(info.counts) == [ref.counts[k] for k in (
+        "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
+        "dropped_side", "doubleton", "free_col_singleton")]
+    np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
+    np.testing.assert_array_equal(red.col_idx, r.col_idx)
+    np.testing.assert_array_equal(red.val, r.val)
+    np.testing.assert_array_equal(red.c, r.c)
+    np.testing.assert_array_equal(red.row_lo, r.row_lo)
+    np.testing.assert_array_equal(red.row_hi, r.row_hi)
+    np.testing.assert_array_equal(red.col_lo, r.col_lo)
+    np.testing.assert_array_equal(red.col_hi, r.col_hi)
+    assert red.obj_offset == r.obj_offset
+
+
+@pytest.mark.parametrize("name,make", _cases()[:4])
+def test_postsolve_matches_oracle_and_is_kkt(name, make):
+    _lib_or_skip()
+    lp = make()
+    ref = PS.presolve(lp)
+    prob = pkg.Problem(lp, None)
+    prob.presolve()
+    red = ref.reduced
+    if red.m == 0:
+        pytest.skip("nothing left to solve")
+    _, xr, yr = highs_solve(red)
+    xo, yo, zo = PS.postsolve(ref, xr, yr)
+    xc, yc, zc = prob.postsolve_from(xr, yr)
+    scale = 1 + max(np.max(np.abs(xo)), np.max(np.abs(yo)), np.max(np.abs(zo)))
+    assert np.max(np.abs(xc - xo)) <= 1e-12 * scale
+    assert np.max(np.abs(yc - yo)) <= 1e-12 * scale
+    assert np.max(np.abs(zc - zo)) <= 1e-12 * scale
+    k = oracle.rel_kkt(lp, xc, yc)
+    assert k["rel_kkt"] <= 1e-8
+    if np.isfinite(lp.p_star if hasattr(lp, "p_star") else np.nan):
+        assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+
+
+def test_host_rel_kkt_matches_oracle():
+    _lib_or_skip()
+    lp = lpgen.general_structure(300, 700, 5, nnz_target=4000, one_sided=0.3)
+    prob = pkg.Problem(lp, None)
+    rng = np.random.default_rng(0)
+    x = lp.x_star + 0.01 * rng.standard_normal(lp.n)
+    y = lp.y_star + 0.01 * rng.standard_normal(lp.m)
+    a = prob.rel_kkt(x, y)
+    b = oracle.rel_kkt(lp, x, y)
+    for k in ("rel_kkt", "rel_p", "rel_d", "rel_gap", "p", "d"):
+        assert abs(a[k] - b[k]) <= 1e-12 * (1 + abs(b[k])), k
+
+
+@pytest.mark.parametrize("bad", ["nan_val", "bad_ptr", "dup_col", "lo_gt_hi", "col_range"])
+def test_create_rejects_malformed_input(bad):
+    _lib_or_skip()
+    lp = lpgen.tiny_box(3, 4, 1)
+    if bad == "nan_val":
+        lp.val = lp.val.copy()
+        lp.val[0] = np.nan
+    elif bad == "bad_ptr":
+        lp.row_ptr = lp.row_ptr.copy()
+        lp.row_ptr[1], lp.row_ptr[2] = lp.row_ptr[2], lp.row_ptr[1]
+    elif bad == "dup_col":
+        lp.col_idx = lp.col_idx.copy()
+        lp.col_idx[1] = lp.col_idx[0]
+    elif bad == "lo_gt_hi":
+        lp.col_lo = lp.col_lo.copy()
+        lp.col_lo[0] = lp.col_hi[0] + 1
+    elif bad == "col_range":
+        lp.col_idx = lp.col_idx.copy()
+        lp.col_idx[-1] = lp.n + 3
+    with pytest.raises(pkg.LPError) as ei:
+        pkg.Problem(lp, None)
+    assert ei.value.code == -1
+
+
+def test_solve_without_device_is_state_error():
+    _lib_or_skip()
+    prob = pkg.Problem(lpgen.tiny_box(3, 4, 1), None)
+    with pytest.raises(pkg.LPError) as ei:
+        prob.solve()
+    assert ei.value.code == -4
