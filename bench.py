@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative KKT error 1e-6 on a planted LP, on GB300.
+
+Default workload: the presolvable planted LP with m = 200k rows, n = 500k
+columns and ~5M nonzeros (seeded, synthetic).  One step = one full device
+solve of the presolved LP (GPU scaling, power-iteration step size,
+restarted reflected Halpern PDHG to rel-KKT <= 1e-6) with the reduced LP
+resident in HBM.  `e2e` times the whole C-ABI path from host buffers
+(lp_create, lp_presolve, lp_solve with its H2D upload, lp_postsolve with the
+D2H of the solution).
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
+replica of the workload (no collective on the data path; replicas only).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c1|c3]
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel-KKT 1e-6 (s); SpMV HBM GB/s vs peak; batched LPs/s with p50/p99"
+
+# Iterations the device path needs to reach rel-KKT 1e-6 on each seeded
+# workload (FP64), measured with this repository's GPU solver on GB300.  The
+# oracle runs the same iteration, so the reference arm extrapolates its timed
+# sample with this count (at the 200 x 400 workload both take 1217).
+ITERS_TO_TOL = {"c2": 13313, "c1": 1217, "c3": 20000}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c2", choices=["c2", "c1", "c3"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-iters", type=int, default=20)
+    p.add_argument("--profile-iters", type=int, default=0,
+                   help="ncu capture command: one solve capped at this many iterations, "
+                        "no timing and no JSON line")
+    return p.parse_args()
+
+
+def make_workload(name):
+    import lpgen
+
+    if name == "c1":
+        return lpgen.c1_small(), "planted LP 200 x 400, ~2,000 nnz, equality rows, x >= 0"
+    if name == "c3":
+        return lpgen.c3_powerlaw(), ("planted LP 2M x 5M, ~50M nnz, power-law rows + 5,000 "
+                                     "dense columns, box bounds")
+    return lpgen.c2_presolvable(), ("presolvable planted LP 200k x 500k, ~5M nnz "
+                                    "(lognormal rows, 60% eq / 40% ranged, singleton, "
+                                    "doubleton, fixed, mixed bounds)")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [q.strip() for q in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("solver.cu", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_23951_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str, precision: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[f"{kernel}/{workload}/{precision}"]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def oracle_sample(lp, n_iter_gpu, cpu_iters, workload):
+    """The oracle as it stands on this host: presolve, then setup + a bounded
+    number of PDHG iterations; extrapolated to n_iter_gpu iterations."""
+    import oracle
+    from oracle import presolve as PS
+
+    t0 = time.perf_counter()
+    pres = PS.presolve(lp) if workload == "c2" else None
+    t_pre = time.perf_counter() - t0
+    red = pres.reduced if pres is not None else lp
+    t0 = time.perf_counter()
+    oracle.pdhg_solve(red, oracle.Opts(max_iter=1, eps_rel=0.0))
+    t_1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pdhg_solve(red, oracle.Opts(max_iter=1 + cpu_iters, eps_rel=0.0))
+    t_s = time.perf_counter() - t0
+    per_iter = max(t_s - t_1, 0.0) / cpu_iters
+    est = t_pre + t_1 + per_iter * max(n_iter_gpu - 1, 0)
+    sample = (f"oracle presolve ({t_pre:.2f} s) + scaling/step-size setup and 1 iteration "
+              f"({t_1:.2f} s) + {cpu_iters} timed PDHG iterations ({per_iter * 1e3:.1f} ms each) "
+              f"on the presolved LP, extrapolated to {n_iter_gpu} iterations")
+    return est, sample, t_pre + t_s
+
+
+# ---------------------------------------------------------------------------
+# arms
+
+
+def run_reference(args):
+    import numpy as np  # noqa: F401
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    lp, desc = make_workload(args.workload)
+    n_iter = ITERS_TO_TOL[args.workload]
+    import oracle
+    from oracle import presolve as PS
+
+    t0 = time.perf_counter()
+    pres = PS.presolve(lp) if args.workload == "c2" else None
+    t_pre = time.perf_counter() - t0
+    red = pres.reduced if pres is not None else lp
+    vals = []
+    t_first = None
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.pdhg_solve(red, oracle.Opts(max_iter=1, eps_rel=0.0))
+        t_1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.pdhg_solve(red, oracle.Opts(max_iter=1 + args.cpu_iters, eps_rel=0.0))
+        t_s = time.perf_counter() - t0
+        per_iter = max(t_s - t_1, 0.0) / args.cpu_iters
+        est = t_pre + t_1 + per_iter * (n_iter - 1)
+        if step >= args.warmup:
+            vals.append(est)
+        t_first = t_first or est
+    value = statistics.mean(vals)
+    sample = (f"each step: oracle scaling/step-size setup + 1 iteration, then {args.cpu_iters} "
+              f"PDHG iterations on the presolved LP (oracle presolve {t_pre:.2f} s measured once), "
+              f"extrapolated to {n_iter} iterations")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2604_23951_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pkg.load()
+    lp, desc = make_workload(args.workload)
+    dev = pkg.TorchDevice(local)
+    prec = pkg.LP_MIXED if args.precision == "mixed" else pkg.LP_FP64
+    prob = pkg.Problem(lp, dev)
+    info = prob.presolve() if args.workload == "c2" else None
+    prob.upload()
+    m, n, nnz = prob.dims()
+    if args.profile_iters > 0:
+        r = prob.solve(precision=prec, max_iter=args.profile_iters, eps_rel=0.0)
+        print(f"profile case: {args.workload} {args.precision} m={m} n={n} nnz={nnz} "
+              f"iterations={r.iterations} launches={r.kernel_launches}", flush=True)
+        return 0
+    for _ in range(args.warmup):
+        r = prob.solve(precision=prec)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = dev.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(prob.solve(precision=prec))
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], device=f"cuda:{local}", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    value = elapsed / args.steps
+    r = results[-1]
+    launches = int(sum(x.kernel_launches for x in results))
+    # per-kernel timing (CUDA events, cold L2) for the roofline
+    prof = prob.profile_kernels(reps=10)
+    peak, peak_kind = peaks()
+    cand = {"primal": (prof["primal_ms"], prof["primal_bytes"]),
+            "dual": (prof["dual_ms"], prof["dual_bytes"])}
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, byt = cand[dom]
+    achieved = byt / (ms * 1e-3) / 1e9
+    kname = {"primal": "k_primal", "dual": "k_dual"}[dom]
+    traffic = ncu_traffic(kname, args.workload, args.precision)
+    # end to end through the C ABI from host buffers
+    barrier()
+    e2e_times = []
+    h2d = d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = pkg.Problem(lp, dev)
+        if args.workload == "c2":
+            p2.presolve()
+        r2 = p2.solve(precision=prec)
+        x, y, z = p2.postsolve()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        m2, n2, nnz2 = p2.dims()
+        h2d = 2 * nnz2 * 12 + 4 * (m2 + 1) + 4 * (n2 + 1) + 8 * (3 * n2 + 2 * m2)
+        d2h = 8 * (3 * n2 + 2 * m2)
+        p2.close()
+    e2e = statistics.mean(e2e_times)
+    kkt_orig = None
+    try:
+        import oracle
+
+        kk = oracle.rel_kkt(lp, x, y)
+        kkt_orig = kk["rel_kkt"]
+        obj_err = abs(kk["p"] - lp.p_star) / (1 + abs(lp.p_star))
+    except Exception:
+        obj_err = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, sample, spent = oracle_sample(lp, int(r.iterations), args.cpu_iters, args.workload)
+        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+               "cpu_seconds_spent": round(spent, 2)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == pkg.LP_FP64 else "f32 SpMV / f64 iterates",
+            "data": "synthetic",
+            "config": {
+                "workload": desc, "m": int(lp.m), "n": int(lp.n), "nnz": int(lp.nnz),
+                "reduced": {"m": m, "n": n, "nnz": nnz} if info is not None else None,
+                "presolve_s": round(info.seconds, 4) if info is not None else None,
+                "precision": args.precision, "parallelism": f"replicas{world}",
+                "l2": "inputs larger than L2: each iteration streams > 129 MB",
+            },
+            "iterations": int(r.iterations), "restarts": int(r.restarts),
+            "rel_kkt": r.rel_kkt, "rel_kkt_original_after_postsolve": kkt_orig,
+            "objective_rel_err_vs_planted": obj_err,
+            "us_per_iteration": 1e6 * r.t_solve_s / max(1, r.iterations),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                         "peak_kind": peak_kind, "kernel_ms": ms, "algorithmic_bytes": byt,
+                         "other_kernels": {k: {"ms": v[0], "GB/s": v[1] / (v[0] * 1e-3) / 1e9}
+                                           for k, v in cand.items()}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -208,6 +208,16 @@ int lp_get_data(const lp_problem *lp, int64_t *row_ptr, int32_t *col_idx,
  * rel_d, rel_gap, primal_obj, dual_obj (6 doubles). */
 int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, double *out);
 
+/* Measurement hook (no counterpart in the paper): time the PDHG iteration
+ * kernels of the last lp_solve one launch at a time with CUDA events on the
+ * problem's stream, each launch after a 256 MiB write that evicts L2.
+ * reps >= 1.  out (8 doubles): mean ms of the primal kernel (A^T y + primal
+ * epilogue), mean ms of the dual kernel (A xbar + dual epilogue), their
+ * algorithmic bytes per launch, then the same four for the two KKT kernels.
+ * Fails LP_ERR_STATE without a prior solve.  Changes the internal iterate
+ * (not the stored solution). */
+int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out);
+
 void lp_destroy(lp_problem *lp);
 
 /* ---- batched solving and continuous-batching server ------------------ */

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("lp_get_dims", C.c_int, [_P, _I32, _I32, _I64, _I32, _I32]),
     ("lp_get_data", C.c_int, [_P, _I64, _I32, _D, _D, _D, _D, _D, _D, _D]),
     ("lp_host_rel_kkt", C.c_int, [_P, _D, _D, _D]),
+    ("lp_profile_kernels", C.c_int, [_P, C.c_int32, _D]),
     ("lp_destroy", None, [_P]),
     ("lp_server_create", C.c_int, [C.c_size_t, C.POINTER(lp_device_ctx),
                                    C.POINTER(lp_solve_opts), C.c_int32, _PP]),
@@ -289,6 +290,13 @@ class Problem:
         ns.m, ns.n, ns.row_ptr, ns.col_idx, ns.val, ns.c = m, n, rp, ci, va, c
         ns.obj_offset, ns.row_lo, ns.row_hi, ns.col_lo, ns.col_hi = off.value, lo, hi, lx, ux
         return ns
+
+    def profile_kernels(self, reps: int = 20):
+        out = np.zeros(8)
+        check(self.lib.lp_profile_kernels(self.h, int(reps), dptr(out)))
+        keys = ("primal_ms", "dual_ms", "primal_bytes", "dual_bytes", "kkt_rows_ms",
+                "kkt_cols_ms", "kkt_rows_bytes", "kkt_cols_bytes")
+        return dict(zip(keys, out))
 
     def rel_kkt(self, x, y):
         out = np.zeros(6)

@@ -350,6 +350,17 @@ int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, doub
   API_GUARD_END
 }
 
+int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out) {
+  API_GUARD_BEGIN
+  if (!lp || !out || reps < 1) return fail(LP_ERR_INVALID, "invalid argument");
+  if (!lp->dlp) return fail(LP_ERR_STATE, "profile needs a prior solve");
+  std::string err;
+  int rc = dev_profile(lp->dlp, reps, out, err);
+  if (rc != LP_OK) return fail(rc, err);
+  return LP_OK;
+  API_GUARD_END
+}
+
 void lp_destroy(lp_problem *lp) {
   if (!lp) return;
   try {

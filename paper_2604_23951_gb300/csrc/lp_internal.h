@@ -71,6 +71,7 @@ bool dev_uploaded(const DeviceLP *d);
 int dev_solve(DeviceLP *d, const HostLP &lp, const lp_solve_opts &opts, lp_result *res,
               DeviceSolution &sol, std::string &err);
 void dev_destroy(DeviceLP *d);
+int dev_profile(DeviceLP *d, int reps, double *out, std::string &err);
 
 // ---- shared device-memory helpers (solver.cu) ----------------------------
 struct DevAlloc {

@@ -626,6 +626,7 @@ struct DeviceLP {
   double *c0 = nullptr, *lx0 = nullptr, *ux0 = nullptr, *lc0 = nullptr, *uc0 = nullptr;
   double *c = nullptr, *lx = nullptr, *ux = nullptr, *lc = nullptr, *uc = nullptr;
   double *dr = nullptr, *dc = nullptr, *dr2 = nullptr, *dc2 = nullptr;
+  double *dr_main = nullptr, *dc_main = nullptr;  // where dr / dc live after scaling
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
   double *pv = nullptr, *pw = nullptr, *pu = nullptr;
@@ -640,6 +641,9 @@ struct DeviceLP {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_K[2] = {0, 0};
   long long launches = 0;
+  int last_precision = -1;
+  void *flush = nullptr;
+  size_t flush_bytes = 0;
 
   void *dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -856,6 +860,8 @@ int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
     double **rows_[] = {&d->lc0, &d->uc0, &d->lc, &d->uc, &d->dr, &d->dr2, &d->y, &d->y0,
                         &d->yhat, &d->pu, &d->oy, &d->oyi};
     for (double **p : rows_) *p = d->dalloc_n<double>(m);
+    d->dr_main = d->dr;
+    d->dc_main = d->dc;
     d->xbar_f = d->dalloc_n<float>(n);
     d->yf = d->dalloc_n<float>(m);
     int tiles = std::max(d->binsA.ntiles, d->binsT.ntiles);
@@ -988,6 +994,19 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
     std::swap(d->dc, d->dc2);
     d->launches += 2;
   }
+  // the ping-pong above may leave the result in the scratch buffers; the
+  // captured iteration graph reads dr / dc from fixed addresses, so move the
+  // final scales back to the canonical buffers
+  if (d->dr != d->dr_main) {
+    CK(cudaMemcpyAsync(d->dr_main, d->dr, sizeof(double) * std::max(m, 1),
+                       cudaMemcpyDeviceToDevice, d->s));
+    std::swap(d->dr, d->dr2);
+  }
+  if (d->dc != d->dc_main) {
+    CK(cudaMemcpyAsync(d->dc_main, d->dc, sizeof(double) * std::max(n, 1),
+                       cudaMemcpyDeviceToDevice, d->s));
+    std::swap(d->dc, d->dc2);
+  }
   k_apply_matrix<false><<<gwm, kBlock, 0, d->s>>>(m, d->A_rp, d->A_ci, d->A_v0, d->dr, d->dc,
                                                   d->A_v, mixed ? d->A_vf : nullptr);
   k_apply_matrix<true><<<gwn, kBlock, 0, d->s>>>(n, d->T_rp, d->T_ci, d->T_v0, d->dc, d->dr,
@@ -1031,6 +1050,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     const int m = d->m, n = d->n;
     const int K = std::max(1, o.check_every);
     d->launches = 0;
+    d->last_precision = o.precision;
     // state constants
     State init{};
     init.rho = o.rho;
@@ -1236,6 +1256,107 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
   } catch (const DeviceOOM &e) {
     err = e.what();
     return LP_ERR_OOM;
+  } catch (const std::exception &e) {
+    err = e.what();
+    return LP_ERR_CUDA;
+  }
+  return LP_OK;
+}
+
+
+// Time the iteration kernels one launch at a time with CUDA events on the
+// library's stream, each launch preceded by a write of a 256 MiB buffer so it
+// starts with a cold L2.  Needs a prior dev_solve (scaled matrices present);
+// perturbs the internal iterate (not the returned solution).
+// out: [K1 ms, K2 ms, K1 bytes, K2 bytes, K3a ms, K3b ms, K3a bytes, K3b bytes]
+int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
+  try {
+    CK(cudaSetDevice(d->device));
+    if (d->last_precision < 0) {
+      err = "profile needs a prior solve";
+      return LP_ERR_STATE;
+    }
+    const bool mixed = d->last_precision == LP_MIXED;
+    const int m = d->m, n = d->n;
+    const double nnz = (double)d->nnz;
+    if (!d->flush) {
+      d->flush_bytes = size_t(256) << 20;
+      d->flush = d->dalloc(d->flush_bytes);
+    }
+    State saved;
+    CK(cudaMemcpyAsync(&saved, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+    CK(cudaStreamSynchronize(d->s));
+    State run = saved;
+    run.status = ST_RUNNING;
+    CK(cudaMemcpyAsync(d->st, &run, sizeof(State), cudaMemcpyHostToDevice, d->s));
+    CK(cudaStreamSynchronize(d->s));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    double tot[4] = {0, 0, 0, 0};
+    const int gA = std::max(1, std::min(d->binsA.ntiles, d->G));
+    const int gT = std::max(1, std::min(d->binsT.ntiles, d->G));
+    for (int r = 0; r < reps; ++r) {
+      for (int which = 0; which < 4; ++which) {
+        CK(cudaMemsetAsync(d->flush, r & 0xff, d->flush_bytes, d->s));
+        CK(cudaEventRecord(a, d->s));
+        if (which == 0) {
+          if (mixed)
+            k_primal<float, false><<<gT, kBlock, 0, d->s>>>(
+                d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y, d->yf, d->c, d->lx, d->ux, d->x,
+                d->x0, d->xbar, d->xbar_f, d->xhat, d->st, 1, d->partials, d->G);
+          else
+            k_primal<double, false><<<gT, kBlock, 0, d->s>>>(
+                d->T_rp, d->T_ci, d->T_v, d->binsT, d->y, d->yf, d->c, d->lx, d->ux, d->x,
+                d->x0, d->xbar, d->xbar_f, d->xhat, d->st, 1, d->partials, d->G);
+        } else if (which == 1) {
+          if (mixed)
+            k_dual<float, false><<<gA, kBlock, 0, d->s>>>(
+                d->A_rp, d->A_ci, d->A_vf, d->binsA, d->xbar, d->xbar_f, d->lc, d->uc, d->y,
+                d->y0, d->yf, d->yhat, d->st, 1, d->partials, d->G);
+          else
+            k_dual<double, false><<<gA, kBlock, 0, d->s>>>(
+                d->A_rp, d->A_ci, d->A_v, d->binsA, d->xbar, d->xbar_f, d->lc, d->uc, d->y,
+                d->y0, nullptr, d->yhat, d->st, 1, d->partials, d->G);
+        } else if (which == 2) {
+          k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat,
+                                                d->dr, d->lc0, d->uc0, d->yhat, d->st, 1,
+                                                d->partials, d->G);
+        } else {
+          k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat,
+                                                d->c, d->dc, d->c0, d->lx0, d->ux0, d->xhat,
+                                                d->zbuf, d->st, 1, d->partials, d->G);
+        }
+        CK(cudaEventRecord(b, d->s));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        tot[which] += ms;
+      }
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(d->st, &saved, sizeof(State), cudaMemcpyHostToDevice, d->s));
+    CK(cudaStreamSynchronize(d->s));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    // algorithmic bytes: matrix values + column indices + row offsets, each
+    // gathered vector counted once, every epilogue vector read / written once
+    const double sv = mixed ? 4.0 : 8.0;
+    const double sg = mixed ? 4.0 : 8.0;  // gathered vector element
+    const double k1 = nnz * (sv + 4.0) + 4.0 * (n + 1) + sg * m + 8.0 * 5 * n + 8.0 * n +
+                      (mixed ? 4.0 : 8.0) * n;
+    const double k2 = nnz * (sv + 4.0) + 4.0 * (m + 1) + sg * n + 8.0 * 4 * m + 8.0 * m +
+                      (mixed ? 4.0 * m : 0.0);
+    const double k3a = nnz * 12.0 + 4.0 * (m + 1) + 8.0 * n + 8.0 * 4 * m;
+    const double k3b = nnz * 12.0 + 4.0 * (n + 1) + 8.0 * m + 8.0 * 6 * n + 8.0 * n;
+    out[0] = tot[0] / reps;
+    out[1] = tot[1] / reps;
+    out[2] = k1;
+    out[3] = k2;
+    out[4] = tot[2] / reps;
+    out[5] = tot[3] / reps;
+    out[6] = k3a;
+    out[7] = k3b;
   } catch (const std::exception &e) {
     err = e.what();
     return LP_ERR_CUDA;

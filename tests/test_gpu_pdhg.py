@@ -167,3 +167,21 @@ def test_warm_start_from_solution_converges_at_first_check(pkg, dev):
     prob = pkg.Problem(lp, dev)
     r = prob.solve(x_init=lp.x_star, y_init=lp.y_star)
     assert r.termination == pkg.LP_OPTIMAL and r.iterations == 1
+
+
+def test_resolve_after_other_options_matches_fresh_solve(pkg, dev):
+    # a CUDA graph captured during an earlier solve must see the current
+    # scaling: a re-solve behaves exactly like a solve on a fresh problem
+    lp = lpgen.c1_small()
+    fresh = pkg.Problem(lp, dev)
+    r0 = fresh.solve()
+    x0, y0, _ = fresh.solution()
+    prob = pkg.Problem(lp, dev)
+    prob.solve(max_iter=50, eps_rel=0.0, step_size=0.05, primal_weight=1.3)
+    prob.solve(max_iter=700, ruiz_iters=3, pock_chambolle=0)
+    r = prob.solve()
+    assert r.termination == pkg.LP_OPTIMAL
+    assert r.iterations == r0.iterations and r.restarts == r0.restarts
+    x, y, _ = prob.solution()
+    np.testing.assert_array_equal(x, x0)
+    np.testing.assert_array_equal(y, y0)
