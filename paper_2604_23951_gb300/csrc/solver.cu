@@ -1,8 +1,8 @@
 // Single-LP GPU path: restarted reflected Halpern PDHG for eq. (1).
 //
 // Data layout in HBM (built once per problem by dev_upload):
-//   * rows of A and rows of A^T (= columns of A) are each sorted by a length
-//     class (stable), so every class is a contiguous index range; the LP is
+//   * rows of A and rows of A^T (= columns of A) are each sorted by length
+//     (longest first) and cut into tiles (see spmv_tile.cuh); the LP is
 //     renumbered with those permutations, so the epilogues of the SpMV
 //     kernels read and write their vectors contiguously;
 //   * A (m rows) and its stored transpose A^T (n rows) in CSR with int32
@@ -25,6 +25,11 @@
 //   K5  on restart: x = x0 = xh, y = y0 = yh
 // A CUDA graph holds one check iteration plus K - 1 plain iterations and the
 // D2H copy of the state word; the host replays it until the state says done.
+//
+// FP64 instruction budget (GB300 runs FP64 at about 2 lanes per clock per
+// SM): the SpMV costs one DFMA per nonzero at full lanes; the epilogues use
+// precomputed Halpern coefficients a = lam (1 + rho), b = -lam rho,
+// g = 1 - lam and the division-free dual prox v + clamp(-v, sigma l, sigma u).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,20 +41,11 @@
 
 #include "device_common.cuh"
 #include "lp_internal.h"
+#include "spmv_tile.cuh"
 
 namespace gb300lp {
 
-constexpr int kBlock = 256;
-constexpr int kMaxBins = 8;
-constexpr int kBlockRowLog = 8;  // vlog marking the block-per-row class
-
-struct Bins {
-  int nbins = 0;
-  int ntiles = 0;
-  int tile_begin[kMaxBins + 1] = {0};
-  int row_begin[kMaxBins + 1] = {0};
-  int vlog[kMaxBins] = {0};
-};
+constexpr int kBlock = kTB;
 
 constexpr int ST_RUNNING = -1;
 
@@ -67,71 +63,12 @@ struct State {
   int status;
   int restart_flag;
   int halpern, restarts_on;
+  int err;  // set by a kernel whose bounded wait expired
 };
 
 enum {
   Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P, Q_CN, Q_BN, Q_PW, NQ
 };
-
-// ---------------------------------------------------------------------------
-// generic binned row loop: each row reduced by a group of V lanes (V = 1..32)
-// or by the whole CTA (block-per-row class); epi.row(r, value) is called once
-// per row by one thread.
-
-template <typename Acc>
-__device__ __forceinline__ Acc group_sum(Acc s, int vlog) {
-  for (int o = (1 << vlog) >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-  return s;
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc block_sum_bcast0(Acc s, Acc *red) {
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  Acc tot = 0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < kBlock / 32; ++w) tot += red[w];
-  }
-  __syncthreads();
-  return tot;
-}
-
-// SpMV row loop: value of row r = sum_k va[k] * vec[ci[k]] in Acc precision
-template <typename T, typename V, typename Acc, class Epi>
-__device__ __forceinline__ void spmv_loop(const int *__restrict__ rp, const int *__restrict__ ci,
-                                          const T *__restrict__ va, const V *__restrict__ vec,
-                                          const Bins &bins, Epi &epi) {
-  __shared__ Acc red[kBlock / 32];
-  for (int t = blockIdx.x; t < bins.ntiles; t += gridDim.x) {
-    int b = 0;
-    while (t >= bins.tile_begin[b + 1]) ++b;
-    const int vlog = bins.vlog[b];
-    if (vlog != kBlockRowLog) {
-      const int rpt = kBlock >> vlog;
-      const int r = bins.row_begin[b] + (t - bins.tile_begin[b]) * rpt + (threadIdx.x >> vlog);
-      const int lane = threadIdx.x & ((1 << vlog) - 1);
-      const bool valid = r < bins.row_begin[b + 1];
-      Acc s = 0;
-      if (valid) {
-        const int e = rp[r + 1];
-        const int step = 1 << vlog;
-#pragma unroll 4
-        for (int k = rp[r] + lane; k < e; k += step) s += (Acc)va[k] * (Acc)vec[ci[k]];
-      }
-      s = group_sum(s, vlog);
-      if (valid && lane == 0) epi.row(r, (double)s);
-    } else {
-      const int r = bins.row_begin[b] + (t - bins.tile_begin[b]);
-      const int e = rp[r + 1];
-      Acc s = 0;
-#pragma unroll 4
-      for (int k = rp[r] + threadIdx.x; k < e; k += kBlock) s += (Acc)va[k] * (Acc)vec[ci[k]];
-      s = block_sum_bcast0(s, red);
-      if (threadIdx.x == 0) epi.row(r, (double)s);
-    }
-  }
-}
 
 // deterministic block reduction of NQL accumulators into partials[q * G + block]
 template <int NQL>
@@ -254,8 +191,18 @@ __global__ void k_fill(double *p, double v, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// power iteration on A~^T A~
+// tiled kernels: every SpMV below walks the tile table of its matrix with the
+// engine of spmv_tile.cuh; dynamic shared memory holds TileSmem<T, Acc>.
 
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+struct MatDev {
+  const int4 *tiles;
+  int ntiles;
+  const int *rp, *ci;
+};
+
+// power iteration on A~^T A~
 struct StoreEpi {
   double *out;
   __device__ __forceinline__ void row(int r, double s) { out[r] = s; }
@@ -269,23 +216,23 @@ struct StoreSqEpi {
   }
 };
 
-__global__ void __launch_bounds__(kBlock) k_spmv_store(const int *__restrict__ rp,
-                                                       const int *__restrict__ ci,
-                                                       const double *__restrict__ va,
-                                                       const double *__restrict__ vec, Bins bins,
-                                                       double *out) {
+__global__ void __launch_bounds__(kBlock, 4) k_spmv_store(MatDev M, const double *__restrict__ va,
+                                                       const double *__restrict__ vec, double *out,
+                                                       int *err) {
+  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   StoreEpi e{out};
-  spmv_loop<double, double, double>(rp, ci, va, vec, bins, e);
+  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, err,
+                                    blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(kBlock) k_spmv_store_sq(const int *__restrict__ rp,
-                                                          const int *__restrict__ ci,
-                                                          const double *__restrict__ va,
+__global__ void __launch_bounds__(kBlock, 4) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
                                                           const double *__restrict__ vec,
-                                                          Bins bins, double *out,
-                                                          double *partials, int G) {
+                                                          double *out, double *partials, int G,
+                                                          int *err) {
+  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   StoreSqEpi e{out, 0.0};
-  spmv_loop<double, double, double>(rp, ci, va, vec, bins, e);
+  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, err,
+                                    blockIdx.x, gridDim.x);
   double acc[1] = {e.acc};
   const int qi[1] = {Q_PW};
   store_partials<1>(acc, qi, partials, G);
@@ -321,6 +268,7 @@ __global__ void k_setup_final(State *st, const double *partials, int G, double e
     st->restarts = 0;
     st->status = ST_RUNNING;
     st->restart_flag = 0;
+    st->err = 0;
     st->r0 = st->r_prev = st->last_r = 0.0;
     st->rel_kkt = INFINITY;
   }
@@ -346,13 +294,30 @@ __global__ void k_init_y(int m, const double *__restrict__ dr, const double *__r
   }
 }
 
+// 1 / dr and 1 / dc for the unscaling in the KKT kernels
+__global__ void k_reciprocal(int n, const double *__restrict__ d, double *__restrict__ inv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    inv[i] = 1.0 / d[i];
+}
+
 // ---------------------------------------------------------------------------
 // the iteration kernels
 
-__device__ __forceinline__ double halpern_weight(const State *st, int j) {
-  if (!st->halpern) return 1.0;
-  int k = (j == 0) ? st->k_base : st->k_off + j;
-  return (k + 1.0) / (k + 2.0);
+// Halpern coefficients of iteration position j: z+ = a T(z) + b z + g z0
+struct Halpern {
+  double a, b, g;
+};
+__device__ __forceinline__ Halpern halpern_coeffs(const State *st, int j) {
+  double lam = 1.0;
+  if (st->halpern) {
+    int k = (j == 0) ? st->k_base : st->k_off + j;
+    lam = (k + 1.0) / (k + 2.0);
+  }
+  Halpern h;
+  h.a = lam * (1.0 + st->rho);
+  h.b = -lam * st->rho;
+  h.g = 1.0 - lam;
+  return h;
 }
 
 template <bool CHECK, bool MIXED>
@@ -360,14 +325,15 @@ struct PrimalEpi {
   const double *c, *lx, *ux;
   double *x, *x0, *xbar, *xhat;
   float *xbar_f;
-  double tau, lam, rho;
+  double tau;
+  Halpern hc;
   double acc0, acc1;
   __device__ __forceinline__ void row(int j, double g) {
-    double xk = x[j];
-    double xh = clampd(xk - tau * (c[j] - g), lx[j], ux[j]);
-    double xb = 2.0 * xh - xk;
-    double a0 = x0[j];
-    x[j] = lam * ((1.0 + rho) * xh - rho * xk) + (1.0 - lam) * a0;
+    const double xk = x[j];
+    const double xh = clampd(fma(-tau, c[j] - g, xk), lx[j], ux[j]);
+    const double xb = fma(2.0, xh, -xk);
+    const double a0 = x0[j];
+    x[j] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
     if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
     if (CHECK) {
       xhat[j] = xh;
@@ -378,20 +344,24 @@ struct PrimalEpi {
 };
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_primal(
-    const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ va, Bins bins,
-    const double *__restrict__ y, const float *__restrict__ yf, const double *__restrict__ c,
-    const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
-    double *xbar, float *xbar_f, double *xhat, const State *__restrict__ st, int j,
-    double *partials, int G) {
+__global__ void __launch_bounds__(kBlock, 4) k_primal(
+    MatDev M, const T *__restrict__ va, const double *__restrict__ y,
+    const float *__restrict__ yf, const double *__restrict__ c, const double *__restrict__ lx,
+    const double *__restrict__ ux, double *x, double *x0, double *xbar, float *xbar_f,
+    double *xhat, const State *__restrict__ st, int j, double *partials, int G, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
-  PrimalEpi<CHECK, MIXED> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau, halpern_weight(st, j),
-                            st->rho, 0.0, 0.0};
-  if (MIXED)
-    spmv_loop<T, float, float>(rp, ci, va, yf, bins, e);
-  else
-    spmv_loop<T, double, double>(rp, ci, va, y, bins, e);
+  PrimalEpi<CHECK, MIXED> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau, halpern_coeffs(st, j),
+                            0.0, 0.0};
+  if (MIXED) {
+    auto &sm = *reinterpret_cast<TileSmem<T, float> *>(g_smem);
+    tile_spmv<T, float, float>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e, err, blockIdx.x,
+                               gridDim.x);
+  } else {
+    auto &sm = *reinterpret_cast<TileSmem<T, double> *>(g_smem);
+    tile_spmv<T, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, y, e, err, blockIdx.x,
+                                 gridDim.x);
+  }
   if (CHECK) {
     double acc[2] = {e.acc0, e.acc1};
     const int qi[2] = {Q_XRES, Q_XD};
@@ -404,14 +374,16 @@ struct DualEpi {
   const double *lc, *uc;
   double *y, *y0, *yhat;
   float *yf;
-  double sigma, lam, rho;
+  double sigma;
+  Halpern hc;
   double acc0, acc1;
   __device__ __forceinline__ void row(int i, double h) {
-    double yk = y[i];
-    double v = yk - sigma * h;
-    double yh = v + sigma * clampd(-v / sigma, lc[i], uc[i]);
-    double a0 = y0[i];
-    double yn = lam * ((1.0 + rho) * yh - rho * yk) + (1.0 - lam) * a0;
+    const double yk = y[i];
+    const double v = fma(-sigma, h, yk);
+    // v + sigma proj_[l,u](-v / sigma) = v + proj_[sigma l, sigma u](-v)
+    const double yh = v + clampd(-v, sigma * lc[i], sigma * uc[i]);
+    const double a0 = y0[i];
+    const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
     y[i] = yn;
     if (MIXED) yf[i] = (float)yn;
     if (CHECK) {
@@ -423,19 +395,23 @@ struct DualEpi {
 };
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock) k_dual(
-    const int *__restrict__ rp, const int *__restrict__ ci, const T *__restrict__ va, Bins bins,
-    const double *__restrict__ xbar, const float *__restrict__ xbar_f,
-    const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
-    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int G) {
+__global__ void __launch_bounds__(kBlock, 4) k_dual(
+    MatDev M, const T *__restrict__ va, const double *__restrict__ xbar,
+    const float *__restrict__ xbar_f, const double *__restrict__ lc,
+    const double *__restrict__ uc, double *y, double *y0, float *yf, double *yhat,
+    const State *__restrict__ st, int j, double *partials, int G, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
-  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_weight(st, j), st->rho,
-                          0.0, 0.0};
-  if (MIXED)
-    spmv_loop<T, float, float>(rp, ci, va, xbar_f, bins, e);
-  else
-    spmv_loop<T, double, double>(rp, ci, va, xbar, bins, e);
+  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0};
+  if (MIXED) {
+    auto &sm = *reinterpret_cast<TileSmem<T, float> *>(g_smem);
+    tile_spmv<T, float, float>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e, err, blockIdx.x,
+                               gridDim.x);
+  } else {
+    auto &sm = *reinterpret_cast<TileSmem<T, double> *>(g_smem);
+    tile_spmv<T, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xbar, e, err, blockIdx.x,
+                                 gridDim.x);
+  }
   if (CHECK) {
     double acc[2] = {e.acc0, e.acc1};
     const int qi[2] = {Q_YRES, Q_YD};
@@ -445,15 +421,14 @@ __global__ void __launch_bounds__(kBlock) k_dual(
 
 // K3a: rows of A: primal residual of the unscaled A x and the y terms
 struct KktRowEpi {
-  const double *dr, *lc0, *uc0, *yhat;
+  const double *dr, *idr, *lc0, *uc0, *yhat;
   double rp2, rdy2, dy;
   __device__ __forceinline__ void row(int i, double h) {
-    double d = dr[i];
-    double ax = h / d;
-    double lo = lc0[i], hi = uc0[i];
-    double pr = clampd(ax, lo, hi);
+    const double ax = h * idr[i];
+    const double lo = lc0[i], hi = uc0[i];
+    const double pr = clampd(ax, lo, hi);
     rp2 += (ax - pr) * (ax - pr);
-    double yv = d * yhat[i];
+    const double yv = dr[i] * yhat[i];
     double yp = yv;
     if (!isfinite(lo)) yp = fmin(yp, 0.0);
     if (!isfinite(hi)) yp = fmax(yp, 0.0);
@@ -462,15 +437,17 @@ struct KktRowEpi {
   }
 };
 
-__global__ void __launch_bounds__(kBlock) k_kkt_rows(
-    const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ va,
-    Bins bins, const double *__restrict__ xhat, const double *__restrict__ dr,
+__global__ void __launch_bounds__(kBlock, 4) k_kkt_rows(
+    MatDev M, const double *__restrict__ va, const double *__restrict__ xhat,
+    const double *__restrict__ dr, const double *__restrict__ idr,
     const double *__restrict__ lc0, const double *__restrict__ uc0,
     const double *__restrict__ yhat, const State *__restrict__ st, int force, double *partials,
-    int G) {
+    int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
-  KktRowEpi e{dr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
-  spmv_loop<double, double, double>(rp, ci, va, xhat, bins, e);
+  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
+  KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
+  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, err,
+                                    blockIdx.x, gridDim.x);
   double acc[3] = {e.rp2, e.rdy2, e.dy};
   const int qi[3] = {Q_RP, Q_RDY, Q_DY};
   store_partials<3>(acc, qi, partials, G);
@@ -478,14 +455,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_rows(
 
 // K3b: rows of A^T: dual residual, lambda terms and the primal objective
 struct KktColEpi {
-  const double *c, *dc, *c0, *lx0, *ux0, *xhat;
+  const double *c, *dc, *idc, *c0, *lx0, *ux0, *xhat;
   double *zbuf;
   double rd2, dl, p;
   __device__ __forceinline__ void row(int j, double h) {
-    double d = dc[j];
-    double g = (c[j] - h) / d;
-    double lo = lx0[j], hi = ux0[j];
-    bool lf = isfinite(lo), uf = isfinite(hi);
+    const double d = dc[j];
+    const double g = (c[j] - h) * idc[j];
+    const double lo = lx0[j], hi = ux0[j];
+    const bool lf = isfinite(lo), uf = isfinite(hi);
     double lam = g;
     if (!lf && !uf) lam = 0.0;
     else if (lf && !uf) lam = fmax(lam, 0.0);
@@ -497,15 +474,17 @@ struct KktColEpi {
   }
 };
 
-__global__ void __launch_bounds__(kBlock) k_kkt_cols(
-    const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ va,
-    Bins bins, const double *__restrict__ yhat, const double *__restrict__ c,
-    const double *__restrict__ dc, const double *__restrict__ c0, const double *__restrict__ lx0,
-    const double *__restrict__ ux0, const double *__restrict__ xhat, double *zbuf,
-    const State *__restrict__ st, int force, double *partials, int G) {
+__global__ void __launch_bounds__(kBlock, 4) k_kkt_cols(
+    MatDev M, const double *__restrict__ va, const double *__restrict__ yhat,
+    const double *__restrict__ c, const double *__restrict__ dc, const double *__restrict__ idc,
+    const double *__restrict__ c0, const double *__restrict__ lx0, const double *__restrict__ ux0,
+    const double *__restrict__ xhat, double *zbuf, const State *__restrict__ st, int force,
+    double *partials, int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
-  KktColEpi e{c, dc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
-  spmv_loop<double, double, double>(rp, ci, va, yhat, bins, e);
+  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
+  KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
+  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, err,
+                                    blockIdx.x, gridDim.x);
   double acc[3] = {e.rd2, e.dl, e.p};
   const int qi[3] = {Q_RD, Q_DL, Q_P};
   store_partials<3>(acc, qi, partials, G);
@@ -608,6 +587,9 @@ __global__ void k_unscale(int n, int m, const double *__restrict__ dc, const dou
 // ---------------------------------------------------------------------------
 // host side
 
+constexpr size_t kSmem64 = sizeof(TileSmem<double, double>);
+constexpr size_t kSmem32 = sizeof(TileSmem<float, float>);
+
 struct DeviceLP {
   lp_device_ctx ctx{};
   cudaStream_t s = nullptr;
@@ -618,7 +600,8 @@ struct DeviceLP {
   int m = 0, n = 0;
   long long nnz = 0;
   std::vector<int> rperm, cperm;  // new -> old
-  Bins binsA, binsT;
+  int ntilesA = 0, ntilesT = 0;
+  int4 *tilesA = nullptr, *tilesT = nullptr;
   int G = 1;
   int *A_rp = nullptr, *A_ci = nullptr, *T_rp = nullptr, *T_ci = nullptr;
   double *A_v0 = nullptr, *T_v0 = nullptr, *A_v = nullptr, *T_v = nullptr;
@@ -627,6 +610,7 @@ struct DeviceLP {
   double *c = nullptr, *lx = nullptr, *ux = nullptr, *lc = nullptr, *uc = nullptr;
   double *dr = nullptr, *dc = nullptr, *dr2 = nullptr, *dc2 = nullptr;
   double *dr_main = nullptr, *dc_main = nullptr;  // where dr / dc live after scaling
+  double *idr = nullptr, *idc = nullptr;
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
   double *pv = nullptr, *pw = nullptr, *pu = nullptr;
@@ -644,6 +628,10 @@ struct DeviceLP {
   int last_precision = -1;
   void *flush = nullptr;
   size_t flush_bytes = 0;
+
+  MatDev matA() const { return MatDev{tilesA, ntilesA, A_rp, A_ci}; }
+  MatDev matT() const { return MatDev{tilesT, ntilesT, T_rp, T_ci}; }
+  int *errp() const { return &st->err; }
 
   void *dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -678,6 +666,7 @@ struct DeviceLP {
       else cudaFreeAsync(p, s);
     }
     allocs.clear();
+    flush = nullptr;
     uploaded = false;
   }
   int grid_for(long long work) const {
@@ -687,50 +676,46 @@ struct DeviceLP {
   }
 };
 
-static void plan_bins(const std::vector<int64_t> &len, int items, int block_min, Bins &bins,
-                      std::vector<int> &perm) {
-  // class c in 0..5: V = 2^c lanes per row; class 6: whole CTA per row
-  const int nclass = 7;
-  int rows = (int)len.size();
-  std::vector<int> cls(rows);
-  std::vector<int> count(nclass, 0);
-  for (int r = 0; r < rows; ++r) {
-    int64_t L = len[r];
-    int cc;
-    if (L >= block_min) {
-      cc = 6;
-    } else {
-      int64_t need = (L + items - 1) / items;
-      cc = 0;
-      while ((1LL << cc) < need && cc < 5) ++cc;
-    }
-    cls[r] = cc;
-    count[cc]++;
+// Sort rows by length (longest first, stable) and cut them into tiles.
+static void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
+                       std::vector<int4> &tiles) {
+  const int rows = (int)len.size();
+  int64_t lmax = 0;
+  for (int64_t L : len) lmax = std::max(lmax, L);
+  const int64_t cap = std::min<int64_t>(lmax, (int64_t)kTileNnz + 1);
+  std::vector<int> cnt(cap + 2, 0);
+  for (int64_t L : len) cnt[std::min(L, cap)]++;
+  // descending by min(L, cap); rows longer than a tile keep their order
+  std::vector<int> start(cap + 2, 0);
+  int acc = 0;
+  for (int64_t L = cap; L >= 0; --L) {
+    start[L] = acc;
+    acc += cnt[L];
   }
-  std::vector<int> start(nclass + 1, 0);
-  for (int q = 0; q < nclass; ++q) start[q + 1] = start[q] + count[q];
   perm.assign(rows, 0);
-  std::vector<int> pos(start.begin(), start.end() - 1);
-  for (int r = 0; r < rows; ++r) perm[pos[cls[r]]++] = r;
-  bins = Bins();
-  int nb = 0, tiles = 0;
-  for (int q = 0; q < nclass; ++q) {
-    if (count[q] == 0) continue;
-    bins.row_begin[nb] = start[q];
-    bins.tile_begin[nb] = tiles;
-    int vlog = q == 6 ? kBlockRowLog : q;
-    bins.vlog[nb] = vlog;
-    int rpt = q == 6 ? 1 : (kBlock >> q);
-    tiles += (count[q] + rpt - 1) / rpt;
-    ++nb;
-  }
-  bins.nbins = nb;
-  bins.ntiles = tiles;
-  bins.row_begin[nb] = rows;
-  bins.tile_begin[nb] = tiles;
-  for (int q = nb + 1; q <= kMaxBins; ++q) {
-    bins.row_begin[q] = rows;
-    bins.tile_begin[q] = tiles;
+  for (int r = 0; r < rows; ++r) perm[start[std::min(len[r], cap)]++] = r;
+  tiles.clear();
+  int i = 0;
+  int64_t k = 0;
+  while (i < rows) {
+    const int64_t L = len[perm[i]];
+    if (L > kTileNnz || L >= 192) {
+      int mode = L > kTileNnz ? TM_LONG : TM_BLOCK;
+      tiles.push_back(make_int4(i, (i + 1) | (mode << kModeShift), (int)k, (int)(k + L)));
+      k += L;
+      ++i;
+      continue;
+    }
+    int j = i;
+    int64_t nz = 0;
+    while (j < rows && j - i < kTileRows && nz + len[perm[j]] <= kTileNnz) {
+      nz += len[perm[j]];
+      ++j;
+    }
+    int mode = L <= 24 ? TM_THREAD : TM_WARP;
+    tiles.push_back(make_int4(i, j | (mode << kModeShift), (int)k, (int)(k + nz)));
+    k += nz;
+    i = j;
   }
 }
 
@@ -748,6 +733,22 @@ DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
       d->own_stream = true;
     }
     CK(cudaHostAlloc(reinterpret_cast<void **>(&d->hst), sizeof(State), cudaHostAllocDefault));
+    static bool attrs_done = false;
+    if (!attrs_done) {
+      CK(cudaFuncSetAttribute(k_primal<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_primal<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_primal<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
+      CK(cudaFuncSetAttribute(k_primal<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
+      CK(cudaFuncSetAttribute(k_dual<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_dual<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_dual<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
+      CK(cudaFuncSetAttribute(k_dual<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
+      CK(cudaFuncSetAttribute(k_kkt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_kkt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_spmv_store, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      CK(cudaFuncSetAttribute(k_spmv_store_sq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
+      attrs_done = true;
+    }
   } catch (const std::exception &e) {
     err = e.what();
     delete d;
@@ -769,11 +770,11 @@ void dev_destroy(DeviceLP *d) {
   delete d;
 }
 
-int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
+int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &err) {
   try {
     CK(cudaSetDevice(d->device));
     d->release_all();
-    if (h.nnz() >= (int64_t)INT32_MAX) {
+    if (h.nnz() >= (int64_t)INT32_MAX - 64) {
       err = "nnz must be below 2^31 on the device";
       return LP_ERR_INVALID;
     }
@@ -782,20 +783,20 @@ int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
     d->m = m;
     d->n = n;
     d->nnz = nnz;
-    const int items = tile_items > 0 ? tile_items : 4;
-    const int block_min = 32 * items * 16;
-    // row classes of A and of A^T
     std::vector<int64_t> rlen(m), clen(n, 0);
     for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
     for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
-    plan_bins(rlen, items, block_min, d->binsA, d->rperm);
-    plan_bins(clen, items, block_min, d->binsT, d->cperm);
+    std::vector<int4> tA, tT;
+    plan_tiles(rlen, d->rperm, tA);
+    plan_tiles(clen, d->cperm, tT);
+    d->ntilesA = (int)tA.size();
+    d->ntilesT = (int)tT.size();
     std::vector<int> rinv(m), cinv(n);
     for (int i = 0; i < m; ++i) rinv[d->rperm[i]] = i;
     for (int j = 0; j < n; ++j) cinv[d->cperm[j]] = j;
     // permuted A
-    std::vector<int> arp(m + 1, 0), aci(nnz);
-    std::vector<double> av(nnz);
+    std::vector<int> arp(m + 1, 0), aci(nnz + kTilePad, 0);
+    std::vector<double> av(nnz + kTilePad, 0.0);
     for (int i = 0; i < m; ++i) {
       int o = d->rperm[i];
       arp[i + 1] = arp[i] + (int)rlen[o];
@@ -806,8 +807,8 @@ int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
       }
     }
     // transpose of the permuted A, rows in new column order, entries by new row
-    std::vector<int> trp(n + 1, 0), tci(nnz);
-    std::vector<double> tv(nnz);
+    std::vector<int> trp(n + 1, 0), tci(nnz + kTilePad, 0);
+    std::vector<double> tv(nnz + kTilePad, 0.0);
     for (int j = 0; j < n; ++j) trp[j + 1] = trp[j] + (int)clen[d->cperm[j]];
     {
       std::vector<int> cur(trp.begin(), trp.end() - 1);
@@ -842,43 +843,59 @@ int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
     d->bnorm = std::sqrt(bn2);
     d->cnorm = std::sqrt(cn2);
     d->off = h.off;
-    // device buffers
+    // device buffers (value / index arrays padded for the aligned tile copies)
+    const size_t nzp = (size_t)nnz + kTilePad;
     d->A_rp = d->dalloc_n<int>(m + 1);
-    d->A_ci = d->dalloc_n<int>(nnz);
-    d->A_v0 = d->dalloc_n<double>(nnz);
-    d->A_v = d->dalloc_n<double>(nnz);
+    d->A_ci = d->dalloc_n<int>(nzp);
+    d->A_v0 = d->dalloc_n<double>(nzp);
+    d->A_v = d->dalloc_n<double>(nzp);
     d->T_rp = d->dalloc_n<int>(n + 1);
-    d->T_ci = d->dalloc_n<int>(nnz);
-    d->T_v0 = d->dalloc_n<double>(nnz);
-    d->T_v = d->dalloc_n<double>(nnz);
-    d->A_vf = d->dalloc_n<float>(nnz);
-    d->T_vf = d->dalloc_n<float>(nnz);
+    d->T_ci = d->dalloc_n<int>(nzp);
+    d->T_v0 = d->dalloc_n<double>(nzp);
+    d->T_v = d->dalloc_n<double>(nzp);
+    d->A_vf = d->dalloc_n<float>(nzp);
+    d->T_vf = d->dalloc_n<float>(nzp);
+    d->tilesA = d->dalloc_n<int4>(std::max<size_t>(tA.size(), 1));
+    d->tilesT = d->dalloc_n<int4>(std::max<size_t>(tT.size(), 1));
     double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
-                        &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv, &d->pw,
-                        &d->ox, &d->oxi};
+                        &d->idc, &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv,
+                        &d->pw, &d->ox, &d->oxi};
     for (double **p : cols_) *p = d->dalloc_n<double>(n);
-    double **rows_[] = {&d->lc0, &d->uc0, &d->lc, &d->uc, &d->dr, &d->dr2, &d->y, &d->y0,
-                        &d->yhat, &d->pu, &d->oy, &d->oyi};
+    double **rows_[] = {&d->lc0, &d->uc0, &d->lc, &d->uc, &d->dr, &d->dr2, &d->idr, &d->y,
+                        &d->y0, &d->yhat, &d->pu, &d->oy, &d->oyi};
     for (double **p : rows_) *p = d->dalloc_n<double>(m);
     d->dr_main = d->dr;
     d->dc_main = d->dc;
     d->xbar_f = d->dalloc_n<float>(n);
     d->yf = d->dalloc_n<float>(m);
-    int tiles = std::max(d->binsA.ntiles, d->binsT.ntiles);
-    d->G = std::max(1, std::min(tiles, d->sm_count * 4));
+    int occ = 1;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_primal<double, true>, kBlock, kSmem64));
+    occ = std::max(occ, 1);
+    int tiles = std::max(d->ntilesA, d->ntilesT);
+    d->G = std::max(1, std::min(tiles, d->sm_count * occ));
     d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
     d->st = d->dalloc_n<State>(1);
     CK(cudaMemcpyAsync(d->A_rp, arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_ci, aci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_v0, av.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_ci, aci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_v0, av.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->T_rp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_ci, tci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_v0, tv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_ci, tci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_v0, tv.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
+    if (!tA.empty())
+      CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int4) * tA.size(), cudaMemcpyHostToDevice, d->s));
+    if (!tT.empty())
+      CK(cudaMemcpyAsync(d->tilesT, tT.data(), sizeof(int4) * tT.size(), cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->c0, c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lx0, lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->ux0, ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lc0, lc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->uc0, uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+    // the padding of the scaled copies is never used by the arithmetic, but
+    // the tile copies read it: give it defined contents
+    CK(cudaMemsetAsync(d->A_v, 0, sizeof(double) * nzp, d->s));
+    CK(cudaMemsetAsync(d->T_v, 0, sizeof(double) * nzp, d->s));
+    CK(cudaMemsetAsync(d->A_vf, 0, sizeof(float) * nzp, d->s));
+    CK(cudaMemsetAsync(d->T_vf, 0, sizeof(float) * nzp, d->s));
     CK(cudaStreamSynchronize(d->s));
     d->uploaded = true;
   } catch (const DeviceOOM &e) {
@@ -893,63 +910,80 @@ int dev_upload(DeviceLP *d, const HostLP &h, int tile_items, std::string &err) {
 
 namespace {
 
+template <typename T>
+void launch_primal(DeviceLP *d, bool wr, int grid, int j) {
+  const T *va;
+  size_t smem;
+  if constexpr (sizeof(T) == 4) {
+    va = reinterpret_cast<const T *>(d->T_vf);
+    smem = kSmem32;
+  } else {
+    va = reinterpret_cast<const T *>(d->T_v);
+    smem = kSmem64;
+  }
+  if (wr)
+    k_primal<T, true><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->y, d->yf, d->c, d->lx,
+                                                    d->ux, d->x, d->x0, d->xbar, d->xbar_f,
+                                                    d->xhat, d->st, j, d->partials, d->G,
+                                                    d->errp());
+  else
+    k_primal<T, false><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->y, d->yf, d->c, d->lx,
+                                                     d->ux, d->x, d->x0, d->xbar, d->xbar_f,
+                                                     d->xhat, d->st, j, d->partials, d->G,
+                                                     d->errp());
+}
+
+template <typename T>
+void launch_dual(DeviceLP *d, bool wr, int grid, int j) {
+  const T *va;
+  size_t smem;
+  float *yf;
+  if constexpr (sizeof(T) == 4) {
+    va = reinterpret_cast<const T *>(d->A_vf);
+    smem = kSmem32;
+    yf = d->yf;
+  } else {
+    va = reinterpret_cast<const T *>(d->A_v);
+    smem = kSmem64;
+    yf = nullptr;
+  }
+  if (wr)
+    k_dual<T, true><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->xbar, d->xbar_f, d->lc,
+                                                  d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
+                                                  d->partials, d->G, d->errp());
+  else
+    k_dual<T, false><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->xbar, d->xbar_f, d->lc,
+                                                   d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
+                                                   d->partials, d->G, d->errp());
+}
+
+void launch_kkt(DeviceLP *d, int force) {
+  k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr, d->lc0,
+                                              d->uc0, d->yhat, d->st, force, d->partials, d->G,
+                                              d->errp());
+  k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc, d->idc,
+                                              d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st,
+                                              force, d->partials, d->G, d->errp());
+}
+
 // one PDHG iteration (position j in its chunk); check adds K3, K4, K5
 void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only) {
-  const int gA = std::max(1, std::min(d->binsA.ntiles, d->G));
-  const int gT = std::max(1, std::min(d->binsT.ntiles, d->G));
+  const int gA = std::max(1, std::min(d->ntilesA, d->G));
+  const int gT = std::max(1, std::min(d->ntilesT, d->G));
   const bool wr = check || hat_only;
-  // the partial-producing kernels must cover all G slots: use G CTAs then
+  // kernels that write partials cover all G slots
   const int gT1 = wr ? d->G : gT;
   const int gA1 = wr ? d->G : gA;
   if (mixed) {
-    if (wr)
-      k_primal<float, true><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y,
-                                                       d->yf, d->c, d->lx, d->ux, d->x, d->x0,
-                                                       d->xbar, d->xbar_f, d->xhat, d->st, j,
-                                                       d->partials, d->G);
-    else
-      k_primal<float, false><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y,
-                                                        d->yf, d->c, d->lx, d->ux, d->x, d->x0,
-                                                        d->xbar, d->xbar_f, d->xhat, d->st, j,
-                                                        d->partials, d->G);
-    if (wr)
-      k_dual<float, true><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_vf, d->binsA, d->xbar,
-                                                     d->xbar_f, d->lc, d->uc, d->y, d->y0, d->yf,
-                                                     d->yhat, d->st, j, d->partials, d->G);
-    else
-      k_dual<float, false><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_vf, d->binsA,
-                                                      d->xbar, d->xbar_f, d->lc, d->uc, d->y,
-                                                      d->y0, d->yf, d->yhat, d->st, j,
-                                                      d->partials, d->G);
+    launch_primal<float>(d, wr, gT1, j);
+    launch_dual<float>(d, wr, gA1, j);
   } else {
-    if (wr)
-      k_primal<double, true><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->y,
-                                                        d->yf, d->c, d->lx, d->ux, d->x, d->x0,
-                                                        d->xbar, d->xbar_f, d->xhat, d->st, j,
-                                                        d->partials, d->G);
-    else
-      k_primal<double, false><<<gT1, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->y,
-                                                         d->yf, d->c, d->lx, d->ux, d->x, d->x0,
-                                                         d->xbar, d->xbar_f, d->xhat, d->st, j,
-                                                         d->partials, d->G);
-    if (wr)
-      k_dual<double, true><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xbar,
-                                                      d->xbar_f, d->lc, d->uc, d->y, d->y0,
-                                                      nullptr, d->yhat, d->st, j, d->partials,
-                                                      d->G);
-    else
-      k_dual<double, false><<<gA1, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA,
-                                                       d->xbar, d->xbar_f, d->lc, d->uc, d->y,
-                                                       d->y0, nullptr, d->yhat, d->st, j,
-                                                       d->partials, d->G);
+    launch_primal<double>(d, wr, gT1, j);
+    launch_dual<double>(d, wr, gA1, j);
   }
   d->launches += 2;
   if (check) {
-    k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat, d->dr,
-                                          d->lc0, d->uc0, d->yhat, d->st, 0, d->partials, d->G);
-    k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat, d->c,
-                                          d->dc, d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st,
-                                          0, d->partials, d->G);
+    launch_kkt(d, 0);
     k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 0);
     k_restart<<<d->grid_for(std::max(d->m, d->n)), kBlock, 0, d->s>>>(
         d->st, d->n, d->m, d->x, d->x0, d->xhat, d->y, d->y0, d->yhat, mixed ? d->yf : nullptr);
@@ -958,11 +992,7 @@ void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only)
 }
 
 void final_eval(DeviceLP *d) {
-  k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat, d->dr,
-                                        d->lc0, d->uc0, d->yhat, d->st, 1, d->partials, d->G);
-  k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat, d->c, d->dc,
-                                        d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st, 1,
-                                        d->partials, d->G);
+  launch_kkt(d, 1);
   k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 1);
   d->launches += 3;
 }
@@ -1015,21 +1045,23 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
                                           d->partials, d->G);
   k_apply_rows<<<d->G, kBlock, 0, d->s>>>(m, d->lc0, d->uc0, d->dr, d->lc, d->uc, d->partials,
                                           d->G);
-  d->launches += 4;
+  k_reciprocal<<<gm, kBlock, 0, d->s>>>(m, d->dr, d->idr);
+  k_reciprocal<<<gn, kBlock, 0, d->s>>>(n, d->dc, d->idc);
+  d->launches += 6;
   bool power = !(o.step_size > 0) && n > 0 && m > 0;
   if (power) {
     k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
     d->launches += 1;
+    const int gA = std::max(1, std::min(d->ntilesA, d->G));
     for (int it = 0; it < o.power_iters; ++it) {
-      k_spmv_store<<<std::max(1, std::min(d->binsA.ntiles, d->G)), kBlock, 0, d->s>>>(
-          d->A_rp, d->A_ci, d->A_v, d->pv, d->binsA, d->pu);
-      k_spmv_store_sq<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->pu, d->binsT, d->pw,
-                                                 d->partials, d->G);
+      k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());
+      k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
+                                                       d->partials, d->G, d->errp());
       k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->partials, d->G);
       d->launches += 3;
     }
-    k_spmv_store_sq<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->pv, d->binsA, d->pu,
-                                               d->partials, d->G);
+    k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu,
+                                                     d->partials, d->G, d->errp());
     d->launches += 1;
   }
   k_init_x<<<gn, kBlock, 0, d->s>>>(n, d->lx, d->ux, d->dc, xinit_perm, d->x, d->x0);
@@ -1127,11 +1159,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       }
       return e;
     };
-    bool done = false;
     bool timed_out = false;
     const double tl = o.time_limit_s > 0 ? o.time_limit_s : 1e30;
     size_t head = 0;
-    while (!done) {
+    for (;;) {
       // keep up to two chunks in flight
       while (evs.size() - head < 2 && launched < max_iter) {
         long long rem = max_iter - launched;
@@ -1157,10 +1188,8 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       pool.push_back(evs[head]);
       ++head;
       volatile int status = d->hst->status;
-      if (status != ST_RUNNING) {
-        done = true;
-        break;
-      }
+      volatile int kerr = d->hst->err;
+      if (status != ST_RUNNING || kerr) break;
       double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
       if (el > tl) {
         timed_out = true;
@@ -1171,6 +1200,13 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     for (size_t q = head; q < evs.size(); ++q) pool.push_back(evs[q]);
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
+    if (d->hst->err) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaEventDestroy(e2);
+      err = "a bounded device wait expired (tile copy did not complete)";
+      return LP_ERR_TIMEOUT;
+    }
     int status = d->hst->status;
     long long iters = d->hst->iters;
     if (status == ST_RUNNING) {
@@ -1263,7 +1299,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
   return LP_OK;
 }
 
-
 // Time the iteration kernels one launch at a time with CUDA events on the
 // library's stream, each launch preceded by a write of a 256 MiB buffer so it
 // starts with a cold L2.  Needs a prior dev_solve (scaled matrices present);
@@ -1294,38 +1329,27 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     double tot[4] = {0, 0, 0, 0};
-    const int gA = std::max(1, std::min(d->binsA.ntiles, d->G));
-    const int gT = std::max(1, std::min(d->binsT.ntiles, d->G));
+    const int gA = std::max(1, std::min(d->ntilesA, d->G));
+    const int gT = std::max(1, std::min(d->ntilesT, d->G));
     for (int r = 0; r < reps; ++r) {
       for (int which = 0; which < 4; ++which) {
         CK(cudaMemsetAsync(d->flush, r & 0xff, d->flush_bytes, d->s));
         CK(cudaEventRecord(a, d->s));
         if (which == 0) {
-          if (mixed)
-            k_primal<float, false><<<gT, kBlock, 0, d->s>>>(
-                d->T_rp, d->T_ci, d->T_vf, d->binsT, d->y, d->yf, d->c, d->lx, d->ux, d->x,
-                d->x0, d->xbar, d->xbar_f, d->xhat, d->st, 1, d->partials, d->G);
-          else
-            k_primal<double, false><<<gT, kBlock, 0, d->s>>>(
-                d->T_rp, d->T_ci, d->T_v, d->binsT, d->y, d->yf, d->c, d->lx, d->ux, d->x,
-                d->x0, d->xbar, d->xbar_f, d->xhat, d->st, 1, d->partials, d->G);
+          if (mixed) launch_primal<float>(d, false, gT, 1);
+          else launch_primal<double>(d, false, gT, 1);
         } else if (which == 1) {
-          if (mixed)
-            k_dual<float, false><<<gA, kBlock, 0, d->s>>>(
-                d->A_rp, d->A_ci, d->A_vf, d->binsA, d->xbar, d->xbar_f, d->lc, d->uc, d->y,
-                d->y0, d->yf, d->yhat, d->st, 1, d->partials, d->G);
-          else
-            k_dual<double, false><<<gA, kBlock, 0, d->s>>>(
-                d->A_rp, d->A_ci, d->A_v, d->binsA, d->xbar, d->xbar_f, d->lc, d->uc, d->y,
-                d->y0, nullptr, d->yhat, d->st, 1, d->partials, d->G);
+          if (mixed) launch_dual<float>(d, false, gA, 1);
+          else launch_dual<double>(d, false, gA, 1);
         } else if (which == 2) {
-          k_kkt_rows<<<d->G, kBlock, 0, d->s>>>(d->A_rp, d->A_ci, d->A_v, d->binsA, d->xhat,
-                                                d->dr, d->lc0, d->uc0, d->yhat, d->st, 1,
-                                                d->partials, d->G);
+          k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr,
+                                                      d->lc0, d->uc0, d->yhat, d->st, 1,
+                                                      d->partials, d->G, d->errp());
         } else {
-          k_kkt_cols<<<d->G, kBlock, 0, d->s>>>(d->T_rp, d->T_ci, d->T_v, d->binsT, d->yhat,
-                                                d->c, d->dc, d->c0, d->lx0, d->ux0, d->xhat,
-                                                d->zbuf, d->st, 1, d->partials, d->G);
+          k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc,
+                                                      d->idc, d->c0, d->lx0, d->ux0, d->xhat,
+                                                      d->zbuf, d->st, 1, d->partials, d->G,
+                                                      d->errp());
         }
         CK(cudaEventRecord(b, d->s));
         CK(cudaEventSynchronize(b));
@@ -1343,12 +1367,14 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     // gathered vector counted once, every epilogue vector read / written once
     const double sv = mixed ? 4.0 : 8.0;
     const double sg = mixed ? 4.0 : 8.0;  // gathered vector element
+    // K1 reads x, x0, c, lx, ux and writes x and xbar (4 bytes when mixed)
     const double k1 = nnz * (sv + 4.0) + 4.0 * (n + 1) + sg * m + 8.0 * 5 * n + 8.0 * n +
                       (mixed ? 4.0 : 8.0) * n;
+    // K2 reads y, y0, lc, uc and writes y (+ its FP32 shadow when mixed)
     const double k2 = nnz * (sv + 4.0) + 4.0 * (m + 1) + sg * n + 8.0 * 4 * m + 8.0 * m +
                       (mixed ? 4.0 * m : 0.0);
-    const double k3a = nnz * 12.0 + 4.0 * (m + 1) + 8.0 * n + 8.0 * 4 * m;
-    const double k3b = nnz * 12.0 + 4.0 * (n + 1) + 8.0 * m + 8.0 * 6 * n + 8.0 * n;
+    const double k3a = nnz * 12.0 + 4.0 * (m + 1) + 8.0 * n + 8.0 * 6 * m;
+    const double k3b = nnz * 12.0 + 4.0 * (n + 1) + 8.0 * m + 8.0 * 8 * n + 8.0 * n;
     out[0] = tot[0] / reps;
     out[1] = tot[1] / reps;
     out[2] = k1;
