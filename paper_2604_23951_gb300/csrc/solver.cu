@@ -41,11 +41,19 @@
 
 #include "device_common.cuh"
 #include "lp_internal.h"
-#include "spmv_tile.cuh"
+#include "spmv_warp.cuh"
 
 namespace gb300lp {
 
-constexpr int kBlock = kTB;
+#ifndef GB300_BLOCK
+#define GB300_BLOCK 256
+#endif
+constexpr int kBlock = GB300_BLOCK;
+constexpr int kTilePad = 8;  // value / index arrays padded past nnz
+#ifndef GB300_MIN_BLOCKS
+#define GB300_MIN_BLOCKS (1024 / GB300_BLOCK)
+#endif
+constexpr int kMinBlocks = GB300_MIN_BLOCKS;
 
 constexpr int ST_RUNNING = -1;
 
@@ -191,48 +199,52 @@ __global__ void k_fill(double *p, double v, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// tiled kernels: every SpMV below walks the tile table of its matrix with the
-// engine of spmv_tile.cuh; dynamic shared memory holds TileSmem<T, Acc>.
-
-extern __shared__ __align__(16) unsigned char g_smem[];
+// SpMV kernels: every SpMV below walks the warp-tile table of its matrix with
+// the engine of spmv_warp.cuh (one warp per tile, no CTA barrier).
 
 struct MatDev {
-  const int4 *tiles;
+  const int2 *tiles;
   int ntiles;
+  int nlong;  // rows [0, nlong) are long rows reduced by a whole CTA
   const int *rp, *ci;
 };
+
+// kBlock / 32 accumulators of shared memory for the whole-CTA rows
+template <typename T, typename V, typename Acc>
+__device__ __forceinline__ Acc *red_smem() {
+  __shared__ Acc red[kBlock / 32];
+  return red;
+}
 
 // power iteration on A~^T A~
 struct StoreEpi {
   double *out;
+  __device__ __forceinline__ void pre(int) {}
   __device__ __forceinline__ void row(int r, double s) { out[r] = s; }
 };
 struct StoreSqEpi {
   double *out;
   double acc;
+  __device__ __forceinline__ void pre(int) {}
   __device__ __forceinline__ void row(int r, double s) {
     out[r] = s;
     acc += s * s;
   }
 };
 
-__global__ void __launch_bounds__(kBlock, 4) k_spmv_store(MatDev M, const double *__restrict__ va,
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, const double *__restrict__ va,
                                                        const double *__restrict__ vec, double *out,
                                                        int *err) {
-  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   StoreEpi e{out};
-  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, err,
-                                    blockIdx.x, gridDim.x);
+  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, red_smem<double, double, double>());
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
                                                           const double *__restrict__ vec,
                                                           double *out, double *partials, int G,
                                                           int *err) {
-  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   StoreSqEpi e{out, 0.0};
-  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, err,
-                                    blockIdx.x, gridDim.x);
+  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, red_smem<double, double, double>());
   double acc[1] = {e.acc};
   const int qi[1] = {Q_PW};
   store_partials<1>(acc, qi, partials, G);
@@ -328,11 +340,17 @@ struct PrimalEpi {
   double tau;
   Halpern hc;
   double acc0, acc1;
+  double xk, cj, lo, hi, a0;
+  __device__ __forceinline__ void pre(int j) {
+    xk = x[j];
+    cj = c[j];
+    lo = lx[j];
+    hi = ux[j];
+    a0 = x0[j];
+  }
   __device__ __forceinline__ void row(int j, double g) {
-    const double xk = x[j];
-    const double xh = clampd(fma(-tau, c[j] - g, xk), lx[j], ux[j]);
+    const double xh = clampd(fma(-tau, cj - g, xk), lo, hi);
     const double xb = fma(2.0, xh, -xk);
-    const double a0 = x0[j];
     x[j] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
     if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
     if (CHECK) {
@@ -344,7 +362,7 @@ struct PrimalEpi {
 };
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock, 4) k_primal(
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
     MatDev M, const T *__restrict__ va, const double *__restrict__ y,
     const float *__restrict__ yf, const double *__restrict__ c, const double *__restrict__ lx,
     const double *__restrict__ ux, double *x, double *x0, double *xbar, float *xbar_f,
@@ -352,15 +370,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_primal(
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
   PrimalEpi<CHECK, MIXED> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau, halpern_coeffs(st, j),
-                            0.0, 0.0};
+                            0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (MIXED) {
-    auto &sm = *reinterpret_cast<TileSmem<T, float> *>(g_smem);
-    tile_spmv<T, float, float>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e, err, blockIdx.x,
-                               gridDim.x);
+      warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e, red_smem<T, float, float>());
   } else {
-    auto &sm = *reinterpret_cast<TileSmem<T, double> *>(g_smem);
-    tile_spmv<T, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, y, e, err, blockIdx.x,
-                                 gridDim.x);
+      warp_spmv<kBlock, T, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, y, e, red_smem<T, double, double>());
   }
   if (CHECK) {
     double acc[2] = {e.acc0, e.acc1};
@@ -377,12 +391,17 @@ struct DualEpi {
   double sigma;
   Halpern hc;
   double acc0, acc1;
+  double yk, lo, hi, a0;
+  __device__ __forceinline__ void pre(int i) {
+    yk = y[i];
+    lo = lc[i];
+    hi = uc[i];
+    a0 = y0[i];
+  }
   __device__ __forceinline__ void row(int i, double h) {
-    const double yk = y[i];
     const double v = fma(-sigma, h, yk);
     // v + sigma proj_[l,u](-v / sigma) = v + proj_[sigma l, sigma u](-v)
-    const double yh = v + clampd(-v, sigma * lc[i], sigma * uc[i]);
-    const double a0 = y0[i];
+    const double yh = v + clampd(-v, sigma * lo, sigma * hi);
     const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
     y[i] = yn;
     if (MIXED) yf[i] = (float)yn;
@@ -395,22 +414,19 @@ struct DualEpi {
 };
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock, 4) k_dual(
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
     MatDev M, const T *__restrict__ va, const double *__restrict__ xbar,
     const float *__restrict__ xbar_f, const double *__restrict__ lc,
     const double *__restrict__ uc, double *y, double *y0, float *yf, double *yhat,
     const State *__restrict__ st, int j, double *partials, int G, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
-  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0};
+  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
+                          0.0, 0.0, 0.0, 0.0};
   if (MIXED) {
-    auto &sm = *reinterpret_cast<TileSmem<T, float> *>(g_smem);
-    tile_spmv<T, float, float>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e, err, blockIdx.x,
-                               gridDim.x);
+      warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e, red_smem<T, float, float>());
   } else {
-    auto &sm = *reinterpret_cast<TileSmem<T, double> *>(g_smem);
-    tile_spmv<T, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xbar, e, err, blockIdx.x,
-                                 gridDim.x);
+      warp_spmv<kBlock, T, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar, e, red_smem<T, double, double>());
   }
   if (CHECK) {
     double acc[2] = {e.acc0, e.acc1};
@@ -423,6 +439,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_dual(
 struct KktRowEpi {
   const double *dr, *idr, *lc0, *uc0, *yhat;
   double rp2, rdy2, dy;
+  __device__ __forceinline__ void pre(int) {}
   __device__ __forceinline__ void row(int i, double h) {
     const double ax = h * idr[i];
     const double lo = lc0[i], hi = uc0[i];
@@ -437,17 +454,15 @@ struct KktRowEpi {
   }
 };
 
-__global__ void __launch_bounds__(kBlock, 4) k_kkt_rows(
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     MatDev M, const double *__restrict__ va, const double *__restrict__ xhat,
     const double *__restrict__ dr, const double *__restrict__ idr,
     const double *__restrict__ lc0, const double *__restrict__ uc0,
     const double *__restrict__ yhat, const State *__restrict__ st, int force, double *partials,
     int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
-  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
-  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, err,
-                                    blockIdx.x, gridDim.x);
+  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>());
   double acc[3] = {e.rp2, e.rdy2, e.dy};
   const int qi[3] = {Q_RP, Q_RDY, Q_DY};
   store_partials<3>(acc, qi, partials, G);
@@ -458,6 +473,7 @@ struct KktColEpi {
   const double *c, *dc, *idc, *c0, *lx0, *ux0, *xhat;
   double *zbuf;
   double rd2, dl, p;
+  __device__ __forceinline__ void pre(int) {}
   __device__ __forceinline__ void row(int j, double h) {
     const double d = dc[j];
     const double g = (c[j] - h) * idc[j];
@@ -474,17 +490,15 @@ struct KktColEpi {
   }
 };
 
-__global__ void __launch_bounds__(kBlock, 4) k_kkt_cols(
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     MatDev M, const double *__restrict__ va, const double *__restrict__ yhat,
     const double *__restrict__ c, const double *__restrict__ dc, const double *__restrict__ idc,
     const double *__restrict__ c0, const double *__restrict__ lx0, const double *__restrict__ ux0,
     const double *__restrict__ xhat, double *zbuf, const State *__restrict__ st, int force,
     double *partials, int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
-  auto &sm = *reinterpret_cast<TileSmem<double, double> *>(g_smem);
   KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
-  tile_spmv<double, double, double>(sm, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, err,
-                                    blockIdx.x, gridDim.x);
+  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>());
   double acc[3] = {e.rd2, e.dl, e.p};
   const int qi[3] = {Q_RD, Q_DL, Q_P};
   store_partials<3>(acc, qi, partials, G);
@@ -587,8 +601,8 @@ __global__ void k_unscale(int n, int m, const double *__restrict__ dc, const dou
 // ---------------------------------------------------------------------------
 // host side
 
-constexpr size_t kSmem64 = sizeof(TileSmem<double, double>);
-constexpr size_t kSmem32 = sizeof(TileSmem<float, float>);
+constexpr size_t kSmem64 = 0;  // the warp engine needs no dynamic shared memory
+constexpr size_t kSmem32 = 0;
 
 struct DeviceLP {
   lp_device_ctx ctx{};
@@ -600,8 +614,8 @@ struct DeviceLP {
   int m = 0, n = 0;
   long long nnz = 0;
   std::vector<int> rperm, cperm;  // new -> old
-  int ntilesA = 0, ntilesT = 0;
-  int4 *tilesA = nullptr, *tilesT = nullptr;
+  int ntilesA = 0, ntilesT = 0, nlongA = 0, nlongT = 0;
+  int2 *tilesA = nullptr, *tilesT = nullptr;
   int G = 1;
   int *A_rp = nullptr, *A_ci = nullptr, *T_rp = nullptr, *T_ci = nullptr;
   double *A_v0 = nullptr, *T_v0 = nullptr, *A_v = nullptr, *T_v = nullptr;
@@ -629,8 +643,8 @@ struct DeviceLP {
   void *flush = nullptr;
   size_t flush_bytes = 0;
 
-  MatDev matA() const { return MatDev{tilesA, ntilesA, A_rp, A_ci}; }
-  MatDev matT() const { return MatDev{tilesT, ntilesT, T_rp, T_ci}; }
+  MatDev matA() const { return MatDev{tilesA, ntilesA, nlongA, A_rp, A_ci}; }
+  MatDev matT() const { return MatDev{tilesT, ntilesT, nlongT, T_rp, T_ci}; }
   int *errp() const { return &st->err; }
 
   void *dalloc(size_t bytes) {
@@ -669,6 +683,10 @@ struct DeviceLP {
     flush = nullptr;
     uploaded = false;
   }
+  // persistent grid for a warp-tile table (8 warps per CTA), at most G CTAs
+  int grid_tiles(int ntiles, int nlong) const {
+    return std::max(1, std::min(std::max((ntiles + kBlock / 32 - 1) / (kBlock / 32), nlong), G));
+  }
   int grid_for(long long work) const {
     long long g = (work + kBlock - 1) / kBlock;
     g = std::max<long long>(1, std::min<long long>(g, (long long)sm_count * 8));
@@ -676,16 +694,18 @@ struct DeviceLP {
   }
 };
 
-// Sort rows by length (longest first, stable) and cut them into tiles.
+// Sort rows by length (longest first, stable).  Rows longer than kLongRow
+// come first (nlong of them, one whole-CTA reduction each); the rest are cut
+// into warp tiles of at most 32 rows and about kWarpTileNnz nonzeros, each
+// reducing its rows with 2^v lanes so no lane owns more than kWarpItems.
 static void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
-                       std::vector<int4> &tiles) {
+                       std::vector<int2> &tiles, int &nlong) {
   const int rows = (int)len.size();
   int64_t lmax = 0;
   for (int64_t L : len) lmax = std::max(lmax, L);
-  const int64_t cap = std::min<int64_t>(lmax, (int64_t)kTileNnz + 1);
+  const int64_t cap = std::min<int64_t>(lmax, (int64_t)kLongRow + 1);
   std::vector<int> cnt(cap + 2, 0);
   for (int64_t L : len) cnt[std::min(L, cap)]++;
-  // descending by min(L, cap); rows longer than a tile keep their order
   std::vector<int> start(cap + 2, 0);
   int acc = 0;
   for (int64_t L = cap; L >= 0; --L) {
@@ -696,26 +716,17 @@ static void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
   for (int r = 0; r < rows; ++r) perm[start[std::min(len[r], cap)]++] = r;
   tiles.clear();
   int i = 0;
-  int64_t k = 0;
+  while (i < rows && len[perm[i]] > kLongRow) ++i;
+  nlong = i;
   while (i < rows) {
     const int64_t L = len[perm[i]];
-    if (L > kTileNnz || L >= 192) {
-      int mode = L > kTileNnz ? TM_LONG : TM_BLOCK;
-      tiles.push_back(make_int4(i, (i + 1) | (mode << kModeShift), (int)k, (int)(k + L)));
-      k += L;
-      ++i;
-      continue;
-    }
-    int j = i;
-    int64_t nz = 0;
-    while (j < rows && j - i < kTileRows && nz + len[perm[j]] <= kTileNnz) {
-      nz += len[perm[j]];
-      ++j;
-    }
-    int mode = L <= 24 ? TM_THREAD : TM_WARP;
-    tiles.push_back(make_int4(i, j | (mode << kModeShift), (int)k, (int)(k + nz)));
-    k += nz;
-    i = j;
+    int vlog = 0;
+    const int64_t per = (L + kWarpItems - 1) / kWarpItems;
+    while ((1LL << vlog) < per && vlog < 5) ++vlog;
+    int nr = (int)std::max<int64_t>(1, std::min<int64_t>(32, kWarpTileNnz / std::max<int64_t>(L, 1)));
+    nr = std::min(nr, rows - i);
+    tiles.push_back(make_int2(i, nr | (vlog << 8)));
+    i += nr;
   }
 }
 
@@ -733,22 +744,6 @@ DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
       d->own_stream = true;
     }
     CK(cudaHostAlloc(reinterpret_cast<void **>(&d->hst), sizeof(State), cudaHostAllocDefault));
-    static bool attrs_done = false;
-    if (!attrs_done) {
-      CK(cudaFuncSetAttribute(k_primal<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_primal<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_primal<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
-      CK(cudaFuncSetAttribute(k_primal<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
-      CK(cudaFuncSetAttribute(k_dual<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_dual<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_dual<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
-      CK(cudaFuncSetAttribute(k_dual<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32));
-      CK(cudaFuncSetAttribute(k_kkt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_kkt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_spmv_store, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      CK(cudaFuncSetAttribute(k_spmv_store_sq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64));
-      attrs_done = true;
-    }
   } catch (const std::exception &e) {
     err = e.what();
     delete d;
@@ -786,9 +781,9 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     std::vector<int64_t> rlen(m), clen(n, 0);
     for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
     for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
-    std::vector<int4> tA, tT;
-    plan_tiles(rlen, d->rperm, tA);
-    plan_tiles(clen, d->cperm, tT);
+    std::vector<int2> tA, tT;
+    plan_tiles(rlen, d->rperm, tA, d->nlongA);
+    plan_tiles(clen, d->cperm, tT, d->nlongT);
     d->ntilesA = (int)tA.size();
     d->ntilesT = (int)tT.size();
     std::vector<int> rinv(m), cinv(n);
@@ -855,8 +850,8 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     d->T_v = d->dalloc_n<double>(nzp);
     d->A_vf = d->dalloc_n<float>(nzp);
     d->T_vf = d->dalloc_n<float>(nzp);
-    d->tilesA = d->dalloc_n<int4>(std::max<size_t>(tA.size(), 1));
-    d->tilesT = d->dalloc_n<int4>(std::max<size_t>(tT.size(), 1));
+    d->tilesA = d->dalloc_n<int2>(std::max<size_t>(tA.size(), 1));
+    d->tilesT = d->dalloc_n<int2>(std::max<size_t>(tT.size(), 1));
     double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
                         &d->idc, &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv,
                         &d->pw, &d->ox, &d->oxi};
@@ -871,8 +866,10 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     int occ = 1;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_primal<double, true>, kBlock, kSmem64));
     occ = std::max(occ, 1);
-    int tiles = std::max(d->ntilesA, d->ntilesT);
-    d->G = std::max(1, std::min(tiles, d->sm_count * occ));
+    const int wpb = kBlock / 32;
+    int need = std::max(std::max((d->ntilesA + wpb - 1) / wpb, d->nlongA),
+                        std::max((d->ntilesT + wpb - 1) / wpb, d->nlongT));
+    d->G = std::max(1, std::min(need, d->sm_count * occ));
     d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
     d->st = d->dalloc_n<State>(1);
     CK(cudaMemcpyAsync(d->A_rp, arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
@@ -882,9 +879,9 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     CK(cudaMemcpyAsync(d->T_ci, tci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->T_v0, tv.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
     if (!tA.empty())
-      CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int4) * tA.size(), cudaMemcpyHostToDevice, d->s));
+      CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int2) * tA.size(), cudaMemcpyHostToDevice, d->s));
     if (!tT.empty())
-      CK(cudaMemcpyAsync(d->tilesT, tT.data(), sizeof(int4) * tT.size(), cudaMemcpyHostToDevice, d->s));
+      CK(cudaMemcpyAsync(d->tilesT, tT.data(), sizeof(int2) * tT.size(), cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->c0, c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lx0, lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->ux0, ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
@@ -968,8 +965,8 @@ void launch_kkt(DeviceLP *d, int force) {
 
 // one PDHG iteration (position j in its chunk); check adds K3, K4, K5
 void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only) {
-  const int gA = std::max(1, std::min(d->ntilesA, d->G));
-  const int gT = std::max(1, std::min(d->ntilesT, d->G));
+  const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
+  const int gT = d->grid_tiles(d->ntilesT, d->nlongT);
   const bool wr = check || hat_only;
   // kernels that write partials cover all G slots
   const int gT1 = wr ? d->G : gT;
@@ -1052,7 +1049,7 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
   if (power) {
     k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
     d->launches += 1;
-    const int gA = std::max(1, std::min(d->ntilesA, d->G));
+    const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     for (int it = 0; it < o.power_iters; ++it) {
       k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());
       k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
@@ -1329,8 +1326,8 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     double tot[4] = {0, 0, 0, 0};
-    const int gA = std::max(1, std::min(d->ntilesA, d->G));
-    const int gT = std::max(1, std::min(d->ntilesT, d->G));
+    const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
+    const int gT = d->grid_tiles(d->ntilesT, d->nlongT);
     for (int r = 0; r < reps; ++r) {
       for (int which = 0; which < 4; ++which) {
         CK(cudaMemsetAsync(d->flush, r & 0xff, d->flush_bytes, d->s));
