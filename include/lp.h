@@ -220,6 +220,33 @@ int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out);
 
 void lp_destroy(lp_problem *lp);
 
+/* Power-iteration estimate of ||A||_2 that allocates no memory (the paper
+ * has no counterpart; it is the step-size estimate lp_solve computes, as a
+ * stand-alone call).  For callers that cannot allocate device memory where
+ * they need it: a process that reserved the GPU's memory for its own pool,
+ * or a latency-critical path where a cudaMalloc -- which can synchronize the
+ * device or fail on a fragmented heap -- is not allowed.
+ *   m, n        rows and columns of A; requires m + 2 n <= 1047551
+ *               (LP_ERR_INVALID with a message otherwise)
+ *   a_*         CSR of A on the device: row_ptr (m + 1), col_idx, val
+ *   at_*        CSR of A^T on the device (n + 1 row pointers)
+ *   iters       power iterations (lp_solve uses 100); start vector 1/sqrt(n),
+ *               v <- A^T A v / ||.||, estimate ||A v||
+ *   stream      cudaStream_t the kernels run on (NULL: legacy stream)
+ *   norm_out    host double that receives the estimate (0 if m or n is 0)
+ * All work vectors live in one file-scope device array of 2^20 doubles
+ * (8 MiB) that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (a
+ * one-time set-up per device): make it before any stream capture.  Every
+ * call shares the array and it keeps the last call's contents; calls that
+ * overlap on the GPU (other streams, other threads) race on it.  The call
+ * returns after synchronizing `stream`. */
+int lp_power_norm_static(int32_t m, int32_t n, const int32_t *a_row_ptr,
+                         const int32_t *a_col_idx, const double *a_val,
+                         const int32_t *at_row_ptr, const int32_t *at_col_idx,
+                         const double *at_val, int32_t iters, void *stream,
+                         double *norm_out);
+
 /* ---- batched solving and continuous-batching server ------------------ */
 
 /* A server holds up to hbm_budget_bytes of device memory (allocated once),

@@ -90,6 +90,8 @@ SIGNATURES = [
     ("lp_host_rel_kkt", C.c_int, [_P, _D, _D, _D]),
     ("lp_profile_kernels", C.c_int, [_P, C.c_int32, _D]),
     ("lp_destroy", None, [_P]),
+    ("lp_power_norm_static", C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int32,
+                                       _P, _D]),
     ("lp_server_create", C.c_int, [C.c_size_t, C.POINTER(lp_device_ctx),
                                    C.POINTER(lp_solve_opts), C.c_int32, _PP]),
     ("lp_batch_submit", C.c_int, [_P, _P, C.POINTER(C.c_uint64)]),
