@@ -148,6 +148,8 @@ typedef struct {
   double t_solve_s;      /* PDHG iterations (device)                        */
   double t_total_s;      /* wall time of the call                           */
   int64_t kernel_launches; /* kernels launched by this call                 */
+  int64_t fp32_iterations; /* LP_MIXED: iterations run with the FP32 SpMV
+                              before the switch to FP64 (see lp_solve)      */
 } lp_result;
 
 /* Defaults above; always call before filling in a field. */
@@ -177,7 +179,11 @@ int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *
 int lp_upload(lp_problem *lp);
 
 /* Solve the current (reduced) LP on the GPU.  May be called repeatedly;
- * every call starts from the initial (or warm-start) point. */
+ * every call starts from the initial (or warm-start) point.  LP_MIXED runs
+ * the SpMV in FP32 until the relative KKT error is within 10 x eps_rel, or
+ * has not halved over 32 checks once below 1e-4 (the FP32 rounding floor),
+ * or over 256 checks anywhere; then it finishes with the FP64 SpMV, and the
+ * iterates, anchor and weights carry over. */
 int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res);
 
 /* Solution of the current (reduced) LP: x (n), y (m), z = c - A^T y (n).
@@ -259,8 +265,9 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
                      const lp_solve_opts *opts, int32_t worker, lp_server **out);
 
 /* Queue a problem (its current, possibly presolved LP).  The server borrows
- * `lp` until its result has been polled.  Fails LP_ERR_BUDGET if the
- * problem alone exceeds the budget. */
+ * `lp` until its result has been polled; the polled answer is also stored in
+ * `lp` (lp_get_solution / lp_postsolve work on it).  Fails LP_ERR_BUDGET if
+ * the problem alone exceeds the budget. */
 int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket);
 
 /* LP_PENDING while in flight; LP_OK once done: res, x (n), y (m) of the
@@ -275,8 +282,10 @@ int lp_server_pump(lp_server *srv, int32_t periods);
  * termination LP_CANCELLED. */
 int lp_batch_cancel(lp_server *srv, uint64_t ticket);
 
-/* Statistics: out[0] admitted, out[1] finished, out[2] periods launched,
- * out[3] peak resident bytes, out[4] kernel launches, out[5] queue length. */
+/* Statistics (10 int64): out[0] admitted, out[1] finished, out[2] periods
+ * launched, out[3] peak resident bytes, out[4] kernel launches, out[5] queue
+ * length, out[6..9] shape index the autotuner uses for each size bucket
+ * (nonzeros < 16Ki, < 128Ki, < 1Mi, larger). */
 int lp_server_stats(const lp_server *srv, int64_t *out);
 
 void lp_server_destroy(lp_server *srv);

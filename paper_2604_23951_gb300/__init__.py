@@ -14,6 +14,7 @@ from .capi import (  # noqa: F401
     LP_NUMERICAL,
     LPError,
     Problem,
+    Server,
     TorchDevice,
     load,
     solve_opts,

@@ -60,7 +60,7 @@ class lp_result(C.Structure):
                 ("gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("eta", C.c_double), ("omega", C.c_double), ("t_setup_s", C.c_double),
                 ("t_solve_s", C.c_double), ("t_total_s", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("fp32_iterations", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -304,3 +304,80 @@ class Problem:
         out = np.zeros(6)
         check(self.lib.lp_host_rel_kkt(self.h, dptr(_f64(x)), dptr(_f64(y)), dptr(out)))
         return dict(zip(("rel_kkt", "rel_p", "rel_d", "rel_gap", "p", "d"), out))
+
+
+class Server:
+    """Continuous-batching server (lp_server_*): problems are queued with
+    submit(), admitted into the device arena as memory frees up, and solved
+    by the batched kernel; poll() returns the result when it is done."""
+
+    def __init__(self, budget_bytes: int, device: TorchDevice, worker: bool = False, **opts):
+        self.lib = load()
+        self.device = device
+        o = solve_opts(**opts)
+        h = C.c_void_p()
+        check(self.lib.lp_server_create(int(budget_bytes), C.byref(device.ctx), C.byref(o),
+                                        1 if worker else 0, C.byref(h)))
+        self.h = h
+        self._problems = {}
+
+    def submit(self, problem: "Problem") -> int:
+        t = C.c_uint64()
+        check(self.lib.lp_batch_submit(self.h, problem.h, C.byref(t)))
+        self._problems[t.value] = problem
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (lp_result, x, y) for the problem's current LP."""
+        p = self._problems[ticket]
+        m, n, _ = p.dims()
+        x, y = np.zeros(n), np.zeros(m)
+        r = lp_result()
+        rc = check(self.lib.lp_batch_poll(self.h, C.c_uint64(ticket), C.byref(r), dptr(x),
+                                          dptr(y)))
+        if rc == LP_PENDING:
+            return None
+        del self._problems[ticket]
+        return r, x, y
+
+    def pump(self, periods: int = 1) -> int:
+        return check(self.lib.lp_server_pump(self.h, int(periods)))
+
+    def cancel(self, ticket: int):
+        check(self.lib.lp_batch_cancel(self.h, C.c_uint64(ticket)))
+
+    def stats(self):
+        out = np.zeros(10, dtype=np.int64)
+        check(self.lib.lp_server_stats(self.h, out.ctypes.data_as(_I64)))
+        keys = ("admitted", "finished", "periods", "peak_resident_bytes", "launches",
+                "queued", "shape_b0", "shape_b1", "shape_b2", "shape_b3")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def run_all(self, tickets, max_periods: int = 1_000_000):
+        """Drive the device loop (non-worker servers) until every ticket is done."""
+        results = {}
+        pending = list(tickets)
+        for _ in range(max_periods):
+            left = []
+            for t in pending:
+                got = self.poll(t)
+                if got is None:
+                    left.append(t)
+                else:
+                    results[t] = got
+            pending = left
+            if not pending:
+                break
+            self.pump(1)
+        return results
+
+    def close(self):
+        if self.h:
+            self.lib.lp_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

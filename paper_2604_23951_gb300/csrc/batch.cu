@@ -1,22 +1,1317 @@
-// Batched solving and the continuous-batching server (entry points of
-// include/lp.h).  Placeholder until the segmented persistent kernel lands.
+// Batched PDHG and the continuous-batching server (lp_server_* / lp_batch_*).
+//
+// Many independent LPs ("slots") live in one device arena sized by the
+// server's HBM budget.  One persistent launch processes every live slot of a
+// size bucket: a thread-block cluster of CL CTAs owns one slot at a time and
+// runs K iterations of the same restarted reflected Halpern PDHG as the
+// single-LP path (one check iteration, then K - 1 plain ones), with
+// cluster.sync() between the phases (A^T y + primal epilogue, A xbar + dual
+// epilogue, the check's two KKT products, the decision, the restart copy).
+// Reductions are deterministic: warp trees, then the warps of a CTA in
+// order, then the CTAs of the cluster in rank order through distributed
+// shared memory.  A slot's first launch also runs its set-up (Ruiz +
+// Pock-Chambolle scaling, the power iteration for the step, omega_0,
+// initial point).  Between launches the host retires finished slots, copies
+// their results out and admits queued requests into the freed arena space:
+// requests that arrive while others run are admitted as memory frees up and
+// their iterations overlap on the device.
+//
+// Precision: LP_MIXED runs the set-up arithmetic and the SpMV in FP32
+// (FP32 values, FP32 accumulation) and keeps the iterates, anchor,
+// epilogues, reductions and decisions in FP64; LP_FP64 runs everything in
+// FP64.  KKT checks always use the FP64 scaled matrix.
+//
+// Autotuner: for each size bucket (by nonzeros) the server times the
+// candidate (cluster size, CTA size) shapes on its first launches and keeps
+// the fastest per nonzero-iteration.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "device_common.cuh"
 #include "lp_internal.h"
+#include "pdhg_state.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gb300lp {
+
 void set_last_error(const std::string &m);
+const HostLP &problem_current(const lp_problem *lp);
+void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
+                            const std::vector<double> &y, const std::vector<double> &z);
+
+constexpr int ST_SETUP = -2;
+constexpr int kMaxCluster = 8;
+constexpr int kMaxWarps = 16;  // CTAs of up to 512 threads
+
+struct SlotDesc {
+  int m, n;
+  long long nnz;
+  const int *a_rp, *a_ci, *t_rp, *t_ci;
+  const double *a_v0, *t_v0;
+  double *a_v, *t_v;
+  float *a_vf, *t_vf;
+  const double *c0, *lx0, *ux0, *lc0, *uc0;
+  double *c, *lx, *ux, *lc, *uc;
+  double *dr, *dc, *dr2, *dc2;
+  double *x, *x0, *xbar, *xhat, *y, *y0, *yhat;
+  float *xbarf, *yf, *pwf;
+  double *xout, *yout, *zout;
+};
+
+struct BatchConst {
+  int K, ruiz_iters, pock_chambolle, power_iters;
+  long long max_iter;
+  double step_size, primal_weight;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+// control words of the slot a cluster is working on; every CTA keeps its own
+// copy in shared memory, written by rank 0 through distributed shared memory
+// before a cluster barrier, so every control-flow decision is read from the
+// CTA's own shared memory and is identical across the cluster
+struct Ctl {
+  int status, restart_flag, k_base, k_off, halpern, mixed_active;
+  long long t;
+  double tau, sigma, rho;
+};
+
+struct BatchShared {
+  double wsum[kMaxWarps][NQ];
+  double part[kMaxCluster][NQ];  // used on rank 0
+  double total[NQ];
+  Ctl ctl;
+  double bcast;
+};
+
+// thread 0 of a CTA: read the slot's control words from global memory
+// (volatile: no stale L1 copy); the caller synchronizes the CTA
+__device__ __forceinline__ void load_ctl(const State *st, Ctl &c) {
+  const volatile State *v = st;
+  c.status = v->status;
+  c.restart_flag = v->restart_flag;
+  c.k_base = v->k_base;
+  c.k_off = v->k_off;
+  c.halpern = v->halpern;
+  c.mixed_active = v->mixed_active;
+  c.t = v->t;
+  c.tau = v->tau;
+  c.sigma = v->sigma;
+  c.rho = v->rho;
 }
 
+// rank 0 thread 0, after updating *st: copy its control words into the
+// shared memory of every CTA of the cluster (the caller then syncs the cluster)
+__device__ __forceinline__ void bcast_ctl(const State *st, BatchShared &sh,
+                                          cg::cluster_group &cl) {
+  Ctl c;
+  c.status = st->status;
+  c.restart_flag = st->restart_flag;
+  c.k_base = st->k_base;
+  c.k_off = st->k_off;
+  c.halpern = st->halpern;
+  c.mixed_active = st->mixed_active;
+  c.t = st->t;
+  c.tau = st->tau;
+  c.sigma = st->sigma;
+  c.rho = st->rho;
+  for (int r = 0; r < (int)cl.num_blocks(); ++r) cl.map_shared_rank(&sh, r)->ctl = c;
+}
+
+__device__ __forceinline__ Halpern halpern_ctl(const Ctl &c, int j) {
+  double lam = 1.0;
+  if (c.halpern) {
+    int k = (j == 0) ? c.k_base : c.k_off + j;
+    lam = (k + 1.0) / (k + 2.0);
+  }
+  Halpern h;
+  h.a = lam * (1.0 + c.rho);
+  h.b = -lam * c.rho;
+  h.g = 1.0 - lam;
+  return h;
+}
+
+// Deterministic cluster-wide sum of acc[0..nq) (quantity ids qid[]); the
+// result lands in sh.total[qid[q]] of rank 0 (returned to rank 0 thread 0).
+template <int NQL>
+__device__ __forceinline__ void cluster_sum(const double (&acc)[NQL], const int (&qid)[NQL],
+                                            BatchShared &sh, cg::cluster_group &cl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQL; ++q) {
+    double v = warp_sum(acc[q]);
+    if (lane == 0) sh.wsum[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQL) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh.wsum[w][threadIdx.x];
+    BatchShared *r0 = cl.map_shared_rank(&sh, 0);
+    r0->part[cl.block_rank()][threadIdx.x] = s;
+  }
+  cl.sync();
+  if (cl.block_rank() == 0 && threadIdx.x < NQL) {
+    double s = 0.0;
+    for (int r = 0; r < (int)cl.num_blocks(); ++r) s += sh.part[r][threadIdx.x];
+    sh.total[qid[threadIdx.x]] = s;
+  }
+  __syncthreads();
+}
+
+// thread-per-row dot product of row r: sum_k va[k] * vec[ci[k]]
+template <typename T, typename V, typename Acc>
+__device__ __forceinline__ Acc row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
+                                       const T *__restrict__ va, const V *vec, int r) {
+  const int e = rp[r + 1];
+  int k = rp[r];
+  Acc s0 = 0, s1 = 0;
+  for (; k + 3 < e; k += 4) {
+    const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
+    const V g0 = vec[j0], g1 = vec[j1], g2 = vec[j2], g3 = vec[j3];
+    s0 += (Acc)va[k] * (Acc)g0;
+    s1 += (Acc)va[k + 1] * (Acc)g1;
+    s0 += (Acc)va[k + 2] * (Acc)g2;
+    s1 += (Acc)va[k + 3] * (Acc)g3;
+  }
+  for (; k < e; ++k) s0 += (Acc)va[k] * (Acc)vec[ci[k]];
+  return s0 + s1;
+}
+
+// one Ruiz / Pock-Chambolle pass over the rows of a matrix: dnew[r] =
+// dself[r] / sqrt(max or sum_k (dr |a|) dc); S is the arithmetic type
+template <typename S, bool TRANSPOSED, bool SUM>
+__device__ __forceinline__ void scale_rows(int rows, const int *rp, const int *ci,
+                                           const double *a0, const double *dself,
+                                           const double *dother, double *dnew, int gt,
+                                           int gs) {
+  for (int r = gt; r < rows; r += gs) {
+    const S ds = (S)dself[r];
+    S acc = 0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const S v = TRANSPOSED ? ((S)dother[ci[k]] * (S)fabs(a0[k])) * ds
+                             : (ds * (S)fabs(a0[k])) * (S)dother[ci[k]];
+      acc = SUM ? acc + v : (v > acc ? v : acc);
+    }
+    dnew[r] = acc > (S)0 ? (double)(ds / sqrt(acc)) : (double)ds;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// set-up of one slot (scaling, step size, primal weight, initial point)
+
+template <bool MIXED>
+__device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, BatchShared &sh,
+                           cg::cluster_group &cl) {
+  using S = typename std::conditional<MIXED, float, double>::type;
+  const int m = D.m, n = D.n;
+  const int gt = cl.block_rank() * blockDim.x + threadIdx.x;
+  const int gs = cl.num_blocks() * blockDim.x;
+  double *dr = D.dr, *dc = D.dc, *dr2 = D.dr2, *dc2 = D.dc2;
+  for (int i = gt; i < m; i += gs) dr[i] = 1.0;
+  for (int j = gt; j < n; j += gs) dc[j] = 1.0;
+  cl.sync();
+  for (int it = 0; it < C.ruiz_iters; ++it) {
+    scale_rows<S, false, false>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
+    scale_rows<S, true, false>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
+    cl.sync();
+    double *t = dr; dr = dr2; dr2 = t;
+    t = dc; dc = dc2; dc2 = t;
+  }
+  if (C.pock_chambolle) {
+    scale_rows<S, false, true>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
+    scale_rows<S, true, true>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
+    cl.sync();
+    double *t = dr; dr = dr2; dr2 = t;
+    t = dc; dc = dc2; dc2 = t;
+  }
+  if (dr != D.dr) {
+    for (int i = gt; i < m; i += gs) D.dr[i] = dr[i];
+    for (int j = gt; j < n; j += gs) D.dc[j] = dc[j];
+    cl.sync();
+  }
+  dr = D.dr;
+  dc = D.dc;
+  // scaled problem; norms of c~ and bhat~
+  double acc[2] = {0.0, 0.0};
+  for (int i = gt; i < m; i += gs) {
+    const double d = dr[i];
+    for (int k = D.a_rp[i]; k < D.a_rp[i + 1]; ++k) {
+      const double v = (d * D.a_v0[k]) * dc[D.a_ci[k]];
+      D.a_v[k] = v;
+      if (MIXED) D.a_vf[k] = (float)v;
+    }
+    const double l = d * D.lc0[i], u = d * D.uc0[i];
+    D.lc[i] = l;
+    D.uc[i] = u;
+    const bool lf = isfinite(l), uf = isfinite(u);
+    if (lf) acc[1] += l * l;
+    if (uf && !(lf && l == u)) acc[1] += u * u;
+  }
+  for (int j = gt; j < n; j += gs) {
+    const double d = dc[j];
+    for (int k = D.t_rp[j]; k < D.t_rp[j + 1]; ++k) {
+      const double v = (dr[D.t_ci[k]] * D.t_v0[k]) * d;
+      D.t_v[k] = v;
+      if (MIXED) D.t_vf[k] = (float)v;
+    }
+    const double cj = d * D.c0[j];
+    D.c[j] = cj;
+    D.lx[j] = D.lx0[j] / d;
+    D.ux[j] = D.ux0[j] / d;
+    acc[0] += cj * cj;
+  }
+  {
+    const int qid[2] = {Q_CN, Q_BN};
+    cluster_sum<2>(acc, qid, sh, cl);
+  }
+  // power iteration on A~^T A~ (v in pwf / xhat, u in yf / yhat, w in xbarf / xbar)
+  double eta = C.step_size;
+  if (!(eta > 0.0)) {
+    double pw = 0.0;
+    if (m > 0 && n > 0) {
+      const double v0 = 1.0 / sqrt((double)n);
+      for (int j = gt; j < n; j += gs) {
+        if (MIXED) D.pwf[j] = (float)v0; else D.xhat[j] = v0;
+      }
+      cl.sync();
+      for (int it = 0; it <= C.power_iters; ++it) {
+        for (int i = gt; i < m; i += gs) {
+          if (MIXED) D.yf[i] = row_dot<float, float, float>(D.a_rp, D.a_ci, D.a_vf, D.pwf, i);
+          else D.yhat[i] = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xhat, i);
+        }
+        cl.sync();
+        double a2[1] = {0.0};
+        if (it == C.power_iters) {
+          for (int i = gt; i < m; i += gs) {
+            const double u = MIXED ? (double)D.yf[i] : D.yhat[i];
+            a2[0] += u * u;
+          }
+          const int qid[1] = {Q_PW};
+          cluster_sum<1>(a2, qid, sh, cl);
+          if (cl.block_rank() == 0 && threadIdx.x == 0) pw = sqrt(sh.total[Q_PW]);
+          break;
+        }
+        for (int j = gt; j < n; j += gs) {
+          if (MIXED) {
+            const float w = row_dot<float, float, float>(D.t_rp, D.t_ci, D.t_vf, D.yf, j);
+            D.xbarf[j] = w;
+            a2[0] += (double)w * (double)w;
+          } else {
+            const double w = row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.yhat, j);
+            D.xbar[j] = w;
+            a2[0] += w * w;
+          }
+        }
+        const int qid[1] = {Q_PW};
+        cluster_sum<1>(a2, qid, sh, cl);
+        // broadcast ||w|| to every CTA's shared memory
+        if (cl.block_rank() == 0 && threadIdx.x == 0) {
+          const double nwv = sqrt(sh.total[Q_PW]);
+          for (int r = 0; r < (int)cl.num_blocks(); ++r) cl.map_shared_rank(&sh, r)->bcast = nwv;
+        }
+        cl.sync();
+        const double nw = sh.bcast;
+        for (int j = gt; j < n; j += gs) {
+          if (MIXED) D.pwf[j] = nw > 0.0 ? (float)((double)D.xbarf[j] / nw) : 0.0f;
+          else D.xhat[j] = nw > 0.0 ? D.xbar[j] / nw : 0.0;
+        }
+        cl.sync();
+      }
+    }
+    if (cl.block_rank() == 0 && threadIdx.x == 0) eta = pw > 0.0 ? 0.998 / pw : 1.0;
+  }
+  // initial point and state
+  for (int j = gt; j < n; j += gs) {
+    const double v = clampd(0.0, D.lx[j], D.ux[j]);
+    D.x[j] = v;
+    D.x0[j] = v;
+  }
+  for (int i = gt; i < m; i += gs) {
+    D.y[i] = 0.0;
+    D.y0[i] = 0.0;
+    if (MIXED) D.yf[i] = 0.0f;
+  }
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    const double cn = sqrt(sh.total[Q_CN]), bn = sqrt(sh.total[Q_BN]);
+    const double om = C.primal_weight > 0 ? C.primal_weight : ((cn > 0 && bn > 0) ? cn / bn : 1.0);
+    st->eta = eta;
+    st->omega = om;
+    st->tau = eta / om;
+    st->sigma = eta * om;
+    st->t = 0;
+    st->iters = 0;
+    st->k_base = 0;
+    st->k_off = 0;
+    st->restarts = 0;
+    st->restart_flag = 0;
+    st->r0 = st->r_prev = st->last_r = 0.0;
+    st->rel_kkt = INFINITY;
+    st->status = ST_RUNNING;
+    bcast_ctl(st, sh, cl);
+  }
+  cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// K iterations of one slot
+
+template <bool MIXED>
+__device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, BatchShared &sh,
+                             cg::cluster_group &cl) {
+  const int m = D.m, n = D.n;
+  const int gt = cl.block_rank() * blockDim.x + threadIdx.x;
+  const int gs = cl.num_blocks() * blockDim.x;
+  for (int j = 0; j < C.K; ++j) {
+    if (sh.ctl.status != ST_RUNNING) break;
+    const bool check = (j == 0);
+    if (check && sh.ctl.t >= C.max_iter) {
+      // LP_ITER_LIMIT: the last check's point is the answer
+      cl.sync();
+      if (cl.block_rank() == 0 && threadIdx.x == 0) {
+        st->status = 1;
+        st->iters = st->t;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) sh.ctl.status = 1;
+      __syncthreads();
+      break;
+    }
+    const Halpern hc = halpern_ctl(sh.ctl, j);
+    const double tau = sh.ctl.tau, sigma = sh.ctl.sigma;
+    const bool f32 = MIXED && sh.ctl.mixed_active;  // FP32 SpMV until the FP64 switch
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // K1: rows of A^T
+    for (int c = gt; c < n; c += gs) {
+      double g;
+      if (f32) g = (double)row_dot<float, float, float>(D.t_rp, D.t_ci, D.t_vf, D.yf, c);
+      else g = row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.y, c);
+      const double xk = D.x[c];
+      const double xh = clampd(fma(-tau, D.c[c] - g, xk), D.lx[c], D.ux[c]);
+      const double xb = fma(2.0, xh, -xk);
+      const double a0 = D.x0[c];
+      D.x[c] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
+      if (f32) D.xbarf[c] = (float)xb; else D.xbar[c] = xb;
+      if (check) {
+        D.xhat[c] = xh;
+        acc[0] += (xk - xh) * (xk - xh);
+        acc[1] += (xh - a0) * (xh - a0);
+      }
+    }
+    cl.sync();
+    // K2: rows of A
+    for (int r = gt; r < m; r += gs) {
+      double h;
+      if (f32) h = (double)row_dot<float, float, float>(D.a_rp, D.a_ci, D.a_vf, D.xbarf, r);
+      else h = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xbar, r);
+      const double yk = D.y[r];
+      const double v = fma(-sigma, h, yk);
+      const double yh = v + clampd(-v, sigma * D.lc[r], sigma * D.uc[r]);
+      const double a0 = D.y0[r];
+      const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
+      D.y[r] = yn;
+      if (f32) D.yf[r] = (float)yn;
+      if (check) {
+        D.yhat[r] = yh;
+        acc[2] += (yk - yh) * (yk - yh);
+        acc[3] += (yh - a0) * (yh - a0);
+      }
+    }
+    cl.sync();
+    if (!check) continue;
+    // K3: KKT on the unscaled problem, FP64 scaled matrix
+    for (int r = gt; r < m; r += gs) {
+      const double d = D.dr[r];
+      const double ax = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xhat, r) / d;
+      const double lo = D.lc0[r], hi = D.uc0[r];
+      const double pr = clampd(ax, lo, hi);
+      acc[4] += (ax - pr) * (ax - pr);
+      const double yv = d * D.yhat[r];
+      double yp = yv;
+      if (!isfinite(lo)) yp = fmin(yp, 0.0);
+      if (!isfinite(hi)) yp = fmax(yp, 0.0);
+      acc[5] += (yv - yp) * (yv - yp);
+      acc[6] += support_term(yp, lo, hi);
+    }
+    for (int c = gt; c < n; c += gs) {
+      const double d = D.dc[c];
+      const double g = (D.c[c] - row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.yhat, c)) / d;
+      const double lo = D.lx0[c], hi = D.ux0[c];
+      const bool lf = isfinite(lo), uf = isfinite(hi);
+      double lam = g;
+      if (!lf && !uf) lam = 0.0;
+      else if (lf && !uf) lam = fmax(lam, 0.0);
+      else if (!lf && uf) lam = fmin(lam, 0.0);
+      acc[7] += (g - lam) * (g - lam);
+      acc[8] += support_term(lam, lo, hi);
+      acc[9] += D.c0[c] * (d * D.xhat[c]);
+      D.zout[c] = g;
+    }
+    {
+      const int qid[10] = {Q_XRES, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P};
+      cluster_sum<10>(acc, qid, sh, cl);
+    }
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
+      check_update(st, sh.total, false);
+      bcast_ctl(st, sh, cl);
+    }
+    cl.sync();
+    if (sh.ctl.status != ST_RUNNING) break;
+    if (sh.ctl.restart_flag) {
+      for (int c = gt; c < n; c += gs) {
+        const double v = D.xhat[c];
+        D.x[c] = v;
+        D.x0[c] = v;
+      }
+      for (int r = gt; r < m; r += gs) {
+        const double v = D.yhat[r];
+        D.y[r] = v;
+        D.y0[r] = v;
+        if (MIXED) D.yf[r] = (float)v;
+      }
+      cl.sync();
+    }
+  }
+  // finished slots: unscaled answer (the last check's T(z))
+  if (sh.ctl.status != ST_RUNNING && sh.ctl.status != ST_SETUP) {
+    for (int c = gt; c < n; c += gs) D.xout[c] = D.dc[c] * D.xhat[c];
+    for (int r = gt; r < m; r += gs) D.yout[r] = D.dr[r] * D.yhat[r];
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(512) k_batch(const SlotDesc *__restrict__ desc, State *states,
+                                               const int *__restrict__ order, int nord,
+                                               BatchConst C) {
+  __shared__ BatchShared sh;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = (int)cl.num_blocks();
+  const int ncl = gridDim.x / CL;
+  const int cid = blockIdx.x / CL;
+  for (int oi = cid; oi < nord; oi += ncl) {
+    const int s = order[oi];
+    const SlotDesc &D = desc[s];
+    State *st = states + s;
+    // the slot's state was written by an earlier launch: every CTA reads the
+    // same control words
+    if (threadIdx.x == 0) load_ctl(st, sh.ctl);
+    __syncthreads();
+    if (sh.ctl.status == ST_SETUP) slot_setup<MIXED>(D, st, C, sh, cl);
+    if (sh.ctl.status == ST_RUNNING) slot_iterate<MIXED>(D, st, C, sh, cl);
+    cl.sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: arena, slots, autotuner, server loop
+
+struct Shape {
+  int cl, block;
+};
+
+static const Shape kShapes[] = {{1, 128}, {1, 256}, {2, 256}, {4, 256}, {8, 256}, {8, 512}};
+constexpr int kNumBuckets = 4;
+
+static int bucket_of(long long nnz) {
+  if (nnz < 16384) return 0;
+  if (nnz < 131072) return 1;
+  if (nnz < 1048576) return 2;
+  return 3;
+}
+
+// candidate shapes per bucket (indices into kShapes)
+static std::vector<int> candidates(int bucket) {
+  switch (bucket) {
+    case 0: return {0, 1};
+    case 1: return {0, 1, 2};
+    case 2: return {1, 2, 3, 4};
+    default: return {3, 4, 5};
+  }
+}
+
+struct Tuner {
+  std::vector<int> cand;
+  std::vector<double> best_ns;  // per candidate: best ns per nonzero-iteration
+  int next = 0;
+  int chosen = -1;
+  int trials = 0;
+  Shape pick() {
+    if (chosen >= 0) return kShapes[chosen];
+    return kShapes[cand[next]];
+  }
+  int current() const { return chosen >= 0 ? chosen : cand[next]; }
+  void record(double ns_per_nnz_iter) {
+    if (chosen >= 0) return;
+    best_ns[next] = std::min(best_ns[next], ns_per_nnz_iter);
+    ++trials;
+    next = (next + 1) % (int)cand.size();
+    if (trials >= 2 * (int)cand.size()) {
+      int b = 0;
+      for (int q = 1; q < (int)cand.size(); ++q)
+        if (best_ns[q] < best_ns[b]) b = q;
+      chosen = cand[b];
+    }
+  }
+};
+
+// first-fit allocator over [0, size) with coalescing of free ranges
+struct RangeAlloc {
+  std::map<size_t, size_t> free_;  // offset -> bytes
+  void init(size_t size) {
+    free_.clear();
+    free_[0] = size;
+  }
+  bool alloc(size_t bytes, size_t &off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        off = it->first;
+        size_t rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+// host copy of one request, packed in the slot's device layout
+struct Packed {
+  int m = 0, n = 0;
+  long long nnz = 0;
+  std::vector<unsigned char> blob;  // bytes copied to the slot's arena block
+  size_t bytes = 0;
+  SlotDesc rel{};  // pointers as offsets from the block start
+  double bnorm = 0, cnorm = 0, off = 0;
+};
+
+static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+static void pack_request(const HostLP &h, Packed &p) {
+  p.m = h.m;
+  p.n = h.n;
+  p.nnz = h.nnz();
+  const int m = h.m, n = h.n;
+  const long long nnz = h.nnz();
+  size_t cur = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = cur;
+    cur += align16(std::max<size_t>(bytes, 16));
+    return o;
+  };
+  SlotDesc &r = p.rel;
+  auto P = [](size_t o) { return reinterpret_cast<void *>(o); };
+  size_t o_arp = take(sizeof(int) * (m + 1)), o_aci = take(sizeof(int) * nnz);
+  size_t o_trp = take(sizeof(int) * (n + 1)), o_tci = take(sizeof(int) * nnz);
+  size_t o_av0 = take(8 * nnz), o_tv0 = take(8 * nnz), o_av = take(8 * nnz), o_tv = take(8 * nnz);
+  size_t o_avf = take(4 * nnz), o_tvf = take(4 * nnz);
+  size_t o_c0 = take(8 * n), o_lx0 = take(8 * n), o_ux0 = take(8 * n);
+  size_t o_lc0 = take(8 * m), o_uc0 = take(8 * m);
+  r.m = m;
+  r.n = n;
+  r.nnz = nnz;
+  r.a_rp = (const int *)P(o_arp);
+  r.a_ci = (const int *)P(o_aci);
+  r.t_rp = (const int *)P(o_trp);
+  r.t_ci = (const int *)P(o_tci);
+  r.a_v0 = (const double *)P(o_av0);
+  r.t_v0 = (const double *)P(o_tv0);
+  r.a_v = (double *)P(o_av);
+  r.t_v = (double *)P(o_tv);
+  r.a_vf = (float *)P(o_avf);
+  r.t_vf = (float *)P(o_tvf);
+  r.c0 = (const double *)P(o_c0);
+  r.lx0 = (const double *)P(o_lx0);
+  r.ux0 = (const double *)P(o_ux0);
+  r.lc0 = (const double *)P(o_lc0);
+  r.uc0 = (const double *)P(o_uc0);
+  const size_t input_end = cur;
+  double **colv[] = {&r.c, &r.lx, &r.ux, &r.dc, &r.dc2, &r.x, &r.x0, &r.xbar, &r.xhat, &r.xout,
+                     &r.zout};
+  for (double **q : colv) *q = (double *)P(take(8 * n));
+  double **rowv[] = {&r.lc, &r.uc, &r.dr, &r.dr2, &r.y, &r.y0, &r.yhat, &r.yout};
+  for (double **q : rowv) *q = (double *)P(take(8 * m));
+  r.xbarf = (float *)P(take(4 * n));
+  r.pwf = (float *)P(take(4 * n));
+  r.yf = (float *)P(take(4 * m));
+  p.bytes = align16(cur);
+  // the host blob covers the inputs; the rest of the block is device work space
+  p.blob.assign(input_end, 0);
+  unsigned char *b = p.blob.data();
+  int *arp = (int *)(b + o_arp), *aci = (int *)(b + o_aci);
+  int *trp = (int *)(b + o_trp), *tci = (int *)(b + o_tci);
+  double *av0 = (double *)(b + o_av0), *tv0 = (double *)(b + o_tv0);
+  for (int i = 0; i <= m; ++i) arp[i] = (int)h.row_ptr[i];
+  for (long long k = 0; k < nnz; ++k) {
+    aci[k] = h.col_idx[k];
+    av0[k] = h.val[k];
+  }
+  // transpose (rows of A^T in column order, entries by row)
+  std::vector<int> cnt(n + 1, 0);
+  for (long long k = 0; k < nnz; ++k) cnt[h.col_idx[k] + 1]++;
+  for (int j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
+  for (int j = 0; j <= n; ++j) trp[j] = cnt[j];
+  for (int i = 0; i < m; ++i)
+    for (int64_t k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) {
+      int j = h.col_idx[k];
+      tci[cnt[j]] = i;
+      tv0[cnt[j]] = h.val[k];
+      ++cnt[j];
+    }
+  std::memcpy(b + o_c0, h.c.data(), 8 * n);
+  std::memcpy(b + o_lx0, h.col_lo.data(), 8 * n);
+  std::memcpy(b + o_ux0, h.col_hi.data(), 8 * n);
+  std::memcpy(b + o_lc0, h.row_lo.data(), 8 * m);
+  std::memcpy(b + o_uc0, h.row_hi.data(), 8 * m);
+  double bn2 = 0, cn2 = 0;
+  for (int i = 0; i < m; ++i) {
+    bool lf = std::isfinite(h.row_lo[i]), uf = std::isfinite(h.row_hi[i]);
+    if (lf) bn2 += h.row_lo[i] * h.row_lo[i];
+    if (uf && !(lf && h.row_lo[i] == h.row_hi[i])) bn2 += h.row_hi[i] * h.row_hi[i];
+  }
+  for (int j = 0; j < n; ++j) cn2 += h.c[j] * h.c[j];
+  p.bnorm = std::sqrt(bn2);
+  p.cnorm = std::sqrt(cn2);
+  p.off = h.off;
+}
+
+static SlotDesc relocate(const SlotDesc &rel, unsigned char *base) {
+  SlotDesc d = rel;
+  auto R = [base](auto p) { return reinterpret_cast<decltype(p)>(base + reinterpret_cast<size_t>(p)); };
+  d.a_rp = R(rel.a_rp);
+  d.a_ci = R(rel.a_ci);
+  d.t_rp = R(rel.t_rp);
+  d.t_ci = R(rel.t_ci);
+  d.a_v0 = R(rel.a_v0);
+  d.t_v0 = R(rel.t_v0);
+  d.a_v = R(rel.a_v);
+  d.t_v = R(rel.t_v);
+  d.a_vf = R(rel.a_vf);
+  d.t_vf = R(rel.t_vf);
+  d.c0 = R(rel.c0);
+  d.lx0 = R(rel.lx0);
+  d.ux0 = R(rel.ux0);
+  d.lc0 = R(rel.lc0);
+  d.uc0 = R(rel.uc0);
+  d.c = R(rel.c);
+  d.lx = R(rel.lx);
+  d.ux = R(rel.ux);
+  d.lc = R(rel.lc);
+  d.uc = R(rel.uc);
+  d.dr = R(rel.dr);
+  d.dc = R(rel.dc);
+  d.dr2 = R(rel.dr2);
+  d.dc2 = R(rel.dc2);
+  d.x = R(rel.x);
+  d.x0 = R(rel.x0);
+  d.xbar = R(rel.xbar);
+  d.xhat = R(rel.xhat);
+  d.y = R(rel.y);
+  d.y0 = R(rel.y0);
+  d.yhat = R(rel.yhat);
+  d.xbarf = R(rel.xbarf);
+  d.yf = R(rel.yf);
+  d.pwf = R(rel.pwf);
+  d.xout = R(rel.xout);
+  d.yout = R(rel.yout);
+  d.zout = R(rel.zout);
+  return d;
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  lp_problem *lp = nullptr;
+  Packed pk;
+  double t_submit = 0;
+  bool cancelled = false;
+};
+
+struct Done {
+  lp_result res{};
+  std::vector<double> x, y, z;
+  lp_problem *lp = nullptr;
+};
+
+struct Slot {
+  bool used = false;
+  uint64_t ticket = 0;
+  lp_problem *lp = nullptr;
+  size_t off = 0, bytes = 0;
+  int m = 0, n = 0;
+  long long nnz = 0;
+  int bucket = 0;
+  SlotDesc desc{};
+  double t_submit = 0, t_admit = 0;
+  bool cancel = false;
+};
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace gb300lp
+
+using namespace gb300lp;
+
+struct lp_server {
+  lp_device_ctx ctx{};
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  cudaStream_t bs[kNumBuckets] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_b0[kNumBuckets] = {}, ev_b1[kNumBuckets] = {};
+  int device = 0, sm_count = 0;
+  lp_solve_opts opts{};
+  unsigned char *arena = nullptr;
+  size_t arena_bytes = 0;
+  RangeAlloc ralloc;
+  int max_slots = 0;
+  SlotDesc *d_desc = nullptr;
+  State *d_state = nullptr;
+  int *d_order = nullptr;
+  State *h_state = nullptr;  // pinned mirror
+  int *h_order = nullptr;    // pinned
+  std::vector<Slot> slots;
+  std::deque<Request> queue;
+  std::map<uint64_t, Done> done;
+  std::map<uint64_t, int> where;  // ticket -> 0 queued, 1 running, 2 done
+  uint64_t next_ticket = 1;
+  Tuner tuner[kNumBuckets];
+  long long n_admitted = 0, n_finished = 0, n_periods = 0, launches = 0;
+  size_t resident = 0, peak_resident = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  bool use_worker = false;
+  std::string worker_err;
+};
+
+namespace {
+
+void server_state_init(const lp_server *srv, State &st, const Packed &pk) {
+  std::memset(&st, 0, sizeof(st));
+  const lp_solve_opts &o = srv->opts;
+  st.rho = o.rho;
+  st.beta_suff = o.beta_suff;
+  st.beta_nec = o.beta_nec;
+  st.beta_art = o.beta_art;
+  st.theta = o.theta;
+  st.eps_rel = o.eps_rel;
+  st.bnorm = pk.bnorm;
+  st.cnorm = pk.cnorm;
+  st.off = pk.off;
+  st.K = std::max(1, o.check_every);
+  st.halpern = o.halpern ? 1 : 0;
+  st.restarts_on = o.restarts ? 1 : 0;
+  st.status = ST_SETUP;
+  st.mixed_active = o.precision == LP_MIXED ? 1 : 0;
+  st.stall = 0;
+  st.best_rel = INFINITY;
+  st.t_switch = -1;
+}
+
+// Admit queued requests while a slot and arena space are free (caller holds mu)
+void admit(lp_server *srv) {
+  while (!srv->queue.empty()) {
+    Request &rq = srv->queue.front();
+    if (rq.cancelled) {
+      Done d;
+      d.res.termination = LP_CANCELLED;
+      srv->done[rq.ticket] = std::move(d);
+      srv->where[rq.ticket] = 2;
+      srv->queue.pop_front();
+      continue;
+    }
+    int sid = -1;
+    for (int q = 0; q < srv->max_slots; ++q)
+      if (!srv->slots[q].used) {
+        sid = q;
+        break;
+      }
+    if (sid < 0) return;
+    size_t off = 0;
+    if (!srv->ralloc.alloc(rq.pk.bytes, off)) return;
+    Slot &sl = srv->slots[sid];
+    sl = Slot();
+    sl.used = true;
+    sl.ticket = rq.ticket;
+    sl.lp = rq.lp;
+    sl.off = off;
+    sl.bytes = rq.pk.bytes;
+    sl.m = rq.pk.m;
+    sl.n = rq.pk.n;
+    sl.nnz = rq.pk.nnz;
+    sl.bucket = bucket_of(rq.pk.nnz);
+    sl.t_submit = rq.t_submit;
+    sl.t_admit = now_s();
+    sl.desc = relocate(rq.pk.rel, srv->arena + off);
+    CK(cudaMemcpyAsync(srv->arena + off, rq.pk.blob.data(), rq.pk.blob.size(),
+                       cudaMemcpyHostToDevice, srv->s));
+    CK(cudaMemcpyAsync(srv->d_desc + sid, &sl.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice,
+                       srv->s));
+    server_state_init(srv, srv->h_state[sid], rq.pk);
+    CK(cudaMemcpyAsync(srv->d_state + sid, &srv->h_state[sid], sizeof(State),
+                       cudaMemcpyHostToDevice, srv->s));
+    CK(cudaStreamSynchronize(srv->s));  // the pageable blob may be freed next
+    srv->where[rq.ticket] = 1;
+    srv->resident += rq.pk.bytes;
+    srv->peak_resident = std::max(srv->peak_resident, srv->resident);
+    ++srv->n_admitted;
+    srv->queue.pop_front();
+  }
+}
+
+void launch_bucket(lp_server *srv, int b, const int *d_order, int nord, const Shape &sh,
+                   cudaStream_t st) {
+  BatchConst C;
+  C.K = std::max(1, srv->opts.check_every);
+  C.ruiz_iters = srv->opts.ruiz_iters;
+  C.pock_chambolle = srv->opts.pock_chambolle;
+  C.power_iters = srv->opts.power_iters;
+  C.max_iter = srv->opts.max_iter;
+  C.step_size = srv->opts.step_size;
+  C.primal_weight = srv->opts.primal_weight;
+  const int max_clusters = std::max(1, srv->sm_count * 4 / sh.cl);
+  const int nclusters = std::min(nord, max_clusters);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * sh.cl);
+  cfg.blockDim = dim3(sh.block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = sh.cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (srv->opts.precision == LP_MIXED)
+    CK(cudaLaunchKernelEx(&cfg, k_batch<true>, (const SlotDesc *)srv->d_desc, srv->d_state,
+                          d_order, nord, C));
+  else
+    CK(cudaLaunchKernelEx(&cfg, k_batch<false>, (const SlotDesc *)srv->d_desc, srv->d_state,
+                          d_order, nord, C));
+  srv->launches++;
+  (void)b;
+}
+
+// One launch period over every live slot; then retire finished slots.
+// Caller holds mu.  Returns the number of live + queued requests.
+int period(lp_server *srv) {
+  admit(srv);
+  std::vector<int> lists[kNumBuckets];
+  for (int q = 0; q < srv->max_slots; ++q) {
+    Slot &sl = srv->slots[q];
+    if (!sl.used) continue;
+    if (sl.cancel) continue;
+    lists[sl.bucket].push_back(q);
+  }
+  // order within a bucket: largest first (longest slots start first)
+  int total = 0;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    std::sort(lists[b].begin(), lists[b].end(),
+              [&](int a, int c) { return srv->slots[a].nnz > srv->slots[c].nnz; });
+    total += (int)lists[b].size();
+  }
+  if (total > 0) {
+    int pos = 0;
+    int start[kNumBuckets];
+    for (int b = 0; b < kNumBuckets; ++b) {
+      start[b] = pos;
+      for (int q : lists[b]) srv->h_order[pos++] = q;
+    }
+    CK(cudaMemcpyAsync(srv->d_order, srv->h_order, sizeof(int) * total, cudaMemcpyHostToDevice,
+                       srv->s));
+    CK(cudaEventRecord(srv->ev_fork, srv->s));
+    Shape used[kNumBuckets];
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (lists[b].empty()) continue;
+      CK(cudaStreamWaitEvent(srv->bs[b], srv->ev_fork, 0));
+      used[b] = srv->tuner[b].pick();
+      // few live slots: give each the widest cluster so the tail does not run
+      // on a handful of SMs
+      if ((int)lists[b].size() * used[b].cl * 4 < srv->sm_count && srv->tuner[b].chosen >= 0)
+        used[b] = Shape{8, 256};
+      CK(cudaEventRecord(srv->ev_b0[b], srv->bs[b]));
+      launch_bucket(srv, b, srv->d_order + start[b], (int)lists[b].size(), used[b], srv->bs[b]);
+      CK(cudaEventRecord(srv->ev_b1[b], srv->bs[b]));
+      CK(cudaStreamWaitEvent(srv->s, srv->ev_b1[b], 0));
+    }
+    int hi = 0;
+    for (int q = 0; q < srv->max_slots; ++q)
+      if (srv->slots[q].used) hi = q + 1;
+    CK(cudaMemcpyAsync(srv->h_state, srv->d_state, sizeof(State) * hi, cudaMemcpyDeviceToHost,
+                       srv->s));
+    CK(cudaStreamSynchronize(srv->s));
+    ++srv->n_periods;
+    // autotuner bookkeeping: ns per nonzero-iteration of the period
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (lists[b].empty()) continue;
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, srv->ev_b0[b], srv->ev_b1[b]));
+      double work = 0;
+      for (int q : lists[b]) work += (double)std::max<long long>(srv->slots[q].nnz, 1);
+      work *= std::max(1, srv->opts.check_every);
+      srv->tuner[b].record(1e6 * ms / work);
+    }
+  }
+  // retire finished (or cancelled) slots
+  const double tnow = now_s();
+  for (int q = 0; q < srv->max_slots; ++q) {
+    Slot &sl = srv->slots[q];
+    if (!sl.used) continue;
+    const State &S = srv->h_state[q];
+    bool finished = S.status >= 0;
+    bool timeout = srv->opts.time_limit_s > 0 && tnow - sl.t_admit > srv->opts.time_limit_s;
+    if (!finished && !timeout && !sl.cancel) continue;
+    Done d;
+    d.lp = sl.lp;
+    d.x.assign(sl.n, 0.0);
+    d.y.assign(sl.m, 0.0);
+    d.z.assign(sl.n, 0.0);
+    if (finished) {
+      if (sl.n) {
+        CK(cudaMemcpy(d.x.data(), sl.desc.xout, 8 * sl.n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(d.z.data(), sl.desc.zout, 8 * sl.n, cudaMemcpyDeviceToHost));
+      }
+      if (sl.m) CK(cudaMemcpy(d.y.data(), sl.desc.yout, 8 * sl.m, cudaMemcpyDeviceToHost));
+    }
+    lp_result &r = d.res;
+    r.termination = sl.cancel ? LP_CANCELLED : (finished ? S.status : LP_TIME_LIMIT);
+    r.restarts = S.restarts;
+    r.iterations = finished ? S.iters : S.t;
+    r.rel_kkt = S.rel_kkt;
+    r.rel_p = S.rel_p;
+    r.rel_d = S.rel_d;
+    r.rel_gap = S.rel_gap;
+    r.r_p = S.r_p;
+    r.r_d = S.r_d;
+    r.gap = S.gap;
+    r.primal_obj = S.pobj;
+    r.dual_obj = S.dobj;
+    r.eta = S.eta;
+    r.omega = S.omega;
+    r.t_setup_s = sl.t_admit - sl.t_submit;  // queueing delay
+    r.t_solve_s = tnow - sl.t_admit;
+    r.t_total_s = tnow - sl.t_submit;
+    r.kernel_launches = srv->launches;
+    r.fp32_iterations = srv->opts.precision == LP_MIXED
+                            ? (S.t_switch >= 0 ? S.t_switch : r.iterations) : 0;
+    srv->done[sl.ticket] = std::move(d);
+    srv->where[sl.ticket] = 2;
+    srv->ralloc.release(sl.off, sl.bytes);
+    srv->resident -= sl.bytes;
+    sl.used = false;
+    ++srv->n_finished;
+  }
+  admit(srv);
+  int live = (int)srv->queue.size();
+  for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
+  return live;
+}
+
+void worker_main(lp_server *srv) {
+  cudaSetDevice(srv->device);
+  std::unique_lock<std::mutex> lk(srv->mu);
+  while (!srv->stop) {
+    int live = (int)srv->queue.size();
+    for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
+    if (live == 0) {
+      srv->cv.wait_for(lk, std::chrono::milliseconds(50));
+      continue;
+    }
+    try {
+      period(srv);
+    } catch (const std::exception &e) {
+      srv->worker_err = e.what();
+      srv->stop = true;
+    }
+    srv->cv.notify_all();
+    // let submitters / pollers in between periods
+    lk.unlock();
+    std::this_thread::yield();
+    lk.lock();
+  }
+  srv->cv.notify_all();
+}
+
+}  // namespace
+
 extern "C" {
-int lp_server_create(size_t, const lp_device_ctx *, const lp_solve_opts *, int32_t,
-                     lp_server **out) {
-  if (out) *out = nullptr;
-  gb300lp::set_last_error("batched server not available in this build");
-  return LP_ERR_STATE;
+
+int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp_solve_opts *opts,
+                     int32_t worker, lp_server **out) {
+  if (!out) {
+    set_last_error("out is NULL");
+    return LP_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (hbm_budget_bytes < (1u << 20)) {
+    set_last_error("budget below 1 MiB");
+    return LP_ERR_BUDGET;
+  }
+  lp_server *srv = new lp_server();
+  try {
+    if (dev) srv->ctx = *dev;
+    srv->device = srv->ctx.device;
+    lp_solve_opts_default(&srv->opts);
+    if (opts) srv->opts = *opts;
+    srv->opts.x_init = nullptr;
+    srv->opts.y_init = nullptr;
+    CK(cudaSetDevice(srv->device));
+    CK(cudaDeviceGetAttribute(&srv->sm_count, cudaDevAttrMultiProcessorCount, srv->device));
+    if (srv->ctx.stream) {
+      srv->s = static_cast<cudaStream_t>(srv->ctx.stream);
+    } else {
+      CK(cudaStreamCreateWithFlags(&srv->s, cudaStreamNonBlocking));
+      srv->own_stream = true;
+    }
+    for (int b = 0; b < kNumBuckets; ++b) {
+      CK(cudaStreamCreateWithFlags(&srv->bs[b], cudaStreamNonBlocking));
+      CK(cudaEventCreate(&srv->ev_b0[b]));
+      CK(cudaEventCreate(&srv->ev_b1[b]));
+      srv->tuner[b].cand = candidates(b);
+      srv->tuner[b].best_ns.assign(srv->tuner[b].cand.size(), 1e300);
+    }
+    CK(cudaEventCreateWithFlags(&srv->ev_fork, cudaEventDisableTiming));
+    // the budget covers the slot arena and the slot tables
+    srv->max_slots = 4096;
+    const size_t tables = srv->max_slots * (sizeof(SlotDesc) + sizeof(State) + sizeof(int)) + 4096;
+    if (hbm_budget_bytes <= tables + (1u << 16)) {
+      throw std::runtime_error("budget too small for the slot tables");
+    }
+    srv->arena_bytes = (hbm_budget_bytes - tables) & ~size_t(255);
+    void *mem = nullptr;
+    if (srv->ctx.alloc) {
+      mem = srv->ctx.alloc(hbm_budget_bytes, srv->ctx.user);
+      if (!mem) {
+        delete srv;
+        set_last_error("device allocation of the budget failed");
+        return LP_ERR_OOM;
+      }
+    } else {
+      cudaError_t e = cudaMalloc(&mem, hbm_budget_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete srv;
+        set_last_error(std::string("device allocation of the budget failed: ") +
+                       cudaGetErrorString(e));
+        return LP_ERR_OOM;
+      }
+    }
+    unsigned char *base = static_cast<unsigned char *>(mem);
+    srv->arena = base;
+    srv->d_desc = reinterpret_cast<SlotDesc *>(base + srv->arena_bytes);
+    srv->d_state = reinterpret_cast<State *>(reinterpret_cast<unsigned char *>(srv->d_desc) +
+                                             srv->max_slots * sizeof(SlotDesc));
+    srv->d_order = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(srv->d_state) +
+                                           srv->max_slots * sizeof(State));
+    srv->ralloc.init(srv->arena_bytes);
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_state), sizeof(State) * srv->max_slots,
+                     cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_order), sizeof(int) * srv->max_slots,
+                     cudaHostAllocDefault));
+    std::memset(srv->h_state, 0, sizeof(State) * srv->max_slots);
+    srv->slots.assign(srv->max_slots, Slot());
+    srv->use_worker = worker != 0;
+    if (srv->use_worker) srv->worker = std::thread(worker_main, srv);
+  } catch (const std::exception &e) {
+    set_last_error(e.what());
+    delete srv;
+    return LP_ERR_CUDA;
+  }
+  *out = srv;
+  return LP_OK;
 }
-int lp_batch_submit(lp_server *, lp_problem *, uint64_t *) { return LP_ERR_STATE; }
-int lp_batch_poll(lp_server *, uint64_t, lp_result *, double *, double *) { return LP_ERR_STATE; }
-int lp_server_pump(lp_server *, int32_t) { return LP_ERR_STATE; }
-int lp_batch_cancel(lp_server *, uint64_t) { return LP_ERR_STATE; }
-int lp_server_stats(const lp_server *, int64_t *) { return LP_ERR_STATE; }
-void lp_server_destroy(lp_server *) {}
+
+int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket) {
+  if (!srv || !lp || !ticket) {
+    set_last_error("NULL argument");
+    return LP_ERR_INVALID;
+  }
+  try {
+    Request rq;
+    pack_request(problem_current(lp), rq.pk);
+    if (rq.pk.bytes > srv->arena_bytes) {
+      set_last_error("request needs " + std::to_string(rq.pk.bytes) +
+                     " bytes, more than the server's budget");
+      return LP_ERR_BUDGET;
+    }
+    if (rq.pk.nnz >= (long long)INT32_MAX) {
+      set_last_error("request too large (nnz >= 2^31)");
+      return LP_ERR_INVALID;
+    }
+    rq.lp = lp;
+    rq.t_submit = now_s();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (!srv->worker_err.empty()) {
+      set_last_error("server worker failed: " + srv->worker_err);
+      return LP_ERR_CUDA;
+    }
+    rq.ticket = srv->next_ticket++;
+    *ticket = rq.ticket;
+    srv->where[rq.ticket] = 0;
+    srv->queue.push_back(std::move(rq));
+    srv->cv.notify_all();
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return LP_ERR_OOM;
+  } catch (const std::exception &e) {
+    set_last_error(e.what());
+    return LP_ERR_INVALID;
+  }
+  return LP_OK;
 }
+
+int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, double *y) {
+  if (!srv) {
+    set_last_error("server is NULL");
+    return LP_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (!srv->worker_err.empty()) {
+    set_last_error("server worker failed: " + srv->worker_err);
+    return LP_ERR_CUDA;
+  }
+  auto w = srv->where.find(ticket);
+  if (w == srv->where.end()) {
+    set_last_error("unknown ticket");
+    return LP_ERR_INVALID;
+  }
+  if (w->second != 2) return LP_PENDING;
+  Done &d = srv->done[ticket];
+  if (res) *res = d.res;
+  if (x && !d.x.empty()) std::memcpy(x, d.x.data(), 8 * d.x.size());
+  if (y && !d.y.empty()) std::memcpy(y, d.y.data(), 8 * d.y.size());
+  // hand the answer to the problem so lp_postsolve can map it back
+  if (d.lp && d.res.termination >= 0 && d.res.termination <= LP_NUMERICAL)
+    problem_store_solution(d.lp, d.x, d.y, d.z);
+  srv->where.erase(w);
+  srv->done.erase(ticket);
+  return LP_OK;
+}
+
+int lp_server_pump(lp_server *srv, int32_t periods) {
+  if (!srv) {
+    set_last_error("server is NULL");
+    return LP_ERR_INVALID;
+  }
+  if (srv->use_worker) {
+    set_last_error("server runs its own worker thread");
+    return LP_ERR_STATE;
+  }
+  try {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    CK(cudaSetDevice(srv->device));
+    int live = 0;
+    for (int p = 0; p < std::max(periods, 1); ++p) {
+      live = period(srv);
+      if (live == 0) break;
+    }
+    return live;
+  } catch (const std::exception &e) {
+    set_last_error(e.what());
+    return LP_ERR_CUDA;
+  }
+}
+
+int lp_batch_cancel(lp_server *srv, uint64_t ticket) {
+  if (!srv) {
+    set_last_error("server is NULL");
+    return LP_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto w = srv->where.find(ticket);
+  if (w == srv->where.end()) {
+    set_last_error("unknown ticket");
+    return LP_ERR_INVALID;
+  }
+  if (w->second == 0) {
+    for (Request &rq : srv->queue)
+      if (rq.ticket == ticket) rq.cancelled = true;
+  } else if (w->second == 1) {
+    for (Slot &sl : srv->slots)
+      if (sl.used && sl.ticket == ticket) sl.cancel = true;
+  }
+  return LP_OK;
+}
+
+int lp_server_stats(const lp_server *srv, int64_t *out) {
+  if (!srv || !out) {
+    set_last_error("NULL argument");
+    return LP_ERR_INVALID;
+  }
+  lp_server *s = const_cast<lp_server *>(srv);
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = s->n_admitted;
+  out[1] = s->n_finished;
+  out[2] = s->n_periods;
+  out[3] = (int64_t)s->peak_resident;
+  out[4] = s->launches;
+  out[5] = (int64_t)s->queue.size();
+  for (int b = 0; b < kNumBuckets; ++b) out[6 + b] = s->tuner[b].current();
+  return LP_OK;
+}
+
+void lp_server_destroy(lp_server *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    srv->cv.notify_all();
+  }
+  if (srv->worker.joinable()) srv->worker.join();
+  cudaSetDevice(srv->device);
+  cudaStreamSynchronize(srv->s);
+  for (int b = 0; b < kNumBuckets; ++b) {
+    if (srv->bs[b]) {
+      cudaStreamSynchronize(srv->bs[b]);
+      cudaStreamDestroy(srv->bs[b]);
+    }
+    if (srv->ev_b0[b]) cudaEventDestroy(srv->ev_b0[b]);
+    if (srv->ev_b1[b]) cudaEventDestroy(srv->ev_b1[b]);
+  }
+  if (srv->ev_fork) cudaEventDestroy(srv->ev_fork);
+  if (srv->arena) {
+    if (srv->ctx.free) srv->ctx.free(srv->arena, srv->ctx.user);
+    else cudaFree(srv->arena);
+  }
+  if (srv->h_state) cudaFreeHost(srv->h_state);
+  if (srv->h_order) cudaFreeHost(srv->h_order);
+  if (srv->own_stream) cudaStreamDestroy(srv->s);
+  delete srv;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Per-LP PDHG state and the restart / termination decision shared by the
+// single-LP path (solver.cu) and the batched path (batch.cu).
+//
+// The decision follows the solver reading documented with the oracle:
+// checks at t = 0, K, 2K, ...; stop when the relative KKT error of T(z) is at
+// most eps_rel (or a value is not finite); with r = ||z - T(z)||_omega,
+// record r0 = r_prev = r at the first check, otherwise restart when
+// r <= beta_suff r0, or r <= beta_nec r0 and r > r_prev, or k >= beta_art t;
+// a restart moves the anchor and the iterate to T(z) and smooths the primal
+// weight omega <- exp(theta log(dy / dx) + (1 - theta) log omega).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gb300lp {
+
+constexpr int ST_RUNNING = -1;
+
+struct State {
+  double eta, omega, tau, sigma;
+  double rho, beta_suff, beta_nec, beta_art, theta, eps_rel;
+  double r0, r_prev, last_r;
+  double bnorm, cnorm, off;
+  double rel_kkt, rel_p, rel_d, rel_gap, r_p, r_d, gap, pobj, dobj;
+  long long t;
+  long long iters;
+  int K;
+  int k_base, k_off;
+  int restarts;
+  int status;
+  int restart_flag;
+  int halpern, restarts_on;
+  int err;  // set by a kernel whose bounded wait expired
+  // mixed precision: 1 while the SpMV runs in FP32; the check switches the
+  // LP to FP64 SpMV for good once rel-KKT <= kPolishRatio * eps_rel, or once
+  // it has not halved for kPolishStall checks near the FP32 rounding floor
+  // (best rel-KKT <= kPolishFloor), or for kPolishStallFar checks anywhere
+  int mixed_active;
+  int stall;
+  double best_rel;
+  long long t_switch;  // iteration of the FP64 switch (or -1)
+};
+
+constexpr double kPolishRatio = 10.0;
+constexpr double kPolishFloor = 1e-4;
+constexpr int kPolishStall = 32;
+constexpr int kPolishStallFar = 256;
+
+// reduced quantities of a check (and of the set-up)
+enum {
+  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P, Q_CN, Q_BN, Q_PW, NQ
+};
+
+// Halpern coefficients of iteration position j of a check period:
+// z+ = a T(z) + b z + g z0
+struct Halpern {
+  double a, b, g;
+};
+__device__ __forceinline__ Halpern halpern_coeffs(const State *st, int j) {
+  double lam = 1.0;
+  if (st->halpern) {
+    int k = (j == 0) ? st->k_base : st->k_off + j;
+    lam = (k + 1.0) / (k + 2.0);
+  }
+  Halpern h;
+  h.a = lam * (1.0 + st->rho);
+  h.b = -lam * st->rho;
+  h.g = 1.0 - lam;
+  return h;
+}
+
+// One thread: fold the check quantities q[0..Q_P] into st.  eval_only: fill
+// in the KKT fields and mark LP_ITER_LIMIT (1) if still running.
+__device__ __forceinline__ void check_update(State *st, const double *q, bool eval_only) {
+  double rp = sqrt(q[Q_RP]);
+  double rd = sqrt(q[Q_RD] + q[Q_RDY]);
+  double p = q[Q_P] + st->off;
+  double d = q[Q_DY] + q[Q_DL] + st->off;
+  double relp = rp / (1.0 + st->bnorm);
+  double reld = rd / (1.0 + st->cnorm);
+  double gap = fabs(p - d);
+  double relg = gap / (1.0 + fabs(p) + fabs(d));
+  double rel = fmax(relp, fmax(reld, relg));
+  st->rel_kkt = rel;
+  st->rel_p = relp;
+  st->rel_d = reld;
+  st->rel_gap = relg;
+  st->r_p = rp;
+  st->r_d = rd;
+  st->gap = gap;
+  st->pobj = p;
+  st->dobj = d;
+  if (eval_only) {
+    if (st->status == ST_RUNNING) st->status = 1;  // LP_ITER_LIMIT
+    return;
+  }
+  bool finite = isfinite(rel) && isfinite(q[Q_XRES]) && isfinite(q[Q_YRES]);
+  if (!finite || rel <= st->eps_rel) {
+    st->status = finite ? 0 : 3;  // LP_OPTIMAL : LP_NUMERICAL
+    st->iters = st->t + 1;
+    st->restart_flag = 0;
+    return;
+  }
+  if (st->mixed_active) {
+    if (rel < 0.5 * st->best_rel) {
+      st->best_rel = rel;
+      st->stall = 0;
+    } else {
+      st->stall += 1;
+    }
+    if (rel <= kPolishRatio * st->eps_rel ||
+        (st->stall >= kPolishStall && st->best_rel <= kPolishFloor) ||
+        st->stall >= kPolishStallFar) {
+      st->mixed_active = 0;
+      st->t_switch = st->t;
+    }
+  }
+  double om = st->omega;
+  double r = sqrt(om * q[Q_XRES] + q[Q_YRES] / om);
+  st->last_r = r;
+  int kb = st->k_base;
+  int restart = 0;
+  if (kb == 0) {
+    st->r0 = st->r_prev = r;
+  } else if (st->restarts_on &&
+             (r <= st->beta_suff * st->r0 || (r <= st->beta_nec * st->r0 && r > st->r_prev) ||
+              (double)kb >= st->beta_art * (double)st->t)) {
+    double dx = sqrt(q[Q_XD]), dy = sqrt(q[Q_YD]);
+    if (dx > 1e-10 && dy > 1e-10) om = exp(st->theta * log(dy / dx) + (1.0 - st->theta) * log(om));
+    st->omega = om;
+    st->tau = st->eta / om;
+    st->sigma = st->eta * om;
+    st->r0 = st->r_prev = r;
+    st->restarts += 1;
+    restart = 1;
+  } else {
+    st->r_prev = r;
+  }
+  st->restart_flag = restart;
+  st->k_off = restart ? -1 : kb;
+  st->k_base = st->k_off + st->K;
+  st->t += st->K;
+}
+
+}  // namespace gb300lp

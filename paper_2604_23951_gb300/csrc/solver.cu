@@ -41,6 +41,7 @@
 
 #include "device_common.cuh"
 #include "lp_internal.h"
+#include "pdhg_state.cuh"
 #include "spmv_warp.cuh"
 
 namespace gb300lp {
@@ -54,29 +55,6 @@ constexpr int kTilePad = 8;  // value / index arrays padded past nnz
 #define GB300_MIN_BLOCKS (1024 / GB300_BLOCK)
 #endif
 constexpr int kMinBlocks = GB300_MIN_BLOCKS;
-
-constexpr int ST_RUNNING = -1;
-
-struct State {
-  double eta, omega, tau, sigma;
-  double rho, beta_suff, beta_nec, beta_art, theta, eps_rel;
-  double r0, r_prev, last_r;
-  double bnorm, cnorm, off;
-  double rel_kkt, rel_p, rel_d, rel_gap, r_p, r_d, gap, pobj, dobj;
-  long long t;
-  long long iters;
-  int K;
-  int k_base, k_off;
-  int restarts;
-  int status;
-  int restart_flag;
-  int halpern, restarts_on;
-  int err;  // set by a kernel whose bounded wait expired
-};
-
-enum {
-  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P, Q_CN, Q_BN, Q_PW, NQ
-};
 
 // deterministic block reduction of NQL accumulators into partials[q * G + block]
 template <int NQL>
@@ -315,23 +293,6 @@ __global__ void k_reciprocal(int n, const double *__restrict__ d, double *__rest
 // ---------------------------------------------------------------------------
 // the iteration kernels
 
-// Halpern coefficients of iteration position j: z+ = a T(z) + b z + g z0
-struct Halpern {
-  double a, b, g;
-};
-__device__ __forceinline__ Halpern halpern_coeffs(const State *st, int j) {
-  double lam = 1.0;
-  if (st->halpern) {
-    int k = (j == 0) ? st->k_base : st->k_off + j;
-    lam = (k + 1.0) / (k + 2.0);
-  }
-  Halpern h;
-  h.a = lam * (1.0 + st->rho);
-  h.b = -lam * st->rho;
-  h.g = 1.0 - lam;
-  return h;
-}
-
 template <bool CHECK, bool MIXED>
 struct PrimalEpi {
   const double *c, *lx, *ux;
@@ -361,23 +322,34 @@ struct PrimalEpi {
   }
 };
 
+// T = float: the mixed-precision kernel; it runs the FP32 SpMV while
+// st->mixed_active is set and the FP64 one (va64, y) after the switch
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
-    MatDev M, const T *__restrict__ va, const double *__restrict__ y,
-    const float *__restrict__ yf, const double *__restrict__ c, const double *__restrict__ lx,
-    const double *__restrict__ ux, double *x, double *x0, double *xbar, float *xbar_f,
-    double *xhat, const State *__restrict__ st, int j, double *partials, int G, int *err) {
+    MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
+    const double *__restrict__ y, const float *__restrict__ yf, const double *__restrict__ c,
+    const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
+    double *xbar, float *xbar_f, double *xhat, const State *__restrict__ st, int j,
+    double *partials, int G, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
-  PrimalEpi<CHECK, MIXED> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau, halpern_coeffs(st, j),
-                            0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (MIXED) {
-      warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e, red_smem<T, float, float>());
+  double acc[2];
+  if (MIXED && st->mixed_active) {
+    PrimalEpi<CHECK, true> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
+                             halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
+                                       red_smem<T, float, float>());
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
   } else {
-      warp_spmv<kBlock, T, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, y, e, red_smem<T, double, double>());
+    PrimalEpi<CHECK, false> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
+                              halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y,
+                                              e, red_smem<double, double, double>());
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
   }
   if (CHECK) {
-    double acc[2] = {e.acc0, e.acc1};
     const int qi[2] = {Q_XRES, Q_XD};
     store_partials<2>(acc, qi, partials, G);
   }
@@ -415,21 +387,30 @@ struct DualEpi {
 
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
-    MatDev M, const T *__restrict__ va, const double *__restrict__ xbar,
-    const float *__restrict__ xbar_f, const double *__restrict__ lc,
-    const double *__restrict__ uc, double *y, double *y0, float *yf, double *yhat,
-    const State *__restrict__ st, int j, double *partials, int G, int *err) {
+    MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
+    const double *__restrict__ xbar, const float *__restrict__ xbar_f,
+    const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
+    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int G,
+    int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
-  DualEpi<CHECK, MIXED> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
-                          0.0, 0.0, 0.0, 0.0};
-  if (MIXED) {
-      warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e, red_smem<T, float, float>());
+  double acc[2];
+  if (MIXED && st->mixed_active) {
+    DualEpi<CHECK, true> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
+                           0.0, 0.0, 0.0, 0.0};
+    warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
+                                       red_smem<T, float, float>());
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
   } else {
-      warp_spmv<kBlock, T, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar, e, red_smem<T, double, double>());
+    DualEpi<CHECK, false> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
+                            0.0, 0.0, 0.0, 0.0};
+    warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64,
+                                              xbar, e, red_smem<double, double, double>());
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
   }
   if (CHECK) {
-    double acc[2] = {e.acc0, e.acc1};
     const int qi[2] = {Q_YRES, Q_YD};
     store_partials<2>(acc, qi, partials, G);
   }
@@ -510,59 +491,7 @@ __global__ void k_check(State *st, const double *partials, int G, int eval_only)
   double q[NQ];
   for (int i = 0; i < Q_CN; ++i) q[i] = reduce_partials(partials, i, G);
   if (threadIdx.x != 0) return;
-  double rp = sqrt(q[Q_RP]);
-  double rd = sqrt(q[Q_RD] + q[Q_RDY]);
-  double p = q[Q_P] + st->off;
-  double d = q[Q_DY] + q[Q_DL] + st->off;
-  double relp = rp / (1.0 + st->bnorm);
-  double reld = rd / (1.0 + st->cnorm);
-  double gap = fabs(p - d);
-  double relg = gap / (1.0 + fabs(p) + fabs(d));
-  double rel = fmax(relp, fmax(reld, relg));
-  st->rel_kkt = rel;
-  st->rel_p = relp;
-  st->rel_d = reld;
-  st->rel_gap = relg;
-  st->r_p = rp;
-  st->r_d = rd;
-  st->gap = gap;
-  st->pobj = p;
-  st->dobj = d;
-  if (eval_only) {
-    if (st->status == ST_RUNNING) st->status = 1;  // LP_ITER_LIMIT
-    return;
-  }
-  bool finite = isfinite(rel) && isfinite(q[Q_XRES]) && isfinite(q[Q_YRES]);
-  if (!finite || rel <= st->eps_rel) {
-    st->status = finite ? 0 : 3;  // LP_OPTIMAL : LP_NUMERICAL
-    st->iters = st->t + 1;
-    return;
-  }
-  double om = st->omega;
-  double r = sqrt(om * q[Q_XRES] + q[Q_YRES] / om);
-  st->last_r = r;
-  int kb = st->k_base;
-  int restart = 0;
-  if (kb == 0) {
-    st->r0 = st->r_prev = r;
-  } else if (st->restarts_on &&
-             (r <= st->beta_suff * st->r0 || (r <= st->beta_nec * st->r0 && r > st->r_prev) ||
-              (double)kb >= st->beta_art * (double)st->t)) {
-    double dx = sqrt(q[Q_XD]), dy = sqrt(q[Q_YD]);
-    if (dx > 1e-10 && dy > 1e-10) om = exp(st->theta * log(dy / dx) + (1.0 - st->theta) * log(om));
-    st->omega = om;
-    st->tau = st->eta / om;
-    st->sigma = st->eta * om;
-    st->r0 = st->r_prev = r;
-    st->restarts += 1;
-    restart = 1;
-  } else {
-    st->r_prev = r;
-  }
-  st->restart_flag = restart;
-  st->k_off = restart ? -1 : kb;
-  st->k_base = st->k_off + st->K;
-  st->t += st->K;
+  check_update(st, q, eval_only != 0);
 }
 
 // K5: on restart, x = x0 = xh and y = y0 = yh
@@ -919,12 +848,12 @@ void launch_primal(DeviceLP *d, bool wr, int grid, int j) {
     smem = kSmem64;
   }
   if (wr)
-    k_primal<T, true><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->y, d->yf, d->c, d->lx,
+    k_primal<T, true><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                     d->ux, d->x, d->x0, d->xbar, d->xbar_f,
                                                     d->xhat, d->st, j, d->partials, d->G,
                                                     d->errp());
   else
-    k_primal<T, false><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->y, d->yf, d->c, d->lx,
+    k_primal<T, false><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                      d->ux, d->x, d->x0, d->xbar, d->xbar_f,
                                                      d->xhat, d->st, j, d->partials, d->G,
                                                      d->errp());
@@ -945,11 +874,11 @@ void launch_dual(DeviceLP *d, bool wr, int grid, int j) {
     yf = nullptr;
   }
   if (wr)
-    k_dual<T, true><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->xbar, d->xbar_f, d->lc,
+    k_dual<T, true><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                   d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
                                                   d->partials, d->G, d->errp());
   else
-    k_dual<T, false><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->xbar, d->xbar_f, d->lc,
+    k_dual<T, false><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                    d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
                                                    d->partials, d->G, d->errp());
 }
@@ -1095,6 +1024,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     init.halpern = o.halpern ? 1 : 0;
     init.restarts_on = o.restarts ? 1 : 0;
     init.status = ST_RUNNING;
+    init.mixed_active = mixed ? 1 : 0;
+    init.stall = 0;
+    init.best_rel = INFINITY;
+    init.t_switch = -1;
     CK(cudaMemcpyAsync(d->st, &init, sizeof(State), cudaMemcpyHostToDevice, d->s));
     // warm start, permuted to the device order
     double *xin = nullptr, *yin = nullptr;
@@ -1285,6 +1218,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       res->t_total_s =
           std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
       res->kernel_launches = d->launches;
+      res->fp32_iterations = mixed ? (S.t_switch >= 0 ? S.t_switch : iters) : 0;
     }
   } catch (const DeviceOOM &e) {
     err = e.what();
@@ -1320,6 +1254,7 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     CK(cudaStreamSynchronize(d->s));
     State run = saved;
     run.status = ST_RUNNING;
+    run.mixed_active = mixed ? 1 : 0;  // time the FP32 SpMV of a mixed solve
     CK(cudaMemcpyAsync(d->st, &run, sizeof(State), cudaMemcpyHostToDevice, d->s));
     CK(cudaStreamSynchronize(d->s));
     cudaEvent_t a, b;

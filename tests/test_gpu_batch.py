@@ -1,0 +1,161 @@
+"""Batched solving and the continuous-batching server against the oracle.
+
+Tolerances: rel-KKT <= 1e-6 bounds the duality gap by 1e-6 (1 + |p| + |d|),
+not the objective error by 1e-6 (1 + |p*|); so FP64 runs that assert
+objectives within 1e-6 relative of the planted optimum solve to
+eps_rel = 1e-7.  Mixed precision (FP32 SpMV) solves to 1e-6 and is checked
+against the FP64 optimum at 1e-5.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import presolve as PS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2604_23951_gb300 as p
+
+    p.load()
+    return p
+
+
+@pytest.fixture(scope="module")
+def dev(pkg):
+    return pkg.TorchDevice(0)
+
+
+def rel_obj(p, q):
+    return abs(p - q) / (1.0 + abs(q))
+
+
+def small_batch(count, seed=77, m_lo=30, m_hi=600):
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=count)).astype(int)
+    return [lpgen.equality_nonneg(int(m), 2 * int(m), seed + 1000 * (j + 1), 4, 30)
+            for j, m in enumerate(ms)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_oracle(pkg, dev, precision):
+    lps = small_batch(24)
+    eps = 1e-7 if precision == 0 else 1e-6
+    srv = pkg.Server(1 << 30, dev, precision=precision, eps_rel=eps)
+    probs = [pkg.Problem(lp, dev) for lp in lps]
+    tickets = [srv.submit(p) for p in probs]
+    res = srv.run_all(tickets)
+    tol = 1e-6 if precision == 0 else 1e-5
+    for lp, t in zip(lps, tickets):
+        r, x, y = res[t]
+        assert r.termination == pkg.LP_OPTIMAL, r.as_dict()
+        assert r.rel_kkt <= eps
+        k = oracle.rel_kkt(lp, x, y)
+        assert k["rel_kkt"] <= 2 * eps, k
+        assert rel_obj(r.primal_obj, lp.p_star) <= tol
+    st = srv.stats()
+    assert st["finished"] == len(lps) and st["queued"] == 0
+    srv.close()
+
+
+def test_single_lp_batch_of_one_matches_single_path(pkg, dev):
+    lp = lpgen.c1_small()
+    ref = oracle.pdhg_solve(lp)
+    srv = pkg.Server(1 << 28, dev, precision=0)
+    p = pkg.Problem(lp, dev)
+    t = srv.submit(p)
+    r, x, y = srv.run_all([t])[t]
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    assert rel_obj(r.primal_obj, ref.kkt["p"]) <= 1e-6
+    # same algorithm, same arithmetic type: the iteration count matches the
+    # oracle's unless a restart test lands on a near-tie
+    assert abs(r.iterations - ref.iterations) <= 128
+    srv.close()
+
+
+@pytest.mark.parametrize("precision,eps,tol", [(0, 1e-7, 1e-6), (1, 1e-6, 1e-5)])
+def test_alone_and_in_the_mix_agree(pkg, dev, precision, eps, tol):
+    target = lpgen.equality_nonneg(300, 600, 4242, 4, 30)
+    others = small_batch(30, seed=99)
+    srv = pkg.Server(1 << 30, dev, precision=precision, eps_rel=eps)
+    pa = pkg.Problem(target, dev)
+    ta = srv.submit(pa)
+    ra, xa, ya = srv.run_all([ta])[ta]
+    srv.close()
+    srv = pkg.Server(1 << 30, dev, precision=precision, eps_rel=eps)
+    probs = [pkg.Problem(lp, dev) for lp in others[:15]]
+    tickets = [srv.submit(p) for p in probs]
+    pb = pkg.Problem(target, dev)
+    tb = srv.submit(pb)
+    probs2 = [pkg.Problem(lp, dev) for lp in others[15:]]
+    tickets += [srv.submit(p) for p in probs2]
+    res = srv.run_all(tickets + [tb])
+    rb, xb, yb = res[tb]
+    assert ra.termination == rb.termination == pkg.LP_OPTIMAL
+    assert rel_obj(ra.primal_obj, rb.primal_obj) <= tol
+    assert rel_obj(ra.primal_obj, target.p_star) <= tol
+    assert ra.rel_kkt <= eps and rb.rel_kkt <= eps
+    srv.close()
+
+
+def test_cancel_and_budget(pkg, dev):
+    srv = pkg.Server(1 << 26, dev, precision=1)
+    lp = lpgen.equality_nonneg(200, 400, 5, 4, 30)
+    t = srv.submit(pkg.Problem(lp, dev))
+    srv.cancel(t)
+    r, _, _ = srv.run_all([t])[t]
+    assert r.termination == 6  # LP_CANCELLED
+    big = lpgen.equality_nonneg(60000, 120000, 6, 20, 30)
+    with pytest.raises(pkg.LPError) as ei:
+        srv.submit(pkg.Problem(big, dev))
+    assert ei.value.code == -5
+    srv.close()
+
+
+def test_worker_thread_continuous_batching(pkg, dev):
+    lps = small_batch(20, seed=5)
+    srv = pkg.Server(1 << 30, dev, worker=True, precision=1)
+    probs = [pkg.Problem(lp, dev) for lp in lps]
+    first = [srv.submit(p) for p in probs[:10]]
+    time.sleep(0.05)  # the first wave is running when the second arrives
+    second = [srv.submit(p) for p in probs[10:]]
+    pending = set(first + second)
+    out = {}
+    t0 = time.time()
+    while pending and time.time() - t0 < 120:
+        for t in list(pending):
+            got = srv.poll(t)
+            if got is not None:
+                out[t] = got
+                pending.discard(t)
+        time.sleep(0.002)
+    assert not pending
+    for lp, t in zip(lps, first + second):
+        r, x, y = out[t]
+        assert r.termination == pkg.LP_OPTIMAL
+        assert rel_obj(r.primal_obj, lp.p_star) <= 1e-5
+    srv.close()
+
+
+def test_presolved_requests_postsolve_to_kkt(pkg, dev):
+    lps = [lpgen.general_structure(400 + 50 * j, 1000 + 120 * j, 300 + j, nnz_target=6000)
+           for j in range(4)]
+    srv = pkg.Server(1 << 30, dev, precision=0, eps_rel=1e-7)
+    probs = [pkg.Problem(lp, dev) for lp in lps]
+    for p in probs:
+        p.presolve()
+    tickets = [srv.submit(p) for p in probs]
+    res = srv.run_all(tickets)
+    for lp, p, t in zip(lps, probs, tickets):
+        r, _, _ = res[t]
+        assert r.termination == pkg.LP_OPTIMAL
+        x, y, z = p.postsolve()
+        k = oracle.rel_kkt(lp, x, y)
+        assert k["rel_kkt"] <= 1e-5
+        assert rel_obj(k["p"], lp.p_star) <= 1e-6
+    srv.close()
