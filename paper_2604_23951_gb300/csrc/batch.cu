@@ -51,6 +51,7 @@ namespace gb300lp {
 
 void set_last_error(const std::string &m);
 const HostLP &problem_current(const lp_problem *lp);
+constexpr long long kSoloNnz = 2000000;  // larger requests run on the single-LP grid path
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z);
 
@@ -753,9 +754,18 @@ struct Request {
   uint64_t ticket = 0;
   lp_problem *lp = nullptr;
   Packed pk;
+  bool solo = false;
+  size_t solo_bytes = 0;  // arena estimate of a solo request
   double t_submit = 0;
   bool cancelled = false;
 };
+
+// device bytes the single-LP path allocates for an LP (upper estimate)
+static size_t solo_estimate(const HostLP &h) {
+  const size_t nz = (size_t)h.nnz() + 64;
+  return nz * 2 * (4 + 8 + 8 + 4) + (size_t)h.m * 8 * 16 + (size_t)h.n * 8 * 22 +
+         (size_t)(h.m + h.n) * 8 + (size_t(64) << 20);
+}
 
 struct Done {
   lp_result res{};
@@ -811,6 +821,10 @@ struct lp_server {
   long long n_admitted = 0, n_finished = 0, n_periods = 0, launches = 0;
   size_t resident = 0, peak_resident = 0;
   std::mutex mu;
+  std::mutex arena_mu;  // guards ralloc, resident, solo_blocks
+  std::map<size_t, size_t> solo_blocks;
+  std::vector<std::thread> solo_threads;
+  int solo_running = 0;
   std::condition_variable cv;
   std::thread worker;
   bool stop = false;
@@ -842,6 +856,89 @@ void server_state_init(const lp_server *srv, State &st, const Packed &pk) {
   st.t_switch = -1;
 }
 
+// device memory of solo requests comes from the server's arena
+void *arena_alloc(size_t bytes, void *user) {
+  lp_server *srv = static_cast<lp_server *>(user);
+  bytes = (bytes + 255) & ~size_t(255);
+  std::lock_guard<std::mutex> ak(srv->arena_mu);
+  size_t off = 0;
+  if (!srv->ralloc.alloc(bytes, off)) return nullptr;
+  srv->solo_blocks[off] = bytes;
+  srv->resident += bytes;
+  srv->peak_resident = std::max(srv->peak_resident, srv->resident);
+  return srv->arena + off;
+}
+
+void arena_free(void *p, void *user) {
+  lp_server *srv = static_cast<lp_server *>(user);
+  std::lock_guard<std::mutex> ak(srv->arena_mu);
+  size_t off = static_cast<unsigned char *>(p) - srv->arena;
+  auto it = srv->solo_blocks.find(off);
+  if (it == srv->solo_blocks.end()) return;
+  srv->ralloc.release(off, it->second);
+  srv->resident -= it->second;
+  srv->solo_blocks.erase(it);
+}
+
+size_t largest_free(lp_server *srv) {
+  std::lock_guard<std::mutex> ak(srv->arena_mu);
+  size_t b = 0;
+  for (auto &kv : srv->ralloc.free_) b = std::max(b, kv.second);
+  return b;
+}
+
+// A large request: the single-LP grid path on its own stream, driven by its
+// own host thread; device memory from the arena.  Caller holds mu.
+bool start_solo(lp_server *srv, Request &rq) {
+  if (srv->solo_running >= 2) return false;
+  if (largest_free(srv) < rq.solo_bytes) return false;
+  srv->solo_running += 1;
+  srv->where[rq.ticket] = 1;
+  ++srv->n_admitted;
+  const uint64_t ticket = rq.ticket;
+  lp_problem *lp = rq.lp;
+  const double t_submit = rq.t_submit;
+  srv->solo_threads.emplace_back([srv, ticket, lp, t_submit]() {
+    const double t_admit = now_s();
+    Done d;
+    d.lp = lp;
+    std::string err;
+    int rc = LP_OK;
+    cudaSetDevice(srv->device);
+    lp_device_ctx ctx{};
+    ctx.alloc = arena_alloc;
+    ctx.free = arena_free;
+    ctx.user = srv;
+    ctx.stream = nullptr;
+    ctx.device = srv->device;
+    DeviceLP *dl = dev_create(&ctx, err);
+    if (!dl) rc = LP_ERR_CUDA;
+    const HostLP &h = problem_current(lp);
+    DeviceSolution sol;
+    if (rc == LP_OK) rc = dev_upload(dl, h, 0, err);
+    if (rc == LP_OK) rc = dev_solve(dl, h, srv->opts, &d.res, sol, err);
+    if (dl) dev_destroy(dl);
+    if (rc == LP_OK) {
+      d.x = std::move(sol.x);
+      d.y = std::move(sol.y);
+      d.z = std::move(sol.z);
+    } else {
+      d.res.termination = LP_NUMERICAL;
+    }
+    const double tnow = now_s();
+    d.res.t_setup_s = t_admit - t_submit;
+    d.res.t_solve_s = tnow - t_admit;
+    d.res.t_total_s = tnow - t_submit;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->done[ticket] = std::move(d);
+    srv->where[ticket] = 2;
+    ++srv->n_finished;
+    srv->solo_running -= 1;
+    srv->cv.notify_all();
+  });
+  return true;
+}
+
 // Admit queued requests while a slot and arena space are free (caller holds mu)
 void admit(lp_server *srv) {
   while (!srv->queue.empty()) {
@@ -861,8 +958,18 @@ void admit(lp_server *srv) {
         break;
       }
     if (sid < 0) return;
+    if (rq.solo) {
+      if (!start_solo(srv, rq)) return;
+      srv->queue.pop_front();
+      continue;
+    }
     size_t off = 0;
-    if (!srv->ralloc.alloc(rq.pk.bytes, off)) return;
+    {
+      std::lock_guard<std::mutex> ak(srv->arena_mu);
+      if (!srv->ralloc.alloc(rq.pk.bytes, off)) return;
+      srv->resident += rq.pk.bytes;
+      srv->peak_resident = std::max(srv->peak_resident, srv->resident);
+    }
     Slot &sl = srv->slots[sid];
     sl = Slot();
     sl.used = true;
@@ -886,8 +993,6 @@ void admit(lp_server *srv) {
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaStreamSynchronize(srv->s));  // the pageable blob may be freed next
     srv->where[rq.ticket] = 1;
-    srv->resident += rq.pk.bytes;
-    srv->peak_resident = std::max(srv->peak_resident, srv->resident);
     ++srv->n_admitted;
     srv->queue.pop_front();
   }
@@ -1031,13 +1136,16 @@ int period(lp_server *srv) {
                             ? (S.t_switch >= 0 ? S.t_switch : r.iterations) : 0;
     srv->done[sl.ticket] = std::move(d);
     srv->where[sl.ticket] = 2;
-    srv->ralloc.release(sl.off, sl.bytes);
-    srv->resident -= sl.bytes;
+    {
+      std::lock_guard<std::mutex> ak(srv->arena_mu);
+      srv->ralloc.release(sl.off, sl.bytes);
+      srv->resident -= sl.bytes;
+    }
     sl.used = false;
     ++srv->n_finished;
   }
   admit(srv);
-  int live = (int)srv->queue.size();
+  int live = (int)srv->queue.size() + srv->solo_running;
   for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
   return live;
 }
@@ -1048,7 +1156,7 @@ void worker_main(lp_server *srv) {
   while (!srv->stop) {
     int live = (int)srv->queue.size();
     for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
-    if (live == 0) {
+    if (live == 0 && srv->solo_running == 0) {
       srv->cv.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
@@ -1163,7 +1271,17 @@ int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket) {
   }
   try {
     Request rq;
-    pack_request(problem_current(lp), rq.pk);
+    const HostLP &h = problem_current(lp);
+    if (h.nnz() >= kSoloNnz) {
+      rq.solo = true;
+      rq.solo_bytes = solo_estimate(h);
+      rq.pk.m = h.m;
+      rq.pk.n = h.n;
+      rq.pk.nnz = h.nnz();
+      rq.pk.bytes = rq.solo_bytes;
+    } else {
+      pack_request(h, rq.pk);
+    }
     if (rq.pk.bytes > srv->arena_bytes) {
       set_last_error("request needs " + std::to_string(rq.pk.bytes) +
                      " bytes, more than the server's budget");
@@ -1239,6 +1357,9 @@ int lp_server_pump(lp_server *srv, int32_t periods) {
     for (int p = 0; p < std::max(periods, 1); ++p) {
       live = period(srv);
       if (live == 0) break;
+      bool batch_live = false;
+      for (const Slot &sl : srv->slots) batch_live = batch_live || sl.used;
+      if (!batch_live && srv->queue.empty()) break;  // only solo requests left
     }
     return live;
   } catch (const std::exception &e) {
@@ -1293,6 +1414,8 @@ void lp_server_destroy(lp_server *srv) {
     srv->cv.notify_all();
   }
   if (srv->worker.joinable()) srv->worker.join();
+  for (std::thread &t : srv->solo_threads)
+    if (t.joinable()) t.join();
   cudaSetDevice(srv->device);
   cudaStreamSynchronize(srv->s);
   for (int b = 0; b < kNumBuckets; ++b) {

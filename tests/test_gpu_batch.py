@@ -159,3 +159,39 @@ def test_presolved_requests_postsolve_to_kkt(pkg, dev):
         assert k["rel_kkt"] <= 1e-5
         assert rel_obj(k["p"], lp.p_star) <= 1e-6
     srv.close()
+
+
+def test_large_request_runs_on_the_solo_lane_beside_batched_ones(pkg, dev):
+    # >= 2M nonzeros: the server solves it with the single-LP grid path on
+    # its own stream while the small requests keep batching
+    big = lpgen.general_structure(80_000, 200_000, 17, nnz_target=2_100_000)
+    smalls = small_batch(8, seed=8)
+    srv = pkg.Server(8 << 30, dev, worker=True, precision=0)
+    pb = pkg.Problem(big, dev)
+    pb.presolve()
+    if pb.dims()[2] < 2_000_000:
+        pytest.skip("presolved request below the solo size")
+    probs = [pkg.Problem(lp, dev) for lp in smalls]
+    tb = srv.submit(pb)
+    ts = [srv.submit(p) for p in probs]
+    pending = set([tb] + ts)
+    out = {}
+    t0 = time.time()
+    while pending and time.time() - t0 < 300:
+        for t in list(pending):
+            got = srv.poll(t)
+            if got is not None:
+                out[t] = got
+                pending.discard(t)
+        time.sleep(0.005)
+    assert not pending
+    r, _, _ = out[tb]
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    x, y, _ = pb.postsolve()
+    k = oracle.rel_kkt(big, x, y)
+    assert k["rel_kkt"] <= 1e-5
+    for lp, t in zip(smalls, ts):
+        r, _, _ = out[t]
+        assert r.termination == pkg.LP_OPTIMAL
+        assert rel_obj(r.primal_obj, lp.p_star) <= 1e-5
+    srv.close()
