@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--requests", type=int, default=96, help="c5: stream length")
     p.add_argument("--rate", type=float, default=200.0, help="c5: arrivals per second")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--solo-nnz", type=int, default=0,
+                   help="c4/c5: nonzeros from which a request runs the single-LP path (0: default)")
+    p.add_argument("--solo-max", type=int, default=-1, help="c4/c5: concurrent solo requests")
+    p.add_argument("--launch-ms", type=float, default=0.0,
+                   help="c4/c5: device time budget of one bucket launch (0: default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-iters", type=int, default=20)
     p.add_argument("--profile-iters", type=int, default=0,
@@ -414,6 +419,7 @@ def run_batch(args):
         def one_step():
             probs = [pkg.Problem(lp, dev) for lp in lps]
             srv = pkg.Server(int(40e9), dev, precision=prec)
+            srv.tune(args.solo_nnz, args.solo_max, args.launch_ms)
             t0 = time.perf_counter()
             tickets = [srv.submit(p) for p in probs]
             res = srv.run_all(tickets)
@@ -479,6 +485,7 @@ def run_batch(args):
 
     def serve():
         srv = pkg.Server(int(150e9), dev, worker=True, precision=prec)
+        srv.tune(args.solo_nnz, args.solo_max, args.launch_ms)
         probs = [None] * len(lps)
         tickets = [None] * len(lps)
         arrivals = [None] * len(lps)

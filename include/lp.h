@@ -257,10 +257,17 @@ int lp_power_norm_static(int32_t m, int32_t n, const int32_t *a_row_ptr,
 
 /* A server holds up to hbm_budget_bytes of device memory (allocated once),
  * packs admitted problems into slots of a persistent segmented batch and
- * runs them with one launch per period; finished slots are refilled from the
- * queue.  `opts` applies to every request (precision, eps_rel, ...).
- * worker: 1 = a background host thread drives the device loop; 0 = the
- * caller drives it through lp_server_pump. */
+ * runs them.  Slots are grouped in four size buckets (by nonzeros); each
+ * bucket has its own stream and launch loop, so small problems never wait
+ * for large ones.  One bucket launch gives every live slot of the bucket at
+ * least one block of check_every iterations and keeps going while the
+ * launch's device time budget lasts; finished slots are retired and their
+ * memory refilled from the queue between launches.  Requests with at least
+ * solo_nnz nonzeros (default 2,000,000) instead run the single-LP grid path
+ * on their own stream, with device memory from the same budget, at most
+ * solo_max (default 2) at once.  `opts` applies to every request
+ * (precision, eps_rel, ...).  worker: 1 = a background host thread drives
+ * the device loop; 0 = the caller drives it through lp_server_pump. */
 int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
                      const lp_solve_opts *opts, int32_t worker, lp_server **out);
 
@@ -274,16 +281,26 @@ int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket);
  * current LP are filled (pointers may be NULL) and the ticket is released. */
 int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, double *y);
 
-/* Drive the device loop for at most `periods` launch periods (worker = 0).
+/* Drive the device loop (worker = 0) for at most `periods` scheduler steps.
+ * A step waits for the oldest bucket launch in flight (if any), retires what
+ * it finished, admits queued requests and starts a launch for every idle
+ * bucket with live slots; launches may still be running when it returns.
  * Returns the number of requests still queued or running. */
 int lp_server_pump(lp_server *srv, int32_t periods);
+
+/* Scheduler settings; call before submitting.  solo_nnz > 0: the nonzero
+ * count from which a request runs on the single-LP path (<= 0: keep);
+ * solo_max in [1, 64]: solo requests running at once (negative: keep);
+ * launch_ms in (0, 1000]: device time budget of one bucket launch (default
+ * 2 ms; <= 0: keep).  LP_ERR_INVALID for values out of range. */
+int lp_server_tune(lp_server *srv, int64_t solo_nnz, int32_t solo_max, double launch_ms);
 
 /* Cancel a queued or running request: its poll returns LP_OK with
  * termination LP_CANCELLED. */
 int lp_batch_cancel(lp_server *srv, uint64_t ticket);
 
-/* Statistics (10 int64): out[0] admitted, out[1] finished, out[2] periods
- * launched, out[3] peak resident bytes, out[4] kernel launches, out[5] queue
+/* Statistics (10 int64): out[0] admitted, out[1] finished, out[2] bucket
+ * launches, out[3] peak resident bytes, out[4] kernel launches, out[5] queue
  * length, out[6..9] shape index the autotuner uses for each size bucket
  * (nonzeros < 16Ki, < 128Ki, < 1Mi, larger). */
 int lp_server_stats(const lp_server *srv, int64_t *out);

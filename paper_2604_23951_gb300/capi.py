@@ -97,6 +97,7 @@ SIGNATURES = [
     ("lp_batch_submit", C.c_int, [_P, _P, C.POINTER(C.c_uint64)]),
     ("lp_batch_poll", C.c_int, [_P, C.c_uint64, C.POINTER(lp_result), _D, _D]),
     ("lp_server_pump", C.c_int, [_P, C.c_int32]),
+    ("lp_server_tune", C.c_int, [_P, C.c_int64, C.c_int32, C.c_double]),
     ("lp_batch_cancel", C.c_int, [_P, C.c_uint64]),
     ("lp_server_stats", C.c_int, [_P, _I64]),
     ("lp_server_destroy", None, [_P]),
@@ -342,6 +343,10 @@ class Server:
 
     def pump(self, periods: int = 1) -> int:
         return check(self.lib.lp_server_pump(self.h, int(periods)))
+
+    def tune(self, solo_nnz: int = 0, solo_max: int = -1, launch_ms: float = 0.0):
+        """Scheduler settings (lp_server_tune); non-positive values keep the default."""
+        check(self.lib.lp_server_tune(self.h, int(solo_nnz), int(solo_max), float(launch_ms)))
 
     def cancel(self, ticket: int):
         check(self.lib.lp_batch_cancel(self.h, C.c_uint64(ticket)))

@@ -43,7 +43,10 @@
 
 #include "device_common.cuh"
 #include "lp_internal.h"
+#include "layout.h"
+#include "pdhg_epi.cuh"
 #include "pdhg_state.cuh"
+#include "spmv_warp.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -59,16 +62,20 @@ constexpr int ST_SETUP = -2;
 constexpr int kMaxCluster = 8;
 constexpr int kMaxWarps = 16;  // CTAs of up to 512 threads
 
+// One slot's device layout: A and A^T renumbered and cut into warp tiles as
+// in the single-LP path (layout.h), so vectors are in the permuted order.
 struct SlotDesc {
   int m, n;
   long long nnz;
+  int a_ntiles, a_nlong, t_ntiles, t_nlong;
+  const int2 *a_tiles, *t_tiles;
   const int *a_rp, *a_ci, *t_rp, *t_ci;
   const double *a_v0, *t_v0;
   double *a_v, *t_v;
   float *a_vf, *t_vf;
   const double *c0, *lx0, *ux0, *lc0, *uc0;
   double *c, *lx, *ux, *lc, *uc;
-  double *dr, *dc, *dr2, *dc2;
+  double *dr, *dc, *dr2, *dc2, *idr, *idc;
   double *x, *x0, *xbar, *xhat, *y, *y0, *yhat;
   float *xbarf, *yf, *pwf;
   double *xout, *yout, *zout;
@@ -78,6 +85,7 @@ struct BatchConst {
   int K, ruiz_iters, pock_chambolle, power_iters;
   long long max_iter;
   double step_size, primal_weight;
+  long long budget_ns;  // device time a launch gives its slots (>= one block of K each)
 };
 
 // ---------------------------------------------------------------------------
@@ -94,11 +102,14 @@ struct Ctl {
 };
 
 struct BatchShared {
+  double redd[kMaxWarps];  // whole-CTA rows of the warp engine
+  float redf[kMaxWarps];
   double wsum[kMaxWarps][NQ];
   double part[kMaxCluster][NQ];  // used on rank 0
   double total[NQ];
   Ctl ctl;
   double bcast;
+  int cont;
 };
 
 // thread 0 of a CTA: read the slot's control words from global memory
@@ -176,25 +187,6 @@ __device__ __forceinline__ void cluster_sum(const double (&acc)[NQL], const int 
   __syncthreads();
 }
 
-// thread-per-row dot product of row r: sum_k va[k] * vec[ci[k]]
-template <typename T, typename V, typename Acc>
-__device__ __forceinline__ Acc row_dot(const int *__restrict__ rp, const int *__restrict__ ci,
-                                       const T *__restrict__ va, const V *vec, int r) {
-  const int e = rp[r + 1];
-  int k = rp[r];
-  Acc s0 = 0, s1 = 0;
-  for (; k + 3 < e; k += 4) {
-    const int j0 = ci[k], j1 = ci[k + 1], j2 = ci[k + 2], j3 = ci[k + 3];
-    const V g0 = vec[j0], g1 = vec[j1], g2 = vec[j2], g3 = vec[j3];
-    s0 += (Acc)va[k] * (Acc)g0;
-    s1 += (Acc)va[k + 1] * (Acc)g1;
-    s0 += (Acc)va[k + 2] * (Acc)g2;
-    s1 += (Acc)va[k + 3] * (Acc)g3;
-  }
-  for (; k < e; ++k) s0 += (Acc)va[k] * (Acc)vec[ci[k]];
-  return s0 + s1;
-}
-
 // one Ruiz / Pock-Chambolle pass over the rows of a matrix: dnew[r] =
 // dself[r] / sqrt(max or sum_k (dr |a|) dc); S is the arithmetic type
 template <typename S, bool TRANSPOSED, bool SUM>
@@ -258,6 +250,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
       D.a_v[k] = v;
       if (MIXED) D.a_vf[k] = (float)v;
     }
+    D.idr[i] = 1.0 / d;
     const double l = d * D.lc0[i], u = d * D.uc0[i];
     D.lc[i] = l;
     D.uc[i] = u;
@@ -272,6 +265,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
       D.t_v[k] = v;
       if (MIXED) D.t_vf[k] = (float)v;
     }
+    D.idc[j] = 1.0 / d;
     const double cj = d * D.c0[j];
     D.c[j] = cj;
     D.lx[j] = D.lx0[j] / d;
@@ -292,33 +286,39 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
         if (MIXED) D.pwf[j] = (float)v0; else D.xhat[j] = v0;
       }
       cl.sync();
+      const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
       for (int it = 0; it <= C.power_iters; ++it) {
-        for (int i = gt; i < m; i += gs) {
-          if (MIXED) D.yf[i] = row_dot<float, float, float>(D.a_rp, D.a_ci, D.a_vf, D.pwf, i);
-          else D.yhat[i] = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xhat, i);
-        }
-        cl.sync();
+        // u = A~ v
         double a2[1] = {0.0};
+        if (MIXED) {
+          StoreSqEpi<float> e{D.yf, 0.0};
+          warp_spmv<float, float, float>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_vf,
+                                         D.pwf, e, sh.redf, rank, CL);
+          a2[0] = e.acc;
+        } else {
+          StoreSqEpi<double> e{D.yhat, 0.0};
+          warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci,
+                                            D.a_v, D.xhat, e, sh.redd, rank, CL);
+          a2[0] = e.acc;
+        }
         if (it == C.power_iters) {
-          for (int i = gt; i < m; i += gs) {
-            const double u = MIXED ? (double)D.yf[i] : D.yhat[i];
-            a2[0] += u * u;
-          }
           const int qid[1] = {Q_PW};
           cluster_sum<1>(a2, qid, sh, cl);
           if (cl.block_rank() == 0 && threadIdx.x == 0) pw = sqrt(sh.total[Q_PW]);
           break;
         }
-        for (int j = gt; j < n; j += gs) {
-          if (MIXED) {
-            const float w = row_dot<float, float, float>(D.t_rp, D.t_ci, D.t_vf, D.yf, j);
-            D.xbarf[j] = w;
-            a2[0] += (double)w * (double)w;
-          } else {
-            const double w = row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.yhat, j);
-            D.xbar[j] = w;
-            a2[0] += w * w;
-          }
+        cl.sync();
+        // w = A~^T u
+        if (MIXED) {
+          StoreSqEpi<float> e{D.xbarf, 0.0};
+          warp_spmv<float, float, float>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_vf,
+                                         D.yf, e, sh.redf, rank, CL);
+          a2[0] = e.acc;
+        } else {
+          StoreSqEpi<double> e{D.xbar, 0.0};
+          warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci,
+                                            D.t_v, D.yhat, e, sh.redd, rank, CL);
+          a2[0] = e.acc;
         }
         const int qid[1] = {Q_PW};
         cluster_sum<1>(a2, qid, sh, cl);
@@ -373,12 +373,57 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
 // ---------------------------------------------------------------------------
 // K iterations of one slot
 
+// K1 (rows of A^T) or K2 (rows of A) with the shared epilogues; f32 selects
+// the FP32 SpMV of the mixed mode
+template <bool CHECK>
+__device__ __forceinline__ void phase_primal(const SlotDesc &D, bool f32, double tau,
+                                             const Halpern &hc, BatchShared &sh, int rank, int CL,
+                                             double (&acc)[10]) {
+  if (f32) {
+    PrimalEpi<CHECK, true> e{D.c, D.lx, D.ux, D.x, D.x0, D.xbar, D.xhat, D.xbarf, tau, hc,
+                             0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<float, float, float>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_vf, D.yf,
+                                   e, sh.redf, rank, CL);
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
+  } else {
+    PrimalEpi<CHECK, false> e{D.c, D.lx, D.ux, D.x, D.x0, D.xbar, D.xhat, D.xbarf, tau, hc,
+                              0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_v,
+                                      D.y, e, sh.redd, rank, CL);
+    acc[0] = e.acc0;
+    acc[1] = e.acc1;
+  }
+}
+
+template <bool CHECK>
+__device__ __forceinline__ void phase_dual(const SlotDesc &D, bool f32, double sigma,
+                                           const Halpern &hc, BatchShared &sh, int rank, int CL,
+                                           double (&acc)[10]) {
+  if (f32) {
+    DualEpi<CHECK, true> e{D.lc, D.uc, D.y, D.y0, D.yhat, D.yf, sigma, hc,
+                           0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<float, float, float>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_vf,
+                                   D.xbarf, e, sh.redf, rank, CL);
+    acc[2] = e.acc0;
+    acc[3] = e.acc1;
+  } else {
+    DualEpi<CHECK, false> e{D.lc, D.uc, D.y, D.y0, D.yhat, D.yf, sigma, hc,
+                            0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_v,
+                                      D.xbar, e, sh.redd, rank, CL);
+    acc[2] = e.acc0;
+    acc[3] = e.acc1;
+  }
+}
+
 template <bool MIXED>
 __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, BatchShared &sh,
                              cg::cluster_group &cl) {
   const int m = D.m, n = D.n;
   const int gt = cl.block_rank() * blockDim.x + threadIdx.x;
   const int gs = cl.num_blocks() * blockDim.x;
+  const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   for (int j = 0; j < C.K; ++j) {
     if (sh.ctl.status != ST_RUNNING) break;
     const bool check = (j == 0);
@@ -399,70 +444,30 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
     const bool f32 = MIXED && sh.ctl.mixed_active;  // FP32 SpMV until the FP64 switch
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // K1: rows of A^T
-    for (int c = gt; c < n; c += gs) {
-      double g;
-      if (f32) g = (double)row_dot<float, float, float>(D.t_rp, D.t_ci, D.t_vf, D.yf, c);
-      else g = row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.y, c);
-      const double xk = D.x[c];
-      const double xh = clampd(fma(-tau, D.c[c] - g, xk), D.lx[c], D.ux[c]);
-      const double xb = fma(2.0, xh, -xk);
-      const double a0 = D.x0[c];
-      D.x[c] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
-      if (f32) D.xbarf[c] = (float)xb; else D.xbar[c] = xb;
-      if (check) {
-        D.xhat[c] = xh;
-        acc[0] += (xk - xh) * (xk - xh);
-        acc[1] += (xh - a0) * (xh - a0);
-      }
-    }
+    if (check) phase_primal<true>(D, f32, tau, hc, sh, rank, CL, acc);
+    else phase_primal<false>(D, f32, tau, hc, sh, rank, CL, acc);
     cl.sync();
     // K2: rows of A
-    for (int r = gt; r < m; r += gs) {
-      double h;
-      if (f32) h = (double)row_dot<float, float, float>(D.a_rp, D.a_ci, D.a_vf, D.xbarf, r);
-      else h = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xbar, r);
-      const double yk = D.y[r];
-      const double v = fma(-sigma, h, yk);
-      const double yh = v + clampd(-v, sigma * D.lc[r], sigma * D.uc[r]);
-      const double a0 = D.y0[r];
-      const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
-      D.y[r] = yn;
-      if (f32) D.yf[r] = (float)yn;
-      if (check) {
-        D.yhat[r] = yh;
-        acc[2] += (yk - yh) * (yk - yh);
-        acc[3] += (yh - a0) * (yh - a0);
-      }
-    }
+    if (check) phase_dual<true>(D, f32, sigma, hc, sh, rank, CL, acc);
+    else phase_dual<false>(D, f32, sigma, hc, sh, rank, CL, acc);
     cl.sync();
     if (!check) continue;
     // K3: KKT on the unscaled problem, FP64 scaled matrix
-    for (int r = gt; r < m; r += gs) {
-      const double d = D.dr[r];
-      const double ax = row_dot<double, double, double>(D.a_rp, D.a_ci, D.a_v, D.xhat, r) / d;
-      const double lo = D.lc0[r], hi = D.uc0[r];
-      const double pr = clampd(ax, lo, hi);
-      acc[4] += (ax - pr) * (ax - pr);
-      const double yv = d * D.yhat[r];
-      double yp = yv;
-      if (!isfinite(lo)) yp = fmin(yp, 0.0);
-      if (!isfinite(hi)) yp = fmax(yp, 0.0);
-      acc[5] += (yv - yp) * (yv - yp);
-      acc[6] += support_term(yp, lo, hi);
+    {
+      KktRowEpi e{D.dr, D.idr, D.lc0, D.uc0, D.yhat, 0.0, 0.0, 0.0};
+      warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_v,
+                                        D.xhat, e, sh.redd, rank, CL);
+      acc[4] = e.rp2;
+      acc[5] = e.rdy2;
+      acc[6] = e.dy;
     }
-    for (int c = gt; c < n; c += gs) {
-      const double d = D.dc[c];
-      const double g = (D.c[c] - row_dot<double, double, double>(D.t_rp, D.t_ci, D.t_v, D.yhat, c)) / d;
-      const double lo = D.lx0[c], hi = D.ux0[c];
-      const bool lf = isfinite(lo), uf = isfinite(hi);
-      double lam = g;
-      if (!lf && !uf) lam = 0.0;
-      else if (lf && !uf) lam = fmax(lam, 0.0);
-      else if (!lf && uf) lam = fmin(lam, 0.0);
-      acc[7] += (g - lam) * (g - lam);
-      acc[8] += support_term(lam, lo, hi);
-      acc[9] += D.c0[c] * (d * D.xhat[c]);
-      D.zout[c] = g;
+    {
+      KktColEpi e{D.c, D.dc, D.idc, D.c0, D.lx0, D.ux0, D.xhat, D.zout, 0.0, 0.0, 0.0};
+      warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_v,
+                                        D.yhat, e, sh.redd, rank, CL);
+      acc[7] = e.rd2;
+      acc[8] = e.dl;
+      acc[9] = e.p;
     }
     {
       const int qid[10] = {Q_XRES, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P};
@@ -496,15 +501,28 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
   }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One launch over the slots order[0..nord): each cluster takes slots
+// cid, cid + ncl, ...; a slot runs blocks of K iterations until it finishes
+// or its share of the launch's time budget is spent (at least one block).
+// On leaving a slot, rank 0 copies its state to sout[oi] for the host.
 template <bool MIXED>
 __global__ void __launch_bounds__(512) k_batch(const SlotDesc *__restrict__ desc, State *states,
                                                const int *__restrict__ order, int nord,
-                                               BatchConst C) {
+                                               State *sout, BatchConst C) {
   __shared__ BatchShared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int CL = (int)cl.num_blocks();
   const int ncl = gridDim.x / CL;
   const int cid = blockIdx.x / CL;
+  const bool lead = cl.block_rank() == 0 && threadIdx.x == 0;
+  const int rounds = (nord + ncl - 1) / ncl;
+  const long long share = C.budget_ns / (rounds > 0 ? rounds : 1);
   for (int oi = cid; oi < nord; oi += ncl) {
     const int s = order[oi];
     const SlotDesc &D = desc[s];
@@ -513,8 +531,18 @@ __global__ void __launch_bounds__(512) k_batch(const SlotDesc *__restrict__ desc
     // same control words
     if (threadIdx.x == 0) load_ctl(st, sh.ctl);
     __syncthreads();
+    const unsigned long long t0 = lead ? global_ns() : 0ull;
     if (sh.ctl.status == ST_SETUP) slot_setup<MIXED>(D, st, C, sh, cl);
-    if (sh.ctl.status == ST_RUNNING) slot_iterate<MIXED>(D, st, C, sh, cl);
+    while (sh.ctl.status == ST_RUNNING) {
+      slot_iterate<MIXED>(D, st, C, sh, cl);
+      if (lead) {
+        const int go = sh.ctl.status == ST_RUNNING && (long long)(global_ns() - t0) < share;
+        for (int r = 0; r < CL; ++r) cl.map_shared_rank(&sh, r)->cont = go;
+      }
+      cl.sync();
+      if (!sh.cont) break;
+    }
+    if (lead) sout[oi] = *st;
     cl.sync();
   }
 }
@@ -615,11 +643,14 @@ struct Packed {
   size_t bytes = 0;
   SlotDesc rel{};  // pointers as offsets from the block start
   double bnorm = 0, cnorm = 0, off = 0;
+  std::vector<int> rperm, cperm;  // device order -> request order
 };
 
 static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 static void pack_request(const HostLP &h, Packed &p) {
+  Layout L;
+  build_layout(h, L);
   p.m = h.m;
   p.n = h.n;
   p.nnz = h.nnz();
@@ -633,6 +664,8 @@ static void pack_request(const HostLP &h, Packed &p) {
   };
   SlotDesc &r = p.rel;
   auto P = [](size_t o) { return reinterpret_cast<void *>(o); };
+  const size_t ntA = L.tA.size(), ntT = L.tT.size();
+  size_t o_tA = take(sizeof(int2) * ntA), o_tT = take(sizeof(int2) * ntT);
   size_t o_arp = take(sizeof(int) * (m + 1)), o_aci = take(sizeof(int) * nnz);
   size_t o_trp = take(sizeof(int) * (n + 1)), o_tci = take(sizeof(int) * nnz);
   size_t o_av0 = take(8 * nnz), o_tv0 = take(8 * nnz), o_av = take(8 * nnz), o_tv = take(8 * nnz);
@@ -642,6 +675,12 @@ static void pack_request(const HostLP &h, Packed &p) {
   r.m = m;
   r.n = n;
   r.nnz = nnz;
+  r.a_ntiles = (int)ntA;
+  r.t_ntiles = (int)ntT;
+  r.a_nlong = L.nlongA;
+  r.t_nlong = L.nlongT;
+  r.a_tiles = (const int2 *)P(o_tA);
+  r.t_tiles = (const int2 *)P(o_tT);
   r.a_rp = (const int *)P(o_arp);
   r.a_ci = (const int *)P(o_aci);
   r.t_rp = (const int *)P(o_trp);
@@ -658,10 +697,10 @@ static void pack_request(const HostLP &h, Packed &p) {
   r.lc0 = (const double *)P(o_lc0);
   r.uc0 = (const double *)P(o_uc0);
   const size_t input_end = cur;
-  double **colv[] = {&r.c, &r.lx, &r.ux, &r.dc, &r.dc2, &r.x, &r.x0, &r.xbar, &r.xhat, &r.xout,
-                     &r.zout};
+  double **colv[] = {&r.c, &r.lx, &r.ux, &r.dc, &r.dc2, &r.idc, &r.x, &r.x0, &r.xbar, &r.xhat,
+                     &r.xout, &r.zout};
   for (double **q : colv) *q = (double *)P(take(8 * n));
-  double **rowv[] = {&r.lc, &r.uc, &r.dr, &r.dr2, &r.y, &r.y0, &r.yhat, &r.yout};
+  double **rowv[] = {&r.lc, &r.uc, &r.dr, &r.dr2, &r.idr, &r.y, &r.y0, &r.yhat, &r.yout};
   for (double **q : rowv) *q = (double *)P(take(8 * m));
   r.xbarf = (float *)P(take(4 * n));
   r.pwf = (float *)P(take(4 * n));
@@ -670,46 +709,36 @@ static void pack_request(const HostLP &h, Packed &p) {
   // the host blob covers the inputs; the rest of the block is device work space
   p.blob.assign(input_end, 0);
   unsigned char *b = p.blob.data();
-  int *arp = (int *)(b + o_arp), *aci = (int *)(b + o_aci);
-  int *trp = (int *)(b + o_trp), *tci = (int *)(b + o_tci);
-  double *av0 = (double *)(b + o_av0), *tv0 = (double *)(b + o_tv0);
-  for (int i = 0; i <= m; ++i) arp[i] = (int)h.row_ptr[i];
-  for (long long k = 0; k < nnz; ++k) {
-    aci[k] = h.col_idx[k];
-    av0[k] = h.val[k];
-  }
-  // transpose (rows of A^T in column order, entries by row)
-  std::vector<int> cnt(n + 1, 0);
-  for (long long k = 0; k < nnz; ++k) cnt[h.col_idx[k] + 1]++;
-  for (int j = 0; j < n; ++j) cnt[j + 1] += cnt[j];
-  for (int j = 0; j <= n; ++j) trp[j] = cnt[j];
-  for (int i = 0; i < m; ++i)
-    for (int64_t k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) {
-      int j = h.col_idx[k];
-      tci[cnt[j]] = i;
-      tv0[cnt[j]] = h.val[k];
-      ++cnt[j];
-    }
-  std::memcpy(b + o_c0, h.c.data(), 8 * n);
-  std::memcpy(b + o_lx0, h.col_lo.data(), 8 * n);
-  std::memcpy(b + o_ux0, h.col_hi.data(), 8 * n);
-  std::memcpy(b + o_lc0, h.row_lo.data(), 8 * m);
-  std::memcpy(b + o_uc0, h.row_hi.data(), 8 * m);
-  double bn2 = 0, cn2 = 0;
-  for (int i = 0; i < m; ++i) {
-    bool lf = std::isfinite(h.row_lo[i]), uf = std::isfinite(h.row_hi[i]);
-    if (lf) bn2 += h.row_lo[i] * h.row_lo[i];
-    if (uf && !(lf && h.row_lo[i] == h.row_hi[i])) bn2 += h.row_hi[i] * h.row_hi[i];
-  }
-  for (int j = 0; j < n; ++j) cn2 += h.c[j] * h.c[j];
-  p.bnorm = std::sqrt(bn2);
-  p.cnorm = std::sqrt(cn2);
-  p.off = h.off;
+  auto put = [b](size_t o, const void *src, size_t bytes) {
+    if (bytes) std::memcpy(b + o, src, bytes);
+  };
+  put(o_tA, L.tA.data(), sizeof(int2) * ntA);
+  put(o_tT, L.tT.data(), sizeof(int2) * ntT);
+  put(o_arp, L.arp.data(), sizeof(int) * (m + 1));
+  put(o_aci, L.aci.data(), sizeof(int) * nnz);
+  put(o_trp, L.trp.data(), sizeof(int) * (n + 1));
+  put(o_tci, L.tci.data(), sizeof(int) * nnz);
+  put(o_av0, L.av.data(), 8 * nnz);
+  put(o_tv0, L.tv.data(), 8 * nnz);
+  put(o_c0, L.c0.data(), 8 * n);
+  put(o_lx0, L.lx0.data(), 8 * n);
+  put(o_ux0, L.ux0.data(), 8 * n);
+  put(o_lc0, L.lc0.data(), 8 * m);
+  put(o_uc0, L.uc0.data(), 8 * m);
+  p.bnorm = L.bnorm;
+  p.cnorm = L.cnorm;
+  p.off = L.off;
+  p.rperm = std::move(L.rperm);
+  p.cperm = std::move(L.cperm);
 }
 
 static SlotDesc relocate(const SlotDesc &rel, unsigned char *base) {
   SlotDesc d = rel;
   auto R = [base](auto p) { return reinterpret_cast<decltype(p)>(base + reinterpret_cast<size_t>(p)); };
+  d.a_tiles = R(rel.a_tiles);
+  d.t_tiles = R(rel.t_tiles);
+  d.idr = R(rel.idr);
+  d.idc = R(rel.idc);
   d.a_rp = R(rel.a_rp);
   d.a_ci = R(rel.a_ci);
   d.t_rp = R(rel.t_rp);
@@ -782,8 +811,20 @@ struct Slot {
   long long nnz = 0;
   int bucket = 0;
   SlotDesc desc{};
+  std::vector<int> rperm, cperm;
   double t_submit = 0, t_admit = 0;
   bool cancel = false;
+  long long last_t = 0;   // iteration count after the last launch
+  long long launches = 0; // launches the slot took part in
+};
+
+// one size bucket: its launch loop runs independently of the others
+struct Bucket {
+  Tuner tuner;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+  bool inflight = false;
+  bool tail = false;       // launch used the tail shape (not timed)
+  std::vector<int> order;  // slots of the launch in flight
 };
 
 static double now_s() {
@@ -800,8 +841,11 @@ struct lp_server {
   cudaStream_t s = nullptr;
   bool own_stream = false;
   cudaStream_t bs[kNumBuckets] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_b0[kNumBuckets] = {}, ev_b1[kNumBuckets] = {};
+  Bucket buckets[kNumBuckets];
   int device = 0, sm_count = 0;
+  long long solo_nnz = kSoloNnz;  // requests at least this large run on the single-LP path
+  int solo_max = 2;               // solo requests running at once
+  double launch_ms = 2.0;         // device time budget of one bucket launch
   lp_solve_opts opts{};
   unsigned char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -809,15 +853,16 @@ struct lp_server {
   int max_slots = 0;
   SlotDesc *d_desc = nullptr;
   State *d_state = nullptr;
-  int *d_order = nullptr;
-  State *h_state = nullptr;  // pinned mirror
-  int *h_order = nullptr;    // pinned
+  int *d_order = nullptr;    // kNumBuckets x max_slots
+  State *d_sout = nullptr;   // kNumBuckets x max_slots: states in launch order
+  State *h_state = nullptr;  // pinned, initial states of admitted slots
+  int *h_order = nullptr;    // pinned, kNumBuckets x max_slots
+  State *h_sout = nullptr;   // pinned, kNumBuckets x max_slots
   std::vector<Slot> slots;
   std::deque<Request> queue;
   std::map<uint64_t, Done> done;
   std::map<uint64_t, int> where;  // ticket -> 0 queued, 1 running, 2 done
   uint64_t next_ticket = 1;
-  Tuner tuner[kNumBuckets];
   long long n_admitted = 0, n_finished = 0, n_periods = 0, launches = 0;
   size_t resident = 0, peak_resident = 0;
   std::mutex mu;
@@ -890,7 +935,7 @@ size_t largest_free(lp_server *srv) {
 // A large request: the single-LP grid path on its own stream, driven by its
 // own host thread; device memory from the arena.  Caller holds mu.
 bool start_solo(lp_server *srv, Request &rq) {
-  if (srv->solo_running >= 2) return false;
+  if (srv->solo_running >= srv->solo_max) return false;
   if (largest_free(srv) < rq.solo_bytes) return false;
   srv->solo_running += 1;
   srv->where[rq.ticket] = 1;
@@ -984,6 +1029,8 @@ void admit(lp_server *srv) {
     sl.t_submit = rq.t_submit;
     sl.t_admit = now_s();
     sl.desc = relocate(rq.pk.rel, srv->arena + off);
+    sl.rperm = std::move(rq.pk.rperm);
+    sl.cperm = std::move(rq.pk.cperm);
     CK(cudaMemcpyAsync(srv->arena + off, rq.pk.blob.data(), rq.pk.blob.size(),
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaMemcpyAsync(srv->d_desc + sid, &sl.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice,
@@ -998,8 +1045,7 @@ void admit(lp_server *srv) {
   }
 }
 
-void launch_bucket(lp_server *srv, int b, const int *d_order, int nord, const Shape &sh,
-                   cudaStream_t st) {
+void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
   BatchConst C;
   C.K = std::max(1, srv->opts.check_every);
   C.ruiz_iters = srv->opts.ruiz_iters;
@@ -1008,13 +1054,14 @@ void launch_bucket(lp_server *srv, int b, const int *d_order, int nord, const Sh
   C.max_iter = srv->opts.max_iter;
   C.step_size = srv->opts.step_size;
   C.primal_weight = srv->opts.primal_weight;
+  C.budget_ns = (long long)(srv->launch_ms * 1e6);
   const int max_clusters = std::max(1, srv->sm_count * 4 / sh.cl);
   const int nclusters = std::min(nord, max_clusters);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * sh.cl);
   cfg.blockDim = dim3(sh.block);
   cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
+  cfg.stream = srv->bs[b];
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = sh.cl;
@@ -1022,132 +1069,176 @@ void launch_bucket(lp_server *srv, int b, const int *d_order, int nord, const Sh
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const int *d_order = srv->d_order + (size_t)b * srv->max_slots;
+  State *d_sout = srv->d_sout + (size_t)b * srv->max_slots;
   if (srv->opts.precision == LP_MIXED)
     CK(cudaLaunchKernelEx(&cfg, k_batch<true>, (const SlotDesc *)srv->d_desc, srv->d_state,
-                          d_order, nord, C));
+                          d_order, nord, d_sout, C));
   else
     CK(cudaLaunchKernelEx(&cfg, k_batch<false>, (const SlotDesc *)srv->d_desc, srv->d_state,
-                          d_order, nord, C));
+                          d_order, nord, d_sout, C));
   srv->launches++;
-  (void)b;
 }
 
-// One launch period over every live slot; then retire finished slots.
-// Caller holds mu.  Returns the number of live + queued requests.
-int period(lp_server *srv) {
-  admit(srv);
-  std::vector<int> lists[kNumBuckets];
-  for (int q = 0; q < srv->max_slots; ++q) {
-    Slot &sl = srv->slots[q];
-    if (!sl.used) continue;
-    if (sl.cancel) continue;
-    lists[sl.bucket].push_back(q);
-  }
-  // order within a bucket: largest first (longest slots start first)
-  int total = 0;
-  for (int b = 0; b < kNumBuckets; ++b) {
-    std::sort(lists[b].begin(), lists[b].end(),
-              [&](int a, int c) { return srv->slots[a].nnz > srv->slots[c].nnz; });
-    total += (int)lists[b].size();
-  }
-  if (total > 0) {
-    int pos = 0;
-    int start[kNumBuckets];
-    for (int b = 0; b < kNumBuckets; ++b) {
-      start[b] = pos;
-      for (int q : lists[b]) srv->h_order[pos++] = q;
+// Hand a slot's result to its ticket and free its arena block.  The slot's
+// bucket has no launch in flight.  Caller holds mu.
+void retire(lp_server *srv, int q, const State *S, double tnow) {
+  Slot &sl = srv->slots[q];
+  const bool finished = S && S->status >= 0;
+  Done d;
+  d.lp = sl.lp;
+  d.x.assign(sl.n, 0.0);
+  d.y.assign(sl.m, 0.0);
+  d.z.assign(sl.n, 0.0);
+  if (finished) {
+    // outputs are in the slot's device order: scatter back
+    std::vector<double> buf(std::max(sl.n, sl.m));
+    if (sl.n) {
+      CK(cudaMemcpy(buf.data(), sl.desc.xout, 8 * sl.n, cudaMemcpyDeviceToHost));
+      for (int j = 0; j < sl.n; ++j) d.x[sl.cperm[j]] = buf[j];
+      CK(cudaMemcpy(buf.data(), sl.desc.zout, 8 * sl.n, cudaMemcpyDeviceToHost));
+      for (int j = 0; j < sl.n; ++j) d.z[sl.cperm[j]] = buf[j];
     }
-    CK(cudaMemcpyAsync(srv->d_order, srv->h_order, sizeof(int) * total, cudaMemcpyHostToDevice,
-                       srv->s));
-    CK(cudaEventRecord(srv->ev_fork, srv->s));
-    Shape used[kNumBuckets];
-    for (int b = 0; b < kNumBuckets; ++b) {
-      if (lists[b].empty()) continue;
-      CK(cudaStreamWaitEvent(srv->bs[b], srv->ev_fork, 0));
-      used[b] = srv->tuner[b].pick();
-      // few live slots: give each the widest cluster so the tail does not run
-      // on a handful of SMs
-      if ((int)lists[b].size() * used[b].cl * 4 < srv->sm_count && srv->tuner[b].chosen >= 0)
-        used[b] = Shape{8, 256};
-      CK(cudaEventRecord(srv->ev_b0[b], srv->bs[b]));
-      launch_bucket(srv, b, srv->d_order + start[b], (int)lists[b].size(), used[b], srv->bs[b]);
-      CK(cudaEventRecord(srv->ev_b1[b], srv->bs[b]));
-      CK(cudaStreamWaitEvent(srv->s, srv->ev_b1[b], 0));
-    }
-    int hi = 0;
-    for (int q = 0; q < srv->max_slots; ++q)
-      if (srv->slots[q].used) hi = q + 1;
-    CK(cudaMemcpyAsync(srv->h_state, srv->d_state, sizeof(State) * hi, cudaMemcpyDeviceToHost,
-                       srv->s));
-    CK(cudaStreamSynchronize(srv->s));
-    ++srv->n_periods;
-    // autotuner bookkeeping: ns per nonzero-iteration of the period
-    for (int b = 0; b < kNumBuckets; ++b) {
-      if (lists[b].empty()) continue;
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, srv->ev_b0[b], srv->ev_b1[b]));
-      double work = 0;
-      for (int q : lists[b]) work += (double)std::max<long long>(srv->slots[q].nnz, 1);
-      work *= std::max(1, srv->opts.check_every);
-      srv->tuner[b].record(1e6 * ms / work);
+    if (sl.m) {
+      CK(cudaMemcpy(buf.data(), sl.desc.yout, 8 * sl.m, cudaMemcpyDeviceToHost));
+      for (int i = 0; i < sl.m; ++i) d.y[sl.rperm[i]] = buf[i];
     }
   }
-  // retire finished (or cancelled) slots
-  const double tnow = now_s();
-  for (int q = 0; q < srv->max_slots; ++q) {
-    Slot &sl = srv->slots[q];
-    if (!sl.used) continue;
-    const State &S = srv->h_state[q];
-    bool finished = S.status >= 0;
-    bool timeout = srv->opts.time_limit_s > 0 && tnow - sl.t_admit > srv->opts.time_limit_s;
-    if (!finished && !timeout && !sl.cancel) continue;
-    Done d;
-    d.lp = sl.lp;
-    d.x.assign(sl.n, 0.0);
-    d.y.assign(sl.m, 0.0);
-    d.z.assign(sl.n, 0.0);
-    if (finished) {
-      if (sl.n) {
-        CK(cudaMemcpy(d.x.data(), sl.desc.xout, 8 * sl.n, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(d.z.data(), sl.desc.zout, 8 * sl.n, cudaMemcpyDeviceToHost));
-      }
-      if (sl.m) CK(cudaMemcpy(d.y.data(), sl.desc.yout, 8 * sl.m, cudaMemcpyDeviceToHost));
-    }
-    lp_result &r = d.res;
-    r.termination = sl.cancel ? LP_CANCELLED : (finished ? S.status : LP_TIME_LIMIT);
-    r.restarts = S.restarts;
-    r.iterations = finished ? S.iters : S.t;
-    r.rel_kkt = S.rel_kkt;
-    r.rel_p = S.rel_p;
-    r.rel_d = S.rel_d;
-    r.rel_gap = S.rel_gap;
-    r.r_p = S.r_p;
-    r.r_d = S.r_d;
-    r.gap = S.gap;
-    r.primal_obj = S.pobj;
-    r.dual_obj = S.dobj;
-    r.eta = S.eta;
-    r.omega = S.omega;
-    r.t_setup_s = sl.t_admit - sl.t_submit;  // queueing delay
-    r.t_solve_s = tnow - sl.t_admit;
-    r.t_total_s = tnow - sl.t_submit;
-    r.kernel_launches = srv->launches;
+  lp_result &r = d.res;
+  r.termination = sl.cancel ? LP_CANCELLED : (finished ? S->status : LP_TIME_LIMIT);
+  if (S) {
+    r.restarts = S->restarts;
+    r.iterations = finished ? S->iters : S->t;
+    r.rel_kkt = S->rel_kkt;
+    r.rel_p = S->rel_p;
+    r.rel_d = S->rel_d;
+    r.rel_gap = S->rel_gap;
+    r.r_p = S->r_p;
+    r.r_d = S->r_d;
+    r.gap = S->gap;
+    r.primal_obj = S->pobj;
+    r.dual_obj = S->dobj;
+    r.eta = S->eta;
+    r.omega = S->omega;
     r.fp32_iterations = srv->opts.precision == LP_MIXED
-                            ? (S.t_switch >= 0 ? S.t_switch : r.iterations) : 0;
-    srv->done[sl.ticket] = std::move(d);
-    srv->where[sl.ticket] = 2;
-    {
-      std::lock_guard<std::mutex> ak(srv->arena_mu);
-      srv->ralloc.release(sl.off, sl.bytes);
-      srv->resident -= sl.bytes;
+                            ? (S->t_switch >= 0 ? S->t_switch : r.iterations) : 0;
+  }
+  r.t_setup_s = sl.t_admit - sl.t_submit;  // queueing delay
+  r.t_solve_s = tnow - sl.t_admit;
+  r.t_total_s = tnow - sl.t_submit;
+  r.kernel_launches = sl.launches;
+  srv->done[sl.ticket] = std::move(d);
+  srv->where[sl.ticket] = 2;
+  {
+    std::lock_guard<std::mutex> ak(srv->arena_mu);
+    srv->ralloc.release(sl.off, sl.bytes);
+    srv->resident -= sl.bytes;
+  }
+  sl = Slot();
+  ++srv->n_finished;
+}
+
+// A bucket's launch has completed: autotuner bookkeeping, then retire the
+// slots that finished (or were cancelled / ran out of time).  Caller holds mu.
+void complete_bucket(lp_server *srv, int b) {
+  Bucket &B = srv->buckets[b];
+  B.inflight = false;
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, B.ev0, B.ev1));
+  const State *out = srv->h_sout + (size_t)b * srv->max_slots;
+  const double tnow = now_s();
+  double work = 0;
+  for (int oi = 0; oi < (int)B.order.size(); ++oi) {
+    const int q = B.order[oi];
+    Slot &sl = srv->slots[q];
+    const State &S = out[oi];
+    work += (double)std::max<long long>(sl.nnz, 1) * (double)std::max<long long>(S.t - sl.last_t, 0);
+    sl.last_t = S.t;
+    sl.launches += 1;
+    const bool finished = S.status >= 0;
+    const bool timeout = srv->opts.time_limit_s > 0 && tnow - sl.t_admit > srv->opts.time_limit_s;
+    if (finished || timeout || sl.cancel) retire(srv, q, &S, tnow);
+  }
+  if (work > 0 && !B.tail) B.tuner.record(1e6 * ms / work);
+  B.order.clear();
+}
+
+// Start a launch for every idle bucket with live slots.  Caller holds mu.
+void launch_idle(lp_server *srv) {
+  for (int b = 0; b < kNumBuckets; ++b) {
+    Bucket &B = srv->buckets[b];
+    if (B.inflight) continue;
+    // cancelled slots that never ran in this bucket's current launch
+    const double tnow = now_s();
+    B.order.clear();
+    for (int q = 0; q < srv->max_slots; ++q) {
+      Slot &sl = srv->slots[q];
+      if (!sl.used || sl.bucket != b) continue;
+      if (sl.cancel) {
+        retire(srv, q, nullptr, tnow);
+        continue;
+      }
+      B.order.push_back(q);
     }
-    sl.used = false;
-    ++srv->n_finished;
+    if (B.order.empty()) continue;
+    // largest first (the longest slots start first)
+    std::sort(B.order.begin(), B.order.end(),
+              [&](int a, int c) { return srv->slots[a].nnz > srv->slots[c].nnz; });
+    const int nord = (int)B.order.size();
+    int *h_order = srv->h_order + (size_t)b * srv->max_slots;
+    std::copy(B.order.begin(), B.order.end(), h_order);
+    Shape shp = B.tuner.pick();
+    // few live slots: give each the widest cluster so the tail does not run
+    // on a handful of SMs (not timed for the autotuner)
+    B.tail = nord * shp.cl * 4 < srv->sm_count && B.tuner.chosen >= 0;
+    if (B.tail) shp = Shape{8, 256};
+    cudaStream_t st = srv->bs[b];
+    CK(cudaMemcpyAsync(srv->d_order + (size_t)b * srv->max_slots, h_order, sizeof(int) * nord,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(B.ev0, st));
+    launch_bucket(srv, b, nord, shp);
+    CK(cudaEventRecord(B.ev1, st));
+    CK(cudaMemcpyAsync(srv->h_sout + (size_t)b * srv->max_slots,
+                       srv->d_sout + (size_t)b * srv->max_slots, sizeof(State) * nord,
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(B.ev_done, st));
+    B.inflight = true;
+    ++srv->n_periods;
+  }
+}
+
+// One scheduler step: admit, collect completed launches, relaunch idle
+// buckets.  With `wait`, first block until some launch in flight completes.
+// Returns the number of live + queued requests.  Caller holds mu.
+int step(lp_server *srv, bool wait) {
+  admit(srv);
+  if (wait) {
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (srv->buckets[b].inflight) {
+        CK(cudaEventSynchronize(srv->buckets[b].ev_done));
+        break;
+      }
+    }
+  }
+  for (int b = 0; b < kNumBuckets; ++b) {
+    Bucket &B = srv->buckets[b];
+    if (!B.inflight) continue;
+    cudaError_t e = cudaEventQuery(B.ev_done);
+    if (e == cudaErrorNotReady) continue;
+    CK(e);
+    complete_bucket(srv, b);
   }
   admit(srv);
+  launch_idle(srv);
   int live = (int)srv->queue.size() + srv->solo_running;
   for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
   return live;
+}
+
+bool any_inflight(const lp_server *srv) {
+  for (int b = 0; b < kNumBuckets; ++b)
+    if (srv->buckets[b].inflight) return true;
+  return false;
 }
 
 void worker_main(lp_server *srv) {
@@ -1156,20 +1247,20 @@ void worker_main(lp_server *srv) {
   while (!srv->stop) {
     int live = (int)srv->queue.size();
     for (int q = 0; q < srv->max_slots; ++q) live += srv->slots[q].used ? 1 : 0;
-    if (live == 0 && srv->solo_running == 0) {
+    if (live == 0 && !any_inflight(srv)) {
       srv->cv.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
     try {
-      period(srv);
+      step(srv, false);
     } catch (const std::exception &e) {
       srv->worker_err = e.what();
       srv->stop = true;
     }
     srv->cv.notify_all();
-    // let submitters / pollers in between periods
+    // let submitters / pollers in while the launches run
     lk.unlock();
-    std::this_thread::yield();
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
     lk.lock();
   }
   srv->cv.notify_all();
@@ -1208,15 +1299,18 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
     }
     for (int b = 0; b < kNumBuckets; ++b) {
       CK(cudaStreamCreateWithFlags(&srv->bs[b], cudaStreamNonBlocking));
-      CK(cudaEventCreate(&srv->ev_b0[b]));
-      CK(cudaEventCreate(&srv->ev_b1[b]));
-      srv->tuner[b].cand = candidates(b);
-      srv->tuner[b].best_ns.assign(srv->tuner[b].cand.size(), 1e300);
+      Bucket &B = srv->buckets[b];
+      CK(cudaEventCreate(&B.ev0));
+      CK(cudaEventCreate(&B.ev1));
+      CK(cudaEventCreateWithFlags(&B.ev_done, cudaEventDisableTiming));
+      B.tuner.cand = candidates(b);
+      B.tuner.best_ns.assign(B.tuner.cand.size(), 1e300);
     }
-    CK(cudaEventCreateWithFlags(&srv->ev_fork, cudaEventDisableTiming));
     // the budget covers the slot arena and the slot tables
     srv->max_slots = 4096;
-    const size_t tables = srv->max_slots * (sizeof(SlotDesc) + sizeof(State) + sizeof(int)) + 4096;
+    const size_t tables =
+        srv->max_slots * (sizeof(SlotDesc) + sizeof(State) +
+                          kNumBuckets * (sizeof(int) + sizeof(State))) + 4096;
     if (hbm_budget_bytes <= tables + (1u << 16)) {
       throw std::runtime_error("budget too small for the slot tables");
     }
@@ -1244,13 +1338,17 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
     srv->d_desc = reinterpret_cast<SlotDesc *>(base + srv->arena_bytes);
     srv->d_state = reinterpret_cast<State *>(reinterpret_cast<unsigned char *>(srv->d_desc) +
                                              srv->max_slots * sizeof(SlotDesc));
-    srv->d_order = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(srv->d_state) +
-                                           srv->max_slots * sizeof(State));
+    srv->d_sout = reinterpret_cast<State *>(reinterpret_cast<unsigned char *>(srv->d_state) +
+                                            srv->max_slots * sizeof(State));
+    srv->d_order = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(srv->d_sout) +
+                                           kNumBuckets * srv->max_slots * sizeof(State));
     srv->ralloc.init(srv->arena_bytes);
     CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_state), sizeof(State) * srv->max_slots,
                      cudaHostAllocDefault));
-    CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_order), sizeof(int) * srv->max_slots,
-                     cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_order),
+                     sizeof(int) * kNumBuckets * srv->max_slots, cudaHostAllocDefault));
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&srv->h_sout),
+                     sizeof(State) * kNumBuckets * srv->max_slots, cudaHostAllocDefault));
     std::memset(srv->h_state, 0, sizeof(State) * srv->max_slots);
     srv->slots.assign(srv->max_slots, Slot());
     srv->use_worker = worker != 0;
@@ -1272,7 +1370,7 @@ int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket) {
   try {
     Request rq;
     const HostLP &h = problem_current(lp);
-    if (h.nnz() >= kSoloNnz) {
+    if (h.nnz() >= srv->solo_nnz) {
       rq.solo = true;
       rq.solo_bytes = solo_estimate(h);
       rq.pk.m = h.m;
@@ -1355,7 +1453,7 @@ int lp_server_pump(lp_server *srv, int32_t periods) {
     CK(cudaSetDevice(srv->device));
     int live = 0;
     for (int p = 0; p < std::max(periods, 1); ++p) {
-      live = period(srv);
+      live = step(srv, any_inflight(srv));
       if (live == 0) break;
       bool batch_live = false;
       for (const Slot &sl : srv->slots) batch_live = batch_live || sl.used;
@@ -1366,6 +1464,22 @@ int lp_server_pump(lp_server *srv, int32_t periods) {
     set_last_error(e.what());
     return LP_ERR_CUDA;
   }
+}
+
+int lp_server_tune(lp_server *srv, int64_t solo_nnz, int32_t solo_max, double launch_ms) {
+  if (!srv) {
+    set_last_error("server is NULL");
+    return LP_ERR_INVALID;
+  }
+  if (solo_max == 0 || solo_max > 64 || !(launch_ms <= 1000.0)) {
+    set_last_error("solo_max must be in [1, 64] (or negative: keep) and launch_ms <= 1000");
+    return LP_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (solo_nnz > 0) srv->solo_nnz = solo_nnz;
+  if (solo_max >= 0) srv->solo_max = solo_max;
+  if (launch_ms > 0) srv->launch_ms = launch_ms;
+  return LP_OK;
 }
 
 int lp_batch_cancel(lp_server *srv, uint64_t ticket) {
@@ -1402,7 +1516,7 @@ int lp_server_stats(const lp_server *srv, int64_t *out) {
   out[3] = (int64_t)s->peak_resident;
   out[4] = s->launches;
   out[5] = (int64_t)s->queue.size();
-  for (int b = 0; b < kNumBuckets; ++b) out[6 + b] = s->tuner[b].current();
+  for (int b = 0; b < kNumBuckets; ++b) out[6 + b] = s->buckets[b].tuner.current();
   return LP_OK;
 }
 
@@ -1423,16 +1537,18 @@ void lp_server_destroy(lp_server *srv) {
       cudaStreamSynchronize(srv->bs[b]);
       cudaStreamDestroy(srv->bs[b]);
     }
-    if (srv->ev_b0[b]) cudaEventDestroy(srv->ev_b0[b]);
-    if (srv->ev_b1[b]) cudaEventDestroy(srv->ev_b1[b]);
+    Bucket &B = srv->buckets[b];
+    if (B.ev0) cudaEventDestroy(B.ev0);
+    if (B.ev1) cudaEventDestroy(B.ev1);
+    if (B.ev_done) cudaEventDestroy(B.ev_done);
   }
-  if (srv->ev_fork) cudaEventDestroy(srv->ev_fork);
   if (srv->arena) {
     if (srv->ctx.free) srv->ctx.free(srv->arena, srv->ctx.user);
     else cudaFree(srv->arena);
   }
   if (srv->h_state) cudaFreeHost(srv->h_state);
   if (srv->h_order) cudaFreeHost(srv->h_order);
+  if (srv->h_sout) cudaFreeHost(srv->h_sout);
   if (srv->own_stream) cudaStreamDestroy(srv->s);
   delete srv;
 }

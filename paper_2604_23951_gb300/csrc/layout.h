@@ -1,0 +1,32 @@
+// Device layout of one LP, built on the host: rows of A and of A^T sorted by
+// length (longest first) and renumbered, the stored transpose, and the warp
+// tile tables of spmv_warp.cuh.  Shared by the single-LP upload and the
+// batch server's request packing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "lp_internal.h"
+
+namespace gb300lp {
+
+constexpr int kTilePad = 8;  // value / index arrays padded past nnz
+
+struct Layout {
+  int m = 0, n = 0;
+  long long nnz = 0;
+  std::vector<int> rperm, cperm;  // new -> old
+  std::vector<int> arp, aci, trp, tci;  // CSR of the permuted A and A^T (padded)
+  std::vector<double> av, tv;
+  std::vector<int2> tA, tT;  // warp tiles
+  int nlongA = 0, nlongT = 0;
+  std::vector<double> c0, lx0, ux0, lc0, uc0;  // permuted problem vectors
+  double bnorm = 0, cnorm = 0, off = 0;
+};
+
+void build_layout(const HostLP &h, Layout &L);
+
+}  // namespace gb300lp

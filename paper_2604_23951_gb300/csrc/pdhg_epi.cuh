@@ -1,0 +1,134 @@
+// Per-row epilogues of the PDHG SpMVs (used with warp_spmv of
+// spmv_warp.cuh by the single-LP kernels and by the batched cluster kernel).
+//
+// Every epilogue gets pre(r) (prefetch of the row's own vector entries, so
+// those loads overlap the row's gathers) and then row(r, s) with
+// s = (row r of the matrix) . vec, on the same thread.  Vectors are in the
+// renumbered (length-sorted) order of the device layout.
+#pragma once
+
+#include "device_common.cuh"
+#include "pdhg_state.cuh"
+
+namespace gb300lp {
+
+// out[r] = s (power iteration); acc collects sum s^2
+template <typename O>
+struct StoreSqEpi {
+  O *out;
+  double acc;
+  __device__ __forceinline__ void pre(int) {}
+  __device__ __forceinline__ void row(int r, double s) {
+    out[r] = (O)s;
+    acc += s * s;
+  }
+};
+
+// K1: g = (A~^T y)_j; primal half of the operator T (eq. for the primal
+// step of PDHG), the reflection xbar = 2 xh - x and the Halpern update of x.
+// CHECK: also store xh and collect ||x - xh||^2 and ||xh - x0||^2.
+template <bool CHECK, bool MIXED>
+struct PrimalEpi {
+  const double *c, *lx, *ux;
+  double *x, *x0, *xbar, *xhat;
+  float *xbar_f;
+  double tau;
+  Halpern hc;
+  double acc0, acc1;
+  double xk, cj, lo, hi, a0;
+  __device__ __forceinline__ void pre(int j) {
+    xk = x[j];
+    cj = c[j];
+    lo = lx[j];
+    hi = ux[j];
+    a0 = x0[j];
+  }
+  __device__ __forceinline__ void row(int j, double g) {
+    const double xh = clampd(fma(-tau, cj - g, xk), lo, hi);
+    const double xb = fma(2.0, xh, -xk);
+    x[j] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
+    if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
+    if (CHECK) {
+      xhat[j] = xh;
+      acc0 += (xk - xh) * (xk - xh);
+      acc1 += (xh - a0) * (xh - a0);
+    }
+  }
+};
+
+// K2: h = (A~ xbar)_i; dual half of T with the division-free prox
+// v + sigma proj_[l,u](-v / sigma) = v + proj_[sigma l, sigma u](-v), and the
+// Halpern update of y.
+template <bool CHECK, bool MIXED>
+struct DualEpi {
+  const double *lc, *uc;
+  double *y, *y0, *yhat;
+  float *yf;
+  double sigma;
+  Halpern hc;
+  double acc0, acc1;
+  double yk, lo, hi, a0;
+  __device__ __forceinline__ void pre(int i) {
+    yk = y[i];
+    lo = lc[i];
+    hi = uc[i];
+    a0 = y0[i];
+  }
+  __device__ __forceinline__ void row(int i, double h) {
+    const double v = fma(-sigma, h, yk);
+    const double yh = v + clampd(-v, sigma * lo, sigma * hi);
+    const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
+    y[i] = yn;
+    if (MIXED) yf[i] = (float)yn;
+    if (CHECK) {
+      yhat[i] = yh;
+      acc0 += (yk - yh) * (yk - yh);
+      acc1 += (yh - a0) * (yh - a0);
+    }
+  }
+};
+
+// K3a: rows of A at xh: primal residual of the unscaled A x against
+// [l_c, u_c], the y-domain violation and the y part of the dual objective
+struct KktRowEpi {
+  const double *dr, *idr, *lc0, *uc0, *yhat;
+  double rp2, rdy2, dy;
+  __device__ __forceinline__ void pre(int) {}
+  __device__ __forceinline__ void row(int i, double h) {
+    const double ax = h * idr[i];
+    const double lo = lc0[i], hi = uc0[i];
+    const double pr = clampd(ax, lo, hi);
+    rp2 += (ax - pr) * (ax - pr);
+    const double yv = dr[i] * yhat[i];
+    double yp = yv;
+    if (!isfinite(lo)) yp = fmin(yp, 0.0);
+    if (!isfinite(hi)) yp = fmax(yp, 0.0);
+    rdy2 += (yv - yp) * (yv - yp);
+    dy += support_term(yp, lo, hi);
+  }
+};
+
+// K3b: rows of A^T at yh: reduced costs c - A^T y (unscaled, stored in zbuf),
+// the dual residual, the lambda part of the dual objective and c^T x
+struct KktColEpi {
+  const double *c, *dc, *idc, *c0, *lx0, *ux0, *xhat;
+  double *zbuf;
+  double rd2, dl, p;
+  __device__ __forceinline__ void pre(int) {}
+  __device__ __forceinline__ void row(int j, double h) {
+    const double d = dc[j];
+    const double g = (c[j] - h) * idc[j];
+    const double lo = lx0[j], hi = ux0[j];
+    const bool lf = isfinite(lo), uf = isfinite(hi);
+    double lam = g;
+    if (!lf && !uf) lam = 0.0;
+    else if (lf && !uf) lam = fmax(lam, 0.0);
+    else if (!lf && uf) lam = fmin(lam, 0.0);
+    rd2 += (g - lam) * (g - lam);
+    dl += support_term(lam, lo, hi);
+    p += c0[j] * (d * xhat[j]);
+    zbuf[j] = g;
+  }
+};
+
+}  // namespace gb300lp

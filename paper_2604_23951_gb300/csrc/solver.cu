@@ -2,7 +2,7 @@
 //
 // Data layout in HBM (built once per problem by dev_upload):
 //   * rows of A and rows of A^T (= columns of A) are each sorted by length
-//     (longest first) and cut into tiles (see spmv_tile.cuh); the LP is
+//     (longest first) and cut into warp tiles (see spmv_warp.cuh); the LP is
 //     renumbered with those permutations, so the epilogues of the SpMV
 //     kernels read and write their vectors contiguously;
 //   * A (m rows) and its stored transpose A^T (n rows) in CSR with int32
@@ -42,6 +42,8 @@
 #include "device_common.cuh"
 #include "lp_internal.h"
 #include "pdhg_state.cuh"
+#include "layout.h"
+#include "pdhg_epi.cuh"
 #include "spmv_warp.cuh"
 
 namespace gb300lp {
@@ -50,7 +52,6 @@ namespace gb300lp {
 #define GB300_BLOCK 256
 #endif
 constexpr int kBlock = GB300_BLOCK;
-constexpr int kTilePad = 8;  // value / index arrays padded past nnz
 #ifndef GB300_MIN_BLOCKS
 #define GB300_MIN_BLOCKS (1024 / GB300_BLOCK)
 #endif
@@ -194,35 +195,21 @@ __device__ __forceinline__ Acc *red_smem() {
   return red;
 }
 
-// power iteration on A~^T A~
-struct StoreEpi {
-  double *out;
-  __device__ __forceinline__ void pre(int) {}
-  __device__ __forceinline__ void row(int r, double s) { out[r] = s; }
-};
-struct StoreSqEpi {
-  double *out;
-  double acc;
-  __device__ __forceinline__ void pre(int) {}
-  __device__ __forceinline__ void row(int r, double s) {
-    out[r] = s;
-    acc += s * s;
-  }
-};
-
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, const double *__restrict__ va,
                                                        const double *__restrict__ vec, double *out,
                                                        int *err) {
-  StoreEpi e{out};
-  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, red_smem<double, double, double>());
+  StoreSqEpi<double> e{out, 0.0};
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
                                                           const double *__restrict__ vec,
                                                           double *out, double *partials, int G,
                                                           int *err) {
-  StoreSqEpi e{out, 0.0};
-  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e, red_smem<double, double, double>());
+  StoreSqEpi<double> e{out, 0.0};
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
   double acc[1] = {e.acc};
   const int qi[1] = {Q_PW};
   store_partials<1>(acc, qi, partials, G);
@@ -293,35 +280,6 @@ __global__ void k_reciprocal(int n, const double *__restrict__ d, double *__rest
 // ---------------------------------------------------------------------------
 // the iteration kernels
 
-template <bool CHECK, bool MIXED>
-struct PrimalEpi {
-  const double *c, *lx, *ux;
-  double *x, *x0, *xbar, *xhat;
-  float *xbar_f;
-  double tau;
-  Halpern hc;
-  double acc0, acc1;
-  double xk, cj, lo, hi, a0;
-  __device__ __forceinline__ void pre(int j) {
-    xk = x[j];
-    cj = c[j];
-    lo = lx[j];
-    hi = ux[j];
-    a0 = x0[j];
-  }
-  __device__ __forceinline__ void row(int j, double g) {
-    const double xh = clampd(fma(-tau, cj - g, xk), lo, hi);
-    const double xb = fma(2.0, xh, -xk);
-    x[j] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
-    if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
-    if (CHECK) {
-      xhat[j] = xh;
-      acc0 += (xk - xh) * (xk - xh);
-      acc1 += (xh - a0) * (xh - a0);
-    }
-  }
-};
-
 // T = float: the mixed-precision kernel; it runs the FP32 SpMV while
 // st->mixed_active is set and the FP64 one (va64, y) after the switch
 template <typename T, bool CHECK>
@@ -337,15 +295,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
   if (MIXED && st->mixed_active) {
     PrimalEpi<CHECK, true> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                              halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
-                                       red_smem<T, float, float>());
+    warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
+                                       red_smem<T, float, float>(), blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     PrimalEpi<CHECK, false> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                               halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y,
-                                              e, red_smem<double, double, double>());
+    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y,
+                                              e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
@@ -354,36 +312,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
     store_partials<2>(acc, qi, partials, G);
   }
 }
-
-template <bool CHECK, bool MIXED>
-struct DualEpi {
-  const double *lc, *uc;
-  double *y, *y0, *yhat;
-  float *yf;
-  double sigma;
-  Halpern hc;
-  double acc0, acc1;
-  double yk, lo, hi, a0;
-  __device__ __forceinline__ void pre(int i) {
-    yk = y[i];
-    lo = lc[i];
-    hi = uc[i];
-    a0 = y0[i];
-  }
-  __device__ __forceinline__ void row(int i, double h) {
-    const double v = fma(-sigma, h, yk);
-    // v + sigma proj_[l,u](-v / sigma) = v + proj_[sigma l, sigma u](-v)
-    const double yh = v + clampd(-v, sigma * lo, sigma * hi);
-    const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
-    y[i] = yn;
-    if (MIXED) yf[i] = (float)yn;
-    if (CHECK) {
-      yhat[i] = yh;
-      acc0 += (yk - yh) * (yk - yh);
-      acc1 += (yh - a0) * (yh - a0);
-    }
-  }
-};
 
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
@@ -398,15 +326,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
   if (MIXED && st->mixed_active) {
     DualEpi<CHECK, true> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                            0.0, 0.0, 0.0, 0.0};
-    warp_spmv<kBlock, T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
-                                       red_smem<T, float, float>());
+    warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
+                                       red_smem<T, float, float>(), blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     DualEpi<CHECK, false> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                             0.0, 0.0, 0.0, 0.0};
-    warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64,
-                                              xbar, e, red_smem<double, double, double>());
+    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64,
+                                              xbar, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
@@ -416,25 +344,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
   }
 }
 
-// K3a: rows of A: primal residual of the unscaled A x and the y terms
-struct KktRowEpi {
-  const double *dr, *idr, *lc0, *uc0, *yhat;
-  double rp2, rdy2, dy;
-  __device__ __forceinline__ void pre(int) {}
-  __device__ __forceinline__ void row(int i, double h) {
-    const double ax = h * idr[i];
-    const double lo = lc0[i], hi = uc0[i];
-    const double pr = clampd(ax, lo, hi);
-    rp2 += (ax - pr) * (ax - pr);
-    const double yv = dr[i] * yhat[i];
-    double yp = yv;
-    if (!isfinite(lo)) yp = fmin(yp, 0.0);
-    if (!isfinite(hi)) yp = fmax(yp, 0.0);
-    rdy2 += (yv - yp) * (yv - yp);
-    dy += support_term(yp, lo, hi);
-  }
-};
-
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     MatDev M, const double *__restrict__ va, const double *__restrict__ xhat,
     const double *__restrict__ dr, const double *__restrict__ idr,
@@ -443,33 +352,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
-  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>());
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
   double acc[3] = {e.rp2, e.rdy2, e.dy};
   const int qi[3] = {Q_RP, Q_RDY, Q_DY};
   store_partials<3>(acc, qi, partials, G);
 }
-
-// K3b: rows of A^T: dual residual, lambda terms and the primal objective
-struct KktColEpi {
-  const double *c, *dc, *idc, *c0, *lx0, *ux0, *xhat;
-  double *zbuf;
-  double rd2, dl, p;
-  __device__ __forceinline__ void pre(int) {}
-  __device__ __forceinline__ void row(int j, double h) {
-    const double d = dc[j];
-    const double g = (c[j] - h) * idc[j];
-    const double lo = lx0[j], hi = ux0[j];
-    const bool lf = isfinite(lo), uf = isfinite(hi);
-    double lam = g;
-    if (!lf && !uf) lam = 0.0;
-    else if (lf && !uf) lam = fmax(lam, 0.0);
-    else if (!lf && uf) lam = fmin(lam, 0.0);
-    rd2 += (g - lam) * (g - lam);
-    dl += support_term(lam, lo, hi);
-    p += c0[j] * (d * xhat[j]);
-    zbuf[j] = g;
-  }
-};
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     MatDev M, const double *__restrict__ va, const double *__restrict__ yhat,
@@ -479,7 +366,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     double *partials, int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
-  warp_spmv<kBlock, double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>());
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
   double acc[3] = {e.rd2, e.dl, e.p};
   const int qi[3] = {Q_RD, Q_DL, Q_P};
   store_partials<3>(acc, qi, partials, G);
@@ -623,42 +510,6 @@ struct DeviceLP {
   }
 };
 
-// Sort rows by length (longest first, stable).  Rows longer than kLongRow
-// come first (nlong of them, one whole-CTA reduction each); the rest are cut
-// into warp tiles of at most 32 rows and about kWarpTileNnz nonzeros, each
-// reducing its rows with 2^v lanes so no lane owns more than kWarpItems.
-static void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
-                       std::vector<int2> &tiles, int &nlong) {
-  const int rows = (int)len.size();
-  int64_t lmax = 0;
-  for (int64_t L : len) lmax = std::max(lmax, L);
-  const int64_t cap = std::min<int64_t>(lmax, (int64_t)kLongRow + 1);
-  std::vector<int> cnt(cap + 2, 0);
-  for (int64_t L : len) cnt[std::min(L, cap)]++;
-  std::vector<int> start(cap + 2, 0);
-  int acc = 0;
-  for (int64_t L = cap; L >= 0; --L) {
-    start[L] = acc;
-    acc += cnt[L];
-  }
-  perm.assign(rows, 0);
-  for (int r = 0; r < rows; ++r) perm[start[std::min(len[r], cap)]++] = r;
-  tiles.clear();
-  int i = 0;
-  while (i < rows && len[perm[i]] > kLongRow) ++i;
-  nlong = i;
-  while (i < rows) {
-    const int64_t L = len[perm[i]];
-    int vlog = 0;
-    const int64_t per = (L + kWarpItems - 1) / kWarpItems;
-    while ((1LL << vlog) < per && vlog < 5) ++vlog;
-    int nr = (int)std::max<int64_t>(1, std::min<int64_t>(32, kWarpTileNnz / std::max<int64_t>(L, 1)));
-    nr = std::min(nr, rows - i);
-    tiles.push_back(make_int2(i, nr | (vlog << 8)));
-    i += nr;
-  }
-}
-
 DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
   DeviceLP *d = new DeviceLP();
   try {
@@ -707,66 +558,18 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     d->m = m;
     d->n = n;
     d->nnz = nnz;
-    std::vector<int64_t> rlen(m), clen(n, 0);
-    for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
-    for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
-    std::vector<int2> tA, tT;
-    plan_tiles(rlen, d->rperm, tA, d->nlongA);
-    plan_tiles(clen, d->cperm, tT, d->nlongT);
+    Layout L;
+    build_layout(h, L);
+    d->rperm = std::move(L.rperm);
+    d->cperm = std::move(L.cperm);
+    d->nlongA = L.nlongA;
+    d->nlongT = L.nlongT;
+    const std::vector<int2> &tA = L.tA, &tT = L.tT;
     d->ntilesA = (int)tA.size();
     d->ntilesT = (int)tT.size();
-    std::vector<int> rinv(m), cinv(n);
-    for (int i = 0; i < m; ++i) rinv[d->rperm[i]] = i;
-    for (int j = 0; j < n; ++j) cinv[d->cperm[j]] = j;
-    // permuted A
-    std::vector<int> arp(m + 1, 0), aci(nnz + kTilePad, 0);
-    std::vector<double> av(nnz + kTilePad, 0.0);
-    for (int i = 0; i < m; ++i) {
-      int o = d->rperm[i];
-      arp[i + 1] = arp[i] + (int)rlen[o];
-      int w = arp[i];
-      for (int64_t k = h.row_ptr[o]; k < h.row_ptr[o + 1]; ++k, ++w) {
-        aci[w] = cinv[h.col_idx[k]];
-        av[w] = h.val[k];
-      }
-    }
-    // transpose of the permuted A, rows in new column order, entries by new row
-    std::vector<int> trp(n + 1, 0), tci(nnz + kTilePad, 0);
-    std::vector<double> tv(nnz + kTilePad, 0.0);
-    for (int j = 0; j < n; ++j) trp[j + 1] = trp[j] + (int)clen[d->cperm[j]];
-    {
-      std::vector<int> cur(trp.begin(), trp.end() - 1);
-      for (int i = 0; i < m; ++i)
-        for (int k = arp[i]; k < arp[i + 1]; ++k) {
-          int j = aci[k];
-          tci[cur[j]] = i;
-          tv[cur[j]] = av[k];
-          ++cur[j];
-        }
-    }
-    std::vector<double> c0(n), lx0(n), ux0(n), lc0(m), uc0(m);
-    for (int j = 0; j < n; ++j) {
-      int o = d->cperm[j];
-      c0[j] = h.c[o];
-      lx0[j] = h.col_lo[o];
-      ux0[j] = h.col_hi[o];
-    }
-    for (int i = 0; i < m; ++i) {
-      int o = d->rperm[i];
-      lc0[i] = h.row_lo[o];
-      uc0[i] = h.row_hi[o];
-    }
-    // norms of the unscaled data for the relative KKT error
-    double bn2 = 0, cn2 = 0;
-    for (int i = 0; i < m; ++i) {
-      bool lf = std::isfinite(lc0[i]), uf = std::isfinite(uc0[i]);
-      if (lf) bn2 += lc0[i] * lc0[i];
-      if (uf && !(lf && lc0[i] == uc0[i])) bn2 += uc0[i] * uc0[i];
-    }
-    for (int j = 0; j < n; ++j) cn2 += c0[j] * c0[j];
-    d->bnorm = std::sqrt(bn2);
-    d->cnorm = std::sqrt(cn2);
-    d->off = h.off;
+    d->bnorm = L.bnorm;
+    d->cnorm = L.cnorm;
+    d->off = L.off;
     // device buffers (value / index arrays padded for the aligned tile copies)
     const size_t nzp = (size_t)nnz + kTilePad;
     d->A_rp = d->dalloc_n<int>(m + 1);
@@ -801,21 +604,21 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     d->G = std::max(1, std::min(need, d->sm_count * occ));
     d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
     d->st = d->dalloc_n<State>(1);
-    CK(cudaMemcpyAsync(d->A_rp, arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_ci, aci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_v0, av.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_rp, trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_ci, tci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_v0, tv.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_rp, L.arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_ci, L.aci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_v0, L.av.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_rp, L.trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_ci, L.tci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_v0, L.tv.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
     if (!tA.empty())
       CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int2) * tA.size(), cudaMemcpyHostToDevice, d->s));
     if (!tT.empty())
       CK(cudaMemcpyAsync(d->tilesT, tT.data(), sizeof(int2) * tT.size(), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->c0, c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->lx0, lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->ux0, ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->lc0, lc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->uc0, uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->c0, L.c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->lx0, L.lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->ux0, L.ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->lc0, L.lc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->uc0, L.uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
     // the padding of the scaled copies is never used by the arithmetic, but
     // the tile copies read it: give it defined contents
     CK(cudaMemsetAsync(d->A_v, 0, sizeof(double) * nzp, d->s));

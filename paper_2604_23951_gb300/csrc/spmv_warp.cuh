@@ -51,29 +51,31 @@ __device__ __forceinline__ WarpTile load_wtile(const int2 *__restrict__ tiles, i
   return w;
 }
 
-// Rows [0, nlong) are long rows, one per CTA (blockIdx.x, + gridDim.x, ...),
-// reduced by the whole CTA; then each warp walks its warp tiles (wid,
-// wid + wstride, ...).  For every row r: epi.pre(r) then
-// epi.row(r, sum_k va[k] * vec[ci[k]]), both on the same thread.
-// red: kBlock / 32 Acc of shared memory for the CTA rows.
-template <int kBlock, typename T, typename V, typename Acc, class Epi>
+// The work is shared by ncta CTAs (this one is number cta): rows [0, nlong)
+// are long rows, one per CTA (cta, cta + ncta, ...), reduced by the whole
+// CTA; then each warp walks its warp tiles (wid, wid + wstride, ...).  For
+// every row r: epi.pre(r) then epi.row(r, sum_k va[k] * vec[ci[k]]), both on
+// the same thread.  red: blockDim.x / 32 Acc of shared memory.
+template <typename T, typename V, typename Acc, class Epi>
 __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ tiles, int ntiles,
                                           const int *__restrict__ rp, const int *__restrict__ ci,
                                           const T *__restrict__ va, const V *__restrict__ vec,
-                                          Epi &epi, Acc *red) {
+                                          Epi &epi, Acc *red, int cta, int ncta) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  const int nthr = blockDim.x;
+  const int nwarp = nthr >> 5;
   // ---- long rows: whole CTA per row ------------------------------------
-  for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
+  for (int r = cta; r < nlong; r += ncta) {
     if (threadIdx.x == 0) epi.pre(r);
     const int lo = rp[r], hi = rp[r + 1];
     Acc s = 0;
-    for (int base = lo + threadIdx.x; base < hi; base += kBlock * kWarpItems) {
+    for (int base = lo + threadIdx.x; base < hi; base += nthr * kWarpItems) {
       int j[kWarpItems];
       T a[kWarpItems];
 #pragma unroll
       for (int u = 0; u < kWarpItems; ++u) {
-        const int k = base + kBlock * u;
+        const int k = base + nthr * u;
         j[u] = k < hi ? ci[k] : 0;
         a[u] = k < hi ? va[k] : (T)0;
       }
@@ -89,14 +91,14 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
     __syncthreads();
     if (threadIdx.x == 0) {
       Acc t = 0;
-      for (int w = 0; w < kBlock / 32; ++w) t += red[w];
+      for (int w = 0; w < nwarp; ++w) t += red[w];
       epi.row(r, (double)t);
     }
     __syncthreads();
   }
   // ---- warp tiles ---------------------------------------------------------
-  const int wid = blockIdx.x * (kBlock / 32) + warp;
-  const int wstride = gridDim.x * (kBlock / 32);
+  const int wid = cta * nwarp + warp;
+  const int wstride = ncta * nwarp;
   for (int t = wid; t < ntiles; t += wstride) {
     const WarpTile w = load_wtile(tiles, t);
     const bool has = lane < w.nrows;
