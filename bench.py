@@ -151,7 +151,8 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("solver.cu", "device_common.cuh"):
+    for f in ("solver.cu", "device_common.cuh", "spmv_warp.cuh", "pdhg_epi.cuh",
+              "pdhg_state.cuh", "layout.cpp", "layout.h"):
         with open(os.path.join(ROOT, "paper_2604_23951_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
