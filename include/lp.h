@@ -214,6 +214,17 @@ int lp_get_data(const lp_problem *lp, int64_t *row_ptr, int32_t *col_idx,
  * rel_d, rel_gap, primal_obj, dual_obj (6 doubles). */
 int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, double *out);
 
+/* The row plan of the device layout, for `rows` rows of lengths len[]:
+ * perm[new] = old row (rows longer than 512 entries first, then rows longer
+ * than 256, then the rest by length, longest first; stable within a class);
+ * *nlong = the number of rows longer than 512 (each reduced by one CTA);
+ * tiles[2 t], tiles[2 t + 1] = first row and packed word (nrows | lanes_log2
+ * << 8 | entries_per_lane << 12) of warp tile t, for t < *ntiles.  tiles
+ * holds `tile_cap` pairs; LP_ERR_INVALID (and *ntiles = the count needed) if
+ * that is too few.  Host only; no device needed. */
+int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles,
+                 int32_t tile_cap, int32_t *ntiles, int32_t *nlong);
+
 /* Measurement hook (no counterpart in the paper): time the PDHG iteration
  * kernels of the last lp_solve one launch at a time with CUDA events on the
  * problem's stream, each launch after a 256 MiB write that evicts L2.

@@ -17,5 +17,6 @@ from .capi import (  # noqa: F401
     Server,
     TorchDevice,
     load,
+    plan_rows,
     solve_opts,
 )

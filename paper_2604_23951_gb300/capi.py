@@ -97,6 +97,7 @@ SIGNATURES = [
     ("lp_batch_submit", C.c_int, [_P, _P, C.POINTER(C.c_uint64)]),
     ("lp_batch_poll", C.c_int, [_P, C.c_uint64, C.POINTER(lp_result), _D, _D]),
     ("lp_server_pump", C.c_int, [_P, C.c_int32]),
+    ("lp_plan_rows", C.c_int, [C.c_int32, _I64, _I32, _I32, C.c_int32, _I32, _I32]),
     ("lp_server_tune", C.c_int, [_P, C.c_int64, C.c_int32, C.c_double]),
     ("lp_batch_cancel", C.c_int, [_P, C.c_uint64]),
     ("lp_server_stats", C.c_int, [_P, _I64]),
@@ -143,6 +144,22 @@ def dptr(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def plan_rows(lengths):
+    """Row order and warp tiles the device layout uses for rows of the given
+    lengths (lp_plan_rows): (perm, tiles as an (ntiles, 2) int32 array of
+    (first row, packed word), nlong)."""
+    lib = load()
+    L = np.ascontiguousarray(lengths, dtype=np.int64)
+    rows = int(L.size)
+    perm = np.zeros(max(rows, 1), dtype=np.int32)
+    nt, nl = C.c_int32(), C.c_int32()
+    cap = rows + 1
+    tiles = np.zeros(2 * cap, dtype=np.int32)
+    check(lib.lp_plan_rows(rows, L.ctypes.data_as(_I64), perm.ctypes.data_as(_I32),
+                           tiles.ctypes.data_as(_I32), cap, C.byref(nt), C.byref(nl)))
+    return perm[:rows], tiles[: 2 * nt.value].reshape(-1, 2), nl.value
 
 
 # --------------------------------------------------------------------------

@@ -665,11 +665,12 @@ static void pack_request(const HostLP &h, Packed &p) {
   SlotDesc &r = p.rel;
   auto P = [](size_t o) { return reinterpret_cast<void *>(o); };
   const size_t ntA = L.tA.size(), ntT = L.tT.size();
+  const size_t nzA = (size_t)nnz, nzT = (size_t)nnz;
   size_t o_tA = take(sizeof(int2) * ntA), o_tT = take(sizeof(int2) * ntT);
-  size_t o_arp = take(sizeof(int) * (m + 1)), o_aci = take(sizeof(int) * nnz);
-  size_t o_trp = take(sizeof(int) * (n + 1)), o_tci = take(sizeof(int) * nnz);
-  size_t o_av0 = take(8 * nnz), o_tv0 = take(8 * nnz), o_av = take(8 * nnz), o_tv = take(8 * nnz);
-  size_t o_avf = take(4 * nnz), o_tvf = take(4 * nnz);
+  size_t o_arp = take(sizeof(int) * (m + 1)), o_aci = take(sizeof(int) * nzA);
+  size_t o_trp = take(sizeof(int) * (n + 1)), o_tci = take(sizeof(int) * nzT);
+  size_t o_av0 = take(8 * nzA), o_tv0 = take(8 * nzT), o_av = take(8 * nzA), o_tv = take(8 * nzT);
+  size_t o_avf = take(4 * nzA), o_tvf = take(4 * nzT);
   size_t o_c0 = take(8 * n), o_lx0 = take(8 * n), o_ux0 = take(8 * n);
   size_t o_lc0 = take(8 * m), o_uc0 = take(8 * m);
   r.m = m;
@@ -715,11 +716,11 @@ static void pack_request(const HostLP &h, Packed &p) {
   put(o_tA, L.tA.data(), sizeof(int2) * ntA);
   put(o_tT, L.tT.data(), sizeof(int2) * ntT);
   put(o_arp, L.arp.data(), sizeof(int) * (m + 1));
-  put(o_aci, L.aci.data(), sizeof(int) * nnz);
+  put(o_aci, L.aci.data(), sizeof(int) * nzA);
   put(o_trp, L.trp.data(), sizeof(int) * (n + 1));
-  put(o_tci, L.tci.data(), sizeof(int) * nnz);
-  put(o_av0, L.av.data(), 8 * nnz);
-  put(o_tv0, L.tv.data(), 8 * nnz);
+  put(o_tci, L.tci.data(), sizeof(int) * nzT);
+  put(o_av0, L.av.data(), 8 * nzA);
+  put(o_tv0, L.tv.data(), 8 * nzT);
   put(o_c0, L.c0.data(), 8 * n);
   put(o_lx0, L.lx0.data(), 8 * n);
   put(o_ux0, L.ux0.data(), 8 * n);

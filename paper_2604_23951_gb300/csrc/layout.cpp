@@ -3,44 +3,60 @@
 
 #include <algorithm>
 #include <cmath>
+#include <string>
 
 #include "spmv_warp.cuh"
 
 namespace gb300lp {
 
-// Sort rows by length (longest first, stable).  Rows longer than kLongRow
-// come first (nlong of them, one whole-CTA reduction each); the rest are cut
-// into warp tiles of at most 32 rows and about kWarpTileNnz nonzeros, each
-// reducing its rows with 2^v lanes so no lane owns more than kWarpItems.
-static void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
-                       std::vector<int2> &tiles, int &nlong) {
+// Order rows for the warp engine (stable within a class): rows longer than
+// kCtaRow first (nlong of them, one whole CTA each), then rows longer than
+// kLongRow (a single-row warp tile each), then the rest by length, longest
+// first, cut into warp tiles of at most 32 rows and about kWarpTileNnz
+// nonzeros.  A tile's lanes per row 2^v is the least with 2^v * kWarpItems
+// >= its longest row L, and its entries per lane nit = ceil(L / 2^v).
+void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
+                std::vector<int2> &tiles, int &nlong) {
   const int rows = (int)len.size();
-  int64_t lmax = 0;
-  for (int64_t L : len) lmax = std::max(lmax, L);
-  const int64_t cap = std::min<int64_t>(lmax, (int64_t)kLongRow + 1);
-  std::vector<int> cnt(cap + 2, 0);
-  for (int64_t L : len) cnt[std::min(L, cap)]++;
-  std::vector<int> start(cap + 2, 0);
+  // key: the length for rows up to kLongRow, kLongRow + 1 for warp-long
+  // rows, kLongRow + 2 for CTA rows; counting sort by descending key
+  auto key = [](int64_t L) -> int {
+    if (L > kCtaRow) return kLongRow + 2;
+    if (L > kLongRow) return kLongRow + 1;
+    return (int)L;
+  };
+  const int nkeys = kLongRow + 3;
+  std::vector<int> cnt(nkeys, 0);
+  for (int64_t L : len) cnt[key(L)]++;
+  std::vector<int> start(nkeys, 0);
   int acc = 0;
-  for (int64_t L = cap; L >= 0; --L) {
-    start[L] = acc;
-    acc += cnt[L];
+  for (int k = nkeys - 1; k >= 0; --k) {
+    start[k] = acc;
+    acc += cnt[k];
   }
   perm.assign(rows, 0);
-  for (int r = 0; r < rows; ++r) perm[start[std::min(len[r], cap)]++] = r;
+  for (int r = 0; r < rows; ++r) perm[start[key(len[r])]++] = r;
   tiles.clear();
   int i = 0;
-  while (i < rows && len[perm[i]] > kLongRow) ++i;
+  while (i < rows && len[perm[i]] > kCtaRow) ++i;
   nlong = i;
+  while (i < rows && len[perm[i]] > kLongRow) {
+    tiles.push_back(pack_wtile(i, 1, 5, kWarpItems));
+    ++i;
+  }
   while (i < rows) {
     const int64_t L = len[perm[i]];
-    int vlog = 0;
-    const int64_t per = (L + kWarpItems - 1) / kWarpItems;
-    while ((1LL << vlog) < per && vlog < 5) ++vlog;
+#ifndef GB300_MIN_VLOG
+#define GB300_MIN_VLOG 0
+#endif
+    int vlog = GB300_MIN_VLOG;
+    while ((int64_t(1) << vlog) * kWarpItems < L) ++vlog;
+    const int vl = 1 << vlog;
+    const int nit = (int)std::max<int64_t>(1, (L + vl - 1) / vl);
     int nr = (int)std::max<int64_t>(
         1, std::min<int64_t>(32, kWarpTileNnz / std::max<int64_t>(L, 1)));
     nr = std::min(nr, rows - i);
-    tiles.push_back(make_int2(i, nr | (vlog << 8)));
+    tiles.push_back(pack_wtile(i, nr, vlog, nit));
     i += nr;
   }
 }
@@ -115,3 +131,39 @@ void build_layout(const HostLP &h, Layout &L) {
 }
 
 }  // namespace gb300lp
+
+namespace gb300lp {
+void set_last_error(const std::string &m);
+}
+
+extern "C" int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles,
+                            int32_t tile_cap, int32_t *ntiles, int32_t *nlong) {
+  using namespace gb300lp;
+  if (rows < 0 || (rows > 0 && (!len || !perm)) || !ntiles || !nlong || tile_cap < 0 ||
+      (tile_cap > 0 && !tiles)) {
+    set_last_error("lp_plan_rows: invalid argument");
+    return LP_ERR_INVALID;
+  }
+  std::vector<int64_t> L(len, len + rows);
+  for (int64_t v : L)
+    if (v < 0) {
+      set_last_error("lp_plan_rows: negative row length");
+      return LP_ERR_INVALID;
+    }
+  std::vector<int> p;
+  std::vector<int2> t;
+  int nl = 0;
+  plan_tiles(L, p, t, nl);
+  *ntiles = (int32_t)t.size();
+  *nlong = nl;
+  if ((int64_t)t.size() > tile_cap) {
+    set_last_error("lp_plan_rows: tile_cap too small");
+    return LP_ERR_INVALID;
+  }
+  std::copy(p.begin(), p.end(), perm);
+  for (size_t k = 0; k < t.size(); ++k) {
+    tiles[2 * k] = t[k].x;
+    tiles[2 * k + 1] = t[k].y;
+  }
+  return LP_OK;
+}

@@ -29,4 +29,8 @@ struct Layout {
 
 void build_layout(const HostLP &h, Layout &L);
 
+// the row order and warp tiles of one matrix (exposed for the layout checks)
+void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
+                std::vector<int2> &tiles, int &nlong);
+
 }  // namespace gb300lp

@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, con
                                                        int *err) {
   StoreSqEpi<double> e{out, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
-                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, 
                                                           int *err) {
   StoreSqEpi<double> e{out, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
-                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
   double acc[1] = {e.acc};
   const int qi[1] = {Q_PW};
   store_partials<1>(acc, qi, partials, G);
@@ -296,14 +298,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
     PrimalEpi<CHECK, true> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                              halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
-                                       red_smem<T, float, float>(), blockIdx.x, gridDim.x);
+                                       red_smem<T, float, float>(),
+                          blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     PrimalEpi<CHECK, false> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                               halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y,
-                                              e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                              e, red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
@@ -327,14 +331,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
     DualEpi<CHECK, true> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                            0.0, 0.0, 0.0, 0.0};
     warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
-                                       red_smem<T, float, float>(), blockIdx.x, gridDim.x);
+                                       red_smem<T, float, float>(),
+                          blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     DualEpi<CHECK, false> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                             0.0, 0.0, 0.0, 0.0};
     warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64,
-                                              xbar, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                              xbar, e, red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
-  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
   double acc[3] = {e.rp2, e.rdy2, e.dy};
   const int qi[3] = {Q_RP, Q_RDY, Q_DY};
   store_partials<3>(acc, qi, partials, G);
@@ -366,7 +373,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     double *partials, int G, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
-  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>(),
+                          blockIdx.x, gridDim.x);
   double acc[3] = {e.rd2, e.dl, e.p};
   const int qi[3] = {Q_RD, Q_DL, Q_P};
   store_partials<3>(acc, qi, partials, G);
@@ -570,18 +578,18 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     d->bnorm = L.bnorm;
     d->cnorm = L.cnorm;
     d->off = L.off;
-    // device buffers (value / index arrays padded for the aligned tile copies)
-    const size_t nzp = (size_t)nnz + kTilePad;
+    // device buffers (value / index arrays padded past nnz)
+    const size_t nzA = (size_t)nnz + kTilePad, nzT = (size_t)nnz + kTilePad;
     d->A_rp = d->dalloc_n<int>(m + 1);
-    d->A_ci = d->dalloc_n<int>(nzp);
-    d->A_v0 = d->dalloc_n<double>(nzp);
-    d->A_v = d->dalloc_n<double>(nzp);
+    d->A_ci = d->dalloc_n<int>(nzA);
+    d->A_v0 = d->dalloc_n<double>(nzA);
+    d->A_v = d->dalloc_n<double>(nzA);
     d->T_rp = d->dalloc_n<int>(n + 1);
-    d->T_ci = d->dalloc_n<int>(nzp);
-    d->T_v0 = d->dalloc_n<double>(nzp);
-    d->T_v = d->dalloc_n<double>(nzp);
-    d->A_vf = d->dalloc_n<float>(nzp);
-    d->T_vf = d->dalloc_n<float>(nzp);
+    d->T_ci = d->dalloc_n<int>(nzT);
+    d->T_v0 = d->dalloc_n<double>(nzT);
+    d->T_v = d->dalloc_n<double>(nzT);
+    d->A_vf = d->dalloc_n<float>(nzA);
+    d->T_vf = d->dalloc_n<float>(nzT);
     d->tilesA = d->dalloc_n<int2>(std::max<size_t>(tA.size(), 1));
     d->tilesT = d->dalloc_n<int2>(std::max<size_t>(tT.size(), 1));
     double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
@@ -605,11 +613,11 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
     d->st = d->dalloc_n<State>(1);
     CK(cudaMemcpyAsync(d->A_rp, L.arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_ci, L.aci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->A_v0, L.av.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_ci, L.aci.data(), sizeof(int) * nzA, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->A_v0, L.av.data(), sizeof(double) * nzA, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->T_rp, L.trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_ci, L.tci.data(), sizeof(int) * nzp, cudaMemcpyHostToDevice, d->s));
-    CK(cudaMemcpyAsync(d->T_v0, L.tv.data(), sizeof(double) * nzp, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_ci, L.tci.data(), sizeof(int) * nzT, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->T_v0, L.tv.data(), sizeof(double) * nzT, cudaMemcpyHostToDevice, d->s));
     if (!tA.empty())
       CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int2) * tA.size(), cudaMemcpyHostToDevice, d->s));
     if (!tT.empty())
@@ -621,10 +629,10 @@ int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &er
     CK(cudaMemcpyAsync(d->uc0, L.uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
     // the padding of the scaled copies is never used by the arithmetic, but
     // the tile copies read it: give it defined contents
-    CK(cudaMemsetAsync(d->A_v, 0, sizeof(double) * nzp, d->s));
-    CK(cudaMemsetAsync(d->T_v, 0, sizeof(double) * nzp, d->s));
-    CK(cudaMemsetAsync(d->A_vf, 0, sizeof(float) * nzp, d->s));
-    CK(cudaMemsetAsync(d->T_vf, 0, sizeof(float) * nzp, d->s));
+    CK(cudaMemsetAsync(d->A_v, 0, sizeof(double) * nzA, d->s));
+    CK(cudaMemsetAsync(d->T_v, 0, sizeof(double) * nzT, d->s));
+    CK(cudaMemsetAsync(d->A_vf, 0, sizeof(float) * nzA, d->s));
+    CK(cudaMemsetAsync(d->T_vf, 0, sizeof(float) * nzT, d->s));
     CK(cudaStreamSynchronize(d->s));
     d->uploaded = true;
   } catch (const DeviceOOM &e) {

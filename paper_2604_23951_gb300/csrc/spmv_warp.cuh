@@ -4,17 +4,20 @@
 // at most 32 consecutive rows.  Every warp of a persistent grid walks its
 // tiles independently -- no CTA barrier inside the loop -- so the warps of an
 // SM hide each other's memory latency.  In a tile each row is reduced by
-// 2^v lanes (v from the tile's longest row, so no lane owns more than
-// kWarpItems entries); a lane issues all its coalesced value / index loads
-// and all its gathers before its first multiply-add.  Group sums are
+// 2^v lanes, and each lane owns `nit` entries of its row per chunk (v and
+// nit from the tile's longest row, so padding is bounded by the length
+// spread inside one tile); a lane issues all its coalesced value / index
+// loads and all its gathers before its first multiply-add.  Group sums are
 // combined with xor shuffles and moved to lane = row, so the epilogue runs
 // with one lane per row and all lanes active.  A warp tile holds about
-// kWarpTileNnz nonzeros so the tiles balance across warps; rows longer than
-// 32 * kWarpItems come first and are each reduced by a whole CTA.
+// kWarpTileNnz nonzeros so the tiles balance across warps.  Rows longer than
+// kLongRow get a tile of their own (one warp, 32 lanes, chunks of 256
+// entries); rows longer than kCtaRow come first and are each reduced by a
+// whole CTA, so no warp walks a long chain of chunks.
 //
-// FP64 issue is scarce on GB300 (2 FP64 lanes per clock per SM): the
-// length-sorted tiles keep the multiply-adds at full lanes and the epilogue
-// never runs with idle lanes.
+// FP64 issue is scarce on GB300 (2 FP64 lanes per clock per SM): every
+// multiply-add a warp issues has (up to the in-tile length spread) all 32
+// lanes on real entries, and the epilogue never runs with idle lanes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,65 +28,86 @@
 
 namespace gb300lp {
 
-#ifndef GB300_WARP_ITEMS
-#define GB300_WARP_ITEMS 8
-#endif
-constexpr int kWarpItems = GB300_WARP_ITEMS;  // entries one lane owns per pass
-constexpr int kLongRow = 32 * kWarpItems;      // longer rows: single-row tiles
+constexpr int kWarpItems = 8;                 // most entries one lane owns per chunk
+constexpr int kLongRow = 32 * kWarpItems;      // longer rows: single-row warp tiles
+constexpr int kCtaRow = 512;                   // longer rows: one whole CTA each
+constexpr int kWarpTileNnz = 512;              // nonzeros a warp tile aims at
 
-constexpr int kWarpTileNnz = 512;             // nonzeros a warp tile aims at
-
-// A warp tile: rows [r0, r0 + nrows) with lanes per row 2^vlog, packed as
-// int2 {r0, nrows | vlog << 8}.  Rows longer than kLongRow are not in warp
-// tiles: they come first in the row order and each is reduced by a whole CTA.
-constexpr int kWarpLongMode = 6;
-
+// A warp tile: rows [r0, r0 + nrows) with 2^vlog lanes per row and nit
+// entries per lane per chunk, packed as int2 {r0, nrows | vlog << 8 |
+// nit << 12}.
 struct WarpTile {
-  int r0, nrows, vlog;
+  int r0, nrows, vlog, nit;
 };
+
+__host__ __device__ __forceinline__ int2 pack_wtile(int r0, int nrows, int vlog, int nit) {
+  return make_int2(r0, nrows | (vlog << 8) | (nit << 12));
+}
 
 __device__ __forceinline__ WarpTile load_wtile(const int2 *__restrict__ tiles, int t) {
   int2 v = tiles[t];
   WarpTile w;
   w.r0 = v.x;
   w.nrows = v.y & 0xff;
-  w.vlog = v.y >> 8;
+  w.vlog = (v.y >> 8) & 0xf;
+  w.nit = v.y >> 12;
   return w;
 }
 
-// The work is shared by ncta CTAs (this one is number cta): rows [0, nlong)
-// are long rows, one per CTA (cta, cta + ncta, ...), reduced by the whole
-// CTA; then each warp walks its warp tiles (wid, wid + wstride, ...).  For
-// every row r: epi.pre(r) then epi.row(r, sum_k va[k] * vec[ci[k]]), both on
-// the same thread.  red: blockDim.x / 32 Acc of shared memory.
+// sum over the entries lo + gl, lo + gl + vl, ... < hi of va[k] * vec[ci[k]],
+// NIT entries per chunk: all loads and gathers of a chunk before its FMAs
+template <int NIT, typename T, typename V, typename Acc>
+__device__ __forceinline__ Acc group_dot(int lo, int hi, int gl, int vl,
+                                         const int *__restrict__ ci, const T *__restrict__ va,
+                                         const V *__restrict__ vec) {
+  Acc s = 0;
+  const int span = vl * NIT;
+  for (int k0 = lo + gl; k0 < hi; k0 += span) {
+    int j[NIT];
+    T a[NIT];
+#pragma unroll
+    for (int u = 0; u < NIT; ++u) {
+      const int k = k0 + u * vl;
+      j[u] = k < hi ? ci[k] : 0;
+      a[u] = k < hi ? va[k] : (T)0;
+    }
+    V g[NIT];
+#pragma unroll
+    for (int u = 0; u < NIT; ++u) g[u] = vec[j[u]];
+#pragma unroll
+    for (int u = 0; u < NIT; ++u) s += (Acc)a[u] * (Acc)g[u];
+  }
+  return s;
+}
+
+// Rows [0, nlong), one per CTA (cta, cta + ncta, ...), each reduced by the
+// whole CTA (entries per thread sized to the row, at most kWarpItems per
+// chunk); epi.pre / epi.row run on thread 0.
 template <typename T, typename V, typename Acc, class Epi>
-__device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ tiles, int ntiles,
-                                          const int *__restrict__ rp, const int *__restrict__ ci,
-                                          const T *__restrict__ va, const V *__restrict__ vec,
-                                          Epi &epi, Acc *red, int cta, int ncta) {
+__device__ __forceinline__ void cta_rows(int nlong, const int *__restrict__ rp,
+                                         const int *__restrict__ ci, const T *__restrict__ va,
+                                         const V *__restrict__ vec, Epi &epi, Acc *red, int cta,
+                                         int ncta) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nthr = blockDim.x;
   const int nwarp = nthr >> 5;
-  // ---- long rows: whole CTA per row ------------------------------------
   for (int r = cta; r < nlong; r += ncta) {
     if (threadIdx.x == 0) epi.pre(r);
     const int lo = rp[r], hi = rp[r + 1];
+    // entries per thread per chunk: just enough for one chunk, at most
+    // kWarpItems (CTA-uniform)
+    const int nit = min(kWarpItems, max(1, (hi - lo + nthr - 1) / nthr));
     Acc s = 0;
-    for (int base = lo + threadIdx.x; base < hi; base += nthr * kWarpItems) {
-      int j[kWarpItems];
-      T a[kWarpItems];
-#pragma unroll
-      for (int u = 0; u < kWarpItems; ++u) {
-        const int k = base + nthr * u;
-        j[u] = k < hi ? ci[k] : 0;
-        a[u] = k < hi ? va[k] : (T)0;
-      }
-      V g[kWarpItems];
-#pragma unroll
-      for (int u = 0; u < kWarpItems; ++u) g[u] = vec[j[u]];
-#pragma unroll
-      for (int u = 0; u < kWarpItems; ++u) s += (Acc)a[u] * (Acc)g[u];
+    switch (nit) {
+      case 1: s = group_dot<1, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 2: s = group_dot<2, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 3: s = group_dot<3, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 4: s = group_dot<4, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 5: s = group_dot<5, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 6: s = group_dot<6, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      case 7: s = group_dot<7, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
+      default: s = group_dot<8, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -96,6 +120,23 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
     }
     __syncthreads();
   }
+}
+
+// The work is shared by ncta CTAs (this one is number cta): rows [0, nlong)
+// (longer than kCtaRow) are reduced one per CTA (cta, cta + ncta, ...) by the
+// whole CTA; then each warp walks its warp tiles (wid, wid + wstride, ...).  For
+// every row r: epi.pre(r) then epi.row(r, sum_k va[k] * vec[ci[k]]), both on
+// the same thread.  red: blockDim.x / 32 Acc of shared memory.
+template <typename T, typename V, typename Acc, class Epi>
+__device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ tiles, int ntiles,
+                                          const int *__restrict__ rp, const int *__restrict__ ci,
+                                          const T *__restrict__ va, const V *__restrict__ vec,
+                                          Epi &epi, Acc *red, int cta, int ncta) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nthr = blockDim.x;
+  const int nwarp = nthr >> 5;
+  cta_rows<T, V, Acc>(nlong, rp, ci, va, vec, epi, red, cta, ncta);
   // ---- warp tiles ---------------------------------------------------------
   const int wid = cta * nwarp + warp;
   const int wstride = ncta * nwarp;
@@ -117,19 +158,16 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
       const int hi = __shfl_sync(kFull, my_hi, q & 31);
       Acc s = 0;
       if (q < w.nrows) {
-        int j[kWarpItems];
-        T a[kWarpItems];
-#pragma unroll
-        for (int u = 0; u < kWarpItems; ++u) {
-          const int k = lo + gl + u * vl;
-          j[u] = k < hi ? ci[k] : 0;
-          a[u] = k < hi ? va[k] : (T)0;
+        switch (w.nit) {
+          case 1: s = group_dot<1, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 2: s = group_dot<2, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 3: s = group_dot<3, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 4: s = group_dot<4, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 5: s = group_dot<5, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 6: s = group_dot<6, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          case 7: s = group_dot<7, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
+          default: s = group_dot<8, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
         }
-        V gv[kWarpItems];
-#pragma unroll
-        for (int u = 0; u < kWarpItems; ++u) gv[u] = vec[j[u]];
-#pragma unroll
-        for (int u = 0; u < kWarpItems; ++u) s += (Acc)a[u] * (Acc)gv[u];
       }
       for (int o = vl >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
       // lane L keeps the sum of row L when row L was reduced in this pass
