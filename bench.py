@@ -442,6 +442,17 @@ def run_batch(args):
         el = statistics.mean(s_[0] for s_ in steps)
         lat = steps[-1][1]
         value = len(lps) / el
+        # comparator: the same LPs solved singly in plain FP64 (lp_solve, one
+        # after another), on every 16th LP of the batch
+        sub = lps[::16]
+        t0 = time.perf_counter()
+        for lp in sub:
+            p = pkg.Problem(lp, dev)
+            p.solve(precision=pkg.LP_FP64)
+            p.close()
+        ts = time.perf_counter() - t0
+        single = {"LPs_per_s": len(sub) / ts, "sample": f"{len(sub)} of the 512 LPs (every 16th), "
+                  f"each lp_create + lp_solve (FP64) + lp_destroy, one after another ({ts:.1f} s)"}
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             sample = lps[:: len(lps) // 8][:8]
@@ -464,6 +475,7 @@ def run_batch(args):
             "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)),
             "optimal": steps[-1][3], "max_objective_rel_err_vs_planted": max(steps[-1][2]),
+            "single_fp64": single,
             "server_stats": steps[-1][4], "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "LPs/s",
                     "h2d_bytes_per_step": int(sum(lp.nnz * 24 + (lp.m + lp.n) * 24 for lp in lps)),

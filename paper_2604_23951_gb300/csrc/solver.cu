@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -930,6 +931,12 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       ++head;
       volatile int status = d->hst->status;
       volatile int kerr = d->hst->err;
+      if (o.verbose) {
+        const State &V = *d->hst;
+        std::fprintf(stderr, "pdhg t=%lld rel_kkt=%.3e rel_p=%.2e rel_d=%.2e gap=%.2e omega=%.3e "
+                     "restarts=%d fp32=%d\n", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap,
+                     V.omega, V.restarts, V.mixed_active);
+      }
       if (status != ST_RUNNING || kerr) break;
       double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
       if (el > tl) {
