@@ -274,9 +274,9 @@ int lp_power_norm_static(int32_t m, int32_t n, const int32_t *a_row_ptr,
  * least one block of check_every iterations and keeps going while the
  * launch's device time budget lasts; finished slots are retired and their
  * memory refilled from the queue between launches.  Requests with at least
- * solo_nnz nonzeros (default 2,000,000) instead run the single-LP grid path
+ * solo_nnz nonzeros (default 500,000) instead run the single-LP grid path
  * on their own stream, with device memory from the same budget, at most
- * solo_max (default 2) at once.  `opts` applies to every request
+ * solo_max (default 3) at once.  `opts` applies to every request
  * (precision, eps_rel, ...).  worker: 1 = a background host thread drives
  * the device loop; 0 = the caller drives it through lp_server_pump. */
 int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,

@@ -54,7 +54,7 @@ namespace gb300lp {
 
 void set_last_error(const std::string &m);
 const HostLP &problem_current(const lp_problem *lp);
-constexpr long long kSoloNnz = 2000000;  // larger requests run on the single-LP grid path
+constexpr long long kSoloNnz = 500000;  // larger requests run on the single-LP grid path
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z);
 
@@ -845,7 +845,7 @@ struct lp_server {
   Bucket buckets[kNumBuckets];
   int device = 0, sm_count = 0;
   long long solo_nnz = kSoloNnz;  // requests at least this large run on the single-LP path
-  int solo_max = 2;               // solo requests running at once
+  int solo_max = 3;               // solo requests running at once
   double launch_ms = 2.0;         // device time budget of one bucket launch
   lp_solve_opts opts{};
   unsigned char *arena = nullptr;

@@ -162,15 +162,16 @@ def test_presolved_requests_postsolve_to_kkt(pkg, dev):
 
 
 def test_large_request_runs_on_the_solo_lane_beside_batched_ones(pkg, dev):
-    # >= 2M nonzeros: the server solves it with the single-LP grid path on
-    # its own stream while the small requests keep batching
-    big = lpgen.general_structure(80_000, 200_000, 17, nnz_target=2_100_000)
+    # at or above the solo size the server solves a request with the
+    # single-LP grid path on its own stream while the small ones keep batching
+    solo = 400_000
+    big = lpgen.general_structure(24_000, 60_000, 17, nnz_target=600_000)
     smalls = small_batch(8, seed=8)
     srv = pkg.Server(8 << 30, dev, worker=True, precision=0)
+    srv.tune(solo_nnz=solo)
     pb = pkg.Problem(big, dev)
     pb.presolve()
-    if pb.dims()[2] < 2_000_000:
-        pytest.skip("presolved request below the solo size")
+    assert pb.dims()[2] >= solo, "presolved request below the solo size"
     probs = [pkg.Problem(lp, dev) for lp in smalls]
     tb = srv.submit(pb)
     ts = [srv.submit(p) for p in probs]
