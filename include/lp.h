@@ -63,6 +63,11 @@ extern "C" {
 #define LP_PRESOLVE_UNBOUNDED 2
 #define LP_PRESOLVE_SOLVED 3 /* every row and column was removed            */
 
+/* ---- engine (lp_solve_opts.engine) ------------------------------------- */
+#define LP_ENGINE_AUTO 0
+#define LP_ENGINE_GRID 1
+#define LP_ENGINE_CLUSTER 2
+
 /* ---- precision (lp_solve_opts.precision) ------------------------------- */
 #define LP_FP64 0  /* FP64 matrix, FP64 SpMV, FP64 everything               */
 #define LP_MIXED 1 /* FP32 matrix values and SpMV with FP32 accumulation;    */
@@ -132,7 +137,15 @@ typedef struct {
   double primal_weight;  /* 0 = auto: ||c~|| / ||bhat~||                    */
   const double *x_init;  /* NULL or n doubles (current LP): warm start x    */
   const double *y_init;  /* NULL or m doubles: warm start y                 */
-  int32_t tile_items;    /* 0 = auto: target nonzeros per lane in SpMV      */
+  int32_t engine;        /* LP_ENGINE_AUTO (0): the cluster engine for LPs
+                          * under 4,096 nonzeros, the grid engine
+                          * otherwise; LP_ENGINE_GRID (1): CUDA-graph
+                          * replay of the grid-wide kernels;
+                          * LP_ENGINE_CLUSTER (2): one thread-block cluster
+                          * (1-8 CTAs by size) runs the whole solve.  Both
+                          * run the same algorithm with the same results
+                          * semantics; use_graph and lp_profile_kernels
+                          * concern the grid engine only.                  */
   int32_t verbose;
 } lp_solve_opts;
 

@@ -21,6 +21,7 @@ LP_ERR = {-1: "LP_ERR_INVALID", -2: "LP_ERR_OOM", -3: "LP_ERR_CUDA", -4: "LP_ERR
 LP_OPTIMAL, LP_ITER_LIMIT, LP_TIME_LIMIT, LP_NUMERICAL, LP_INFEASIBLE, LP_UNBOUNDED, \
     LP_CANCELLED = range(7)
 LP_FP64, LP_MIXED = 0, 1
+LP_ENGINE_AUTO, LP_ENGINE_GRID, LP_ENGINE_CLUSTER = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -49,7 +50,7 @@ class lp_solve_opts(C.Structure):
                 ("power_iters", C.c_int32), ("halpern", C.c_int32), ("restarts", C.c_int32),
                 ("use_graph", C.c_int32), ("step_size", C.c_double),
                 ("primal_weight", C.c_double), ("x_init", C.POINTER(C.c_double)),
-                ("y_init", C.POINTER(C.c_double)), ("tile_items", C.c_int32),
+                ("y_init", C.POINTER(C.c_double)), ("engine", C.c_int32),
                 ("verbose", C.c_int32)]
 
 

@@ -90,7 +90,7 @@ void lp_solve_opts_default(lp_solve_opts *o) {
   o->primal_weight = 0.0;
   o->x_init = nullptr;
   o->y_init = nullptr;
-  o->tile_items = 0;
+  o->engine = LP_ENGINE_AUTO;
   o->verbose = 0;
 }
 
@@ -206,7 +206,7 @@ int lp_upload(lp_problem *lp) {
     lp->dlp = dev_create(&lp->dev, err);
     if (!lp->dlp) return fail(LP_ERR_CUDA, err);
   }
-  int rc = dev_upload(lp->dlp, lp->cur, 0, err);
+  int rc = dev_upload(lp->dlp, lp->cur, err);
   if (rc != LP_OK) return fail(rc, err);
   return LP_OK;
   API_GUARD_END
@@ -228,15 +228,27 @@ int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res) {
   lp_solve_opts_default(&o);
   if (opts) o = *opts;
   if (!(o.eps_rel >= 0) || o.max_iter < 1 || o.check_every < 1 || o.rho < 0 || o.rho > 1 ||
-      (o.precision != LP_FP64 && o.precision != LP_MIXED))
+      (o.precision != LP_FP64 && o.precision != LP_MIXED) || o.engine < LP_ENGINE_AUTO ||
+      o.engine > LP_ENGINE_CLUSTER)
     return fail(LP_ERR_INVALID, "invalid solve options");
   std::string err;
+  const bool cluster = o.engine == LP_ENGINE_CLUSTER ||
+                       (o.engine == LP_ENGINE_AUTO && lp->cur.nnz() < kClusterEngineNnz);
+  if (cluster) {
+    lp_result r;
+    std::memset(&r, 0, sizeof(r));
+    int rc = cluster_solve(lp->cur, o, &lp->dev, &r, lp->sol, err);
+    if (rc != LP_OK) return fail(rc, err);
+    lp->last_termination = r.termination;
+    if (res) *res = r;
+    return LP_OK;
+  }
   if (!lp->dlp) {
     lp->dlp = dev_create(&lp->dev, err);
     if (!lp->dlp) return fail(LP_ERR_CUDA, err);
   }
   if (!dev_uploaded(lp->dlp)) {
-    int rc = dev_upload(lp->dlp, lp->cur, o.tile_items, err);
+    int rc = dev_upload(lp->dlp, lp->cur, err);
     if (rc != LP_OK) return fail(rc, err);
   }
   lp_result r;

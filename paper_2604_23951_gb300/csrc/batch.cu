@@ -79,6 +79,7 @@ struct SlotDesc {
   double *x, *x0, *xbar, *xhat, *y, *y0, *yhat;
   float *xbarf, *yf, *pwf;
   double *xout, *yout, *zout;
+  const double *xinit, *yinit;  // warm start (unscaled, device order) or NULL
 };
 
 struct BatchConst {
@@ -338,16 +339,17 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
     }
     if (cl.block_rank() == 0 && threadIdx.x == 0) eta = pw > 0.0 ? 0.998 / pw : 1.0;
   }
-  // initial point and state
+  // initial point (projected zero, or the warm start) and state
   for (int j = gt; j < n; j += gs) {
-    const double v = clampd(0.0, D.lx[j], D.ux[j]);
+    const double v = D.xinit ? D.xinit[j] / dc[j] : clampd(0.0, D.lx[j], D.ux[j]);
     D.x[j] = v;
     D.x0[j] = v;
   }
   for (int i = gt; i < m; i += gs) {
-    D.y[i] = 0.0;
-    D.y0[i] = 0.0;
-    if (MIXED) D.yf[i] = 0.0f;
+    const double v = D.yinit ? D.yinit[i] / dr[i] : 0.0;
+    D.y[i] = v;
+    D.y0[i] = v;
+    if (MIXED) D.yf[i] = (float)v;
   }
   if (cl.block_rank() == 0 && threadIdx.x == 0) {
     const double cn = sqrt(sh.total[Q_CN]), bn = sqrt(sh.total[Q_BN]);
@@ -417,6 +419,35 @@ __device__ __forceinline__ void phase_dual(const SlotDesc &D, bool f32, double s
   }
 }
 
+// K3 (the KKT products of the check, FP64 scaled matrix, unscaled
+// quantities) and the cluster-wide sum of acc[0..10) into sh.total (rank 0)
+__device__ __forceinline__ void slot_kkt(const SlotDesc &D, BatchShared &sh,
+                                         cg::cluster_group &cl, double (&acc)[10]) {
+  const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
+  {
+    KktRowEpi e{D.dr, D.idr, D.lc0, D.uc0, D.yhat, 0.0, 0.0, 0.0};
+    warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_v,
+                                      D.xhat, e, sh.redd, rank, CL);
+    acc[4] = e.rp2;
+    acc[5] = e.rdy2;
+    acc[6] = e.dy;
+  }
+  {
+    KktColEpi e{D.c, D.dc, D.idc, D.c0, D.lx0, D.ux0, D.xhat, D.zout, 0.0, 0.0, 0.0};
+    warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_v,
+                                      D.yhat, e, sh.redd, rank, CL);
+    acc[7] = e.rd2;
+    acc[8] = e.dl;
+    acc[9] = e.p;
+  }
+  const int qid[10] = {Q_XRES, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P};
+  cluster_sum<10>(acc, qid, sh, cl);
+}
+
+// One block of iterations t0 .. t0 + K - 1 (t0 = iterations done, a multiple
+// of K): the first is the check iteration.  When max_iter falls inside the
+// block, the block stops there: its last iteration also writes T(z), which
+// is evaluated (KKT, LP_ITER_LIMIT) -- the single-LP path's semantics.
 template <bool MIXED>
 __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, BatchShared &sh,
                              cg::cluster_group &cl) {
@@ -424,77 +455,73 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
   const int gt = cl.block_rank() * blockDim.x + threadIdx.x;
   const int gs = cl.num_blocks() * blockDim.x;
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
-  for (int j = 0; j < C.K; ++j) {
+  const long long rem = C.max_iter - sh.ctl.t;
+  if (rem <= 0) {
+    // defensive: nothing left to run; keep the last check's point
+    cl.sync();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
+      st->status = 1;
+      st->iters = st->t;
+      bcast_ctl(st, sh, cl);
+    }
+    cl.sync();
+    return;
+  }
+  const int jmax = rem < C.K ? (int)rem : C.K;
+  const bool final_block = rem <= C.K;
+  for (int j = 0; j < jmax; ++j) {
     if (sh.ctl.status != ST_RUNNING) break;
     const bool check = (j == 0);
-    if (check && sh.ctl.t >= C.max_iter) {
-      // LP_ITER_LIMIT: the last check's point is the answer
-      cl.sync();
-      if (cl.block_rank() == 0 && threadIdx.x == 0) {
-        st->status = 1;
-        st->iters = st->t;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) sh.ctl.status = 1;
-      __syncthreads();
-      break;
-    }
+    const bool last = final_block && j == jmax - 1;
+    const bool hats = check || last;
     const Halpern hc = halpern_ctl(sh.ctl, j);
     const double tau = sh.ctl.tau, sigma = sh.ctl.sigma;
     const bool f32 = MIXED && sh.ctl.mixed_active;  // FP32 SpMV until the FP64 switch
     double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // K1: rows of A^T
-    if (check) phase_primal<true>(D, f32, tau, hc, sh, rank, CL, acc);
+    if (hats) phase_primal<true>(D, f32, tau, hc, sh, rank, CL, acc);
     else phase_primal<false>(D, f32, tau, hc, sh, rank, CL, acc);
     cl.sync();
     // K2: rows of A
-    if (check) phase_dual<true>(D, f32, sigma, hc, sh, rank, CL, acc);
+    if (hats) phase_dual<true>(D, f32, sigma, hc, sh, rank, CL, acc);
     else phase_dual<false>(D, f32, sigma, hc, sh, rank, CL, acc);
     cl.sync();
-    if (!check) continue;
-    // K3: KKT on the unscaled problem, FP64 scaled matrix
-    {
-      KktRowEpi e{D.dr, D.idr, D.lc0, D.uc0, D.yhat, 0.0, 0.0, 0.0};
-      warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_v,
-                                        D.xhat, e, sh.redd, rank, CL);
-      acc[4] = e.rp2;
-      acc[5] = e.rdy2;
-      acc[6] = e.dy;
-    }
-    {
-      KktColEpi e{D.c, D.dc, D.idc, D.c0, D.lx0, D.ux0, D.xhat, D.zout, 0.0, 0.0, 0.0};
-      warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_v,
-                                        D.yhat, e, sh.redd, rank, CL);
-      acc[7] = e.rd2;
-      acc[8] = e.dl;
-      acc[9] = e.p;
-    }
-    {
-      const int qid[10] = {Q_XRES, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P};
-      cluster_sum<10>(acc, qid, sh, cl);
-    }
-    if (cl.block_rank() == 0 && threadIdx.x == 0) {
-      check_update(st, sh.total, false);
-      bcast_ctl(st, sh, cl);
-    }
-    cl.sync();
-    if (sh.ctl.status != ST_RUNNING) break;
-    if (sh.ctl.restart_flag) {
-      for (int c = gt; c < n; c += gs) {
-        const double v = D.xhat[c];
-        D.x[c] = v;
-        D.x0[c] = v;
+    if (check) {
+      slot_kkt(D, sh, cl, acc);
+      if (cl.block_rank() == 0 && threadIdx.x == 0) {
+        check_update(st, sh.total, false);
+        bcast_ctl(st, sh, cl);
       }
-      for (int r = gt; r < m; r += gs) {
-        const double v = D.yhat[r];
-        D.y[r] = v;
-        D.y0[r] = v;
-        if (MIXED) D.yf[r] = (float)v;
+      cl.sync();
+      if (sh.ctl.status != ST_RUNNING) break;
+      if (sh.ctl.restart_flag) {
+        for (int c = gt; c < n; c += gs) {
+          const double v = D.xhat[c];
+          D.x[c] = v;
+          D.x0[c] = v;
+        }
+        for (int r = gt; r < m; r += gs) {
+          const double v = D.yhat[r];
+          D.y[r] = v;
+          D.y0[r] = v;
+          if (MIXED) D.yf[r] = (float)v;
+        }
+        cl.sync();
+      }
+    }
+    if (last) {
+      // max_iter reached: evaluate the last T(z)
+      double acc2[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      slot_kkt(D, sh, cl, acc2);
+      if (cl.block_rank() == 0 && threadIdx.x == 0) {
+        check_update(st, sh.total, true);
+        st->iters = C.max_iter;
+        bcast_ctl(st, sh, cl);
       }
       cl.sync();
     }
   }
-  // finished slots: unscaled answer (the last check's T(z))
+  // finished slots: unscaled answer (the last T(z) evaluated)
   if (sh.ctl.status != ST_RUNNING && sh.ctl.status != ST_SETUP) {
     for (int c = gt; c < n; c += gs) D.xout[c] = D.dc[c] * D.xhat[c];
     for (int r = gt; r < m; r += gs) D.yout[r] = D.dr[r] * D.yhat[r];
@@ -880,9 +907,8 @@ struct lp_server {
 
 namespace {
 
-void server_state_init(const lp_server *srv, State &st, const Packed &pk) {
+void state_init(const lp_solve_opts &o, State &st, const Packed &pk) {
   std::memset(&st, 0, sizeof(st));
-  const lp_solve_opts &o = srv->opts;
   st.rho = o.rho;
   st.beta_suff = o.beta_suff;
   st.beta_nec = o.beta_nec;
@@ -961,7 +987,7 @@ bool start_solo(lp_server *srv, Request &rq) {
     if (!dl) rc = LP_ERR_CUDA;
     const HostLP &h = problem_current(lp);
     DeviceSolution sol;
-    if (rc == LP_OK) rc = dev_upload(dl, h, 0, err);
+    if (rc == LP_OK) rc = dev_upload(dl, h, err);
     if (rc == LP_OK) rc = dev_solve(dl, h, srv->opts, &d.res, sol, err);
     if (dl) dev_destroy(dl);
     if (rc == LP_OK) {
@@ -1036,7 +1062,7 @@ void admit(lp_server *srv) {
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaMemcpyAsync(srv->d_desc + sid, &sl.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice,
                        srv->s));
-    server_state_init(srv, srv->h_state[sid], rq.pk);
+    state_init(srv->opts, srv->h_state[sid], rq.pk);
     CK(cudaMemcpyAsync(srv->d_state + sid, &srv->h_state[sid], sizeof(State),
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaStreamSynchronize(srv->s));  // the pageable blob may be freed next
@@ -1555,3 +1581,213 @@ void lp_server_destroy(lp_server *srv) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The cluster engine of lp_solve: one LP on one thread-block cluster, the
+// whole solve in a few launches of the batch kernel (no per-iteration launch),
+// for LPs too small to fill the GPU with the grid kernels.
+
+namespace gb300lp {
+
+int cluster_solve(const HostLP &h, const lp_solve_opts &o, const lp_device_ctx *ctx,
+                  lp_result *res, DeviceSolution &sol, std::string &err) {
+  const auto t_start = std::chrono::steady_clock::now();
+  lp_device_ctx dctx{};
+  if (ctx) dctx = *ctx;
+  cudaStream_t s = static_cast<cudaStream_t>(dctx.stream);
+  bool own_stream = false;
+  unsigned char *mem = nullptr;
+  auto release = [&]() {
+    if (mem) {
+      if (dctx.free) dctx.free(mem, dctx.user);
+      else cudaFreeAsync(mem, s);
+      mem = nullptr;
+    }
+    if (own_stream) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+      own_stream = false;
+    }
+  };
+  try {
+    CK(cudaSetDevice(dctx.device));
+    if (!s) {
+      CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      own_stream = true;
+    }
+    const int m = h.m, n = h.n;
+    Packed pk;
+    pack_request(h, pk);
+    const bool warm = o.x_init || o.y_init;
+    auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t o_desc = a256(pk.bytes);
+    const size_t o_state = o_desc + a256(sizeof(SlotDesc));
+    const size_t o_sout = o_state + a256(sizeof(State));
+    const size_t o_order = o_sout + a256(sizeof(State));
+    const size_t o_xi = o_order + 256;
+    const size_t o_yi = o_xi + a256(8 * (size_t)std::max(n, 1));
+    const size_t total = o_yi + a256(8 * (size_t)std::max(m, 1));
+    if (dctx.alloc) {
+      mem = static_cast<unsigned char *>(dctx.alloc(total, dctx.user));
+      if (!mem) {
+        err = "device allocation of " + std::to_string(total) + " bytes failed";
+        release();
+        return LP_ERR_OOM;
+      }
+    } else {
+      cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&mem), total, s);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        mem = nullptr;
+        err = "device allocation of " + std::to_string(total) + " bytes failed";
+        release();
+        return LP_ERR_OOM;
+      }
+      CK(e);
+    }
+    SlotDesc desc = relocate(pk.rel, mem);
+    std::vector<double> xw, yw;
+    if (warm) {
+      // warm start in the device order (unscaled; the set-up divides by the scaling)
+      xw.assign(n, 0.0);
+      yw.assign(m, 0.0);
+      for (int j = 0; j < n; ++j) xw[j] = o.x_init ? o.x_init[pk.cperm[j]] : 0.0;
+      for (int i = 0; i < m; ++i) yw[i] = o.y_init ? o.y_init[pk.rperm[i]] : 0.0;
+      desc.xinit = reinterpret_cast<const double *>(mem + o_xi);
+      desc.yinit = reinterpret_cast<const double *>(mem + o_yi);
+      if (n) CK(cudaMemcpyAsync(mem + o_xi, xw.data(), 8 * n, cudaMemcpyHostToDevice, s));
+      if (m) CK(cudaMemcpyAsync(mem + o_yi, yw.data(), 8 * m, cudaMemcpyHostToDevice, s));
+    }
+    State st0;
+    state_init(o, st0, pk);
+    const int zero = 0;
+    CK(cudaMemcpyAsync(mem, pk.blob.data(), pk.blob.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mem + o_desc, &desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mem + o_state, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mem + o_order, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // host buffers may be freed below
+    const double t_setup =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    // cluster shape by size
+    const long long nnz = h.nnz();
+    const int CLs = nnz < 16384 ? 1 : (nnz < 65536 ? 2 : (nnz < 262144 ? 4 : 8));
+    BatchConst C;
+    C.K = std::max(1, o.check_every);
+    C.ruiz_iters = o.ruiz_iters;
+    C.pock_chambolle = o.pock_chambolle;
+    C.power_iters = o.power_iters;
+    C.max_iter = o.max_iter;
+    C.step_size = o.step_size;
+    C.primal_weight = o.primal_weight;
+    const double tl = o.time_limit_s > 0 ? o.time_limit_s : 1e30;
+    C.budget_ns = (long long)(std::min(0.05, tl) * 1e9);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const SlotDesc *d_desc = reinterpret_cast<const SlotDesc *>(mem + o_desc);
+    State *d_state = reinterpret_cast<State *>(mem + o_state);
+    State *d_sout = reinterpret_cast<State *>(mem + o_sout);
+    const int *d_order = reinterpret_cast<const int *>(mem + o_order);
+    State hs;
+    long long launches = 0;
+    bool timed_out = false;
+    const auto t_solve0 = std::chrono::steady_clock::now();
+    for (;;) {
+      if (o.precision == LP_MIXED)
+        CK(cudaLaunchKernelEx(&cfg, k_batch<true>, d_desc, d_state, d_order, 1, d_sout, C));
+      else
+        CK(cudaLaunchKernelEx(&cfg, k_batch<false>, d_desc, d_state, d_order, 1, d_sout, C));
+      ++launches;
+      CK(cudaMemcpyAsync(&hs, d_sout, sizeof(State), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (o.verbose)
+        std::fprintf(stderr, "pdhg-cluster t=%lld rel_kkt=%.3e omega=%.3e restarts=%d fp32=%d\n",
+                     hs.t, hs.rel_kkt, hs.omega, hs.restarts, hs.mixed_active);
+      if (hs.status >= 0) break;
+      const double el =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      if (el > tl) {
+        timed_out = true;
+        break;
+      }
+    }
+    const double t_solve =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_solve0).count();
+    // outputs: unscale and renumber on the host
+    std::vector<double> xh(n), yh(m), xc(n), yc(m), dc(n), dr(m), zz(n);
+    if (n) {
+      CK(cudaMemcpyAsync(xh.data(), desc.xhat, 8 * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(xc.data(), desc.x, 8 * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(dc.data(), desc.dc, 8 * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(zz.data(), desc.zout, 8 * n, cudaMemcpyDeviceToHost, s));
+    }
+    if (m) {
+      CK(cudaMemcpyAsync(yh.data(), desc.yhat, 8 * m, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(yc.data(), desc.y, 8 * m, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(dr.data(), desc.dr, 8 * m, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    sol.x.assign(n, 0.0);
+    sol.z.assign(n, 0.0);
+    sol.xi.assign(n, 0.0);
+    sol.y.assign(m, 0.0);
+    sol.yi.assign(m, 0.0);
+    for (int j = 0; j < n; ++j) {
+      const int oj = pk.cperm[j];
+      sol.x[oj] = dc[j] * xh[j];
+      sol.xi[oj] = dc[j] * xc[j];
+      sol.z[oj] = zz[j];
+    }
+    for (int i = 0; i < m; ++i) {
+      const int oi = pk.rperm[i];
+      sol.y[oi] = dr[i] * yh[i];
+      sol.yi[oi] = dr[i] * yc[i];
+    }
+    sol.valid = true;
+    release();
+    if (res) {
+      std::memset(res, 0, sizeof(*res));
+      res->termination = timed_out ? LP_TIME_LIMIT : hs.status;
+      res->restarts = hs.restarts;
+      res->iterations = hs.status >= 0 ? hs.iters : hs.t;
+      res->rel_kkt = hs.rel_kkt;
+      res->rel_p = hs.rel_p;
+      res->rel_d = hs.rel_d;
+      res->rel_gap = hs.rel_gap;
+      res->r_p = hs.r_p;
+      res->r_d = hs.r_d;
+      res->gap = hs.gap;
+      res->primal_obj = hs.pobj;
+      res->dual_obj = hs.dobj;
+      res->eta = hs.eta;
+      res->omega = hs.omega;
+      res->t_setup_s = t_setup;
+      res->t_solve_s = t_solve;
+      res->t_total_s =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+      res->kernel_launches = launches;
+      res->fp32_iterations = o.precision == LP_MIXED
+                                 ? (hs.t_switch >= 0 ? hs.t_switch : res->iterations) : 0;
+    }
+  } catch (const DeviceOOM &e) {
+    err = e.what();
+    release();
+    return LP_ERR_OOM;
+  } catch (const std::exception &e) {
+    err = e.what();
+    release();
+    return LP_ERR_CUDA;
+  }
+  return LP_OK;
+}
+
+}  // namespace gb300lp

@@ -66,12 +66,18 @@ struct DeviceSolution {
 };
 
 DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err);
-int dev_upload(DeviceLP *d, const HostLP &lp, int tile_items, std::string &err);
+int dev_upload(DeviceLP *d, const HostLP &lp, std::string &err);
 bool dev_uploaded(const DeviceLP *d);
 int dev_solve(DeviceLP *d, const HostLP &lp, const lp_solve_opts &opts, lp_result *res,
               DeviceSolution &sol, std::string &err);
 void dev_destroy(DeviceLP *d);
 int dev_profile(DeviceLP *d, int reps, double *out, std::string &err);
+
+// The cluster engine: one thread-block cluster runs the whole solve of a
+// small LP (batch.cu); same algorithm and result semantics as dev_solve.
+int cluster_solve(const HostLP &lp, const lp_solve_opts &opts, const lp_device_ctx *ctx,
+                  lp_result *res, DeviceSolution &sol, std::string &err);
+constexpr long long kClusterEngineNnz = 4096;  // LP_ENGINE_AUTO picks it below this size
 
 // ---- shared device-memory helpers (solver.cu) ----------------------------
 struct DevAlloc {

@@ -554,7 +554,7 @@ void dev_destroy(DeviceLP *d) {
   delete d;
 }
 
-int dev_upload(DeviceLP *d, const HostLP &h, int /*tile_items*/, std::string &err) {
+int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
   try {
     CK(cudaSetDevice(d->device));
     d->release_all();

@@ -38,13 +38,17 @@ def rel_obj(p, q):
     return abs(p - q) / (1.0 + abs(q))
 
 
-@pytest.mark.parametrize("iters", [1, 2, 5, 17, 50])
-def test_first_iterates_match_oracle_c1(pkg, dev, iters):
+ENGINES = [1, 2]  # LP_ENGINE_GRID, LP_ENGINE_CLUSTER
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("iters", [1, 2, 5, 17, 50, 64, 65, 130])
+def test_first_iterates_match_oracle_c1(pkg, dev, iters, engine):
     lp = lpgen.c1_small()
     eta, om = 0.05, 1.3
     ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta, omega0=om)
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(max_iter=iters, eps_rel=0.0, step_size=eta, primal_weight=om)
+    r = prob.solve(max_iter=iters, eps_rel=0.0, step_size=eta, primal_weight=om, engine=engine)
     assert r.termination == pkg.LP_ITER_LIMIT and r.iterations == iters
     xi, yi = prob.iterate()
     assert relerr(xi, ref.x_iter) <= 1e-10
@@ -61,30 +65,32 @@ def test_iterates_powerlaw_all_row_classes(pkg, dev):
     lp = lpgen.c3_powerlaw(seed=7, m=3000, n=8000, row_nnz_target=60000, n_dense=20,
                            dense_len=2500, kmax=6000)
     eta, om = 0.02, 0.7
-    for items in (1, 4):
-        ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=40, eps_rel=0.0), eta=eta, omega0=om)
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=40, eps_rel=0.0), eta=eta, omega0=om)
+    for engine in ENGINES:
         prob = pkg.Problem(lp, dev)
-        prob.solve(max_iter=40, eps_rel=0.0, step_size=eta, primal_weight=om, tile_items=items)
+        prob.solve(max_iter=40, eps_rel=0.0, step_size=eta, primal_weight=om, engine=engine)
         xi, yi = prob.iterate()
         assert relerr(xi, ref.x_iter) <= 1e-10
         assert relerr(yi, ref.y_iter) <= 1e-10
         prob.close()
 
 
-def test_step_size_and_weight_match_oracle(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_step_size_and_weight_match_oracle(pkg, dev, engine):
     lp = lpgen.general_structure(500, 1200, 3, nnz_target=7000, one_sided=0.2)
     ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=1, eps_rel=0.0))
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(max_iter=1, eps_rel=0.0)
+    r = prob.solve(max_iter=1, eps_rel=0.0, engine=engine)
     assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
     assert abs(r.omega - ref.omega0) <= 1e-12 * ref.omega0
 
 
-def test_c1_solves_to_tolerance(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_c1_solves_to_tolerance(pkg, dev, engine):
     lp = lpgen.c1_small()
     ref = oracle.pdhg_solve(lp)
     prob = pkg.Problem(lp, dev)
-    r = prob.solve()
+    r = prob.solve(engine=engine)
     assert r.termination == pkg.LP_OPTIMAL
     assert r.rel_kkt <= 1e-6
     x, y, z = prob.solution()
@@ -100,21 +106,22 @@ def test_c1_solves_to_tolerance(pkg, dev):
 def test_graph_and_direct_launches_agree_bitwise(pkg, dev, graph):
     lp = lpgen.general_structure(400, 1000, 8, nnz_target=6000)
     prob = pkg.Problem(lp, dev)
-    r1 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=1)
+    r1 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=1, engine=1)
     x1, y1 = prob.iterate()
-    r2 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=graph)
+    r2 = prob.solve(max_iter=300, eps_rel=0.0, use_graph=graph, engine=1)
     x2, y2 = prob.iterate()
     assert r1.restarts == r2.restarts
     np.testing.assert_array_equal(x1, x2)
     np.testing.assert_array_equal(y1, y2)
 
 
-def test_presolve_solve_postsolve_is_kkt(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_presolve_solve_postsolve_is_kkt(pkg, dev, engine):
     lp = lpgen.general_structure(1500, 3800, 12, nnz_target=30000, one_sided=0.1)
     prob = pkg.Problem(lp, dev)
     info = prob.presolve()
     assert info.m < lp.m
-    r = prob.solve()
+    r = prob.solve(engine=engine)
     assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
     x, y, z = prob.postsolve()
     k = oracle.rel_kkt(lp, x, y)
@@ -125,31 +132,34 @@ def test_presolve_solve_postsolve_is_kkt(pkg, dev):
     assert rel_obj(r.primal_obj, ref.kkt["p"]) <= 1e-6
 
 
-def test_mixed_precision_reaches_tolerance(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_precision_reaches_tolerance(pkg, dev, engine):
     lp = lpgen.c1_small()
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(precision=pkg.LP_MIXED)
+    r = prob.solve(precision=pkg.LP_MIXED, engine=engine)
     assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
     assert rel_obj(r.primal_obj, lp.p_star) <= 1e-5
 
 
-def test_deterministic_reruns(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_deterministic_reruns(pkg, dev, engine):
     lp = lpgen.general_structure(600, 1500, 4, nnz_target=9000)
     prob = pkg.Problem(lp, dev)
-    prob.solve(max_iter=500, eps_rel=0.0)
+    prob.solve(max_iter=500, eps_rel=0.0, engine=engine)
     a = prob.iterate()
-    prob.solve(max_iter=500, eps_rel=0.0)
+    prob.solve(max_iter=500, eps_rel=0.0, engine=engine)
     b = prob.iterate()
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
 
 
-def test_degenerate_shapes(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_degenerate_shapes(pkg, dev, engine):
     # no rows: each column goes to the bound its cost points to
     lp = SimpleLP(np.zeros((0, 3)), [1.0, -2.0, 0.0], [], [], [-1.0, 0.0, -3.0],
                   [4.0, 5.0, 3.0])
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(eps_rel=1e-9)
+    r = prob.solve(eps_rel=1e-9, engine=engine)
     assert r.termination == pkg.LP_OPTIMAL
     x, _, _ = prob.solution()
     assert np.allclose(x, [-1.0, 5.0, 0.0], atol=1e-8)
@@ -157,15 +167,16 @@ def test_degenerate_shapes(pkg, dev):
     lp = SimpleLP([[1.0, 0.0, 1.0], [0.0, 0.0, 0.0]], [1.0, 0.0, 2.0], [1.0, -1.0],
                   [1.0, 1.0], [0.0, 0.0, 0.0], [INF, 2.0, INF])
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(eps_rel=1e-9)
+    r = prob.solve(eps_rel=1e-9, engine=engine)
     assert r.termination == pkg.LP_OPTIMAL
     assert abs(r.primal_obj - 1.0) <= 1e-7
 
 
-def test_warm_start_from_solution_converges_at_first_check(pkg, dev):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_warm_start_from_solution_converges_at_first_check(pkg, dev, engine):
     lp = lpgen.c1_small()
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(x_init=lp.x_star, y_init=lp.y_star)
+    r = prob.solve(x_init=lp.x_star, y_init=lp.y_star, engine=engine)
     assert r.termination == pkg.LP_OPTIMAL and r.iterations == 1
 
 
@@ -174,14 +185,31 @@ def test_resolve_after_other_options_matches_fresh_solve(pkg, dev):
     # scaling: a re-solve behaves exactly like a solve on a fresh problem
     lp = lpgen.c1_small()
     fresh = pkg.Problem(lp, dev)
-    r0 = fresh.solve()
+    r0 = fresh.solve(engine=1)
     x0, y0, _ = fresh.solution()
     prob = pkg.Problem(lp, dev)
-    prob.solve(max_iter=50, eps_rel=0.0, step_size=0.05, primal_weight=1.3)
-    prob.solve(max_iter=700, ruiz_iters=3, pock_chambolle=0)
-    r = prob.solve()
+    prob.solve(max_iter=50, eps_rel=0.0, step_size=0.05, primal_weight=1.3, engine=1)
+    prob.solve(max_iter=700, ruiz_iters=3, pock_chambolle=0, engine=1)
+    r = prob.solve(engine=1)
     assert r.termination == pkg.LP_OPTIMAL
     assert r.iterations == r0.iterations and r.restarts == r0.restarts
     x, y, _ = prob.solution()
     np.testing.assert_array_equal(x, x0)
     np.testing.assert_array_equal(y, y0)
+
+
+def test_engines_agree_on_iterates(pkg, dev):
+    # the cluster engine runs the grid engine's algorithm: after the same
+    # number of iterations both hold the same point up to rounding order
+    lp = lpgen.general_structure(900, 2200, 21, nnz_target=15000, one_sided=0.2)
+    out = []
+    for engine in ENGINES:
+        prob = pkg.Problem(lp, dev)
+        r = prob.solve(max_iter=200, eps_rel=0.0, engine=engine)
+        out.append((r, prob.iterate(), prob.solution()))
+        prob.close()
+    (ra, ia, sa), (rb, ib, sb) = out
+    assert ra.iterations == rb.iterations == 200
+    assert ra.restarts == rb.restarts
+    assert relerr(ia[0], ib[0]) <= 1e-9 and relerr(ia[1], ib[1]) <= 1e-9
+    assert relerr(sa[0], sb[0]) <= 1e-9 and relerr(sa[1], sb[1]) <= 1e-9
