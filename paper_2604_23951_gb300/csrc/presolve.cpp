@@ -33,7 +33,9 @@
 //                            y_i = c_j / a_ij, z_j = 0
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
+#include <thread>
 #include <vector>
 
 #include "lp_internal.h"
@@ -93,10 +95,11 @@ struct SlackStore {
     return -lo - 1;
   }
   void erase_at(int32_t r, int32_t pos) {
-    int64_t s = start[r];
-    for (int32_t q = pos; q + 1 < len[r]; ++q) {
-      idx[s + q] = idx[s + q + 1];
-      val[s + q] = val[s + q + 1];
+    const int64_t s = start[r];
+    const int32_t tail = len[r] - pos - 1;
+    if (tail > 0) {
+      std::memmove(&idx[s + pos], &idx[s + pos + 1], sizeof(int32_t) * tail);
+      std::memmove(&val[s + pos], &val[s + pos + 1], sizeof(double) * tail);
     }
     --len[r];
   }
@@ -125,10 +128,11 @@ struct SlackStore {
     }
     int32_t ins = -p - 1;
     if (len[r] == cap[r]) grow(r);
-    int64_t s = start[r];
-    for (int32_t q = len[r]; q > ins; --q) {
-      idx[s + q] = idx[s + q - 1];
-      val[s + q] = val[s + q - 1];
+    const int64_t s = start[r];
+    const int32_t tail = len[r] - ins;
+    if (tail > 0) {
+      std::memmove(&idx[s + ins + 1], &idx[s + ins], sizeof(int32_t) * tail);
+      std::memmove(&val[s + ins + 1], &val[s + ins], sizeof(double) * tail);
     }
     idx[s + ins] = key;
     val[s + ins] = v;
@@ -162,23 +166,31 @@ struct Presolver {
         if (in.val[k] != 0.0) { ++cnt; ++cl[in.col_idx[k]]; }
       rl[i] = cnt;
     }
+    // input rows are sorted by column and rows arrive in order, so both
+    // stores fill by appends; the column store is built on a second thread
+    std::thread col_builder([&]() {
+      cols.init(n, cl);
+      for (int32_t i = 0; i < m; ++i)
+        for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
+          const double v = in.val[k];
+          if (v == 0.0) continue;
+          const int32_t j = in.col_idx[k];
+          cols.idx[cols.start[j] + cols.len[j]] = i;
+          cols.val[cols.start[j] + cols.len[j]] = v;
+          ++cols.len[j];
+        }
+    });
     rows.init(m, rl);
-    cols.init(n, cl);
     for (int32_t i = 0; i < m; ++i) {
       for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
-        double v = in.val[k];
+        const double v = in.val[k];
         if (v == 0.0) continue;
-        int32_t j = in.col_idx[k];
-        // input rows are sorted by column and rows arrive in order, so these
-        // are appends
-        rows.idx[rows.start[i] + rows.len[i]] = j;
+        rows.idx[rows.start[i] + rows.len[i]] = in.col_idx[k];
         rows.val[rows.start[i] + rows.len[i]] = v;
         ++rows.len[i];
-        cols.idx[cols.start[j] + cols.len[j]] = i;
-        cols.val[cols.start[j] + cols.len[j]] = v;
-        ++cols.len[j];
       }
     }
+    col_builder.join();
     c = in.c;
     off = in.off;
     lo = in.row_lo;
@@ -538,6 +550,12 @@ struct Presolver {
     out.m = (int32_t)po->row_map.size();
     out.n = (int32_t)po->col_map.size();
     out.row_ptr.assign(out.m + 1, 0);
+    int64_t nz = 0;
+    for (int32_t i : po->row_map) nz += rows.len[i];
+    out.col_idx.reserve(nz);
+    out.val.reserve(nz);
+    out.row_lo.reserve(out.m);
+    out.row_hi.reserve(out.m);
     for (int32_t r = 0; r < out.m; ++r) {
       int32_t i = po->row_map[r];
       int64_t s = rows.start[i];
