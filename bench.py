@@ -306,7 +306,10 @@ def run_ours(args):
     value = elapsed / args.steps
     r = results[-1]
     launches = int(sum(x.kernel_launches for x in results))
-    # per-kernel timing (CUDA events, cold L2) for the roofline
+    # per-kernel timing (CUDA events, cold L2) for the roofline: the grid
+    # engine's K1 / K2, set up by a short grid-engine solve (tiny LPs are
+    # solved on the cluster engine)
+    prob.solve(precision=prec, max_iter=128, eps_rel=0.0, engine=pkg.LP_ENGINE_GRID)
     prof = prob.profile_kernels(reps=10)
     peak, peak_kind = peaks()
     cand = {"primal": (prof["primal_ms"], prof["primal_bytes"]),

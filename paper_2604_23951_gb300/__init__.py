@@ -8,6 +8,9 @@ and streams.
 from .capi import (  # noqa: F401
     LP_FP64,
     LP_MIXED,
+    LP_ENGINE_AUTO,
+    LP_ENGINE_GRID,
+    LP_ENGINE_CLUSTER,
     LP_OPTIMAL,
     LP_ITER_LIMIT,
     LP_TIME_LIMIT,
