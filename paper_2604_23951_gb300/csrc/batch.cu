@@ -539,7 +539,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // or its share of the launch's time budget is spent (at least one block).
 // On leaving a slot, rank 0 copies its state to sout[oi] for the host.
 template <bool MIXED>
-__global__ void __launch_bounds__(512) k_batch(const SlotDesc *__restrict__ desc, State *states,
+__global__ void __launch_bounds__(512, 1) k_batch(const SlotDesc *__restrict__ desc, State *states,
                                                const int *__restrict__ order, int nord,
                                                State *sout, BatchConst C) {
   __shared__ BatchShared sh;

@@ -1,0 +1,71 @@
+"""Parity at the benchmark's full size (the presolved C2 workload, grid
+engine, the launch configuration bench.py times).
+
+The oracle runs a few FP64 iterations of the same presolved LP (each takes a
+fraction of a second at this size); the GPU iterates must agree to 1e-10
+relative.  The full solve is then checked through properties that hold at
+any size: rel-KKT <= 1e-6 on the reduced LP from the device, the same
+measure recomputed on the host from the returned point, and the postsolved
+point is KKT for the original LP with the planted objective.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from oracle import presolve as PS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return lpgen.c2_presolvable()
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2604_23951_gb300 as p
+
+    p.load()
+    return p
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+def test_c2_first_iterates_match_oracle(pkg, c2):
+    dev = pkg.TorchDevice(0)
+    red = PS.presolve(c2).reduced
+    eta, om = 0.01, 1.0
+    ref = oracle.pdhg_solve(red, oracle.Opts(max_iter=3, eps_rel=0.0), eta=eta, omega0=om)
+    prob = pkg.Problem(c2, dev)
+    prob.presolve()
+    r = prob.solve(max_iter=3, eps_rel=0.0, step_size=eta, primal_weight=om,
+                   engine=pkg.LP_ENGINE_GRID)
+    assert r.iterations == 3
+    xi, yi = prob.iterate()
+    assert relerr(xi, ref.x_iter) <= 1e-10
+    assert relerr(yi, ref.y_iter) <= 1e-10
+    prob.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_solves_to_tolerance_and_postsolves(pkg, c2, precision):
+    dev = pkg.TorchDevice(0)
+    prob = pkg.Problem(c2, dev)
+    prob.presolve()
+    r = prob.solve(precision=precision, engine=pkg.LP_ENGINE_GRID)
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    # the device's measure, recomputed on the host from the returned point
+    xr, yr, _ = prob.solution()
+    host = prob.rel_kkt(xr, yr)
+    assert host["rel_kkt"] <= 1.0001e-6
+    assert abs(host["p"] - r.primal_obj) <= 1e-9 * (1 + abs(r.primal_obj))
+    x, y, _ = prob.postsolve()
+    k = oracle.rel_kkt(c2, x, y)
+    assert k["rel_kkt"] <= 1e-5
+    tol = 1e-5 if precision == 0 else 1e-4
+    assert abs(k["p"] - c2.p_star) / (1 + abs(c2.p_star)) <= tol
+    prob.close()
