@@ -194,9 +194,12 @@ int lp_upload(lp_problem *lp);
 /* Solve the current (reduced) LP on the GPU.  May be called repeatedly;
  * every call starts from the initial (or warm-start) point.  LP_MIXED runs
  * the SpMV in FP32 until the relative KKT error is within 10 x eps_rel, or
- * has not halved over 32 checks once below 1e-4 (the FP32 rounding floor),
- * or over 256 checks anywhere; then it finishes with the FP64 SpMV, and the
- * iterates, anchor and weights carry over. */
+ * its best value has not halved over 256 checks; then it finishes with the
+ * FP64 SpMV, and the iterates, anchor and weights carry over.  When the
+ * environment variable LP_TRACE names a file, every state read-back (each
+ * check period of the grid engine, each launch of the cluster engine)
+ * appends one JSON line: engine, t, rel_kkt, rel_p, rel_d, rel_gap, omega,
+ * restarts, fp32. */
 int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res);
 
 /* Solution of the current (reduced) LP: x (n), y (m), z = c - A^T y (n).

@@ -15,6 +15,9 @@ from .capi import (  # noqa: F401
     LP_ITER_LIMIT,
     LP_TIME_LIMIT,
     LP_NUMERICAL,
+    LP_INFEASIBLE,
+    LP_UNBOUNDED,
+    LP_CANCELLED,
     LPError,
     Problem,
     Server,

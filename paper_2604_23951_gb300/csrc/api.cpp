@@ -3,6 +3,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <cstdlib>
+#include <cstdio>
 #include <exception>
 #include <limits>
 #include <new>
@@ -24,6 +27,26 @@ int fail(int code, const std::string &msg) {
 
 namespace gb300lp {
 void set_last_error(const std::string &m) { g_err = m; }
+
+void trace_state(const char *engine, long long t, double rel_kkt, double rel_p, double rel_d,
+                 double rel_gap, double omega, int restarts, int fp32) {
+  static std::mutex mu;
+  static bool opened = false;
+  static FILE *f = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!opened) {
+    opened = true;
+    const char *path = std::getenv("LP_TRACE");
+    if (path && *path) f = std::fopen(path, "a");
+  }
+  if (!f) return;
+  std::fprintf(f,
+               "{\"engine\": \"%s\", \"t\": %lld, \"rel_kkt\": %.6e, \"rel_p\": %.6e, "
+               "\"rel_d\": %.6e, \"rel_gap\": %.6e, \"omega\": %.6e, \"restarts\": %d, "
+               "\"fp32\": %d}\n",
+               engine, t, rel_kkt, rel_p, rel_d, rel_gap, omega, restarts, fp32);
+  std::fflush(f);
+}
 }  // namespace gb300lp
 
 struct lp_problem {

@@ -1709,6 +1709,8 @@ int cluster_solve(const HostLP &h, const lp_solve_opts &o, const lp_device_ctx *
       ++launches;
       CK(cudaMemcpyAsync(&hs, d_sout, sizeof(State), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      trace_state("cluster", hs.t, hs.rel_kkt, hs.rel_p, hs.rel_d, hs.rel_gap, hs.omega,
+                  hs.restarts, hs.mixed_active);
       if (o.verbose)
         std::fprintf(stderr, "pdhg-cluster t=%lld rel_kkt=%.3e omega=%.3e restarts=%d fp32=%d\n",
                      hs.t, hs.rel_kkt, hs.omega, hs.restarts, hs.mixed_active);

@@ -73,6 +73,11 @@ int dev_solve(DeviceLP *d, const HostLP &lp, const lp_solve_opts &opts, lp_resul
 void dev_destroy(DeviceLP *d);
 int dev_profile(DeviceLP *d, int reps, double *out, std::string &err);
 
+// Per-check trace: when the environment variable LP_TRACE names a file, one
+// JSON line per state read-back of a solve is appended to it (api.cpp).
+void trace_state(const char *engine, long long t, double rel_kkt, double rel_p, double rel_d,
+                 double rel_gap, double omega, int restarts, int fp32);
+
 // The cluster engine: one thread-block cluster runs the whole solve of a
 // small LP (batch.cu); same algorithm and result semantics as dev_solve.
 int cluster_solve(const HostLP &lp, const lp_solve_opts &opts, const lp_device_ctx *ctx,

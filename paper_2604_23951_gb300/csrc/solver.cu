@@ -931,6 +931,11 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       ++head;
       volatile int status = d->hst->status;
       volatile int kerr = d->hst->err;
+      {
+        const State &V = *d->hst;
+        trace_state("grid", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap, V.omega, V.restarts,
+                    V.mixed_active);
+      }
       if (o.verbose) {
         const State &V = *d->hst;
         std::fprintf(stderr, "pdhg t=%lld rel_kkt=%.3e rel_p=%.2e rel_d=%.2e gap=%.2e omega=%.3e "
