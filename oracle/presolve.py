@@ -7,13 +7,13 @@ A reduction is a presolve transformation plus a postsolve transformation
 (Sec. 2.1).  The explorers used here are the fast ones of Table 1 (empty rows
 and columns, fixed columns, singleton rows, redundant rows / dominated row
 sides from activity bounds, doubleton equality rows, free or implied-free
-column singletons in equality rows), run in rounds that re-examine only what
-the previous round touched (Sec. 3.2).
+column singletons in equality rows, variable locks), run in rounds that
+re-examine only what the previous round touched (Sec. 3.2).
 
 Schedule (READING): each round runs the passes
     empty rows -> empty cols -> fixed cols -> singleton rows
     -> redundant rows / dominated sides -> doubleton equalities
-    -> free column singletons,
+    -> free column singletons -> variable locks,
 each pass scanning its candidates in increasing index order.  Round 1 scans
 every row and column; later rounds scan the rows and columns marked dirty in
 the previous round.  Stop after a round with no reduction or after 20 rounds.
@@ -26,6 +26,14 @@ Tolerances (READING): infeasibility is declared when a lower bound exceeds an
 upper bound by more than 1e-9; coefficients below 1e-12 in magnitude after an
 update are dropped.  Activity sums run over a row's entries in increasing
 column order; comparisons of activities with row bounds are exact.
+
+Variable locks (Sec. 2.3, weak dual exploration): a row i holding x_j
+up-locks it when a_ij > 0 and u_i is finite or a_ij < 0 and l_i is finite,
+and down-locks it in the mirrored cases.  With c_j < 0 and no up-lock every
+optimal x has x_j at its upper bound (z_j < 0 for every dual feasible point),
+so x_j is fixed there; with c_j > 0 and no down-lock, at its lower bound.  An
+infinite target bound makes the LP unbounded (if feasible).  The fixing uses
+the fixed-column reduction and its postsolve.
 
 Postsolve replays the records in reverse order and keeps eq. (2)'s dual
 feasibility c - A^T y - z = 0 of every intermediate problem:
@@ -124,7 +132,7 @@ class Presolver:
         self.status = REDUCED
         self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
                                       "redundant_row", "dropped_side", "doubleton",
-                                      "free_col_singleton")}
+                                      "free_col_singleton", "dual_fix")}
 
     # -- primitive edits with dirty marking --------------------------------
     def _mark_col_bounds(self, j):
@@ -362,6 +370,40 @@ class Presolver:
         self.counts["free_col_singleton"] += 1
         self.changed = True
 
+    def locks(self, j):
+        """(up-locked, down-locked) of column j from its rows' finite bounds"""
+        up = down = False
+        for i, a in self.cols[j].items():
+            lf = not math.isinf(self.lo[i])
+            uf = not math.isinf(self.hi[i])
+            if a > 0:
+                up = up or uf
+                down = down or lf
+            else:
+                up = up or lf
+                down = down or uf
+        return up, down
+
+    def dual_fix(self, j):
+        cj = self.c[j]
+        if cj == 0.0:
+            return
+        up, down = self.locks(j)
+        if cj < 0 and not up:
+            v = self.ux[j]
+        elif cj > 0 and not down:
+            v = self.lx[j]
+        else:
+            return
+        if math.isinf(v):
+            self.status = UNBOUNDED
+            return
+        self.lx[j] = v
+        self.ux[j] = v
+        self.fixed_col(j)
+        self.counts["fixed_col"] -= 1
+        self.counts["dual_fix"] += 1
+
     # -- driver ----------------------------------------------------------------
     def run(self, max_rounds=MAX_ROUNDS):
         rows_c = list(range(self.m))
@@ -402,6 +444,11 @@ class Presolver:
             for j in cols_c:
                 if self.col_on[j] and len(self.cols[j]) == 1:
                     self.free_col_singleton(j)
+            for j in cols_c:
+                if self.col_on[j] and self.cols[j]:
+                    self.dual_fix(j)
+                    if self.status != REDUCED:
+                        return rounds
             if not self.changed:
                 break
             rows_c = sorted(i for i in self.dirty_r if self.row_on[i])

@@ -170,3 +170,59 @@ def test_pdhg_on_reduced_then_postsolve():
     k = oracle.rel_kkt(lp, x, y)
     assert k["rel_kkt"] <= 1e-6
     assert abs(k["p"] - lp.p_star) <= 1e-6 * (1 + abs(lp.p_star))
+
+
+def test_variable_lock_worked_example():
+    # Sec. 2.3: c_1 < 0 and no row keeps x_1 from increasing (x1 + x2 >= 1 has
+    # no upper bound): every optimum has x_1 = 3, its upper bound
+    lp = SimpleLP([[1.0, 1.0]], [-1.0, 1.0], [1.0], [INF], [0.0, 0.0], [3.0, INF])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["dual_fix"] == 1
+    assert x[0] == 3.0 and x[1] == 0.0
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-12
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-12 * (1 + abs(p))
+    assert z[0] < 0  # at its upper bound
+    # the mirrored case: c > 0, the row only bounds x from above
+    lp = SimpleLP([[1.0, -1.0]], [1.0, -1.0], [-INF], [2.0], [-1.0, 0.0], [4.0, 5.0])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["dual_fix"] >= 1
+    k = oracle.rel_kkt(lp, x, y)
+    p, _, _ = highs_solve(lp)
+    assert k["rel_kkt"] <= 1e-12 and abs(k["p"] - p) <= 1e-12 * (1 + abs(p))
+
+
+def test_variable_lock_unbounded():
+    # c_1 < 0, no up-lock, no upper bound: the (feasible) LP is unbounded
+    lp = SimpleLP([[1.0, 1.0]], [-1.0, 1.0], [1.0], [INF], [0.0, 0.0], [INF, INF])
+    assert PS.presolve(lp).status == PS.UNBOUNDED
+
+
+def test_variable_locks_on_one_sided_rows_keep_the_optimum():
+    # rows A x >= b with A >= 0: every column with c_j < 0 and a finite upper
+    # bound has no up-lock and is fixed there; the optimum is unchanged
+    rng = np.random.default_rng(11)
+    m, n = 40, 90
+    A = (rng.random((m, n)) < 0.12) * rng.uniform(0.5, 2.0, (m, n))
+    A[np.arange(m), rng.integers(0, n, m)] += 1.0  # no empty rows
+    c = rng.normal(size=n)
+    lp = SimpleLP(A, c, rng.uniform(0.5, 1.5, m), np.full(m, INF), np.zeros(n),
+                  rng.uniform(1.0, 3.0, n))
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["dual_fix"] >= int(np.sum(c < 0)) // 2
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8
+    p, _, _ = highs_solve(lp)
+    assert abs(k["p"] - p) <= 1e-8 * (1 + abs(p))
+
+
+def test_variable_lock_respects_the_coefficient_sign():
+    # -x1 + x2 >= 1: increasing x1 would violate the row (a < 0 with a finite
+    # lower side is an up-lock), so c_1 < 0 does not fix x1; the optimum is
+    # x = (0, 1) with objective 2, while fixing x1 at 4 would give 6
+    lp = SimpleLP([[-1.0, 1.0]], [-1.0, 2.0], [1.0], [INF], [0.0, 0.0], [4.0, 10.0])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["dual_fix"] == 0
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-12 and abs(k["p"] - 2.0) <= 1e-12
