@@ -101,7 +101,8 @@ typedef struct {
 #define LP_RULE_REDUNDANT_ROW 16
 #define LP_RULE_DOUBLETON 32
 #define LP_RULE_FREE_COL_SINGLETON 64
-#define LP_RULE_ALL 127
+#define LP_RULE_VARIABLE_LOCKS 128 /* weak dual fixing (Sec. 2.3)             */
+#define LP_RULE_ALL 255
 
 typedef struct {
   int32_t status;          /* LP_PRESOLVE_*                                 */
@@ -110,9 +111,10 @@ typedef struct {
   int64_t nnz;
   int32_t m0, n0;          /* original sizes                                */
   int64_t nnz0;
-  int64_t counts[8];       /* reductions per rule: empty_row, empty_col,
+  int64_t counts[12];      /* reductions per rule: empty_row, empty_col,
                               fixed_col, singleton_row, redundant_row,
-                              dropped_side, doubleton, free_col_singleton   */
+                              dropped_side, doubleton, free_col_singleton,
+                              variable locks (dual fixing); 9-11 unused    */
   double seconds;
 } lp_presolve_info;
 
@@ -184,7 +186,11 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
               const lp_device_ctx *dev, lp_problem **out);
 
 /* Presolve in place (Sec. 2-3): the problem becomes the reduced LP; the
- * postsolve record is kept inside.  Host only.  May be called once. */
+ * postsolve record is kept inside.  Host only.  May be called once.  Each
+ * round runs the enabled passes in the order empty rows, empty columns,
+ * fixed columns, singleton rows, redundant rows / dominated row sides,
+ * doubleton equalities, free column singletons, variable locks; round 1
+ * scans everything, later rounds what the previous round changed. */
 int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *info);
 
 /* Copy the current (reduced) LP to the device and build its layout (row

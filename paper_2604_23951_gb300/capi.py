@@ -39,7 +39,7 @@ class lp_presolve_opts(C.Structure):
 class lp_presolve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("rounds", C.c_int32), ("m", C.c_int32),
                 ("n", C.c_int32), ("nnz", C.c_int64), ("m0", C.c_int32), ("n0", C.c_int32),
-                ("nnz0", C.c_int64), ("counts", C.c_int64 * 8), ("seconds", C.c_double)]
+                ("nnz0", C.c_int64), ("counts", C.c_int64 * 12), ("seconds", C.c_double)]
 
 
 class lp_solve_opts(C.Structure):
@@ -246,7 +246,7 @@ class Problem:
                                    C.byref(n0)))
         return m.value, n.value, nnz.value
 
-    def presolve(self, max_rounds: int = 20, enable: int = 127) -> lp_presolve_info:
+    def presolve(self, max_rounds: int = 20, enable: int = 255) -> lp_presolve_info:
         o = lp_presolve_opts(max_rounds, enable)
         info = lp_presolve_info()
         check(self.lib.lp_presolve(self.h, C.byref(o), C.byref(info)))

@@ -6,7 +6,8 @@
 // Rules, schedule and postsolve formulas:
 //   round = empty rows -> empty cols -> fixed cols -> singleton rows ->
 //           redundant rows / dominated sides -> doubleton equalities ->
-//           free (or implied-free) column singletons in equality rows;
+//           free (or implied-free) column singletons in equality rows ->
+//           variable locks (weak dual fixing, Sec. 2.3);
 //   each pass scans candidates in increasing index order; round 1 scans
 //   everything, later rounds what the previous round dirtied; stop after a
 //   round without reductions or after max_rounds.
@@ -59,7 +60,7 @@ enum RecKind {
 
 enum CountIdx {
   C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
-  C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL,
+  C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX,
 };
 
 // Sorted sparse vectors in one pool, each with spare capacity.  A vector that
@@ -442,6 +443,45 @@ struct Presolver {
     po->counts[C_DOUBLETON]++;
     changed = true;
   }
+  // A row holding x_j up-locks it when a_ij > 0 and its upper side is
+  // finite or a_ij < 0 and its lower side is; down-locks mirror that.
+  void locks(int32_t j, bool &up, bool &down) const {
+    up = down = false;
+    const int64_t s = cols.start[j];
+    for (int32_t q = 0; q < cols.len[j]; ++q) {
+      const int32_t i = cols.idx[s + q];
+      const bool lf = !std::isinf(lo[i]), uf = !std::isinf(hi[i]);
+      if (cols.val[s + q] > 0) {
+        up = up || uf;
+        down = down || lf;
+      } else {
+        up = up || lf;
+        down = down || uf;
+      }
+    }
+  }
+  // weak dual fixing: c_j < 0 without an up-lock puts x_j at its upper bound
+  // in every optimum (z_j < 0), c_j > 0 without a down-lock at its lower
+  // bound; the fixed-column reduction does the rest
+  void dual_fix(int32_t j) {
+    const double cj = c[j];
+    if (cj == 0.0) return;
+    bool up, down;
+    locks(j, up, down);
+    double v;
+    if (cj < 0 && !up) v = ux[j];
+    else if (cj > 0 && !down) v = lx[j];
+    else return;
+    if (std::isinf(v)) {
+      status = LP_PRESOLVE_UNBOUNDED;
+      return;
+    }
+    lx[j] = v;
+    ux[j] = v;
+    fixed_col(j);
+    po->counts[C_FIXED_COL]--;
+    po->counts[C_DUAL_FIX]++;
+  }
   void free_col_singleton(int32_t j) {
     int32_t i = cols.idx[cols.start[j]];
     double a = cols.val[cols.start[j]];
@@ -527,6 +567,12 @@ struct Presolver {
       if (mask & LP_RULE_FREE_COL_SINGLETON)
         for (int32_t j : cc)
           if (col_on[j] && cols.len[j] == 1) free_col_singleton(j);
+      if (mask & LP_RULE_VARIABLE_LOCKS)
+        for (int32_t j : cc)
+          if (col_on[j] && cols.len[j] > 0) {
+            dual_fix(j);
+            if (status != LP_PRESOLVE_REDUCED) return rounds;
+          }
       if (!changed) break;
       rc.clear();
       cc.clear();

@@ -25,8 +25,18 @@ def _lib_or_skip():
         pytest.skip(str(e))
 
 
+def _one_sided_rows(seed=11, m=40, n=90):
+    # A x >= b with A >= 0: the variable-lock explorer fixes many columns
+    rng = np.random.default_rng(seed)
+    A = (rng.random((m, n)) < 0.12) * rng.uniform(0.5, 2.0, (m, n))
+    A[np.arange(m), rng.integers(0, n, m)] += 1.0
+    return SimpleLP(A, rng.normal(size=n), rng.uniform(0.5, 1.5, m), np.full(m, INF),
+                    np.zeros(n), rng.uniform(1.0, 3.0, n))
+
+
 def _cases():
     return [
+        ("variable_locks", _one_sided_rows),
         ("general_small", lambda: lpgen.general_structure(600, 1500, 31, nnz_target=9000,
                                                           one_sided=0.2)),
         ("general_b", lambda: lpgen.general_structure(800, 2000, 77, nnz_target=16000)),
@@ -55,7 +65,7 @@ def test_reduced_problem_identical(name, make):
     assert info.rounds == ref.rounds
     assert list(info.counts) == [ref.counts[k] for k in (
         "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
-        "dropped_side", "doubleton", "free_col_singleton")]
+        "dropped_side", "doubleton", "free_col_singleton", "dual_fix")] + [0, 0, 0]
     np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
     np.testing.assert_array_equal(red.col_idx, r.col_idx)
     np.testing.assert_array_equal(red.val, r.val)
