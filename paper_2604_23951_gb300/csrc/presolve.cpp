@@ -343,11 +343,11 @@ struct Presolver {
     po->counts[C_SINGLETON_ROW]++;
     changed = true;
   }
-  void redundant_row(int32_t i) {
+  // redundant rows / dominated sides: the decision for row i given its
+  // activity bounds
+  void redundant_row_with(int32_t i, double amin, double amax) {
     double l = lo[i], h = hi[i];
     if (l == h) return;
-    double amin, amax;
-    activity(i, -1, amin, amax);
     bool lo_imp = std::isinf(l) || amin >= l;
     bool hi_imp = std::isinf(h) || amax <= h;
     if (lo_imp && hi_imp) {
@@ -555,9 +555,30 @@ struct Presolver {
             singleton_row(i);
             if (status != LP_PRESOLVE_REDUCED) return rounds;
           }
-      if (mask & LP_RULE_REDUNDANT_ROW)
+      if (mask & LP_RULE_REDUNDANT_ROW) {
+        // The pass changes no column bound and no other row's entries, so
+        // every candidate's activity bounds can be computed first (in
+        // parallel for large candidate sets, each a sequential sum in the
+        // same order), then the decisions applied in index order.
+        std::vector<int32_t> cand;
         for (int32_t i : rc)
-          if (row_on[i] && rows.len[i] >= 1) redundant_row(i);
+          if (row_on[i] && rows.len[i] >= 1 && lo[i] != hi[i]) cand.push_back(i);
+        std::vector<double> amin(cand.size()), amax(cand.size());
+        const size_t nc = cand.size();
+        const unsigned nt = nc >= 20000 ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
+        auto work = [&](size_t a, size_t b) {
+          for (size_t q = a; q < b; ++q) activity(cand[q], -1, amin[q], amax[q]);
+        };
+        if (nt <= 1) {
+          work(0, nc);
+        } else {
+          std::vector<std::thread> pool;
+          for (unsigned t = 0; t < nt; ++t)
+            pool.emplace_back(work, nc * t / nt, nc * (t + 1) / nt);
+          for (std::thread &th : pool) th.join();
+        }
+        for (size_t q = 0; q < nc; ++q) redundant_row_with(cand[q], amin[q], amax[q]);
+      }
       if (mask & LP_RULE_DOUBLETON)
         for (int32_t i : rc)
           if (row_on[i] && rows.len[i] == 2 && lo[i] == hi[i]) {
