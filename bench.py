@@ -9,11 +9,15 @@ resident in HBM.  `e2e` times the whole C-ABI path from host buffers
 (lp_create, lp_presolve, lp_solve with its H2D upload, lp_postsolve with the
 D2H of the solution).
 
-Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
-replica of the workload (no collective on the data path; replicas only).
+Prints ONE JSON line (rank 0).  Under torchrun the single-LP workloads
+(c1, c2, c3) run one replica per rank (no collective on the data path;
+replicas only) and report the slowest rank's time; the batch (c4) and
+serving (c5) workloads scale weakly: every rank solves its own seeded batch
+or stream (rank 0 the configured one) and the value counts all ranks' LPs
+over the slowest rank's time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c1|c3]
+                  [--workload c2|c1|c3|c4|c5] [--precision fp64|mixed]
 """
 from __future__ import annotations
 
@@ -140,6 +144,24 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 # helpers
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (the job's time), or x alone."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_share(rank: int, per_rank: int) -> int:
+    """First item of rank's share of a batch workload scaled weakly: rank r
+    solves items r * per_rank .. (r + 1) * per_rank - 1 of the seeded
+    sequence, so rank 0 always solves the configuration's own batch."""
+    return rank * per_rank
 
 
 def peaks():
@@ -307,10 +329,7 @@ def run_ours(args):
         elapsed += ev0.elapsed_time(ev1) / 1e3
     barrier()
     clk = clocks.stop()
-    t = torch.tensor([elapsed], device=f"cuda:{local}", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, f"cuda:{local}")
     value = elapsed / args.steps
     r = results[-1]
     launches = int(sum(x.kernel_launches for x in results))
@@ -424,7 +443,8 @@ def run_batch(args):
     dev = pkg.TorchDevice(local)
     prec = pkg.LP_MIXED if args.precision == "mixed" else pkg.LP_FP64
     if args.workload == "c4":
-        lps = lpgen.c4_batch(512)[: max(1, min(512, args.lps))]
+        count = max(1, min(512, args.lps))
+        lps = lpgen.c4_batch(count, first=weak_share(rank, count))
         # device budget: the packed slots with room to spare (~2.2 GB for 512)
         budget = int(max(256 << 20, 3 * sum(lp.nnz * 48 + (lp.m + lp.n) * 200 for lp in lps)))
         desc = (f"{len(lps)} planted LPs, m log-uniform [100, 20k], n = 2m, 4-30 nnz/row, "
@@ -452,9 +472,11 @@ def run_batch(args):
         clocks.start()
         steps = [one_step() for _ in range(args.steps)]
         clk = clocks.stop()
-        el = statistics.mean(s_[0] for s_ in steps)
+        # weak scaling: every rank solves its own batch; the job's time is the
+        # slowest rank's, and the value counts every rank's LPs
+        el = max_over_ranks(statistics.mean(s_[0] for s_ in steps), dist, f"cuda:{local}")
         lat = steps[-1][1]
-        value = len(lps) / el
+        value = world * len(lps) / el
         # comparator: the same LPs solved singly in plain FP64 (lp_solve, one
         # after another), on every 16th LP of the batch
         sub = lps[::16] if len(lps) >= 16 else lps[:1]
@@ -503,7 +525,9 @@ def run_batch(args):
     # ---- c5: serving stream --------------------------------------------------
     import multiprocessing as mp
 
-    reqs = lpgen.c5_stream(count=args.requests, rate=args.rate)
+    # weak scaling: every rank serves its own stream (rank 0: the configured one)
+    reqs = lpgen.c5_stream(count=args.requests, rate=args.rate,
+                           seed=lpgen.BASE_SEED + 5 + 1_000_003 * rank)
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
         lps = pool.map(_gen_c5, reqs)
     desc = (f"Poisson stream: {len(reqs)} planted LPs at {args.rate:g} req/s, nnz log-uniform "
@@ -551,6 +575,7 @@ def run_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     el, done, st = serve()
+    el = max_over_ranks(el, dist, f"cuda:{local}")
     clk = clocks.stop()
     lat = [done[j][0] for j in range(len(lps))]
     opt = sum(1 for j in range(len(lps)) if done[j][1].termination == 0)
@@ -568,7 +593,7 @@ def run_batch(args):
     t_single = time.perf_counter() - t0
     offered = len(lps) / max(reqs[-1].arrival_s, 1e-9)
     line = {
-        "metric": METRIC, "value": len(lps) / el, "unit": "requests/s", "n_gpus": world,
+        "metric": METRIC, "value": world * len(lps) / el, "unit": "requests/s", "n_gpus": world,
         "steps": 1, "warmup": max(1, args.warmup // 3), "ms_per_step": el * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == pkg.LP_FP64 else "f32 SpMV / f64 iterates", "data": "synthetic",
@@ -584,7 +609,7 @@ def run_batch(args):
                         "latency_p99_s": float(np.percentile(single, 99)),
                         "note": "each request presolved, solved and postsolved alone, in order"},
         "server_stats": st,
-        "e2e": {"value": len(lps) / el, "unit": "requests/s",
+        "e2e": {"value": world * len(lps) / el, "unit": "requests/s",
                 "h2d_bytes_per_step": int(sum(lp.nnz * 24 for lp in lps)),
                 "d2h_bytes_per_step": int(sum((2 * lp.n + lp.m) * 8 for lp in lps))},
         "cpu_baseline": None, "clocks": clk, "gpu_launches": st["launches"],

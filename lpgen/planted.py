@@ -453,13 +453,15 @@ def c3_powerlaw(seed: int = BASE_SEED + 3, m: int = 2_000_000, n: int = 5_000_00
 
 
 def c4_batch(count: int = 512, seed: int = BASE_SEED + 4, m_lo: int = 100,
-             m_hi: int = 20_000):
+             m_hi: int = 20_000, first: int = 0):
     """Independent planted LPs: m log-uniform in [m_lo, m_hi], n = 2m,
-    4-30 nnz per row, N(0,1) values, equality rows, x >= 0."""
+    4-30 nnz per row, N(0,1) values, equality rows, x >= 0.  Items
+    first .. first + count - 1 of the seeded sequence (the same LPs whatever
+    slice they are generated in)."""
     rng = np.random.default_rng(seed)
-    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=count)).astype(np.int64)
+    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=first + count)).astype(np.int64)
     out = []
-    for j in range(count):
+    for j in range(first, first + count):
         m = int(ms[j])
         out.append(equality_nonneg(m, 2 * m, seed + 1000 * (j + 1), 4, 30, 0.4,
                                    name=f"c4_item{j}_{m}x{2 * m}"))
