@@ -306,8 +306,10 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
 
 /* Queue a problem (its current, possibly presolved LP).  The server borrows
  * `lp` until its result has been polled; the polled answer is also stored in
- * `lp` (lp_get_solution / lp_postsolve work on it).  Fails LP_ERR_BUDGET if
- * the problem alone exceeds the budget. */
+ * `lp` (lp_get_solution / lp_postsolve work on it).  A problem whose presolve
+ * proved it infeasible or unbounded is answered at once (termination
+ * LP_INFEASIBLE / LP_UNBOUNDED, no device work).  Fails LP_ERR_BUDGET if the
+ * problem alone exceeds the budget. */
 int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket);
 
 /* LP_PENDING while in flight; LP_OK once done: res, x (n), y (m) of the

@@ -64,6 +64,13 @@ struct lp_problem {
 namespace gb300lp {
 // used by the batch server (batch.cu) to read a problem's current LP
 const HostLP &problem_current(const lp_problem *lp) { return lp->cur; }
+// LP_INFEASIBLE / LP_UNBOUNDED when the presolve proved it, else -1
+int problem_proven_status(const lp_problem *lp) {
+  if (!lp->presolved) return -1;
+  if (lp->po.status == LP_PRESOLVE_INFEASIBLE) return LP_INFEASIBLE;
+  if (lp->po.status == LP_PRESOLVE_UNBOUNDED) return LP_UNBOUNDED;
+  return -1;
+}
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z) {
   lp->sol.x = x;

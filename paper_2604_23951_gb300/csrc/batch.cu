@@ -54,6 +54,7 @@ namespace gb300lp {
 
 void set_last_error(const std::string &m);
 const HostLP &problem_current(const lp_problem *lp);
+int problem_proven_status(const lp_problem *lp);
 constexpr long long kSoloNnz = 500000;  // larger requests run on the single-LP grid path
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z);
@@ -1395,6 +1396,19 @@ int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket) {
     return LP_ERR_INVALID;
   }
   try {
+    const int proven = problem_proven_status(lp);
+    if (proven >= 0) {
+      // the presolve already decided it: done without device work
+      std::lock_guard<std::mutex> lk(srv->mu);
+      *ticket = srv->next_ticket++;
+      Done d;
+      d.res.termination = proven;
+      srv->done[*ticket] = std::move(d);
+      srv->where[*ticket] = 2;
+      ++srv->n_admitted;
+      ++srv->n_finished;
+      return LP_OK;
+    }
     Request rq;
     const HostLP &h = problem_current(lp);
     if (h.nnz() >= srv->solo_nnz) {

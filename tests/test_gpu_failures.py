@@ -122,3 +122,15 @@ def test_trace_writes_one_json_line_per_readback(tmp_path):
     assert lines and all(l["engine"] == "grid" for l in lines)
     assert lines[-1]["rel_kkt"] <= 1e-6
     assert max(l["t"] for l in lines) <= iters + 64
+
+
+def test_server_answers_presolve_infeasible_at_once(pkg, dev):
+    lp = SimpleLP([[1.0, 1.0], [1.0, 0.0]], [1.0, 1.0], [-np.inf, -np.inf], [5.0, 0.0],
+                  [1.0, 0.0], [np.inf, np.inf])
+    prob = pkg.Problem(lp, dev)
+    prob.presolve()
+    srv = pkg.Server(1 << 26, dev)
+    t = srv.submit(prob)
+    got = srv.poll(t)  # no pump needed: decided at submission
+    assert got is not None and got[0].termination == pkg.LP_INFEASIBLE
+    srv.close()
