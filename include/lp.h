@@ -102,7 +102,12 @@ typedef struct {
 #define LP_RULE_DOUBLETON 32
 #define LP_RULE_FREE_COL_SINGLETON 64
 #define LP_RULE_VARIABLE_LOCKS 128 /* weak dual fixing (Sec. 2.3)             */
-#define LP_RULE_ALL 255
+#define LP_RULE_COL_SINGLETON_INEQ 256 /* column singleton in an inequality
+                                          row: the row becomes an equality
+                                          at the side every optimum is at  */
+#define LP_RULE_PARALLEL_ROWS 512  /* medium explorer (Table 1): run when a
+                                      round of the others changed nothing  */
+#define LP_RULE_ALL 1023
 
 typedef struct {
   int32_t status;          /* LP_PRESOLVE_*                                 */
@@ -114,7 +119,9 @@ typedef struct {
   int64_t counts[12];      /* reductions per rule: empty_row, empty_col,
                               fixed_col, singleton_row, redundant_row,
                               dropped_side, doubleton, free_col_singleton,
-                              variable locks (dual fixing); 9-11 unused    */
+                              variable locks (dual fixing), inequality
+                              rows made equalities, parallel rows merged;
+                              11 unused                                    */
   double seconds;
 } lp_presolve_info;
 

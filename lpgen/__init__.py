@@ -22,6 +22,7 @@ from .planted import (  # noqa: F401
     c4_batch,
     c5_stream,
     general_structure,
+    medium_structure,
     equality_nonneg,
     tiny_box,
 )

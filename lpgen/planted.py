@@ -520,3 +520,75 @@ def tiny_box(m: int, n: int, seed: int, density: float = 0.7) -> PlantedLP:
     col_kinds = np.full(n, COL_BOX, dtype=np.int64)
     return _finish(f"tiny_box_{m}x{n}_{seed}", m, n, row_ptr, col_idx, val, row_kinds,
                    col_kinds, rng, p_low=0.35, p_up=0.35)
+
+
+def medium_structure(m: int, n: int, seed: int, nnz_target: int | None = None,
+                     frac_parallel: float = 0.08, frac_slack: float = 0.05) -> PlantedLP:
+    """general_structure (with one-sided rows) plus two planted structures:
+
+    * parallel copies: frac_parallel * m extra rows, each a copy of a random
+      row with two or more entries scaled by s in {-3, -0.5, 0.25, 2, 7},
+      with bounds that hold x* strictly (one side possibly infinite) and
+      y* = 0 on the copy;
+    * slack columns: frac_slack * m extra columns, each a single entry in an
+      inequality row whose y*_i is nonzero, with x* = 0 and either x >= 0 or
+      x free; for x >= 0 the coefficient's sign and z* = |a y*_i| / 2 make
+      c_j = a y*_i + z*_j of the sign that pushes x_j against the row.
+
+    The planted optimum (x*, y*, z*) stays optimal, so p* is unchanged.
+    """
+    import scipy.sparse as sp
+
+    base = general_structure(m, n, seed, nnz_target=nnz_target, one_sided=0.3,
+                             name="medium")
+    rng = np.random.default_rng(seed + 7)
+    A = base.csr()
+    lens = np.diff(base.row_ptr)
+    ax = A @ base.x_star
+    # parallel copies
+    src = rng.choice(np.nonzero(lens >= 2)[0], int(round(frac_parallel * m)))
+    scale = rng.choice(np.array([-3.0, -0.5, 0.25, 2.0, 7.0]), src.shape[0])
+    B = sp.diags(scale) @ A[src]
+    w1 = np.exp(rng.standard_normal(src.shape[0])) + 0.1
+    w2 = np.exp(rng.standard_normal(src.shape[0])) + 0.1
+    open_side = rng.random(src.shape[0])
+    lo_c = ax[src] - w1
+    hi_c = ax[src] + w2
+    lo_c[open_side < 0.25] = -np.inf
+    hi_c[(open_side >= 0.25) & (open_side < 0.5)] = np.inf
+    # bounds of s * (a_i x): scale and swap for s < 0
+    blo = np.where(scale > 0, scale * lo_c, scale * hi_c)
+    bhi = np.where(scale > 0, scale * hi_c, scale * lo_c)
+    blo[np.isnan(blo)] = -np.inf
+    bhi[np.isnan(bhi)] = np.inf
+    # slack columns
+    ineq = np.nonzero((base.row_lo != base.row_hi) & (base.y_star != 0.0) & (lens >= 1))[0]
+    rows_s = rng.choice(ineq, min(int(round(frac_slack * m)), ineq.shape[0]), replace=False)
+    k = rows_s.shape[0]
+    mag = np.exp(0.5 * rng.standard_normal(k))
+    free = rng.random(k) < 0.3
+    ys = base.y_star[rows_s]
+    # x >= 0: y* > 0 (lower side active) takes a < 0, y* < 0 takes a > 0
+    a_s = np.where(ys > 0, -mag, mag)
+    z_s = np.where(free, 0.0, 0.5 * np.abs(a_s * ys))
+    c_s = a_s * ys + z_s
+    S = sp.csr_matrix((a_s, (rows_s, np.arange(k))), shape=(m, k))
+    top = sp.hstack([A, S])
+    bot = sp.hstack([B, sp.csr_matrix((src.shape[0], k))])
+    M = sp.vstack([top, bot]).tocsr()
+    M.sort_indices()
+    M.eliminate_zeros()
+    mm, nn = M.shape
+    x = np.concatenate([base.x_star, np.zeros(k)])
+    z = np.concatenate([base.z_star, z_s])
+    y = np.concatenate([base.y_star, np.zeros(src.shape[0])])
+    c = np.concatenate([base.c, c_s])
+    col_lo = np.concatenate([base.col_lo, np.where(free, -np.inf, 0.0)])
+    col_hi = np.concatenate([base.col_hi, np.full(k, np.inf)])
+    return PlantedLP(m=mm, n=nn, row_ptr=M.indptr.astype(np.int64),
+                     col_idx=M.indices.astype(np.int32), val=M.data.astype(np.float64), c=c,
+                     obj_offset=0.0, row_lo=np.concatenate([base.row_lo, blo]),
+                     row_hi=np.concatenate([base.row_hi, bhi]), col_lo=col_lo, col_hi=col_hi,
+                     x_star=x, y_star=y, z_star=z, p_star=float(c @ x),
+                     name=f"medium_{mm}x{nn}",
+                     meta={"parallel": int(src.shape[0]), "slack": int(k)})

@@ -13,10 +13,13 @@ re-examine only what the previous round touched (Sec. 3.2).
 Schedule (READING): each round runs the passes
     empty rows -> empty cols -> fixed cols -> singleton rows
     -> redundant rows / dominated sides -> doubleton equalities
-    -> free column singletons -> variable locks,
+    -> column singletons in inequality rows -> free column singletons
+    -> variable locks,
 each pass scanning its candidates in increasing index order.  Round 1 scans
 every row and column; later rounds scan the rows and columns marked dirty in
-the previous round.  Stop after a round with no reduction or after 20 rounds.
+the previous round.  A round in which these fast passes change nothing runs
+the medium explorer of Table 1 implemented here, parallel rows, over every
+row; the rounds stop when that finds nothing either, or after 20 rounds.
 
 Dirty marking: removing, adding or changing an entry (i, j) dirties row i and
 column j; changing row bounds dirties the row; changing column bounds dirties
@@ -35,6 +38,29 @@ so x_j is fixed there; with c_j > 0 and no down-lock, at its lower bound.  An
 infinite target bound makes the LP unbounded (if feasible).  The fixing uses
 the fixed-column reduction and its postsolve.
 
+Column singleton in an inequality row (Table 1, dual): x_j appears only in
+row i, with l_i < u_i.  Column j's dual constraint is a y_i = c_j - z_j with
+z_j >= 0 when only l_j is finite, z_j <= 0 when only u_j is finite and z_j = 0
+when x_j is free (a boxed x_j says nothing).  With q = c_j / a this bounds y_i
+from one side; when the bound is y_i >= q > 0 (or y_i = q > 0) every optimum
+has the row at its lower side, and with y_i <= q < 0 at its upper side, so the
+row becomes the equality a_i x = l_i (resp. u_i) when that side is finite.
+Postsolve: y_i keeps its value if it has the sign of the side it was fixed
+to, else it is set to 0 (an approximate solution of the reduced problem may
+put it slightly on the wrong side), with z updated over row i's entries so
+that c - A^T y - z = 0 still holds.
+
+Parallel rows (Table 1, medium): rows k and i with the same columns and
+a_k = s a_i.  Rows with two or more entries are grouped by column pattern; in
+increasing index, row k is compared with the earlier rows of its pattern that
+were not merged (at most 32 of them, READING) and merged into the first one
+parallel to it.  Parallel means |a_kj - s a_ij| <= 1e-12 |a_kj| for every
+column, with s = a_kf / a_if at the first column f (READING).  Row k's bounds,
+divided by s (swapped when s < 0), are intersected with row i's; row k is
+removed.  Postsolve: the merged row's y_i goes to row k as y_i / s when its
+sign points at a side that came strictly from row k, otherwise it stays with
+row i; the other row's y is 0.  Either way a_i y_i + a_k y_k is unchanged.
+
 Postsolve replays the records in reverse order and keeps eq. (2)'s dual
 feasibility c - A^T y - z = 0 of every intermediate problem:
   empty row / redundant row      y_i = 0
@@ -52,6 +78,9 @@ feasibility c - A^T y - z = 0 of every intermediate problem:
                                  else y_i = D_j / a_j, z_j = 0 (z_k unchanged)
   free column singleton          x_j = (b - sum_{r != j} a_ir x_r) / a_ij,
                                  y_i = c_j / a_ij, z_j = 0
+  inequality made equality       y_i of the wrong sign -> 0, z_r -= a_ir dy
+  parallel row k merged into i   y_k = y_i / s, y_i = 0 when y_i's sign
+                                 points at a side from row k; else y_k = 0
 
 Pins (tests/test_oracle_presolve.py): the worked examples of Sec. 2 (fixing a
 variable; the redundant row x1 >= 1, x2 >= 2, x1 + 2 x2 >= 5; the doubleton
@@ -69,6 +98,8 @@ import numpy as np
 
 FEAS_TOL = 1e-9
 DROP_TOL = 1e-12
+PAR_TOL = 1e-12
+PAR_CANDIDATES = 32
 MAX_ROUNDS = 20
 
 REDUCED, INFEASIBLE, UNBOUNDED, SOLVED = 0, 1, 2, 3
@@ -132,7 +163,8 @@ class Presolver:
         self.status = REDUCED
         self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
                                       "redundant_row", "dropped_side", "doubleton",
-                                      "free_col_singleton", "dual_fix")}
+                                      "free_col_singleton", "dual_fix", "ineq_to_eq",
+                                      "parallel_row")}
 
     # -- primitive edits with dirty marking --------------------------------
     def _mark_col_bounds(self, j):
@@ -404,6 +436,90 @@ class Presolver:
         self.counts["fixed_col"] -= 1
         self.counts["dual_fix"] += 1
 
+    def col_singleton_ineq(self, j):
+        (i, a), = self.cols[j].items()
+        lo, hi = self.lo[i], self.hi[i]
+        if lo == hi:
+            return
+        lf = not math.isinf(self.lx[j])
+        uf = not math.isinf(self.ux[j])
+        if lf and uf:
+            return
+        # a y_i = c_j - z_j with z_j >= 0 (only l_j finite), <= 0 (only u_j
+        # finite) or = 0 (free): the side of q = c_j / a that y_i must lie on
+        if lf:
+            y_ge_q, y_le_q = a < 0, a > 0
+        elif uf:
+            y_ge_q, y_le_q = a > 0, a < 0
+        else:
+            y_ge_q = y_le_q = True
+        q = self.c[j] / a
+        if y_ge_q and q > 0 and not math.isinf(lo):
+            side = 1
+            self.hi[i] = lo
+        elif y_le_q and q < 0 and not math.isinf(hi):
+            side = -1
+            self.lo[i] = hi
+        else:
+            return
+        self.records.append(("row_to_eq", i, side, sorted(self.rows[i].items())))
+        self.dirty_r.add(i)
+        self.counts["ineq_to_eq"] += 1
+        self.changed = True
+
+    def _parallel_scale(self, i, k):
+        """s with a_k = s a_i (to PAR_TOL), or None; same column pattern."""
+        ri, rk = self.rows[i], self.rows[k]
+        f = min(ri)
+        s = rk[f] / ri[f]
+        for j, a in ri.items():
+            if abs(rk[j] - s * a) > PAR_TOL * abs(rk[j]):
+                return None
+        return s
+
+    def merge_parallel(self, i, k, s):
+        lk, uk = self.lo[k], self.hi[k]
+        if s > 0:
+            nlk = -INF if math.isinf(lk) else lk / s
+            nuk = INF if math.isinf(uk) else uk / s
+        else:
+            nlk = -INF if math.isinf(uk) else uk / s
+            nuk = INF if math.isinf(lk) else lk / s
+        lo_from = nlk > self.lo[i]
+        hi_from = nuk < self.hi[i]
+        nl = nlk if lo_from else self.lo[i]
+        nu = nuk if hi_from else self.hi[i]
+        if nl > nu + FEAS_TOL:
+            self.status = INFEASIBLE
+            return
+        if nl > nu:
+            nl = nu = 0.5 * (nl + nu)
+        self.records.append(("parallel_row", i, k, s, lo_from, hi_from))
+        self._remove_row(k)
+        if nl != self.lo[i] or nu != self.hi[i]:
+            self.lo[i] = nl
+            self.hi[i] = nu
+            self.dirty_r.add(i)
+        self.counts["parallel_row"] += 1
+        self.changed = True
+
+    def parallel_rows(self):
+        reps = {}  # column pattern -> rows not merged, increasing index
+        for k in range(self.m):
+            if not self.row_on[k] or len(self.rows[k]) < 2:
+                continue
+            key = tuple(sorted(self.rows[k]))
+            lst = reps.setdefault(key, [])
+            for i in lst[:PAR_CANDIDATES]:
+                s = self._parallel_scale(i, k)
+                if s is not None:
+                    self.merge_parallel(i, k, s)
+                    if self.status != REDUCED:
+                        return
+                    break
+            else:
+                lst.append(k)
+
     # -- driver ----------------------------------------------------------------
     def run(self, max_rounds=MAX_ROUNDS):
         rows_c = list(range(self.m))
@@ -443,6 +559,9 @@ class Presolver:
                         return rounds
             for j in cols_c:
                 if self.col_on[j] and len(self.cols[j]) == 1:
+                    self.col_singleton_ineq(j)
+            for j in cols_c:
+                if self.col_on[j] and len(self.cols[j]) == 1:
                     self.free_col_singleton(j)
             for j in cols_c:
                 if self.col_on[j] and self.cols[j]:
@@ -450,7 +569,11 @@ class Presolver:
                     if self.status != REDUCED:
                         return rounds
             if not self.changed:
-                break
+                self.parallel_rows()
+                if self.status != REDUCED:
+                    return rounds
+                if not self.changed:
+                    break
             rows_c = sorted(i for i in self.dirty_r if self.row_on[i])
             cols_c = sorted(j for j in self.dirty_c if self.col_on[j])
         return rounds
@@ -537,6 +660,20 @@ def postsolve(res: PresolveResult, x_red, y_red, z_red=None):
             else:
                 y[i] = dj / aj
                 z[j] = 0.0
+        elif kind == "row_to_eq":
+            _, i, side, entries = rec
+            if (side > 0 and y[i] < 0) or (side < 0 and y[i] > 0):
+                d = -y[i]
+                y[i] = 0.0
+                for k, a in entries:
+                    z[k] -= a * d
+        elif kind == "parallel_row":
+            _, i, k, s, lo_from, hi_from = rec
+            if (y[i] > 0 and lo_from) or (y[i] < 0 and hi_from):
+                y[k] = y[i] / s
+                y[i] = 0.0
+            else:
+                y[k] = 0.0
         elif kind == "free_col_singleton":
             _, i, j, a, b, cj, others = rec
             s = b

@@ -11,6 +11,10 @@ from .capi import (  # noqa: F401
     LP_ENGINE_AUTO,
     LP_ENGINE_GRID,
     LP_ENGINE_CLUSTER,
+    LP_RULE_ALL,
+    LP_RULE_COL_SINGLETON_INEQ,
+    LP_RULE_PARALLEL_ROWS,
+    LP_RULE_VARIABLE_LOCKS,
     LP_OPTIMAL,
     LP_ITER_LIMIT,
     LP_TIME_LIMIT,

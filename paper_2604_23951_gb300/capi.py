@@ -22,6 +22,8 @@ LP_OPTIMAL, LP_ITER_LIMIT, LP_TIME_LIMIT, LP_NUMERICAL, LP_INFEASIBLE, LP_UNBOUN
     LP_CANCELLED = range(7)
 LP_FP64, LP_MIXED = 0, 1
 LP_ENGINE_AUTO, LP_ENGINE_GRID, LP_ENGINE_CLUSTER = 0, 1, 2
+LP_RULE_VARIABLE_LOCKS, LP_RULE_COL_SINGLETON_INEQ, LP_RULE_PARALLEL_ROWS = 128, 256, 512
+LP_RULE_ALL = 1023
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -246,7 +248,7 @@ class Problem:
                                    C.byref(n0)))
         return m.value, n.value, nnz.value
 
-    def presolve(self, max_rounds: int = 20, enable: int = 255) -> lp_presolve_info:
+    def presolve(self, max_rounds: int = 20, enable: int = LP_RULE_ALL) -> lp_presolve_info:
         o = lp_presolve_opts(max_rounds, enable)
         info = lp_presolve_info()
         check(self.lib.lp_presolve(self.h, C.byref(o), C.byref(info)))

@@ -6,11 +6,14 @@
 // Rules, schedule and postsolve formulas:
 //   round = empty rows -> empty cols -> fixed cols -> singleton rows ->
 //           redundant rows / dominated sides -> doubleton equalities ->
+//           column singletons in inequality rows (made equalities) ->
 //           free (or implied-free) column singletons in equality rows ->
 //           variable locks (weak dual fixing, Sec. 2.3);
 //   each pass scans candidates in increasing index order; round 1 scans
-//   everything, later rounds what the previous round dirtied; stop after a
-//   round without reductions or after max_rounds.
+//   everything, later rounds what the previous round dirtied.  A round in
+//   which these fast passes change nothing runs the medium explorer
+//   parallel rows over every row; stop when that finds nothing either, or
+//   after max_rounds.
 //   Infeasibility when a lower bound exceeds an upper one by more than 1e-9;
 //   coefficients below 1e-12 in magnitude after an update are dropped;
 //   activities sum a row's entries in increasing column order, compared with
@@ -32,6 +35,12 @@
 //                            otherwise y_i = D_j / a_j, z_j = 0
 //   free column singleton:   x_j = (b - sum_{r != j} a_ir x_r) / a_ij,
 //                            y_i = c_j / a_ij, z_j = 0
+//   inequality row i made an equality at one side:  a y_i of the other sign
+//                            is set to 0 and z_r -= a_ir * (0 - y_i) over the
+//                            row's entries at that time
+//   parallel row k (a_k = s a_i) merged into row i:  y_k = y_i / s, y_i = 0
+//                            when y_i's sign points at a side that came
+//                            strictly from row k; else y_k = 0
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -56,12 +65,19 @@ enum RecKind {
   REC_SINGLETON_ROW = 4,
   REC_DOUBLETON = 5,
   REC_FREE_COL = 6,
+  REC_ROW_TO_EQ = 7,
+  REC_PARALLEL_ROW = 8,
 };
 
 enum CountIdx {
   C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
-  C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX,
+  C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX, C_INEQ_TO_EQ, C_PARALLEL_ROW,
 };
+
+// Parallel rows: coefficients agree to this relative tolerance, and a row is
+// compared with at most this many earlier unmerged rows of its column pattern.
+constexpr double kParTol = 1e-12;
+constexpr int kParCandidates = 32;
 
 // Sorted sparse vectors in one pool, each with spare capacity.  A vector that
 // outgrows its capacity moves to the end of the pool with twice the room.
@@ -522,6 +538,135 @@ struct Presolver {
     changed = true;
   }
 
+  // Column singleton x_j in the inequality row i (Table 1, dual).  Column
+  // j's dual constraint a y_i = c_j - z_j, with z_j >= 0 (only l_j finite),
+  // <= 0 (only u_j finite) or = 0 (free), bounds y_i on one side of
+  // q = c_j / a; y_i >= q > 0 puts every optimum on the row's lower side,
+  // y_i <= q < 0 on its upper side, and the row becomes that equality.
+  void col_singleton_ineq(int32_t j) {
+    const int32_t i = cols.idx[cols.start[j]];
+    const double a = cols.val[cols.start[j]];
+    if (lo[i] == hi[i]) return;
+    const bool lf = !std::isinf(lx[j]), uf = !std::isinf(ux[j]);
+    if (lf && uf) return;
+    bool y_ge_q, y_le_q;
+    if (lf) { y_ge_q = a < 0; y_le_q = a > 0; }
+    else if (uf) { y_ge_q = a > 0; y_le_q = a < 0; }
+    else { y_ge_q = y_le_q = true; }
+    const double q = c[j] / a;
+    int side;
+    if (y_ge_q && q > 0 && !std::isinf(lo[i])) {
+      side = 1;
+      hi[i] = lo[i];
+    } else if (y_le_q && q < 0 && !std::isinf(hi[i])) {
+      side = -1;
+      lo[i] = hi[i];
+    } else {
+      return;
+    }
+    {
+      PostsolveRecord &r = push(REC_ROW_TO_EQ);
+      r.i = i;
+      r.flags = side > 0 ? 1 : 2;
+    }
+    const size_t ri = po->records.size() - 1;
+    const int64_t s = rows.start[i];
+    for (int32_t q2 = 0; q2 < rows.len[i]; ++q2)
+      push_entry(po->records[ri], rows.idx[s + q2], rows.val[s + q2]);
+    dirty_row(i);
+    po->counts[C_INEQ_TO_EQ]++;
+    changed = true;
+  }
+  bool same_pattern(int32_t i, int32_t k) const {
+    if (rows.len[i] != rows.len[k]) return false;
+    return std::memcmp(&rows.idx[rows.start[i]], &rows.idx[rows.start[k]],
+                       sizeof(int32_t) * rows.len[i]) == 0;
+  }
+  // s with a_k = s a_i to kParTol (same pattern), s taken at the first column
+  bool parallel_scale(int32_t i, int32_t k, double &s) const {
+    const double *vi = &rows.val[rows.start[i]];
+    const double *vk = &rows.val[rows.start[k]];
+    s = vk[0] / vi[0];
+    for (int32_t q = 0; q < rows.len[i]; ++q)
+      if (std::fabs(vk[q] - s * vi[q]) > kParTol * std::fabs(vk[q])) return false;
+    return true;
+  }
+  void merge_parallel(int32_t i, int32_t k, double s) {
+    const double lk = lo[k], uk = hi[k];
+    double nlk, nuk;
+    if (s > 0) {
+      nlk = std::isinf(lk) ? -kInf : lk / s;
+      nuk = std::isinf(uk) ? kInf : uk / s;
+    } else {
+      nlk = std::isinf(uk) ? -kInf : uk / s;
+      nuk = std::isinf(lk) ? kInf : lk / s;
+    }
+    const bool lo_from = nlk > lo[i];
+    const bool hi_from = nuk < hi[i];
+    double nl = lo_from ? nlk : lo[i];
+    double nu = hi_from ? nuk : hi[i];
+    if (nl > nu + kFeasTol) { status = LP_PRESOLVE_INFEASIBLE; return; }
+    if (nl > nu) nl = nu = 0.5 * (nl + nu);
+    PostsolveRecord &r = push(REC_PARALLEL_ROW);
+    r.i = i; r.k = k; r.a = s; r.flags = (lo_from ? 1 : 0) | (hi_from ? 2 : 0);
+    remove_row(k);
+    if (nl != lo[i] || nu != hi[i]) {
+      lo[i] = nl;
+      hi[i] = nu;
+      dirty_row(i);
+    }
+    po->counts[C_PARALLEL_ROW]++;
+    changed = true;
+  }
+  // Medium explorer (Table 1): rows grouped by a hash of their column
+  // pattern; within a hash group, in increasing index, a row is merged into
+  // the first of the first kParCandidates earlier unmerged rows of the same
+  // pattern that it is parallel to.  The test reads coefficients only, so
+  // all merges are found first and applied in increasing row order.
+  void parallel_rows() {
+    std::vector<std::pair<uint64_t, int32_t>> key;
+    for (int32_t i = 0; i < m; ++i) {
+      if (!row_on[i] || rows.len[i] < 2) continue;
+      uint64_t h = 1469598103934665603ull ^ (uint64_t)rows.len[i];
+      const int64_t s = rows.start[i];
+      for (int32_t q = 0; q < rows.len[i]; ++q) {
+        h ^= (uint64_t)(uint32_t)rows.idx[s + q];
+        h *= 1099511628211ull;
+      }
+      key.emplace_back(h, i);
+    }
+    std::sort(key.begin(), key.end());
+    struct Merge { int32_t k, i; double s; };
+    std::vector<Merge> merges;
+    std::vector<int32_t> reps;
+    for (size_t a = 0; a < key.size();) {
+      size_t b = a + 1;
+      while (b < key.size() && key[b].first == key[a].first) ++b;
+      if (b - a > 1) {
+        reps.clear();
+        for (size_t t = a; t < b; ++t) {
+          const int32_t k = key[t].second;
+          int found = -1, checked = 0;
+          double s = 0.0;
+          for (int32_t i : reps) {
+            if (!same_pattern(i, k)) continue;
+            if (checked++ >= kParCandidates) break;
+            if (parallel_scale(i, k, s)) { found = i; break; }
+          }
+          if (found >= 0) merges.push_back({k, found, s});
+          else reps.push_back(k);
+        }
+      }
+      a = b;
+    }
+    std::sort(merges.begin(), merges.end(),
+              [](const Merge &x, const Merge &y) { return x.k < y.k; });
+    for (const Merge &g : merges) {
+      merge_parallel(g.i, g.k, g.s);
+      if (status != LP_PRESOLVE_REDUCED) return;
+    }
+  }
+
   int run(int max_rounds, int mask) {
     std::vector<int32_t> rc(m), cc(n);
     for (int32_t i = 0; i < m; ++i) rc[i] = i;
@@ -585,6 +730,9 @@ struct Presolver {
             doubleton(i);
             if (status != LP_PRESOLVE_REDUCED) return rounds;
           }
+      if (mask & LP_RULE_COL_SINGLETON_INEQ)
+        for (int32_t j : cc)
+          if (col_on[j] && cols.len[j] == 1) col_singleton_ineq(j);
       if (mask & LP_RULE_FREE_COL_SINGLETON)
         for (int32_t j : cc)
           if (col_on[j] && cols.len[j] == 1) free_col_singleton(j);
@@ -594,7 +742,13 @@ struct Presolver {
             dual_fix(j);
             if (status != LP_PRESOLVE_REDUCED) return rounds;
           }
-      if (!changed) break;
+      if (!changed) {
+        if (mask & LP_RULE_PARALLEL_ROWS) {
+          parallel_rows();
+          if (status != LP_PRESOLVE_REDUCED) return rounds;
+        }
+        if (!changed) break;
+      }
       rc.clear();
       cc.clear();
       for (int32_t i : dlist_r) if (row_on[i]) rc.push_back(i);
@@ -714,6 +868,24 @@ void postsolve_run(const PresolveOutcome &po, const HostLP &red, const double *x
         } else {
           y[i] = dj / aj;
           z[j] = 0.0;
+        }
+        break;
+      }
+      case REC_ROW_TO_EQ: {
+        if (((r.flags & 1) && y[r.i] < 0) || ((r.flags & 2) && y[r.i] > 0)) {
+          const double d = -y[r.i];
+          y[r.i] = 0.0;
+          for (int64_t e = r.ent_begin; e < r.ent_end; ++e) z[po.ent_idx[e]] -= po.ent_val[e] * d;
+        }
+        break;
+      }
+      case REC_PARALLEL_ROW: {
+        const bool lo_from = r.flags & 1, hi_from = r.flags & 2;
+        if ((y[r.i] > 0 && lo_from) || (y[r.i] < 0 && hi_from)) {
+          y[r.k] = y[r.i] / r.a;
+          y[r.i] = 0.0;
+        } else {
+          y[r.k] = 0.0;
         }
         break;
       }

@@ -226,3 +226,137 @@ def test_variable_lock_respects_the_coefficient_sign():
     assert res.counts["dual_fix"] == 0
     k = oracle.rel_kkt(lp, x, y)
     assert k["rel_kkt"] <= 1e-12 and abs(k["p"] - 2.0) <= 1e-12
+
+
+# Column singleton x0 in the ranged row 1 <= a x0 + x1 + x2 <= 6, with
+# x1 - x2 in [-2, 2] and 0 <= x1, x2 <= 10; (a, c0, l0, u0, side) where side
+# is the row side every optimum sits at (+1 lower, -1 upper).
+_INEQ_CASES = [
+    (-1.0, -1.0, 0.0, INF, 1),    # only l finite, a < 0, c < 0: y >= q > 0
+    (1.0, -1.0, 0.0, INF, -1),    # only l finite, a > 0, c < 0: y <= q < 0
+    (2.0, 1.0, -INF, 5.0, 1),     # only u finite, a > 0, c > 0: y >= q > 0
+    (-2.0, 1.0, -INF, 5.0, -1),   # only u finite, a < 0, c > 0: y <= q < 0
+    (1.0, 2.0, -INF, INF, 1),     # free: y = q > 0
+    (1.0, -0.5, -INF, INF, -1),   # free: y = q < 0
+]
+
+
+def _ineq_lp(a, c0, l0, u0):
+    return SimpleLP([[a, 1.0, 1.0], [0.0, 1.0, -1.0]], [c0, 1.0, 0.5], [1.0, -2.0], [6.0, 2.0],
+                    [l0, 0.0, 0.0], [u0, 10.0, 10.0])
+
+
+@pytest.mark.parametrize("a,c0,l0,u0,side", _INEQ_CASES)
+def test_column_singleton_in_inequality_picks_the_active_side(a, c0, l0, u0, side):
+    lp = _ineq_lp(a, c0, l0, u0)
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["ineq_to_eq"] == 1
+    # every optimum has row 0 at that side: HiGHS's optimum on the original
+    # LP does, and its dual has the matching strict sign
+    p, xh, yh = highs_solve(lp)
+    act = a * xh[0] + xh[1] + xh[2]
+    assert abs(act - (1.0 if side > 0 else 6.0)) <= 1e-9
+    assert yh[0] * side > 0
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9
+    assert abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+    assert y[0] * side > 0
+
+
+def test_column_singleton_in_inequality_not_applied_without_a_sign():
+    # boxed x0, or a cost that does not push y away from 0: no conversion
+    for a, c0, l0, u0 in [(1.0, -1.0, 0.0, 3.0), (-1.0, 1.0, 0.0, INF), (1.0, 0.0, -INF, INF)]:
+        res = PS.presolve(_ineq_lp(a, c0, l0, u0))
+        assert res.counts["ineq_to_eq"] == 0
+
+
+def test_column_singleton_in_inequality_postsolve_clamps_a_wrong_signed_dual():
+    lp = _ineq_lp(-1.0, -1.0, 0.0, INF)
+    res = PS.presolve(lp)
+    assert res.counts["ineq_to_eq"] == 1 and 0 in list(res.row_map)
+    red = res.reduced
+    rng = np.random.default_rng(3)
+    xr = rng.uniform(0.0, 1.0, red.n)
+    yr = rng.normal(size=red.m)
+    yr[list(res.row_map).index(0)] = -0.25  # wrong sign for a lower side
+    x, y, z = PS.postsolve(res, xr, yr)
+    assert y[0] == 0.0
+    # dual feasibility c - A^T y - z = 0 survives the clamp
+    g = lp.c - lp.csr().T @ y
+    assert np.max(np.abs(g - z)) <= 1e-12
+
+
+def test_parallel_rows_worked_example():
+    # x0 + 2 x1 >= 1 and 2 x0 + 4 x1 <= 10 are one row 1 <= x0 + 2 x1 <= 5;
+    # -3 x0 - 6 x1 >= -12 tightens it to <= 4
+    A = [[1.0, 2.0, 0.0], [2.0, 4.0, 0.0], [-3.0, -6.0, 0.0], [1.0, 0.0, 1.0]]
+    lp = SimpleLP(A, [-1.0, -1.0, 1.0], [1.0, -INF, -12.0, 0.5], [INF, 10.0, INF, INF],
+                  [0.0, 0.0, 0.0], [INF, INF, INF])
+    res = PS.presolve(lp)
+    assert res.counts["parallel_row"] == 2
+    par = [r for r in res.records if r[0] == "parallel_row"]
+    # (kept row, merged row, s, lower side from the merged row, upper side from it)
+    assert par == [("parallel_row", 0, 1, 2.0, False, True),
+                   ("parallel_row", 0, 2, -3.0, False, True)]
+    _, x, y, z = solve_via_presolve(lp)
+    p, _, _ = highs_solve(lp)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9 and abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+    # the active side x0 + 2 x1 <= 4 came from row 2 (s = -3): its dual is
+    # y_0 / s >= 0 there, rows 0 and 1 carry none
+    assert y[1] == 0.0 and y[0] == 0.0 and y[2] > 0
+
+
+def test_parallel_rows_infeasible():
+    lp = SimpleLP([[1.0, 1.0], [2.0, 2.0]], [1.0, 1.0], [5.0, -INF], [INF, 4.0],
+                  [0.0, 0.0], [INF, INF])
+    assert PS.presolve(lp).status == PS.INFEASIBLE
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_parallel_rows_planted_copies(seed):
+    # copies of random rows scaled by s (either sign), some with bounds that
+    # cut the optimum, and near-parallel copies (1e-6 off) that must stay
+    base = lpgen.general_structure(120, 300, seed, nnz_target=1500, one_sided=0.3)
+    A = base.csr().toarray()
+    lo, hi = base.row_lo.copy(), base.row_hi.copy()
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(base.m, 30, replace=False)
+    extra_A, extra_lo, extra_hi = [], [], []
+    for t, i in enumerate(rows):
+        s = rng.choice([-3.0, -0.5, 0.25, 2.0, 7.0])
+        a = s * A[i]
+        act = A[i] @ base.x_star
+        l, h = act - rng.uniform(0.0, 2.0), act + rng.uniform(0.0, 2.0)
+        if t % 3 == 2:
+            a = a * (1.0 + 1e-6 * (np.arange(base.n) % 2))
+        if s > 0:
+            extra_lo.append(s * l)
+            extra_hi.append(s * h if t % 2 else INF)
+        else:
+            extra_lo.append(s * h if t % 2 else -INF)
+            extra_hi.append(s * l)
+        extra_A.append(a)
+    lp = SimpleLP(np.vstack([A, extra_A]), base.c, np.concatenate([lo, extra_lo]),
+                  np.concatenate([hi, extra_hi]), base.col_lo, base.col_hi)
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["parallel_row"] >= 15
+    p, _, _ = highs_solve(lp)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8
+    assert abs(k["p"] - p) <= 1e-8 * (1 + abs(p))
+    g = lp.c - lp.csr().T @ y
+    assert np.max(np.abs(g - z)) <= 1e-8 * (1 + np.max(np.abs(lp.c)))
+
+
+@pytest.mark.parametrize("seed", [13, 14])
+def test_medium_structure_keeps_the_planted_optimum(seed):
+    # planted parallel copies and slack column singletons: both explorers
+    # fire, and postsolve of the exact reduced solution is optimal
+    lp = lpgen.medium_structure(600, 1500, seed, nnz_target=9000)
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.counts["parallel_row"] >= lp.meta["parallel"] // 2
+    assert res.counts["ineq_to_eq"] >= lp.meta["slack"] // 2
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))

@@ -34,8 +34,36 @@ def _one_sided_rows(seed=11, m=40, n=90):
                     np.zeros(n), rng.uniform(1.0, 3.0, n))
 
 
+def _parallel_example():
+    A = [[1.0, 2.0, 0.0], [2.0, 4.0, 0.0], [-3.0, -6.0, 0.0], [1.0, 0.0, 1.0]]
+    return SimpleLP(A, [-1.0, -1.0, 1.0], [1.0, -INF, -12.0, 0.5], [INF, 10.0, INF, INF],
+                    [0.0, 0.0, 0.0], [INF, INF, INF])
+
+
+def _ineq_singletons():
+    # column singletons in inequality rows with every sign combination, one
+    # block of two rows and three columns each
+    blocks = [(-1.0, -1.0, 0.0, INF), (1.0, -1.0, 0.0, INF), (2.0, 1.0, -INF, 5.0),
+              (-2.0, 1.0, -INF, 5.0), (1.0, 2.0, -INF, INF), (1.0, -0.5, -INF, INF)]
+    k = len(blocks)
+    A = np.zeros((2 * k, 3 * k))
+    c = np.zeros(3 * k)
+    lo, hi = np.zeros(2 * k), np.zeros(2 * k)
+    lx, ux = np.zeros(3 * k), np.zeros(3 * k)
+    for t, (a, c0, l0, u0) in enumerate(blocks):
+        A[2 * t, 3 * t:3 * t + 3] = [a, 1.0, 1.0]
+        A[2 * t + 1, 3 * t + 1:3 * t + 3] = [1.0, -1.0]
+        c[3 * t:3 * t + 3] = [c0, 1.0, 0.5]
+        lo[2 * t:2 * t + 2] = [1.0, -2.0]
+        hi[2 * t:2 * t + 2] = [6.0, 2.0]
+        lx[3 * t:3 * t + 3] = [l0, 0.0, 0.0]
+        ux[3 * t:3 * t + 3] = [u0, 10.0, 10.0]
+    return SimpleLP(A, c, lo, hi, lx, ux)
+
+
 def _cases():
     return [
+        ("medium", lambda: lpgen.medium_structure(600, 1500, 13, nnz_target=9000)),
         ("variable_locks", _one_sided_rows),
         ("general_small", lambda: lpgen.general_structure(600, 1500, 31, nnz_target=9000,
                                                           one_sided=0.2)),
@@ -48,6 +76,10 @@ def _cases():
              [1.0, 0.0, 1.0, 1.0]],
             [1.0, 2.0, -1.0, 0.5], [1.0, 0.0, 2.0, -INF], [1.0, 0.0, 2.0, 6.0],
             [0.0, 0.0, -1.0, 0.0], [INF, 5.0, 4.0, INF])),
+        ("parallel_example", _parallel_example),
+        ("ineq_singletons", _ineq_singletons),
+        ("medium_b", lambda: lpgen.medium_structure(900, 2000, 29, nnz_target=15000,
+                                                    frac_parallel=0.2, frac_slack=0.1)),
     ]
 
 
@@ -65,7 +97,8 @@ def test_reduced_problem_identical(name, make):
     assert info.rounds == ref.rounds
     assert list(info.counts) == [ref.counts[k] for k in (
         "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
-        "dropped_side", "doubleton", "free_col_singleton", "dual_fix")] + [0, 0, 0]
+        "dropped_side", "doubleton", "free_col_singleton", "dual_fix", "ineq_to_eq",
+        "parallel_row")] + [0]
     np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
     np.testing.assert_array_equal(red.col_idx, r.col_idx)
     np.testing.assert_array_equal(red.val, r.val)
@@ -143,3 +176,31 @@ def test_solve_without_device_is_state_error():
     with pytest.raises(pkg.LPError) as ei:
         prob.solve()
     assert ei.value.code == -4
+
+
+@pytest.mark.parametrize("name,make", [c for c in _cases() if c[0] in
+                                       ("medium", "medium_b", "ineq_singletons")])
+def test_postsolve_matches_oracle_on_perturbed_solutions(name, make):
+    # an approximate reduced solution (exact + noise) takes the branches an
+    # exact one does not: wrong-signed duals of rows made equalities,
+    # merged-row duals of either sign
+    _lib_or_skip()
+    lp = make()
+    ref = PS.presolve(lp)
+    prob = pkg.Problem(lp, None)
+    prob.presolve()
+    red = ref.reduced
+    _, xr, yr = highs_solve(red)
+    rng = np.random.default_rng(7)
+    for scale in (1e-6, 1e-2, 1.0):
+        xp = xr + scale * rng.standard_normal(red.n)
+        yp = yr + scale * rng.standard_normal(red.m)
+        xo, yo, zo = PS.postsolve(ref, xp, yp)
+        xc, yc, zc = prob.postsolve_from(xp, yp)
+        tol = 1e-12 * (1 + max(np.max(np.abs(xo)), np.max(np.abs(yo)), np.max(np.abs(zo))))
+        assert np.max(np.abs(xc - xo)) <= tol
+        assert np.max(np.abs(yc - yo)) <= tol
+        assert np.max(np.abs(zc - zo)) <= tol
+        # dual feasibility c - A^T y - z = 0 holds for any reduced solution
+        g = lp.c - lp.csr().T @ yc
+        assert np.max(np.abs(g - zc)) <= 1e-9 * (1 + np.max(np.abs(lp.c)))
