@@ -27,7 +27,11 @@ the column and every row holding it; changing c_j dirties column j.
 
 Tolerances (READING): infeasibility is declared when a lower bound exceeds an
 upper bound by more than 1e-9; coefficients below 1e-12 in magnitude after an
-update are dropped.  Activity sums run over a row's entries in increasing
+update are dropped; the rules that read the sign of a cost (empty columns,
+variable locks, column singletons in inequality rows) take a cost of
+magnitude at most 1e-12 * max(1, max_j |c_j| of the input LP) as zero, since
+substitutions leave rounding residue (a structurally zero cost of -1e-16
+would otherwise "prove" an unbounded LP).  Activity sums run over a row's entries in increasing
 column order; comparisons of activities with row bounds are exact.
 
 Variable locks (Sec. 2.3, weak dual exploration): a row i holding x_j
@@ -98,6 +102,7 @@ import numpy as np
 
 FEAS_TOL = 1e-9
 DROP_TOL = 1e-12
+COST_TOL = 1e-12
 PAR_TOL = 1e-12
 PAR_CANDIDATES = 32
 MAX_ROUNDS = 20
@@ -149,6 +154,7 @@ class Presolver:
                     self.rows[i][j] = v
                     self.cols[j][i] = v
         self.c = [float(v) for v in lp.c]
+        self.cost_tol = COST_TOL * max([1.0] + [abs(v) for v in self.c])
         self.off = float(lp.obj_offset)
         self.lo = [float(v) for v in lp.row_lo]
         self.hi = [float(v) for v in lp.row_hi]
@@ -234,9 +240,9 @@ class Presolver:
 
     def empty_col(self, j):
         cj = self.c[j]
-        if cj > 0:
+        if cj > self.cost_tol:
             v = self.lx[j]
-        elif cj < 0:
+        elif cj < -self.cost_tol:
             v = self.ux[j]
         else:
             v = min(max(0.0, self.lx[j]), self.ux[j])
@@ -418,7 +424,7 @@ class Presolver:
 
     def dual_fix(self, j):
         cj = self.c[j]
-        if cj == 0.0:
+        if abs(cj) <= self.cost_tol:
             return
         up, down = self.locks(j)
         if cj < 0 and not up:
@@ -443,7 +449,7 @@ class Presolver:
             return
         lf = not math.isinf(self.lx[j])
         uf = not math.isinf(self.ux[j])
-        if lf and uf:
+        if (lf and uf) or abs(self.c[j]) <= self.cost_tol:
             return
         # a y_i = c_j - z_j with z_j >= 0 (only l_j finite), <= 0 (only u_j
         # finite) or = 0 (free): the side of q = c_j / a that y_i must lie on

@@ -15,7 +15,10 @@
 //   parallel rows over every row; stop when that finds nothing either, or
 //   after max_rounds.
 //   Infeasibility when a lower bound exceeds an upper one by more than 1e-9;
-//   coefficients below 1e-12 in magnitude after an update are dropped;
+//   coefficients below 1e-12 in magnitude after an update are dropped; the
+//   rules that read a cost's sign (empty columns, variable locks, column
+//   singletons in inequality rows) take |c_j| <= 1e-12 * max(1, max |c| of
+//   the input) as zero, since substitutions leave rounding residue in c;
 //   activities sum a row's entries in increasing column order, compared with
 //   the row bounds exactly.  Arithmetic is plain IEEE double (the library is
 //   built with -ffp-contract=off), so the decisions are reproducible.
@@ -55,6 +58,7 @@ namespace {
 
 constexpr double kFeasTol = 1e-9;
 constexpr double kDropTol = 1e-12;
+constexpr double kCostTol = 1e-12;
 constexpr double kInf = std::numeric_limits<double>::infinity();
 
 enum RecKind {
@@ -166,6 +170,7 @@ struct Presolver {
   SlackStore rows, cols;
   std::vector<double> c, lo, hi, lx, ux;
   double off;
+  double cost_tol = kCostTol;
   std::vector<uint8_t> row_on, col_on;
   std::vector<uint8_t> dmark_r, dmark_c;
   std::vector<int32_t> dlist_r, dlist_c;
@@ -209,6 +214,11 @@ struct Presolver {
     }
     col_builder.join();
     c = in.c;
+    {
+      double cmax = 1.0;
+      for (double v : c) cmax = std::max(cmax, std::fabs(v));
+      cost_tol = kCostTol * cmax;
+    }
     off = in.off;
     lo = in.row_lo;
     hi = in.row_hi;
@@ -300,8 +310,8 @@ struct Presolver {
   }
   void empty_col(int32_t j) {
     double cj = c[j], v;
-    if (cj > 0) v = lx[j];
-    else if (cj < 0) v = ux[j];
+    if (cj > cost_tol) v = lx[j];
+    else if (cj < -cost_tol) v = ux[j];
     else v = std::min(std::max(0.0, lx[j]), ux[j]);
     if (std::isinf(v)) { status = LP_PRESOLVE_UNBOUNDED; return; }
     off += cj * v;
@@ -481,7 +491,7 @@ struct Presolver {
   // bound; the fixed-column reduction does the rest
   void dual_fix(int32_t j) {
     const double cj = c[j];
-    if (cj == 0.0) return;
+    if (std::fabs(cj) <= cost_tol) return;
     bool up, down;
     locks(j, up, down);
     double v;
@@ -548,7 +558,7 @@ struct Presolver {
     const double a = cols.val[cols.start[j]];
     if (lo[i] == hi[i]) return;
     const bool lf = !std::isinf(lx[j]), uf = !std::isinf(ux[j]);
-    if (lf && uf) return;
+    if ((lf && uf) || std::fabs(c[j]) <= cost_tol) return;
     bool y_ge_q, y_le_q;
     if (lf) { y_ge_q = a < 0; y_le_q = a > 0; }
     else if (uf) { y_ge_q = a > 0; y_le_q = a < 0; }

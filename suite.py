@@ -124,7 +124,10 @@ def run_instance(pkg, dev, lp, eps: float, time_limit: float, precision: int) ->
     info = p.presolve()
     t_pre = time.perf_counter() - t1
     m2, n2, nnz2 = p.dims()
-    if m2 > 0 or n2 > 0:
+    decided = info.status in (1, 2)  # presolve proved infeasible / unbounded
+    if decided:
+        ok_on, iters_on = False, 0
+    elif m2 > 0 or n2 > 0:
         r = p.solve(eps_rel=eps, time_limit_s=time_limit, precision=precision)
         ok_on = bool(r.termination == pkg.LP_OPTIMAL)
         iters_on = int(r.iterations)
@@ -133,12 +136,15 @@ def run_instance(pkg, dev, lp, eps: float, time_limit: float, precision: int) ->
     torch.cuda.synchronize()
     t_on = time.perf_counter() - t0
     t2 = time.perf_counter()
-    x, y, _ = p.postsolve()
+    kkt_on = float("inf")
+    if not decided:
+        x, y, _ = p.postsolve()
+        kkt_on = _kkt_original(pkg, lp, x, y)
     t_post = time.perf_counter() - t2
     p.close()
     rec.update(t_on=t_on, t_presolve=t_pre, t_reduced_solve=t_on - t_pre, t_postsolve=t_post,
-               ok_on=ok_on, iters_on=iters_on, nnz_reduced=int(nnz2),
-               kkt_on=_kkt_original(pkg, lp, x, y))
+               ok_on=ok_on, iters_on=iters_on, nnz_reduced=int(nnz2), presolve_status=info.status,
+               kkt_on=kkt_on)
     rec["ok_off"] = rec["ok_off"] and rec["kkt_off"] <= eps
     rec["ok_on"] = rec["ok_on"] and rec["kkt_on"] <= eps
     return rec
@@ -200,7 +206,7 @@ def main(argv=None) -> int:
         rec.update(target_class=cls, size_class=size_class(rec["nnz"]), seed=seed,
                    t_generate=t_gen)
         recs.append(rec)
-        print(json.dumps({k: (round(v, 4) if isinstance(v, float) else v)
+        print(json.dumps({k: (round(v, 4) if isinstance(v, float) and k.startswith("t_") else v)
                           for k, v in rec.items()}), flush=True)
         del lp
     out = {"eps_rel": args.eps, "time_limit_s": args.time_limit, "precision": args.precision,

@@ -360,3 +360,31 @@ def test_medium_structure_keeps_the_planted_optimum(seed):
     k = oracle.rel_kkt(lp, x, y)
     assert k["rel_kkt"] <= 1e-8
     assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+
+
+def test_rounding_residue_in_a_cost_is_not_a_sign():
+    # a cost of -1e-16 (what substitutions leave of a structurally zero cost)
+    # must neither fix x0 at its infinite upper bound ("unbounded") nor make
+    # row 0 an equality; the LP is bounded with optimum 1 at x = (0, 1) or any
+    # point with x0 + x1 >= 1, x1 >= 1
+    lp = SimpleLP([[1.0, 1.0], [0.0, 1.0]], [-1e-16, 1.0], [1.0, 1.0], [INF, INF],
+                  [0.0, 0.0], [INF, INF])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.status in (PS.REDUCED, PS.SOLVED)
+    assert res.counts["dual_fix"] == 0 and res.counts["ineq_to_eq"] == 0
+    assert abs(float(lp.c @ x) - 1.0) <= 1e-12
+    # an empty column with such a cost sits at proj(0), not at an infinite bound
+    lp = SimpleLP([[0.0, 1.0]], [-1e-17, 1.0], [1.0], [INF], [0.0, 0.0], [INF, INF])
+    res, x, y, z = solve_via_presolve(lp)
+    assert res.status == PS.SOLVED and res.counts["empty_col"] == 2
+    assert x[0] == 0.0 and x[1] == 1.0
+
+
+def test_medium_instance_that_met_cost_residue_stays_bounded():
+    # the instance on which a -1.1e-16 cost left by free-column-singleton
+    # substitutions was once taken for a sign; its planted optimum is finite
+    import suite
+
+    lp = suite.make_instance(300000, 2010)
+    res = PS.presolve(lp)
+    assert res.status == PS.REDUCED
