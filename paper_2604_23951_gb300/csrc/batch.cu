@@ -74,7 +74,7 @@ struct SlotDesc {
   const double *a_v0, *t_v0;
   double *a_v, *t_v;
   float *a_vf, *t_vf;
-  const double *c0, *lx0, *ux0, *lc0, *uc0;
+  const double *c0, *lx0, *ux0, *lc0, *uc0, *pv0;
   double *c, *lx, *ux, *lc, *uc;
   double *dr, *dc, *dr2, *dc2, *idr, *idc;
   double *x, *x0, *xbar, *xhat, *y, *y0, *yhat;
@@ -283,8 +283,8 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
   if (!(eta > 0.0)) {
     double pw = 0.0;
     if (m > 0 && n > 0) {
-      const double v0 = 1.0 / sqrt((double)n);
       for (int j = gt; j < n; j += gs) {
+        const double v0 = D.pv0[j];
         if (MIXED) D.pwf[j] = (float)v0; else D.xhat[j] = v0;
       }
       cl.sync();
@@ -700,7 +700,7 @@ static void pack_request(const HostLP &h, Packed &p) {
   size_t o_av0 = take(8 * nzA), o_tv0 = take(8 * nzT), o_av = take(8 * nzA), o_tv = take(8 * nzT);
   size_t o_avf = take(4 * nzA), o_tvf = take(4 * nzT);
   size_t o_c0 = take(8 * n), o_lx0 = take(8 * n), o_ux0 = take(8 * n);
-  size_t o_lc0 = take(8 * m), o_uc0 = take(8 * m);
+  size_t o_lc0 = take(8 * m), o_uc0 = take(8 * m), o_pv0 = take(8 * n);
   r.m = m;
   r.n = n;
   r.nnz = nnz;
@@ -725,6 +725,7 @@ static void pack_request(const HostLP &h, Packed &p) {
   r.ux0 = (const double *)P(o_ux0);
   r.lc0 = (const double *)P(o_lc0);
   r.uc0 = (const double *)P(o_uc0);
+  r.pv0 = (const double *)P(o_pv0);
   const size_t input_end = cur;
   double **colv[] = {&r.c, &r.lx, &r.ux, &r.dc, &r.dc2, &r.idc, &r.x, &r.x0, &r.xbar, &r.xhat,
                      &r.xout, &r.zout};
@@ -754,6 +755,7 @@ static void pack_request(const HostLP &h, Packed &p) {
   put(o_ux0, L.ux0.data(), 8 * n);
   put(o_lc0, L.lc0.data(), 8 * m);
   put(o_uc0, L.uc0.data(), 8 * m);
+  put(o_pv0, L.pv0.data(), 8 * n);
   p.bnorm = L.bnorm;
   p.cnorm = L.cnorm;
   p.off = L.off;
@@ -783,6 +785,7 @@ static SlotDesc relocate(const SlotDesc &rel, unsigned char *base) {
   d.ux0 = R(rel.ux0);
   d.lc0 = R(rel.lc0);
   d.uc0 = R(rel.uc0);
+  d.pv0 = R(rel.pv0);
   d.c = R(rel.c);
   d.lx = R(rel.lx);
   d.ux = R(rel.ux);

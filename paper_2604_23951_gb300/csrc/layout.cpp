@@ -104,13 +104,16 @@ void build_layout(const HostLP &h, Layout &L) {
   L.c0.resize(n);
   L.lx0.resize(n);
   L.ux0.resize(n);
+  L.pv0.resize(n);
   L.lc0.resize(m);
   L.uc0.resize(m);
+  const double inv_sqrt_n = n > 0 ? 1.0 / std::sqrt((double)n) : 0.0;
   for (int j = 0; j < n; ++j) {
     int o = L.cperm[j];
     L.c0[j] = h.c[o];
     L.lx0[j] = h.col_lo[o];
     L.ux0[j] = h.col_hi[o];
+    L.pv0[j] = power_start(o, inv_sqrt_n);
   }
   for (int i = 0; i < m; ++i) {
     int o = L.rperm[i];

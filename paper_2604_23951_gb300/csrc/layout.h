@@ -15,6 +15,23 @@ namespace gb300lp {
 
 constexpr int kTilePad = 8;  // value / index arrays padded past nnz
 
+#if defined(__CUDACC__)
+#define GB300LP_HD __host__ __device__
+#else
+#define GB300LP_HD
+#endif
+
+// Start vector of the power iteration for ||A||_2, entry of original column
+// j: (0.5 + h(j) / 2^32) / sqrt(n) with the multiplicative hash
+// h(j) = j * 2654435761 mod 2^32 -- a fixed vector in no special direction
+// (an all-ones start is orthogonal to the top singular vector whenever the
+// rows of A sum to zero, e.g. A = [1, -1]).  Indexed by the ORIGINAL column,
+// so every storage order starts from the same vector.
+GB300LP_HD inline double power_start(int j, double inv_sqrt_n) {
+  const unsigned h = (unsigned)j * 2654435761u;
+  return (0.5 + (double)h * (1.0 / 4294967296.0)) * inv_sqrt_n;
+}
+
 struct Layout {
   int m = 0, n = 0;
   long long nnz = 0;
@@ -24,6 +41,7 @@ struct Layout {
   std::vector<int2> tA, tT;  // warp tiles
   int nlongA = 0, nlongT = 0;
   std::vector<double> c0, lx0, ux0, lc0, uc0;  // permuted problem vectors
+  std::vector<double> pv0;  // power-iteration start (power_start of cperm)
   double bnorm = 0, cnorm = 0, off = 0;
 };
 

@@ -452,7 +452,7 @@ struct DeviceLP {
   double *idr = nullptr, *idc = nullptr;
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
-  double *pv = nullptr, *pw = nullptr, *pu = nullptr;
+  double *pv = nullptr, *pv0 = nullptr, *pw = nullptr, *pu = nullptr;
   double *ox = nullptr, *oy = nullptr, *oxi = nullptr, *oyi = nullptr;
   float *xbar_f = nullptr, *yf = nullptr;
   double *partials = nullptr;
@@ -595,7 +595,7 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     d->tilesT = d->dalloc_n<int2>(std::max<size_t>(tT.size(), 1));
     double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
                         &d->idc, &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv,
-                        &d->pw, &d->ox, &d->oxi};
+                        &d->pv0, &d->pw, &d->ox, &d->oxi};
     for (double **p : cols_) *p = d->dalloc_n<double>(n);
     double **rows_[] = {&d->lc0, &d->uc0, &d->lc, &d->uc, &d->dr, &d->dr2, &d->idr, &d->y,
                         &d->y0, &d->yhat, &d->pu, &d->oy, &d->oyi};
@@ -626,6 +626,7 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     CK(cudaMemcpyAsync(d->c0, L.c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lx0, L.lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->ux0, L.ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemcpyAsync(d->pv0, L.pv0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lc0, L.lc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->uc0, L.uc0.data(), sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
     // the padding of the scaled copies is never used by the arithmetic, but
@@ -788,8 +789,7 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
   d->launches += 6;
   bool power = !(o.step_size > 0) && n > 0 && m > 0;
   if (power) {
-    k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
-    d->launches += 1;
+    CK(cudaMemcpyAsync(d->pv, d->pv0, sizeof(double) * n, cudaMemcpyDeviceToDevice, d->s));
     const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     for (int it = 0; it < o.power_iters; ++it) {
       k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());

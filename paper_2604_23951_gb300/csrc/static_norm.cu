@@ -17,6 +17,7 @@
 #include <mutex>
 #include <string>
 
+#include "layout.h"
 #include "lp_internal.h"
 
 namespace gb300lp {
@@ -92,8 +93,9 @@ __global__ void k_sn_normalize(int n, const double *__restrict__ w, double *__re
     v[j] = nw > 0.0 ? w[j] / nw : 0.0;
 }
 
-__global__ void k_sn_fill(int n, double *v, double val) {
-  for (int j = blockIdx.x * kSnBlock + threadIdx.x; j < n; j += gridDim.x * kSnBlock) v[j] = val;
+__global__ void k_sn_fill(int n, double *v, double inv_sqrt_n) {
+  for (int j = blockIdx.x * kSnBlock + threadIdx.x; j < n; j += gridDim.x * kSnBlock)
+    v[j] = gb300lp::power_start(j, inv_sqrt_n);
 }
 
 __global__ void k_sn_final(const double *partials, int nparts, double *result) {

@@ -213,3 +213,18 @@ def test_engines_agree_on_iterates(pkg, dev):
     assert ra.restarts == rb.restarts
     assert relerr(ia[0], ib[0]) <= 1e-9 and relerr(ia[1], ib[1]) <= 1e-9
     assert relerr(sa[0], sb[0]) <= 1e-9 and relerr(sa[1], sb[1]) <= 1e-9
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_rows_summing_to_zero_get_a_real_step(pkg, dev, engine):
+    # A = [1, -1] (A 1 = 0): the step size comes from ||A~|| = sqrt(2) a, as in
+    # the oracle, and the LP min x1 + x2, x1 - x2 = 0.5, 0 <= x <= 10 solves
+    lp = SimpleLP([[1.0, -1.0]], [1.0, 1.0], [0.5], [0.5], [0.0, 0.0], [10.0, 10.0])
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=1, eps_rel=0.0))
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(max_iter=1, eps_rel=0.0, engine=engine)
+    assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(engine=engine)
+    assert r.termination == pkg.LP_OPTIMAL
+    assert abs(r.primal_obj - 0.5) <= 1e-5

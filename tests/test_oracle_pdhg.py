@@ -286,3 +286,16 @@ def test_scaling_closed_form_one_row():
     assert abs(dr[0] - (1 / s3) / math.sqrt(1 + 1 / s3)) <= 1e-15
     assert abs(dc[0] - 3.0 ** 0.25) <= 1e-15
     assert abs(dc[1] - 1 / s3) <= 1e-15
+
+
+def test_power_norm_of_rows_summing_to_zero():
+    # A = [1, -1] has A 1 = 0: an all-ones start would stall at 0; the hashed
+    # start finds ||A|| = sqrt(2) (and a graph incidence matrix its norm)
+    assert abs(P.power_norm(sp.csr_matrix(np.array([[1.0, -1.0]])), 100) - np.sqrt(2.0)) <= 1e-14
+    # incidence matrix of a directed cycle: every row sums to zero
+    k = 7
+    M = np.zeros((k, k))
+    for e in range(k):
+        M[e, e], M[(e + 1) % k, e] = 1.0, -1.0
+    est = P.power_norm(sp.csr_matrix(M), 200)
+    assert abs(est - np.linalg.norm(M, 2)) <= 1e-9
