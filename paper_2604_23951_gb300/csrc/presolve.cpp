@@ -101,6 +101,11 @@ struct SlackStore {
       cap[r] = lens[r] + 2 + lens[r] / 4;
       total += cap[r];
     }
+    // room for vectors that outgrow their slack to move to the end without
+    // reallocating (and copying) the whole pool; reserved pages cost nothing
+    // until they are used
+    idx.reserve(total + total / 4 + 4096);
+    val.reserve(total + total / 4 + 4096);
     idx.assign(total, 0);
     val.assign(total, 0.0);
   }
@@ -173,6 +178,7 @@ struct Presolver {
   double cost_tol = kCostTol;
   std::vector<uint8_t> row_on, col_on;
   std::vector<uint8_t> dmark_r, dmark_c;
+  std::vector<uint8_t> fixmark, rmark;  // scratch of the batched fixed-column pass
   std::vector<int32_t> dlist_r, dlist_c;
   bool changed = false;
   int32_t status = LP_PRESOLVE_REDUCED;
@@ -188,20 +194,31 @@ struct Presolver {
         if (in.val[k] != 0.0) { ++cnt; ++cl[in.col_idx[k]]; }
       rl[i] = cnt;
     }
-    // input rows are sorted by column and rows arrive in order, so both
-    // stores fill by appends; the column store is built on a second thread
-    std::thread col_builder([&]() {
-      cols.init(n, cl);
+    // Input rows are sorted by column and rows arrive in order, so both
+    // stores fill by appends.  The column store is a scatter: it is built
+    // by several threads, each owning a contiguous range of columns and
+    // scanning all rows for the entries of its range (every column still
+    // receives its entries in row order), while this thread fills the rows.
+    cols.init(n, cl);
+    const int64_t nnz_in = in.row_ptr.empty() ? 0 : in.row_ptr.back();
+    const unsigned ncb =
+        nnz_in >= 1000000 ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
+    auto fill_cols = [&](int32_t j0, int32_t j1) {
       for (int32_t i = 0; i < m; ++i)
         for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
+          const int32_t j = in.col_idx[k];
+          if (j < j0 || j >= j1) continue;
           const double v = in.val[k];
           if (v == 0.0) continue;
-          const int32_t j = in.col_idx[k];
           cols.idx[cols.start[j] + cols.len[j]] = i;
           cols.val[cols.start[j] + cols.len[j]] = v;
           ++cols.len[j];
         }
-    });
+    };
+    std::vector<std::thread> col_builders;
+    for (unsigned t = 0; t < ncb; ++t)
+      col_builders.emplace_back(fill_cols, (int32_t)((int64_t)n * t / ncb),
+                                (int32_t)((int64_t)n * (t + 1) / ncb));
     rows.init(m, rl);
     for (int32_t i = 0; i < m; ++i) {
       for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
@@ -212,7 +229,7 @@ struct Presolver {
         ++rows.len[i];
       }
     }
-    col_builder.join();
+    for (std::thread &th : col_builders) th.join();
     c = in.c;
     {
       double cmax = 1.0;
@@ -228,6 +245,24 @@ struct Presolver {
     col_on.assign(n, 1);
     dmark_r.assign(m, 0);
     dmark_c.assign(n, 0);
+    fixmark.assign(n, 0);
+    rmark.assign(m, 0);
+  }
+
+  // Run f(lo, hi) over [0, count) on up to 16 threads when count >= min_par
+  // (contiguous chunks; f must touch disjoint data per index).
+  template <class F>
+  static void parallel_for(size_t count, size_t min_par, F f) {
+    const unsigned nt = count >= min_par
+        ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
+    if (nt <= 1) {
+      f((size_t)0, count);
+      return;
+    }
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t)
+      pool.emplace_back(f, count * t / nt, count * (t + 1) / nt);
+    for (std::thread &th : pool) th.join();
   }
 
   void dirty_row(int32_t i) {
@@ -340,6 +375,70 @@ struct Presolver {
     remove_col(j);
     po->counts[C_FIXED_COL]++;
     changed = true;
+  }
+  // The fixed-column pass as one batch, with the result of one fixed_col
+  // call per column in increasing order: fixing x_j changes row bounds and
+  // removes column j only, so no decision depends on another; each row's
+  // bounds receive the same subtractions in the same (increasing column)
+  // order; each touched row is compacted once instead of one erase per entry.
+  void fixed_cols(const std::vector<int32_t> &cand) {
+    std::vector<int32_t> fx;
+    for (int32_t j : cand)
+      if (col_on[j] && lx[j] == ux[j]) fx.push_back(j);
+    if (fx.size() < 256) {
+      for (int32_t j : fx) fixed_col(j);
+      return;
+    }
+    std::vector<int32_t> touched;
+    for (int32_t j : fx) {
+      const double v = lx[j];
+      {
+        PostsolveRecord &r = push(REC_FIX_COL);
+        r.j = j; r.v = v; r.cj = c[j];
+      }
+      const size_t rec = po->records.size() - 1;
+      const int64_t s = cols.start[j];
+      for (int32_t q = 0; q < cols.len[j]; ++q) {
+        const int32_t i = cols.idx[s + q];
+        push_entry(po->records[rec], i, cols.val[s + q]);
+        if (!rmark[i]) { rmark[i] = 1; touched.push_back(i); }
+      }
+      off += c[j] * v;
+      fixmark[j] = 1;
+      cols.len[j] = 0;
+      col_on[j] = 0;
+      dirty_col(j);
+      po->counts[C_FIXED_COL]++;
+    }
+    changed = true;
+    parallel_for(touched.size(), 4096, [&](size_t a, size_t b) {
+      for (size_t t = a; t < b; ++t) {
+        const int32_t i = touched[t];
+        const int64_t s = rows.start[i];
+        int32_t w = 0;
+        double l = lo[i], h = hi[i];
+        const bool lf = !std::isinf(l), hf = !std::isinf(h);
+        for (int32_t q = 0; q < rows.len[i]; ++q) {
+          const int32_t j = rows.idx[s + q];
+          const double a = rows.val[s + q];
+          if (fixmark[j]) {
+            const double v = lx[j];
+            if (lf) l -= a * v;
+            if (hf) h -= a * v;
+          } else {
+            rows.idx[s + w] = j;
+            rows.val[s + w] = a;
+            ++w;
+          }
+        }
+        lo[i] = l;
+        hi[i] = h;
+        rows.len[i] = w;
+        rmark[i] = 0;
+      }
+    });
+    for (int32_t i : touched) dirty_row(i);
+    for (int32_t j : fx) fixmark[j] = 0;
   }
   void singleton_row(int32_t i) {
     int32_t j = rows.idx[rows.start[i]];
@@ -471,20 +570,18 @@ struct Presolver {
   }
   // A row holding x_j up-locks it when a_ij > 0 and its upper side is
   // finite or a_ij < 0 and its lower side is; down-locks mirror that.
-  void locks(int32_t j, bool &up, bool &down) const {
-    up = down = false;
+  // Whether x_j has a lock in one direction (up: increasing x_j), stopping at
+  // the first row that locks it.
+  bool locked(int32_t j, bool up) const {
     const int64_t s = cols.start[j];
     for (int32_t q = 0; q < cols.len[j]; ++q) {
       const int32_t i = cols.idx[s + q];
-      const bool lf = !std::isinf(lo[i]), uf = !std::isinf(hi[i]);
-      if (cols.val[s + q] > 0) {
-        up = up || uf;
-        down = down || lf;
-      } else {
-        up = up || lf;
-        down = down || uf;
-      }
+      const bool pos = cols.val[s + q] > 0;
+      // up-lock: a > 0 with a finite upper side, a < 0 with a finite lower
+      const double side = (pos == up) ? hi[i] : lo[i];
+      if (!std::isinf(side)) return true;
     }
+    return false;
   }
   // weak dual fixing: c_j < 0 without an up-lock puts x_j at its upper bound
   // in every optimum (z_j < 0), c_j > 0 without a down-lock at its lower
@@ -492,12 +589,9 @@ struct Presolver {
   void dual_fix(int32_t j) {
     const double cj = c[j];
     if (std::fabs(cj) <= cost_tol) return;
-    bool up, down;
-    locks(j, up, down);
-    double v;
-    if (cj < 0 && !up) v = ux[j];
-    else if (cj > 0 && !down) v = lx[j];
-    else return;
+    // c_j < 0 needs no up-lock, c_j > 0 no down-lock
+    if (locked(j, cj < 0)) return;
+    const double v = cj < 0 ? ux[j] : lx[j];
     if (std::isinf(v)) {
       status = LP_PRESOLVE_UNBOUNDED;
       return;
@@ -635,16 +729,20 @@ struct Presolver {
   // all merges are found first and applied in increasing row order.
   void parallel_rows() {
     std::vector<std::pair<uint64_t, int32_t>> key;
-    for (int32_t i = 0; i < m; ++i) {
-      if (!row_on[i] || rows.len[i] < 2) continue;
-      uint64_t h = 1469598103934665603ull ^ (uint64_t)rows.len[i];
-      const int64_t s = rows.start[i];
-      for (int32_t q = 0; q < rows.len[i]; ++q) {
-        h ^= (uint64_t)(uint32_t)rows.idx[s + q];
-        h *= 1099511628211ull;
+    for (int32_t i = 0; i < m; ++i)
+      if (row_on[i] && rows.len[i] >= 2) key.emplace_back(0, i);
+    parallel_for(key.size(), 20000, [&](size_t a, size_t b) {
+      for (size_t t = a; t < b; ++t) {
+        const int32_t i = key[t].second;
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)rows.len[i];
+        const int64_t s = rows.start[i];
+        for (int32_t q = 0; q < rows.len[i]; ++q) {
+          h ^= (uint64_t)(uint32_t)rows.idx[s + q];
+          h *= 1099511628211ull;
+        }
+        key[t].first = h;
       }
-      key.emplace_back(h, i);
-    }
+    });
     std::sort(key.begin(), key.end());
     struct Merge { int32_t k, i; double s; };
     std::vector<Merge> merges;
@@ -701,9 +799,7 @@ struct Presolver {
             empty_col(j);
             if (status != LP_PRESOLVE_REDUCED) return rounds;
           }
-      if (mask & LP_RULE_FIXED_COL)
-        for (int32_t j : cc)
-          if (col_on[j] && lx[j] == ux[j]) fixed_col(j);
+      if (mask & LP_RULE_FIXED_COL) fixed_cols(cc);
       if (mask & LP_RULE_SINGLETON_ROW)
         for (int32_t i : rc)
           if (row_on[i] && rows.len[i] == 1) {
@@ -781,23 +877,25 @@ struct Presolver {
     out.m = (int32_t)po->row_map.size();
     out.n = (int32_t)po->col_map.size();
     out.row_ptr.assign(out.m + 1, 0);
-    int64_t nz = 0;
-    for (int32_t i : po->row_map) nz += rows.len[i];
-    out.col_idx.reserve(nz);
-    out.val.reserve(nz);
-    out.row_lo.reserve(out.m);
-    out.row_hi.reserve(out.m);
-    for (int32_t r = 0; r < out.m; ++r) {
-      int32_t i = po->row_map[r];
-      int64_t s = rows.start[i];
-      for (int32_t q = 0; q < rows.len[i]; ++q) {
-        out.col_idx.push_back(cpos[rows.idx[s + q]]);
-        out.val.push_back(rows.val[s + q]);
+    for (int32_t r = 0; r < out.m; ++r) out.row_ptr[r + 1] = out.row_ptr[r] + rows.len[po->row_map[r]];
+    const int64_t nz = out.row_ptr[out.m];
+    out.col_idx.resize(nz);
+    out.val.resize(nz);
+    out.row_lo.resize(out.m);
+    out.row_hi.resize(out.m);
+    parallel_for((size_t)out.m, 20000, [&](size_t a, size_t b) {
+      for (size_t r = a; r < b; ++r) {
+        const int32_t i = po->row_map[r];
+        const int64_t s = rows.start[i];
+        int64_t w = out.row_ptr[r];
+        for (int32_t q = 0; q < rows.len[i]; ++q, ++w) {
+          out.col_idx[w] = cpos[rows.idx[s + q]];
+          out.val[w] = rows.val[s + q];
+        }
+        out.row_lo[r] = lo[i];
+        out.row_hi[r] = hi[i];
       }
-      out.row_ptr[r + 1] = (int64_t)out.col_idx.size();
-      out.row_lo.push_back(lo[i]);
-      out.row_hi.push_back(hi[i]);
-    }
+    });
     for (int32_t j : po->col_map) {
       out.c.push_back(c[j]);
       out.col_lo.push_back(lx[j]);

@@ -204,3 +204,29 @@ def test_postsolve_matches_oracle_on_perturbed_solutions(name, make):
         # dual feasibility c - A^T y - z = 0 holds for any reduced solution
         g = lp.c - lp.csr().T @ yc
         assert np.max(np.abs(g - zc)) <= 1e-9 * (1 + np.max(np.abs(lp.c)))
+
+
+def test_threaded_paths_match_oracle():
+    # large enough for every threaded / batched path of the library: the
+    # column store built by several threads (>= 1M nonzeros), the batched
+    # fixed-column pass (>= 256 fixed columns, >= 4096 touched rows), the
+    # parallel row hashing and reduced-problem build (>= 20000 rows)
+    _lib_or_skip()
+    lp = lpgen.medium_structure(42_000, 105_000, 17, nnz_target=1_000_000)
+    assert lp.nnz >= 1_000_000
+    ref = PS.presolve(lp)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve()
+    assert info.status == ref.status and info.rounds == ref.rounds
+    assert ref.counts["fixed_col"] >= 256
+    red, r = prob.data(), ref.reduced
+    assert (red.m, red.n) == (r.m, r.n)
+    np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
+    np.testing.assert_array_equal(red.col_idx, r.col_idx)
+    np.testing.assert_array_equal(red.val, r.val)
+    np.testing.assert_array_equal(red.c, r.c)
+    np.testing.assert_array_equal(red.row_lo, r.row_lo)
+    np.testing.assert_array_equal(red.row_hi, r.row_hi)
+    np.testing.assert_array_equal(red.col_lo, r.col_lo)
+    np.testing.assert_array_equal(red.col_hi, r.col_hi)
+    assert red.obj_offset == r.obj_offset
