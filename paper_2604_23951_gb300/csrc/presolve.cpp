@@ -555,9 +555,12 @@ struct Presolver {
       if (!std::isinf(lo[rr])) lo[rr] -= a * sv;
       if (!std::isinf(hi[rr])) hi[rr] -= a * sv;
       double old = rows.get(rr, k, 0.0);
-      remove_entry(rr, j);
+      // column j goes as a whole below: drop (rr, j) from the row store only
+      rows.erase(rr, j);
+      dirty_row(rr);
       set_entry(rr, k, old - a * r);
     }
+    cols.len[j] = 0;
     remove_row(i);
     remove_col(j);
     if (nl != lx[k] || nu != ux[k]) {
