@@ -29,7 +29,7 @@ import numpy as np
 import scipy.sparse as sp
 
 # termination codes (same numbering as the C ABI)
-OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL = 0, 1, 2, 3
+OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL, INFEASIBLE, UNBOUNDED = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
@@ -48,6 +48,8 @@ class Opts:
     power_iters: int = 100
     halpern: bool = True  # False: plain PDHG z <- (1+rho)T(z) - rho z (no anchor)
     restarts: bool = True
+    infeas_every: int = 4  # READING: infeasibility test every 4th check (0: never)
+    eps_infeas: float = 1e-8  # READING: PDLP's infeasibility tolerances
 
 
 @dataclass
@@ -123,6 +125,46 @@ def _support(v, lo, hi):
     if neg.any():
         s += float(np.sum(v[neg] * hi[neg]))
     return s
+
+
+def infeasibility_certificate(lp, A, d, w, eps):
+    """Test a direction (d, w) of the iterates for a certificate that the LP
+    of eq. (1) has no optimum (READING: the paper's solver family detects
+    infeasibility from iterate differences; the tests are the Farkas
+    alternatives of eq. (2) with relative tolerance eps).
+
+    Primal infeasibility (dual ray): wp = w projected on the rows' sign
+    domain, lam = proj_Lambda(-A^T wp); a certificate when the dual objective
+    D = sum(wp^+ l_c - wp^- u_c) + sum(lam^+ l_x - lam^- u_x) > 0 and
+    ||A^T wp + lam||_2 <= eps D (then every dual-feasible point can be moved
+    along (wp, lam) with the dual objective growing without bound).
+
+    Dual infeasibility (primal ray): c^T d < 0 and the violation of A d
+    against the recession cone of [l_c, u_c] ((A d)_i <= 0 where u_ci is
+    finite, >= 0 where l_ci is) together with that of d against the
+    recession cone of [l_x, u_x], in 2-norm, is at most eps (-c^T d).
+
+    A and all vectors in the problem's own (unscaled) units.  Returns
+    INFEASIBLE, UNBOUNDED or None; the dual ray is tested first."""
+    lo, hi = np.asarray(lp.row_lo, np.float64), np.asarray(lp.row_hi, np.float64)
+    lx, ux = np.asarray(lp.col_lo, np.float64), np.asarray(lp.col_hi, np.float64)
+    c = np.asarray(lp.c, np.float64)
+    wp = dual_row_project(w, lo, hi)
+    g = A.T @ wp
+    lam = dual_cone_project(-g, lx, ux)
+    dobj = _support(wp, lo, hi) + _support(lam, lx, ux)
+    if dobj > 0 and float(np.linalg.norm(g + lam)) <= eps * dobj:
+        return INFEASIBLE
+    cd = float(c @ d)
+    if cd < 0:
+        ad = A @ d
+        vr = (np.where(np.isfinite(hi), np.maximum(ad, 0.0), 0.0)
+              + np.where(np.isfinite(lo), np.maximum(-ad, 0.0), 0.0))
+        vc = (np.where(np.isfinite(ux), np.maximum(d, 0.0), 0.0)
+              + np.where(np.isfinite(lx), np.maximum(-d, 0.0), 0.0))
+        if math.sqrt(float(vr @ vr) + float(vc @ vc)) <= eps * (-cd):
+            return UNBOUNDED
+    return None
 
 
 def bhat_norm(row_lo, row_hi):
@@ -284,7 +326,9 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
       1. (xh, yh) = T(z)                                   (pdhg_operator)
       2. if t % K == 0 (a check):
          a. stop if relKKT(unscaled xh, yh) <= eps_rel (return T(z)), or on
-            non-finite values, or past the time limit;
+            non-finite values, or past the time limit; else, at every
+            infeas_every-th check, stop with INFEASIBLE / UNBOUNDED when the
+            direction T(z) - z0 (unscaled) passes infeasibility_certificate;
          b. r = ||z - T(z)||_omega,  ||(a, b)||_omega^2 = omega ||a||^2 + ||b||^2 / omega;
          c. k == 0 (t = 0): r0 = r_prev = r;
             else restart if (i) r <= beta_suff r0, or (ii) r <= beta_nec r0 and
@@ -343,6 +387,12 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                 status = OPTIMAL
             elif time.perf_counter() - start > opts.time_limit_s:
                 status = TIME_LIMIT
+            elif opts.infeas_every > 0 and (t // K) % opts.infeas_every == 0:
+                # direction since the last restart: T(z) - z0, unscaled
+                cert = infeasibility_certificate(lp, sc.A0, sc.dc * (xh - x0), sc.dr * (yh - y0),
+                                                 opts.eps_infeas)
+                if cert is not None:
+                    status = cert
             if status != ITER_LIMIT:
                 t += 1  # count this evaluation of T
                 break

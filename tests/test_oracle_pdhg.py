@@ -299,3 +299,62 @@ def test_power_norm_of_rows_summing_to_zero():
         M[e, e], M[(e + 1) % k, e] = 1.0, -1.0
     est = P.power_norm(sp.csr_matrix(M), 200)
     assert abs(est - np.linalg.norm(M, 2)) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# infeasibility / unboundedness detection
+
+from infeasible_lps import CASES as NO_OPTIMUM  # noqa: E402
+
+
+def _highs_status(lp):
+    from scipy.optimize import linprog
+
+    A = lp.csr()
+    lo, hi = np.asarray(lp.row_lo), np.asarray(lp.row_hi)
+    eq = np.isfinite(lo) & np.isfinite(hi) & (lo == hi)
+    up = np.isfinite(hi) & ~eq
+    dn = np.isfinite(lo) & ~eq
+    kw = {}
+    if up.any() or dn.any():
+        kw.update(A_ub=sp.vstack([A[up], -A[dn]]), b_ub=np.concatenate([hi[up], -lo[dn]]))
+    if eq.any():
+        kw.update(A_eq=A[eq], b_eq=lo[eq])
+    bounds = [(None if not np.isfinite(a) else a, None if not np.isfinite(b) else b)
+              for a, b in zip(lp.col_lo, lp.col_hi)]
+    return linprog(lp.c, bounds=bounds, method="highs", **kw).status
+
+
+@pytest.mark.parametrize("name,make,status", NO_OPTIMUM)
+def test_detects_infeasible_and_unbounded_like_highs(name, make, status):
+    lp = make()
+    # HiGHS: 2 infeasible, 3 unbounded
+    assert _highs_status(lp) == {4: 2, 5: 3}[status]
+    r = oracle.pdhg_solve(lp, oracle.Opts(max_iter=20000))
+    assert r.status == status, (name, r.status, r.iterations)
+
+
+def test_certificate_tests_on_hand_made_rays():
+    A = sp.csr_matrix(np.array([[1.0, 1.0], [1.0, -1.0]]))
+    lp = SimpleLP(A.toarray(), [1.0, 1.0], [-np.inf, -2.0], [-1.0, 2.0], [0.0, 0.0],
+                  [np.inf, np.inf])
+    # Farkas: w = (-1, 0) (row 0 has only u_0 = -1, so w_0 <= 0 is allowed)
+    # gives A^T w = (-1, -1), cancelled by lam = (1, 1) >= 0 on x >= 0, and
+    # the dual objective -w_0^- u_0 = -(1)(-1) = 1 > 0
+    assert P.infeasibility_certificate(lp, A, np.zeros(2), np.array([-1.0, 0.0]), 1e-8) == P.INFEASIBLE
+    # the wrong sign is no certificate (and is projected away)
+    assert P.infeasibility_certificate(lp, A, np.zeros(2), np.array([1.0, 0.0]), 1e-8) is None
+    A = sp.csr_matrix(np.array([[1.0, -1.0]]))
+    lp = SimpleLP(A.toarray(), [-1.0, -1.0], [-1.0], [1.0], [0.0, 0.0], [np.inf, np.inf])
+    assert P.infeasibility_certificate(lp, A, np.array([1.0, 1.0]), np.zeros(1), 1e-8) == P.UNBOUNDED
+    # (1, 0) lowers the cost but leaves the ranged row: no certificate
+    assert P.infeasibility_certificate(lp, A, np.array([1.0, 0.0]), np.zeros(1), 1e-8) is None
+    # (-1, -1) leaves x >= 0
+    assert P.infeasibility_certificate(lp, A, np.array([-1.0, -1.0]), np.zeros(1), 1e-8) is None
+
+
+def test_feasible_lps_are_never_flagged():
+    for s in range(4):
+        lp = lpgen.general_structure(300, 700, 100 + s, nnz_target=4000, one_sided=0.3)
+        r = oracle.pdhg_solve(lp, oracle.Opts(max_iter=50000, infeas_every=1))
+        assert r.status == P.OPTIMAL
