@@ -53,8 +53,10 @@ extern "C" {
 #define LP_ITER_LIMIT 1 /* max_iter iterations done                          */
 #define LP_TIME_LIMIT 2 /* time_limit_s elapsed                              */
 #define LP_NUMERICAL 3  /* a non-finite value appeared                       */
-#define LP_INFEASIBLE 4 /* presolve proved the LP infeasible                 */
-#define LP_UNBOUNDED 5  /* presolve proved the LP unbounded                  */
+#define LP_INFEASIBLE 4 /* presolve proved the LP infeasible, or the solver
+                           found a dual ray (Farkas certificate)             */
+#define LP_UNBOUNDED 5  /* presolve proved the LP unbounded, or the solver
+                           found a primal ray (the dual is infeasible)       */
 #define LP_CANCELLED 6  /* batch request cancelled                           */
 
 /* ---- presolve status (lp_presolve_info.status) ------------------------- */
@@ -156,6 +158,20 @@ typedef struct {
                           * semantics; use_graph and lp_profile_kernels
                           * concern the grid engine only.                  */
   int32_t verbose;
+  int32_t infeas_every;  /* 4: at every infeas_every-th check the direction
+                          * d = T(z) - z0 since the last restart is tested
+                          * for a certificate (0: never).  Dual ray: w =
+                          * d_y projected on the rows' sign domain, lam =
+                          * proj_Lambda(-A^T w), dual objective D =
+                          * sum(w+ l_c - w- u_c) + sum(lam+ l_x - lam- u_x);
+                          * LP_INFEASIBLE when D > 0 and ||A^T w + lam||_2
+                          * <= eps_infeas D.  Primal ray: d_x with c^T d_x
+                          * < 0 whose violation of the recession cones of
+                          * [l_c, u_c] (for A d_x) and [l_x, u_x] is at most
+                          * eps_infeas (-c^T d_x) in 2-norm: LP_UNBOUNDED.
+                          * All in the LP's own units; the returned x, y
+                          * are T(z) of that check.                         */
+  double eps_infeas;     /* 1e-8                                            */
 } lp_solve_opts;
 
 typedef struct {

@@ -53,7 +53,8 @@ class lp_solve_opts(C.Structure):
                 ("use_graph", C.c_int32), ("step_size", C.c_double),
                 ("primal_weight", C.c_double), ("x_init", C.POINTER(C.c_double)),
                 ("y_init", C.POINTER(C.c_double)), ("engine", C.c_int32),
-                ("verbose", C.c_int32)]
+                ("verbose", C.c_int32), ("infeas_every", C.c_int32),
+                ("eps_infeas", C.c_double)]
 
 
 class lp_result(C.Structure):

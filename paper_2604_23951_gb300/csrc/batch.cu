@@ -85,6 +85,7 @@ struct SlotDesc {
 
 struct BatchConst {
   int K, ruiz_iters, pock_chambolle, power_iters;
+  int infeas_every;
   long long max_iter;
   double step_size, primal_weight;
   long long budget_ns;  // device time a launch gives its slots (>= one block of K each)
@@ -423,7 +424,7 @@ __device__ __forceinline__ void phase_dual(const SlotDesc &D, bool f32, double s
 // K3 (the KKT products of the check, FP64 scaled matrix, unscaled
 // quantities) and the cluster-wide sum of acc[0..10) into sh.total (rank 0)
 __device__ __forceinline__ void slot_kkt(const SlotDesc &D, BatchShared &sh,
-                                         cg::cluster_group &cl, double (&acc)[10]) {
+                                         cg::cluster_group &cl, double (&acc)[10], bool inf) {
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   {
     KktRowEpi e{D.dr, D.idr, D.lc0, D.uc0, D.yhat, 0.0, 0.0, 0.0};
@@ -443,6 +444,32 @@ __device__ __forceinline__ void slot_kkt(const SlotDesc &D, BatchShared &sh,
   }
   const int qid[10] = {Q_XRES, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P};
   cluster_sum<10>(acc, qid, sh, cl);
+  if (inf) {
+    // infeasibility test of the direction (xh - x0, yh - y0): xbar (free
+    // after K2) holds d~, yout (written only at the end) the projected w~
+    const int gt = rank * blockDim.x + threadIdx.x, gs = CL * blockDim.x;
+    double ia[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int j = gt; j < D.n; j += gs)
+      inf_col_prep(j, D.xhat, D.x0, D.dc, D.c0, D.lx0, D.ux0, D.xbar, ia[0], ia[1]);
+    cl.sync();
+    {
+      InfRowEpi e{D.dr, D.idr, D.lc0, D.uc0, D.yhat, D.y0, D.yout, 0.0, 0.0};
+      warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci,
+                                        D.a_v, D.xbar, e, sh.redd, rank, CL);
+      ia[2] = e.v2;
+      ia[3] = e.dobj;
+    }
+    cl.sync();
+    {
+      InfColEpi e{D.idc, D.lx0, D.ux0, 0.0, 0.0};
+      warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci,
+                                        D.t_v, D.yout, e, sh.redd, rank, CL);
+      ia[4] = e.r2;
+      ia[5] = e.dobj;
+    }
+    const int iq[6] = {Q_ICD, Q_IPVC, Q_IPVR, Q_IDOR, Q_IDR, Q_IDOC};
+    cluster_sum<6>(ia, iq, sh, cl);
+  }
 }
 
 // One block of iterations t0 .. t0 + K - 1 (t0 = iterations done, a multiple
@@ -488,7 +515,7 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
     else phase_dual<false>(D, f32, sigma, hc, sh, rank, CL, acc);
     cl.sync();
     if (check) {
-      slot_kkt(D, sh, cl, acc);
+      slot_kkt(D, sh, cl, acc, infeas_due(sh.ctl.t, C.K, C.infeas_every));
       if (cl.block_rank() == 0 && threadIdx.x == 0) {
         check_update(st, sh.total, false);
         bcast_ctl(st, sh, cl);
@@ -513,7 +540,7 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
     if (last) {
       // max_iter reached: evaluate the last T(z)
       double acc2[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-      slot_kkt(D, sh, cl, acc2);
+      slot_kkt(D, sh, cl, acc2, false);
       if (cl.block_rank() == 0 && threadIdx.x == 0) {
         check_update(st, sh.total, true);
         st->iters = C.max_iter;
@@ -919,6 +946,8 @@ void state_init(const lp_solve_opts &o, State &st, const Packed &pk) {
   st.beta_art = o.beta_art;
   st.theta = o.theta;
   st.eps_rel = o.eps_rel;
+  st.eps_infeas = o.eps_infeas;
+  st.infeas_every = o.infeas_every;
   st.bnorm = pk.bnorm;
   st.cnorm = pk.cnorm;
   st.off = pk.off;
@@ -1082,6 +1111,7 @@ void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
   C.ruiz_iters = srv->opts.ruiz_iters;
   C.pock_chambolle = srv->opts.pock_chambolle;
   C.power_iters = srv->opts.power_iters;
+  C.infeas_every = srv->opts.infeas_every;
   C.max_iter = srv->opts.max_iter;
   C.step_size = srv->opts.step_size;
   C.primal_weight = srv->opts.primal_weight;
@@ -1693,6 +1723,7 @@ int cluster_solve(const HostLP &h, const lp_solve_opts &o, const lp_device_ctx *
     C.ruiz_iters = o.ruiz_iters;
     C.pock_chambolle = o.pock_chambolle;
     C.power_iters = o.power_iters;
+    C.infeas_every = o.infeas_every;
     C.max_iter = o.max_iter;
     C.step_size = o.step_size;
     C.primal_weight = o.primal_weight;

@@ -131,4 +131,67 @@ struct KktColEpi {
   }
 };
 
+// Infeasibility test, rows of A at d~ = xh - x0 (scaled): squared violation
+// of A d (unscaled) against the recession cone of [l_c, u_c] ((A d)_i <= 0
+// where u_ci is finite, >= 0 where l_ci is); the dual direction
+// w~ = yh - y0 projected on the rows' sign domain (stored in wbuf for the
+// A^T pass) and its part of the dual-ray objective sum(w+ l_c - w- u_c)
+struct InfRowEpi {
+  const double *dr, *idr, *lc0, *uc0, *yhat, *y0;
+  double *wbuf;
+  double v2, dobj;
+  __device__ __forceinline__ void pre(int) {}
+  __device__ __forceinline__ void row(int i, double h) {
+    const double ad = h * idr[i];
+    const double lo = lc0[i], hi = uc0[i];
+    const bool lf = isfinite(lo), uf = isfinite(hi);
+    double v = 0.0;
+    if (uf) v += fmax(ad, 0.0);
+    if (lf) v += fmax(-ad, 0.0);
+    v2 += v * v;
+    double w = yhat[i] - y0[i];
+    if (!lf) w = fmin(w, 0.0);
+    if (!uf) w = fmax(w, 0.0);
+    wbuf[i] = w;
+    dobj += support_term(dr[i] * w, lo, hi);
+  }
+};
+
+// Infeasibility test, rows of A^T at the projected w~: g = A^T w (unscaled),
+// lam = proj_Lambda(-g), the squared residual (g + lam)^2 and the column part
+// of the dual-ray objective sum(lam+ l_x - lam- u_x)
+struct InfColEpi {
+  const double *idc, *lx0, *ux0;
+  double r2, dobj;
+  __device__ __forceinline__ void pre(int) {}
+  __device__ __forceinline__ void row(int j, double h) {
+    const double g = h * idc[j];
+    const double lo = lx0[j], hi = ux0[j];
+    const bool lf = isfinite(lo), uf = isfinite(hi);
+    double lam = -g;
+    if (!lf && !uf) lam = 0.0;
+    else if (lf && !uf) lam = fmax(lam, 0.0);
+    else if (!lf && uf) lam = fmin(lam, 0.0);
+    r2 += (g + lam) * (g + lam);
+    dobj += support_term(lam, lo, hi);
+  }
+};
+
+// Infeasibility test, one column: d~_j = xh_j - x0_j (stored in dbuf for the
+// A pass); c^T d and the squared violation of d (unscaled) against the
+// recession cone of [l_x, u_x]
+__device__ __forceinline__ void inf_col_prep(int j, const double *xhat, const double *x0,
+                                             const double *dc, const double *c0,
+                                             const double *lx0, const double *ux0, double *dbuf,
+                                             double &cd, double &v2) {
+  const double dd = xhat[j] - x0[j];
+  dbuf[j] = dd;
+  const double d = dc[j] * dd;
+  cd += c0[j] * d;
+  double v = 0.0;
+  if (isfinite(ux0[j])) v += fmax(d, 0.0);
+  if (isfinite(lx0[j])) v += fmax(-d, 0.0);
+  v2 += v * v;
+}
+
 }  // namespace gb300lp

@@ -7,7 +7,10 @@
 // record r0 = r_prev = r at the first check, otherwise restart when
 // r <= beta_suff r0, or r <= beta_nec r0 and r > r_prev, or k >= beta_art t;
 // a restart moves the anchor and the iterate to T(z) and smooths the primal
-// weight omega <- exp(theta log(dy / dx) + (1 - theta) log omega).
+// weight omega <- exp(theta log(dy / dx) + (1 - theta) log omega).  At every
+// infeas_every-th check that does not stop, the direction T(z) - z0 is
+// tested for a dual ray (LP_INFEASIBLE) and then a primal ray
+// (LP_UNBOUNDED), from the Q_I* quantities.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,6 +22,8 @@ constexpr int ST_RUNNING = -1;
 struct State {
   double eta, omega, tau, sigma;
   double rho, beta_suff, beta_nec, beta_art, theta, eps_rel;
+  double eps_infeas;
+  int infeas_every;  // 0: no infeasibility test
   double r0, r_prev, last_r;
   double bnorm, cnorm, off;
   double rel_kkt, rel_p, rel_d, rel_gap, r_p, r_d, gap, pobj, dobj;
@@ -48,9 +53,19 @@ constexpr double kPolishRatio = 10.0;
 constexpr int kPolishStall = 256;
 
 // reduced quantities of a check (and of the set-up)
+// Q_I*: infeasibility test of the direction (d, w) = T(z) - z0 (unscaled):
+// c^T d, squared cone violations of d (columns) and A d (rows), squared
+// residual ||A^T w + lam||^2, dual-ray objective (rows, columns)
 enum {
-  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P, Q_CN, Q_BN, Q_PW, NQ
+  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P,
+  Q_ICD, Q_IPVC, Q_IPVR, Q_IDR, Q_IDOR, Q_IDOC,
+  Q_CN, Q_BN, Q_PW, NQ
 };
+
+// whether the check at iteration t tests for infeasibility
+__host__ __device__ __forceinline__ bool infeas_due(long long t, int K, int every) {
+  return every > 0 && ((t / K) % every) == 0;
+}
 
 // Halpern coefficients of iteration position j of a check period:
 // z+ = a T(z) + b z + g z0
@@ -101,6 +116,20 @@ __device__ __forceinline__ void check_update(State *st, const double *q, bool ev
     st->iters = st->t + 1;
     st->restart_flag = 0;
     return;
+  }
+  if (infeas_due(st->t, st->K, st->infeas_every)) {
+    const double dobj = q[Q_IDOR] + q[Q_IDOC];
+    const double cd = q[Q_ICD];
+    int cert = -1;
+    if (dobj > 0 && sqrt(q[Q_IDR]) <= st->eps_infeas * dobj) cert = 4;  // LP_INFEASIBLE
+    else if (cd < 0 && sqrt(q[Q_IPVC] + q[Q_IPVR]) <= st->eps_infeas * (-cd))
+      cert = 5;  // LP_UNBOUNDED
+    if (cert >= 0) {
+      st->status = cert;
+      st->iters = st->t + 1;
+      st->restart_flag = 0;
+      return;
+    }
   }
   if (st->mixed_active) {
     if (rel < 0.5 * st->best_rel) {

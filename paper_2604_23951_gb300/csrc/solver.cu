@@ -381,6 +381,51 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
   store_partials<3>(acc, qi, partials, G);
 }
 
+// Infeasibility test of a check (skipped unless due): the direction
+// (xh - x0, yh - y0); K_I0 the columns (c^T d, cone violation of d; d~ into
+// dbuf), K_I1 the rows of A at d~ (cone violation of A d; projected w~ into
+// wbuf, dual-ray objective), K_I2 the rows of A^T at w~ (residual, objective)
+__global__ void k_inf_prep(const State *__restrict__ st, int n, const double *__restrict__ xhat,
+                           const double *__restrict__ x0, const double *__restrict__ dc,
+                           const double *__restrict__ c0, const double *__restrict__ lx0,
+                           const double *__restrict__ ux0, double *dbuf, double *partials,
+                           int G) {
+  if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
+  double acc[2] = {0.0, 0.0};
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    inf_col_prep(j, xhat, x0, dc, c0, lx0, ux0, dbuf, acc[0], acc[1]);
+  const int qi[2] = {Q_ICD, Q_IPVC};
+  store_partials<2>(acc, qi, partials, G);
+}
+
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_rows(
+    MatDev M, const double *__restrict__ va, const double *__restrict__ dbuf,
+    const double *__restrict__ dr, const double *__restrict__ idr,
+    const double *__restrict__ lc0, const double *__restrict__ uc0,
+    const double *__restrict__ yhat, const double *__restrict__ y0, double *wbuf,
+    const State *__restrict__ st, double *partials, int G) {
+  if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
+  InfRowEpi e{dr, idr, lc0, uc0, yhat, y0, wbuf, 0.0, 0.0};
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, dbuf, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+  double acc[2] = {e.v2, e.dobj};
+  const int qi[2] = {Q_IPVR, Q_IDOR};
+  store_partials<2>(acc, qi, partials, G);
+}
+
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_cols(
+    MatDev M, const double *__restrict__ va, const double *__restrict__ wbuf,
+    const double *__restrict__ idc, const double *__restrict__ lx0,
+    const double *__restrict__ ux0, const State *__restrict__ st, double *partials, int G) {
+  if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
+  InfColEpi e{idc, lx0, ux0, 0.0, 0.0};
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, wbuf, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+  double acc[2] = {e.r2, e.dobj};
+  const int qi[2] = {Q_IDR, Q_IDOC};
+  store_partials<2>(acc, qi, partials, G);
+}
+
 // K4: the check.  eval_only: fill in the KKT fields and mark ITER_LIMIT.
 __global__ void k_check(State *st, const double *partials, int G, int eval_only) {
   if (!eval_only && st->status != ST_RUNNING) return;
@@ -453,6 +498,7 @@ struct DeviceLP {
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
   double *pv = nullptr, *pv0 = nullptr, *pw = nullptr, *pu = nullptr;
+  int infeas_every = 0;  // of the current solve (host copy of the state's)
   double *ox = nullptr, *oy = nullptr, *oxi = nullptr, *oyi = nullptr;
   float *xbar_f = nullptr, *yf = nullptr;
   double *partials = nullptr;
@@ -463,6 +509,7 @@ struct DeviceLP {
   std::vector<void *> allocs;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_K[2] = {0, 0};
+  int graph_inf[2] = {0, 0};  // whether the graph holds the infeasibility test
   long long launches = 0;
   int last_precision = -1;
   void *flush = nullptr;
@@ -723,6 +770,17 @@ void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only)
   d->launches += 2;
   if (check) {
     launch_kkt(d, 0);
+    if (d->infeas_every > 0) {
+      // pw (n) and pu (m) are the power iteration's vectors, free after set-up
+      k_inf_prep<<<d->G, kBlock, 0, d->s>>>(d->st, d->n, d->xhat, d->x0, d->dc, d->c0, d->lx0,
+                                            d->ux0, d->pw, d->partials, d->G);
+      k_inf_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pw, d->dr, d->idr,
+                                                  d->lc0, d->uc0, d->yhat, d->y0, d->pu, d->st,
+                                                  d->partials, d->G);
+      k_inf_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->idc, d->lx0,
+                                                  d->ux0, d->st, d->partials, d->G);
+      d->launches += 3;
+    }
     k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 0);
     k_restart<<<d->grid_for(std::max(d->m, d->n)), kBlock, 0, d->s>>>(
         d->st, d->n, d->m, d->x, d->x0, d->xhat, d->y, d->y0, d->yhat, mixed ? d->yf : nullptr);
@@ -829,6 +887,9 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     init.beta_art = o.beta_art;
     init.theta = o.theta;
     init.eps_rel = o.eps_rel;
+    init.eps_infeas = o.eps_infeas;
+    init.infeas_every = o.infeas_every;
+    d->infeas_every = o.infeas_every;
     init.bnorm = d->bnorm;
     init.cnorm = d->cnorm;
     init.off = d->off;
@@ -872,7 +933,9 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     long long launched = 0;
     int pi = mixed ? 1 : 0;
     bool use_graph = o.use_graph != 0;
-    if (use_graph && (d->graph[pi] == nullptr || d->graph_K[pi] != K)) {
+    const int with_inf = d->infeas_every > 0 ? 1 : 0;
+    if (use_graph &&
+        (d->graph[pi] == nullptr || d->graph_K[pi] != K || d->graph_inf[pi] != with_inf)) {
       if (d->graph[pi]) {
         cudaGraphExecDestroy(d->graph[pi]);
         d->graph[pi] = nullptr;
@@ -886,9 +949,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       CK(cudaGraphInstantiate(&d->graph[pi], g, 0));
       CK(cudaGraphDestroy(g));
       d->graph_K[pi] = K;
+      d->graph_inf[pi] = with_inf;
       d->launches = saved;
     }
-    const long long per_graph = 2LL * K + 4;
+    const long long per_graph = 2LL * K + 4 + 3LL * with_inf;
     std::vector<cudaEvent_t> evs;
     std::vector<cudaEvent_t> pool;
     auto get_event = [&]() {
