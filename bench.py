@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--solo-nnz", type=int, default=0,
                    help="c4/c5: nonzeros from which a request runs the single-LP path (0: default)")
     p.add_argument("--solo-max", type=int, default=-1, help="c4/c5: concurrent solo requests")
+    p.add_argument("--infeas-every", type=int, default=-1,
+                   help="infeasibility test every N-th check (0: off; -1: library default)")
     p.add_argument("--launch-ms", type=float, default=0.0,
                    help="c4/c5: device time budget of one bucket launch (0: default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -171,6 +173,20 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def solver_kw(args):
+    """lp_solve_opts fields set on the command line"""
+    return {"infeas_every": args.infeas_every} if args.infeas_every >= 0 else {}
+
+
+def term_hist(codes):
+    """{termination code: count} (0 optimal, 1 iteration limit, 2 time limit,
+    3 numerical, 4 infeasible, 5 unbounded, 6 cancelled)"""
+    h = {}
+    for c in codes:
+        h[str(int(c))] = h.get(str(int(c)), 0) + 1
+    return h
 
 
 def kernel_source_hash():
@@ -452,7 +468,7 @@ def run_batch(args):
 
         def one_step():
             probs = [pkg.Problem(lp, dev) for lp in lps]
-            srv = pkg.Server(budget, dev, precision=prec)
+            srv = pkg.Server(budget, dev, precision=prec, **solver_kw(args))
             srv.tune(args.solo_nnz, args.solo_max, args.launch_ms)
             t0 = time.perf_counter()
             tickets = [srv.submit(p) for p in probs]
@@ -463,6 +479,7 @@ def run_batch(args):
                     for t, lp in zip(tickets, lps)]
             opt = sum(1 for t in tickets if res[t][0].termination == 0)
             st = srv.stats()
+            st["terminations"] = term_hist(res[t][0].termination for t in tickets)
             srv.close()
             return el, lat, errs, opt, st
 
@@ -534,7 +551,7 @@ def run_batch(args):
             f"[1e3, 1e7], presolvable structure, 150 GB HBM budget")
 
     def serve():
-        srv = pkg.Server(int(150e9), dev, worker=True, precision=prec)
+        srv = pkg.Server(int(150e9), dev, worker=True, precision=prec, **solver_kw(args))
         srv.tune(args.solo_nnz, args.solo_max, args.launch_ms)
         probs = [None] * len(lps)
         tickets = [None] * len(lps)
@@ -579,6 +596,7 @@ def run_batch(args):
     clk = clocks.stop()
     lat = [done[j][0] for j in range(len(lps))]
     opt = sum(1 for j in range(len(lps)) if done[j][1].termination == 0)
+    st["terminations"] = term_hist(done[j][1].termination for j in range(len(lps)))
     # comparator: each request solved singly, FP64, one after another
     t0 = time.perf_counter()
     single = []

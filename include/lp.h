@@ -293,8 +293,9 @@ void lp_destroy(lp_problem *lp);
  *   a_*         CSR of A on the device: row_ptr (m + 1), col_idx, val
  *   at_*        CSR of A^T on the device (n + 1 row pointers)
  *   iters       power iterations (lp_solve uses 100); start vector
- *               v_j = (0.5 + h(j) / 2^32) / sqrt(n), h(j) = j * 2654435761
- *               mod 2^32; v <- A^T A v / ||.||, estimate ||A v||
+ *               1/sqrt(n), v <- A^T A v / ||.||, estimate ||A v||; a step
+ *               giving zero continues from v_j = (0.5 + h(j) / 2^32) /
+ *               sqrt(n), h(j) = j * 2654435761 mod 2^32
  *   stream      cudaStream_t the kernels run on (NULL: legacy stream)
  *   norm_out    host double that receives the estimate (0 if m or n is 0)
  * All work vectors live in one file-scope device array of 2^20 doubles

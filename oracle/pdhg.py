@@ -253,23 +253,23 @@ def ruiz_pc_scaling(A: sp.csr_matrix, ruiz_iters: int = 10, pock_chambolle: bool
 def power_norm(A: sp.spmatrix, iters: int = 100) -> float:
     """Estimate ||A||_2 by power iteration on A^T A.
 
-    READING: start vector v_j = (0.5 + h(j) / 2^32) / sqrt(n) with
-    h(j) = j * 2654435761 mod 2^32 (a fixed vector in no special direction:
-    all-ones / sqrt(n) is orthogonal to the top singular vector when the rows
-    of A sum to zero, e.g. A = [1, -1]); each step v <- A^T (A v) / ||.||;
-    the estimate is ||A v||_2 for the final unit vector v.
+    READING: start vector all-ones / sqrt(n); each step v <- A^T (A v) / ||.||;
+    the estimate is ||A v||_2 for the final vector v.  A step that gives the
+    zero vector (all-ones is orthogonal to every right singular vector with a
+    nonzero value when the rows of A sum to zero, e.g. A = [1, -1]) continues
+    from the fallback v_j = (0.5 + h(j) / 2^32) / sqrt(n), with the
+    multiplicative hash h(j) = j * 2654435761 mod 2^32 of the column index.
     """
     m, n = A.shape
     if n == 0 or m == 0:
         return 0.0
+    v = np.full(n, 1.0 / math.sqrt(n))
     h = (np.arange(n, dtype=np.uint64) * np.uint64(2654435761)) % np.uint64(2 ** 32)
-    v = (0.5 + h.astype(np.float64) / 4294967296.0) * (1.0 / math.sqrt(n))
+    fallback = (0.5 + h.astype(np.float64) / 4294967296.0) * (1.0 / math.sqrt(n))
     for _ in range(iters):
         w = A.T @ (A @ v)
         nw = float(np.linalg.norm(w))
-        if nw == 0.0:
-            return 0.0
-        v = w / nw
+        v = w / nw if nw > 0.0 else fallback
     return float(np.linalg.norm(A @ v))
 
 

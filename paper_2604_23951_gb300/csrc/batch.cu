@@ -284,8 +284,8 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
   if (!(eta > 0.0)) {
     double pw = 0.0;
     if (m > 0 && n > 0) {
+      const double v0 = 1.0 / sqrt((double)n);
       for (int j = gt; j < n; j += gs) {
-        const double v0 = D.pv0[j];
         if (MIXED) D.pwf[j] = (float)v0; else D.xhat[j] = v0;
       }
       cl.sync();
@@ -332,9 +332,10 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
         }
         cl.sync();
         const double nw = sh.bcast;
+        // a zero w continues from the fallback start vector
         for (int j = gt; j < n; j += gs) {
-          if (MIXED) D.pwf[j] = nw > 0.0 ? (float)((double)D.xbarf[j] / nw) : 0.0f;
-          else D.xhat[j] = nw > 0.0 ? D.xbar[j] / nw : 0.0;
+          if (MIXED) D.pwf[j] = nw > 0.0 ? (float)((double)D.xbarf[j] / nw) : (float)D.pv0[j];
+          else D.xhat[j] = nw > 0.0 ? D.xbar[j] / nw : D.pv0[j];
         }
         cl.sync();
       }

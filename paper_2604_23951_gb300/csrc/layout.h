@@ -21,12 +21,13 @@ constexpr int kTilePad = 8;  // value / index arrays padded past nnz
 #define GB300LP_HD
 #endif
 
-// Start vector of the power iteration for ||A||_2, entry of original column
-// j: (0.5 + h(j) / 2^32) / sqrt(n) with the multiplicative hash
-// h(j) = j * 2654435761 mod 2^32 -- a fixed vector in no special direction
-// (an all-ones start is orthogonal to the top singular vector whenever the
-// rows of A sum to zero, e.g. A = [1, -1]).  Indexed by the ORIGINAL column,
-// so every storage order starts from the same vector.
+// Fallback start vector of the power iteration for ||A||_2 (which starts
+// from all-ones / sqrt(n) and continues from this vector when a step gives
+// zero: all-ones is orthogonal to A's row space when the rows of A sum to
+// zero, e.g. A = [1, -1]).  Entry of original column j:
+// (0.5 + h(j) / 2^32) / sqrt(n) with the multiplicative hash
+// h(j) = j * 2654435761 mod 2^32.  Indexed by the ORIGINAL column, so every
+// storage order uses the same vector.
 GB300LP_HD inline double power_start(int j, double inv_sqrt_n) {
   const unsigned h = (unsigned)j * 2654435761u;
   return (0.5 + (double)h * (1.0 / 4294967296.0)) * inv_sqrt_n;
@@ -41,7 +42,7 @@ struct Layout {
   std::vector<int2> tA, tT;  // warp tiles
   int nlongA = 0, nlongT = 0;
   std::vector<double> c0, lx0, ux0, lc0, uc0;  // permuted problem vectors
-  std::vector<double> pv0;  // power-iteration start (power_start of cperm)
+  std::vector<double> pv0;  // power-iteration fallback start (power_start of cperm)
   double bnorm = 0, cnorm = 0, off = 0;
 };
 

@@ -219,11 +219,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, 
 }
 
 // v = w / ||w|| (every CTA reduces the partials in the same fixed order)
+// v = w / ||w||; a zero w (the start was orthogonal to A's row space)
+// continues from the fallback start vector
 __global__ void k_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
-                            const double *partials, int G) {
+                            const double *__restrict__ fallback, const double *partials, int G) {
   double nw = sqrt(reduce_partials(partials, Q_PW, G));
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    v[j] = nw > 0.0 ? w[j] / nw : 0.0;
+    v[j] = nw > 0.0 ? w[j] / nw : fallback[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -847,13 +849,14 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
   d->launches += 6;
   bool power = !(o.step_size > 0) && n > 0 && m > 0;
   if (power) {
-    CK(cudaMemcpyAsync(d->pv, d->pv0, sizeof(double) * n, cudaMemcpyDeviceToDevice, d->s));
+    k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
+    d->launches += 1;
     const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     for (int it = 0; it < o.power_iters; ++it) {
       k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());
       k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
                                                        d->partials, d->G, d->errp());
-      k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->partials, d->G);
+      k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->pv0, d->partials, d->G);
       d->launches += 3;
     }
     k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu,

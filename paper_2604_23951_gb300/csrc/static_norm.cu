@@ -86,16 +86,17 @@ __device__ double sn_sum(const double *partials, int nparts) {
 }
 
 // v = w / ||w|| (0 if w = 0)
+// v = w / ||w||; a zero w continues from the fallback start vector
 __global__ void k_sn_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
                                const double *partials, int nparts) {
   const double nw = sqrt(sn_sum(partials, nparts));
+  const double inv_sqrt_n = 1.0 / sqrt((double)n);
   for (int j = blockIdx.x * kSnBlock + threadIdx.x; j < n; j += gridDim.x * kSnBlock)
-    v[j] = nw > 0.0 ? w[j] / nw : 0.0;
+    v[j] = nw > 0.0 ? w[j] / nw : gb300lp::power_start(j, inv_sqrt_n);
 }
 
-__global__ void k_sn_fill(int n, double *v, double inv_sqrt_n) {
-  for (int j = blockIdx.x * kSnBlock + threadIdx.x; j < n; j += gridDim.x * kSnBlock)
-    v[j] = gb300lp::power_start(j, inv_sqrt_n);
+__global__ void k_sn_fill(int n, double *v, double val) {
+  for (int j = blockIdx.x * kSnBlock + threadIdx.x; j < n; j += gridDim.x * kSnBlock) v[j] = val;
 }
 
 __global__ void k_sn_final(const double *partials, int nparts, double *result) {
