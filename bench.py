@@ -190,11 +190,23 @@ def term_hist(codes):
 
 
 def kernel_source_hash():
+    """Hash of the source K1 / K2 are built from: the engine, epilogue, state
+    and layout files, and in solver.cu the block-size constants and the text
+    from the k_primal template through k_dual (other kernels there do not
+    change the profiled launches)."""
+    csrc = os.path.join(ROOT, "paper_2604_23951_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("solver.cu", "device_common.cuh", "spmv_warp.cuh", "pdhg_epi.cuh",
-              "pdhg_state.cuh", "layout.cpp", "layout.h"):
-        with open(os.path.join(ROOT, "paper_2604_23951_gb300", "csrc", f), "rb") as fh:
+    for f in ("device_common.cuh", "spmv_warp.cuh", "pdhg_epi.cuh", "pdhg_state.cuh",
+              "layout.cpp", "layout.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "solver.cu"), "r") as fh:
+        src = fh.read()
+    a = src.index("constexpr int kBlock")
+    h.update(src[a:src.index("\n\n", a)].encode())
+    a = src.index("__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(")
+    b = src.index("__global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(")
+    h.update(src[a:b].encode())
     return h.hexdigest()[:16]
 
 

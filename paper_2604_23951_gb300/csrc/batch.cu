@@ -1359,8 +1359,14 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
       CK(cudaStreamCreateWithFlags(&srv->s, cudaStreamNonBlocking));
       srv->own_stream = true;
     }
+    // bucket streams by size: smaller LPs get the higher scheduling priority
+    // (their blocks are placed first when the buckets' launches compete for
+    // SMs), larger ones a lower one; the solo lane keeps the default (lowest)
+    int prio_least = 0, prio_greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
     for (int b = 0; b < kNumBuckets; ++b) {
-      CK(cudaStreamCreateWithFlags(&srv->bs[b], cudaStreamNonBlocking));
+      const int prio = std::min(prio_least, prio_greatest + b);
+      CK(cudaStreamCreateWithPriority(&srv->bs[b], cudaStreamNonBlocking, prio));
       Bucket &B = srv->buckets[b];
       CK(cudaEventCreate(&B.ev0));
       CK(cudaEventCreate(&B.ev1));

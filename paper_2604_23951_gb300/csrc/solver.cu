@@ -429,10 +429,22 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_cols(
 }
 
 // K4: the check.  eval_only: fill in the KKT fields and mark ITER_LIMIT.
+// One warp per quantity (fixed lane stride over the G partials, fixed
+// shuffle tree: deterministic), all quantities' loads in flight at once; the
+// infeasibility quantities only on the checks that test for it.
 __global__ void k_check(State *st, const double *partials, int G, int eval_only) {
   if (!eval_only && st->status != ST_RUNNING) return;
-  double q[NQ];
-  for (int i = 0; i < Q_CN; ++i) q[i] = reduce_partials(partials, i, G);
+  __shared__ double q[NQ];
+  const int nq = (!eval_only && infeas_due(st->t, st->K, st->infeas_every)) ? Q_CN : Q_ICD;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < nq; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += partials[i * G + b];
+    s = warp_sum(s);
+    if (lane == 0) q[i] = s;
+  }
+  for (int i = nq + (int)threadIdx.x; i < NQ; i += blockDim.x) q[i] = 0.0;
+  __syncthreads();
   if (threadIdx.x != 0) return;
   check_update(st, q, eval_only != 0);
 }
