@@ -334,7 +334,9 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
  * `lp` (lp_get_solution / lp_postsolve work on it).  A problem whose presolve
  * proved it infeasible or unbounded is answered at once (termination
  * LP_INFEASIBLE / LP_UNBOUNDED, no device work).  Fails LP_ERR_BUDGET if the
- * problem alone exceeds the budget. */
+ * problem alone exceeds the budget.  Several threads may submit to one
+ * server at once: a request's device layout is built on its submitting
+ * thread, outside the server's lock. */
 int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket);
 
 /* LP_PENDING while in flight; LP_OK once done: res, x (n), y (m) of the
