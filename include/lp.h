@@ -212,8 +212,12 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
  * postsolve record is kept inside.  Host only.  May be called once.  Each
  * round runs the enabled passes in the order empty rows, empty columns,
  * fixed columns, singleton rows, redundant rows / dominated row sides,
- * doubleton equalities, free column singletons, variable locks; round 1
- * scans everything, later rounds what the previous round changed. */
+ * doubleton equalities, column singletons in inequality rows, free column
+ * singletons, variable locks; round 1 scans everything, later rounds what
+ * the previous round changed.  A round in which these change nothing runs
+ * the parallel-row explorer over every row; the rounds end when that finds
+ * nothing either (or after max_rounds).  Parts run on several host threads;
+ * the result does not depend on the thread count. */
 int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *info);
 
 /* Copy the current (reduced) LP to the device and build its layout (row
