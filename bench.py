@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--solo-nnz", type=int, default=0,
                    help="c4/c5: nonzeros from which a request runs the single-LP path (0: default)")
     p.add_argument("--solo-max", type=int, default=-1, help="c4/c5: concurrent solo requests")
+    p.add_argument("--propagation", action="store_true",
+                   help="c2/c5: presolve also runs primal propagation (opt-in explorer)")
     p.add_argument("--infeas-every", type=int, default=-1,
                    help="infeasibility test every N-th check (0: off; -1: library default)")
     p.add_argument("--launch-ms", type=float, default=0.0,
@@ -173,6 +175,11 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def presolve_rules(pkg, args):
+    """presolve rule mask: the default set, plus primal propagation if asked"""
+    return pkg.LP_RULE_ALL | (pkg.LP_RULE_PRIMAL_PROPAGATION if args.propagation else 0)
 
 
 def solver_kw(args):
@@ -326,7 +333,7 @@ def run_ours(args):
     dev = pkg.TorchDevice(local)
     prec = pkg.LP_MIXED if args.precision == "mixed" else pkg.LP_FP64
     prob = pkg.Problem(lp, dev)
-    info = prob.presolve() if args.workload == "c2" else None
+    info = prob.presolve(enable=presolve_rules(pkg, args)) if args.workload == "c2" else None
     prob.upload()
     m, n, nnz = prob.dims()
     if args.profile_iters > 0:
@@ -383,7 +390,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         p2 = pkg.Problem(lp, dev)
         if args.workload == "c2":
-            p2.presolve()
+            p2.presolve(enable=presolve_rules(pkg, args))
         r2 = p2.solve(precision=prec)
         x, y, z = p2.postsolve()
         torch.cuda.synchronize()
@@ -602,7 +609,7 @@ def run_batch(args):
                     time.sleep(0.0005)
                 arrivals[j] = time.perf_counter()
                 p = pkg.Problem(lp, dev)
-                p.presolve()
+                p.presolve(enable=presolve_rules(pkg, args))
                 probs[j] = p
                 tickets[j] = srv.submit(p)
 
@@ -639,7 +646,7 @@ def run_batch(args):
     for lp in lps:
         ts = time.perf_counter()
         p = pkg.Problem(lp, dev)
-        p.presolve()
+        p.presolve(enable=presolve_rules(pkg, args))
         p.solve(precision=pkg.LP_FP64)
         p.postsolve()
         p.close()

@@ -110,6 +110,11 @@ typedef struct {
 #define LP_RULE_PARALLEL_ROWS 512  /* medium explorer (Table 1): run when a
                                       round of the others changed nothing  */
 #define LP_RULE_ALL 1023
+#define LP_RULE_PRIMAL_PROPAGATION 1024 /* medium explorer (Table 1), not in
+                                           LP_RULE_ALL: bounds implied by the
+                                           rows' activities (a tightened bound
+                                           that ends active hands its reduced
+                                           cost to the row in postsolve)     */
 
 typedef struct {
   int32_t status;          /* LP_PRESOLVE_*                                 */
@@ -122,8 +127,8 @@ typedef struct {
                               fixed_col, singleton_row, redundant_row,
                               dropped_side, doubleton, free_col_singleton,
                               variable locks (dual fixing), inequality
-                              rows made equalities, parallel rows merged;
-                              11 unused                                    */
+                              rows made equalities, parallel rows merged,
+                              bounds tightened by primal propagation       */
   double seconds;
 } lp_presolve_info;
 

@@ -54,6 +54,24 @@ to, else it is set to 0 (an approximate solution of the reduced problem may
 put it slightly on the wrong side), with z updated over row i's entries so
 that c - A^T y - z = 0 still holds.
 
+Primal propagation (Table 1, medium; off unless asked for): in a round
+where the fast passes changed nothing, before parallel rows, every row with
+two or more entries is scanned in increasing index; at most 2 such sweeps
+per presolve (READING: bound propagation converges slowly, each sweep
+finding small further tightenings).  From its activity
+bounds at the start of the row (finite contributions summed in increasing
+column order, infinite ones counted; a column's "others" bound is the total
+minus its own finite contribution, or the total when its own contribution is
+the only infinite one), each entry a_ij x_j gets a_ij x_j >= l_i - max(others)
+and a_ij x_j <= u_i - min(others) where finite.  The implied bound replaces
+the column's when it is tighter by more than 1e-3 max(1, |bound|) (any finite
+value of magnitude at most 1e6 replaces an infinite bound) (READING); an
+implied lower bound above the upper by more than 1e-9 proves infeasibility,
+one above it by less is set to the upper.  Postsolve: a reduced cost z_j
+whose sign points at a tightened bound (z_j > 0 lower, z_j < 0 upper) belongs
+to row i: y_i += z_j / a_ij and z_k -= a_ik z_j / a_ij over the row's entries
+at that time (z_j becomes 0).
+
 Parallel rows (Table 1, medium): rows k and i with the same columns and
 a_k = s a_i.  Rows with two or more entries are grouped by column pattern; in
 increasing index, row k is compared with the earlier rows of its pattern that
@@ -105,6 +123,9 @@ DROP_TOL = 1e-12
 COST_TOL = 1e-12
 PAR_TOL = 1e-12
 PAR_CANDIDATES = 32
+PROP_STEP = 1e-3
+PROP_MAX_BOUND = 1e6
+PROP_SWEEPS = 2
 MAX_ROUNDS = 20
 
 REDUCED, INFEASIBLE, UNBOUNDED, SOLVED = 0, 1, 2, 3
@@ -170,7 +191,7 @@ class Presolver:
         self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
                                       "redundant_row", "dropped_side", "doubleton",
                                       "free_col_singleton", "dual_fix", "ineq_to_eq",
-                                      "parallel_row")}
+                                      "parallel_row", "tightened")}
 
     # -- primitive edits with dirty marking --------------------------------
     def _mark_col_bounds(self, j):
@@ -509,6 +530,83 @@ class Presolver:
         self.counts["parallel_row"] += 1
         self.changed = True
 
+    def _row_sums(self, i):
+        """finite min / max activity sums over ascending columns and the
+        counts of infinite contributions"""
+        smin = smax = 0.0
+        nmin = nmax = 0
+        for j in sorted(self.rows[i]):
+            a = self.rows[i][j]
+            bl, bu = (self.lx[j], self.ux[j]) if a > 0 else (self.ux[j], self.lx[j])
+            if math.isinf(bl):
+                nmin += 1
+            else:
+                smin += a * bl
+            if math.isinf(bu):
+                nmax += 1
+            else:
+                smax += a * bu
+        return smin, nmin, smax, nmax
+
+    def _better(self, new, old, lower):
+        if math.isinf(new):
+            return False
+        if math.isinf(old):
+            return abs(new) <= PROP_MAX_BOUND
+        step = PROP_STEP * max(1.0, abs(old))
+        return new > old + step if lower else new < old - step
+
+    def propagate_row(self, i):
+        lo, hi = self.lo[i], self.hi[i]
+        smin, nmin, smax, nmax = self._row_sums(i)
+        ents = sorted(self.rows[i].items())
+        found = []
+        for j, a in ents:
+            bl, bu = (self.lx[j], self.ux[j]) if a > 0 else (self.ux[j], self.lx[j])
+            if math.isinf(bu):
+                omax = smax if nmax == 1 else INF
+            else:
+                omax = smax - a * bu if nmax == 0 else INF
+            if math.isinf(bl):
+                omin = smin if nmin == 1 else -INF
+            else:
+                omin = smin - a * bl if nmin == 0 else -INF
+            t_lo = lo - omax if not (math.isinf(lo) or math.isinf(omax)) else -INF  # a x_j >= t_lo
+            t_hi = hi - omin if not (math.isinf(hi) or math.isinf(omin)) else INF   # a x_j <= t_hi
+            if a > 0:
+                nl = t_lo / a if not math.isinf(t_lo) else -INF
+                nu = t_hi / a if not math.isinf(t_hi) else INF
+            else:
+                nl = t_hi / a if not math.isinf(t_hi) else -INF
+                nu = t_lo / a if not math.isinf(t_lo) else INF
+            found.append((j, a, nl, nu))
+        for j, a, nl, nu in found:
+            for side, new in ((0, nl), (1, nu)):
+                old = self.lx[j] if side == 0 else self.ux[j]
+                if not self._better(new, old, side == 0):
+                    continue
+                other = self.ux[j] if side == 0 else self.lx[j]
+                if (new > other + FEAS_TOL) if side == 0 else (new < other - FEAS_TOL):
+                    self.status = INFEASIBLE
+                    return
+                if (new > other) if side == 0 else (new < other):
+                    new = other
+                self.records.append(("tighten", j, i, a, side, ents))
+                if side == 0:
+                    self.lx[j] = new
+                else:
+                    self.ux[j] = new
+                self._mark_col_bounds(j)
+                self.counts["tightened"] += 1
+                self.changed = True
+
+    def propagate(self):
+        for i in range(self.m):
+            if self.row_on[i] and len(self.rows[i]) >= 2:
+                self.propagate_row(i)
+                if self.status != REDUCED:
+                    return
+
     def parallel_rows(self):
         reps = {}  # column pattern -> rows not merged, increasing index
         for k in range(self.m):
@@ -527,7 +625,8 @@ class Presolver:
                 lst.append(k)
 
     # -- driver ----------------------------------------------------------------
-    def run(self, max_rounds=MAX_ROUNDS):
+    def run(self, max_rounds=MAX_ROUNDS, propagation=False):
+        sweeps = 0
         rows_c = list(range(self.m))
         cols_c = list(range(self.n))
         rounds = 0
@@ -575,6 +674,11 @@ class Presolver:
                     if self.status != REDUCED:
                         return rounds
             if not self.changed:
+                if propagation and sweeps < PROP_SWEEPS:
+                    sweeps += 1
+                    self.propagate()
+                    if self.status != REDUCED:
+                        return rounds
                 self.parallel_rows()
                 if self.status != REDUCED:
                     return rounds
@@ -607,10 +711,10 @@ class Presolver:
         return lp, rmap, cmap
 
 
-def presolve(lp, max_rounds: int = MAX_ROUNDS) -> PresolveResult:
+def presolve(lp, max_rounds: int = MAX_ROUNDS, propagation: bool = False) -> PresolveResult:
     t0 = time.perf_counter()
     ps = Presolver(lp)
-    rounds = ps.run(max_rounds)
+    rounds = ps.run(max_rounds, propagation)
     red, rmap, cmap = ps.reduced()
     status = ps.status
     if status == REDUCED and red.m == 0 and red.n == 0:
@@ -673,6 +777,14 @@ def postsolve(res: PresolveResult, x_red, y_red, z_red=None):
                 y[i] = 0.0
                 for k, a in entries:
                     z[k] -= a * d
+        elif kind == "tighten":
+            _, j, i, a, side, entries = rec
+            if (side == 0 and z[j] > 0) or (side == 1 and z[j] < 0):
+                d = z[j] / a
+                y[i] += d
+                for k, ak in entries:
+                    z[k] -= ak * d
+                z[j] = 0.0
         elif kind == "parallel_row":
             _, i, k, s, lo_from, hi_from = rec
             if (y[i] > 0 and lo_from) or (y[i] < 0 and hi_from):

@@ -24,6 +24,7 @@ LP_FP64, LP_MIXED = 0, 1
 LP_ENGINE_AUTO, LP_ENGINE_GRID, LP_ENGINE_CLUSTER = 0, 1, 2
 LP_RULE_VARIABLE_LOCKS, LP_RULE_COL_SINGLETON_INEQ, LP_RULE_PARALLEL_ROWS = 128, 256, 512
 LP_RULE_ALL = 1023
+LP_RULE_PRIMAL_PROPAGATION = 1024  # opt-in, not in LP_RULE_ALL
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

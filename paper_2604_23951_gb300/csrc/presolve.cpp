@@ -41,6 +41,9 @@
 //   inequality row i made an equality at one side:  a y_i of the other sign
 //                            is set to 0 and z_r -= a_ir * (0 - y_i) over the
 //                            row's entries at that time
+//   bound of x_j tightened from row i:  z_j of the sign that points at the
+//                            tightened bound moves to the row: y_i += z_j /
+//                            a_ij, z_r -= a_ir z_j / a_ij over its entries
 //   parallel row k (a_k = s a_i) merged into row i:  y_k = y_i / s, y_i = 0
 //                            when y_i's sign points at a side that came
 //                            strictly from row k; else y_k = 0
@@ -71,12 +74,21 @@ enum RecKind {
   REC_FREE_COL = 6,
   REC_ROW_TO_EQ = 7,
   REC_PARALLEL_ROW = 8,
+  REC_TIGHTEN = 9,
 };
 
 enum CountIdx {
   C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
   C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX, C_INEQ_TO_EQ, C_PARALLEL_ROW,
+  C_TIGHTENED,
 };
+
+// Primal propagation: an implied bound replaces a finite one when tighter by
+// more than kPropStep * max(1, |bound|), an infinite one when its magnitude
+// is at most kPropMaxBound.
+constexpr double kPropStep = 1e-3;
+constexpr double kPropMaxBound = 1e6;
+constexpr int kPropSweeps = 2;  // propagation sweeps per presolve
 
 // Parallel rows: coefficients agree to this relative tolerance, and a row is
 // compared with at most this many earlier unmerged rows of its column pattern.
@@ -778,7 +790,85 @@ struct Presolver {
     }
   }
 
+  // Primal propagation (Table 1, medium; enabled by LP_RULE_PRIMAL_PROPAGATION).
+  // From row i's activity bounds at the start of the row (finite
+  // contributions summed in increasing column order, infinite ones counted;
+  // a column's "others" bound is the total minus its own finite part, or the
+  // total when its own part is the only infinite one): a_ij x_j >= l_i -
+  // max(others), a_ij x_j <= u_i - min(others).
+  static bool prop_better(double nw, double old, bool lower) {
+    if (std::isinf(nw)) return false;
+    if (std::isinf(old)) return std::fabs(nw) <= kPropMaxBound;
+    const double step = kPropStep * std::max(1.0, std::fabs(old));
+    return lower ? nw > old + step : nw < old - step;
+  }
+  void propagate_row(int32_t i) {
+    const double lo_i = lo[i], hi_i = hi[i];
+    const int64_t s = rows.start[i];
+    const int32_t len = rows.len[i];
+    double smin = 0.0, smax = 0.0;
+    int nmin = 0, nmax = 0;
+    for (int32_t q = 0; q < len; ++q) {
+      const int32_t j = rows.idx[s + q];
+      const double a = rows.val[s + q];
+      const double bl = a > 0 ? lx[j] : ux[j], bu = a > 0 ? ux[j] : lx[j];
+      if (std::isinf(bl)) ++nmin; else smin += a * bl;
+      if (std::isinf(bu)) ++nmax; else smax += a * bu;
+    }
+    std::vector<double> nls(len), nus(len);
+    for (int32_t q = 0; q < len; ++q) {
+      const int32_t j = rows.idx[s + q];
+      const double a = rows.val[s + q];
+      const double bl = a > 0 ? lx[j] : ux[j], bu = a > 0 ? ux[j] : lx[j];
+      const double omax = std::isinf(bu) ? (nmax == 1 ? smax : kInf) : (nmax == 0 ? smax - a * bu : kInf);
+      const double omin = std::isinf(bl) ? (nmin == 1 ? smin : -kInf) : (nmin == 0 ? smin - a * bl : -kInf);
+      const double t_lo = (!std::isinf(lo_i) && !std::isinf(omax)) ? lo_i - omax : -kInf;
+      const double t_hi = (!std::isinf(hi_i) && !std::isinf(omin)) ? hi_i - omin : kInf;
+      if (a > 0) {
+        nls[q] = std::isinf(t_lo) ? -kInf : t_lo / a;
+        nus[q] = std::isinf(t_hi) ? kInf : t_hi / a;
+      } else {
+        nls[q] = std::isinf(t_hi) ? -kInf : t_hi / a;
+        nus[q] = std::isinf(t_lo) ? kInf : t_lo / a;
+      }
+    }
+    for (int32_t q = 0; q < len; ++q) {
+      const int32_t j = rows.idx[s + q];
+      const double a = rows.val[s + q];
+      for (int side = 0; side < 2; ++side) {
+        double nw = side == 0 ? nls[q] : nus[q];
+        const double old = side == 0 ? lx[j] : ux[j];
+        if (!prop_better(nw, old, side == 0)) continue;
+        const double other = side == 0 ? ux[j] : lx[j];
+        if (side == 0 ? nw > other + kFeasTol : nw < other - kFeasTol) {
+          status = LP_PRESOLVE_INFEASIBLE;
+          return;
+        }
+        if (side == 0 ? nw > other : nw < other) nw = other;
+        {
+          PostsolveRecord &r = push(REC_TIGHTEN);
+          r.j = j; r.i = i; r.a = a; r.flags = side;
+        }
+        const size_t ri = po->records.size() - 1;
+        for (int32_t q2 = 0; q2 < len; ++q2)
+          push_entry(po->records[ri], rows.idx[s + q2], rows.val[s + q2]);
+        if (side == 0) lx[j] = nw; else ux[j] = nw;
+        mark_col_bounds(j);
+        po->counts[C_TIGHTENED]++;
+        changed = true;
+      }
+    }
+  }
+  void propagate() {
+    for (int32_t i = 0; i < m; ++i)
+      if (row_on[i] && rows.len[i] >= 2) {
+        propagate_row(i);
+        if (status != LP_PRESOLVE_REDUCED) return;
+      }
+  }
+
   int run(int max_rounds, int mask) {
+    int prop_sweeps = 0;
     std::vector<int32_t> rc(m), cc(n);
     for (int32_t i = 0; i < m; ++i) rc[i] = i;
     for (int32_t j = 0; j < n; ++j) cc[j] = j;
@@ -852,6 +942,11 @@ struct Presolver {
             if (status != LP_PRESOLVE_REDUCED) return rounds;
           }
       if (!changed) {
+        if ((mask & LP_RULE_PRIMAL_PROPAGATION) && prop_sweeps < kPropSweeps) {
+          ++prop_sweeps;
+          propagate();
+          if (status != LP_PRESOLVE_REDUCED) return rounds;
+        }
         if (mask & LP_RULE_PARALLEL_ROWS) {
           parallel_rows();
           if (status != LP_PRESOLVE_REDUCED) return rounds;
@@ -987,6 +1082,15 @@ void postsolve_run(const PresolveOutcome &po, const HostLP &red, const double *x
           const double d = -y[r.i];
           y[r.i] = 0.0;
           for (int64_t e = r.ent_begin; e < r.ent_end; ++e) z[po.ent_idx[e]] -= po.ent_val[e] * d;
+        }
+        break;
+      }
+      case REC_TIGHTEN: {
+        if ((r.flags == 0 && z[r.j] > 0) || (r.flags == 1 && z[r.j] < 0)) {
+          const double d = z[r.j] / r.a;
+          y[r.i] += d;
+          for (int64_t e = r.ent_begin; e < r.ent_end; ++e) z[po.ent_idx[e]] -= po.ent_val[e] * d;
+          z[r.j] = 0.0;
         }
         break;
       }

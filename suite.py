@@ -100,7 +100,8 @@ def _kkt_original(pkg, lp, x, y) -> float:
         host.close()
 
 
-def run_instance(pkg, dev, lp, eps: float, time_limit: float, precision: int) -> dict:
+def run_instance(pkg, dev, lp, eps: float, time_limit: float, precision: int,
+                 rules: int | None = None) -> dict:
     """Both arms on one LP; times are wall seconds around the API calls."""
     import torch
 
@@ -121,7 +122,7 @@ def run_instance(pkg, dev, lp, eps: float, time_limit: float, precision: int) ->
     t0 = time.perf_counter()
     p = pkg.Problem(lp, dev)
     t1 = time.perf_counter()
-    info = p.presolve()
+    info = p.presolve(enable=pkg.LP_RULE_ALL if rules is None else rules)
     t_pre = time.perf_counter() - t1
     m2, n2, nnz2 = p.dims()
     decided = info.status in (1, 2)  # presolve proved infeasible / unbounded
@@ -180,6 +181,8 @@ def main(argv=None) -> int:
     ap.add_argument("--time-limit", type=float, default=120.0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=SUITE_SEED)
+    ap.add_argument("--propagation", action="store_true",
+                    help="presolve also runs primal propagation (opt-in explorer)")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -202,7 +205,8 @@ def main(argv=None) -> int:
         t0 = time.perf_counter()
         lp = make_instance(nnz, seed)
         t_gen = time.perf_counter() - t0
-        rec = run_instance(pkg, dev, lp, args.eps, args.time_limit, prec)
+        rules = pkg.LP_RULE_ALL | (pkg.LP_RULE_PRIMAL_PROPAGATION if args.propagation else 0)
+        rec = run_instance(pkg, dev, lp, args.eps, args.time_limit, prec, rules)
         rec.update(target_class=cls, size_class=size_class(rec["nnz"]), seed=seed,
                    t_generate=t_gen)
         recs.append(rec)
@@ -210,6 +214,7 @@ def main(argv=None) -> int:
                           for k, v in rec.items()}), flush=True)
         del lp
     out = {"eps_rel": args.eps, "time_limit_s": args.time_limit, "precision": args.precision,
+           "propagation": bool(args.propagation),
            "gpu": torch.cuda.get_device_name(0), "records": recs,
            "summary": {c: summarize([r for r in recs if r["size_class"] == c], args.time_limit)
                        for c in ("small", "medium", "large")}}

@@ -388,3 +388,59 @@ def test_medium_instance_that_met_cost_residue_stays_bounded():
     lp = suite.make_instance(300000, 2010)
     res = PS.presolve(lp)
     assert res.status == PS.REDUCED
+
+
+# ---------------------------------------------------------------------------
+# primal propagation (opt-in medium explorer)
+
+def solve_via_presolve_prop(lp):
+    res = PS.presolve(lp, propagation=True)
+    assert res.status in (PS.REDUCED, PS.SOLVED)
+    red = res.reduced
+    if red.m == 0:
+        xr = np.where(red.c > 0, red.col_lo, np.where(red.c < 0, red.col_hi,
+                                                      np.clip(0.0, red.col_lo, red.col_hi)))
+        yr = np.zeros(0)
+    else:
+        _, xr, yr = highs_solve(red)
+    x, y, z = PS.postsolve(res, xr, yr)
+    return res, x, y, z
+
+
+def test_propagation_worked_example():
+    # x1 + x2 >= 3 with x2 <= 1 implies x1 >= 2; min x1 + 0.5 x2 puts x2 at 1
+    # and x1 at the implied bound, whose reduced cost moves to the row
+    lp = SimpleLP([[1.0, 1.0], [1.0, -1.0]], [1.0, 0.5], [3.0, -20.0], [np.inf, 20.0],
+                  [0.0, 0.0], [10.0, 1.0])
+    res, x, y, z = solve_via_presolve_prop(lp)
+    tight = [r for r in res.records if r[0] == "tighten"]
+    assert any(r[1] == 0 and r[2] == 0 and r[4] == 0 for r in tight)  # x1's lower from row 0
+    assert abs(res.reduced.col_lo[list(res.col_map).index(0)] - 2.0) <= 1e-15
+    p, _, _ = highs_solve(lp)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9 and abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+    assert abs(x[0] - 2.0) <= 1e-9 and y[0] > 0 and abs(z[0]) <= 1e-12
+
+
+def test_propagation_proves_infeasibility():
+    # x1 + x2 >= 3 with both at most 1
+    lp = SimpleLP([[1.0, 1.0], [1.0, -1.0]], [1.0, 1.0], [3.0, -5.0], [np.inf, 5.0],
+                  [0.0, 0.0], [1.0, 1.0])
+    assert PS.presolve(lp).status == PS.REDUCED  # the fast rules alone do not see it
+    assert PS.presolve(lp, propagation=True).status == PS.INFEASIBLE
+
+
+@pytest.mark.parametrize("make", [
+    lambda: lpgen.general_structure(600, 1500, 31, nnz_target=9000, one_sided=0.2),
+    lambda: lpgen.medium_structure(600, 1500, 13, nnz_target=9000),
+    lambda: lpgen.c2_presolvable(scale=0.005),
+])
+def test_propagation_keeps_the_planted_optimum(make):
+    lp = make()
+    res, x, y, z = solve_via_presolve_prop(lp)
+    assert res.counts["tightened"] > 0
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+    g = lp.c - lp.csr().T @ y
+    assert np.max(np.abs(g - z)) <= 1e-8 * (1 + np.max(np.abs(lp.c)))

@@ -98,7 +98,7 @@ def test_reduced_problem_identical(name, make):
     assert list(info.counts) == [ref.counts[k] for k in (
         "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
         "dropped_side", "doubleton", "free_col_singleton", "dual_fix", "ineq_to_eq",
-        "parallel_row")] + [0]
+        "parallel_row", "tightened")]
     np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
     np.testing.assert_array_equal(red.col_idx, r.col_idx)
     np.testing.assert_array_equal(red.val, r.val)
@@ -230,3 +230,53 @@ def test_threaded_paths_match_oracle():
     np.testing.assert_array_equal(red.col_lo, r.col_lo)
     np.testing.assert_array_equal(red.col_hi, r.col_hi)
     assert red.obj_offset == r.obj_offset
+
+
+def _assert_same_reduced(prob, ref, info):
+    assert info.status == ref.status and info.rounds == ref.rounds
+    red, r = prob.data(), ref.reduced
+    assert (red.m, red.n) == (r.m, r.n)
+    np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
+    np.testing.assert_array_equal(red.col_idx, r.col_idx)
+    np.testing.assert_array_equal(red.val, r.val)
+    np.testing.assert_array_equal(red.c, r.c)
+    np.testing.assert_array_equal(red.row_lo, r.row_lo)
+    np.testing.assert_array_equal(red.row_hi, r.row_hi)
+    np.testing.assert_array_equal(red.col_lo, r.col_lo)
+    np.testing.assert_array_equal(red.col_hi, r.col_hi)
+    assert red.obj_offset == r.obj_offset
+
+
+@pytest.mark.parametrize("name,make", [c for c in _cases() if c[0] in
+                                       ("medium", "general_small", "c2_scaled", "tiny_box",
+                                        "medium_b", "variable_locks")])
+def test_primal_propagation_matches_oracle(name, make):
+    _lib_or_skip()
+    lp = make()
+    ref = PS.presolve(lp, propagation=True)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PRIMAL_PROPAGATION)
+    _assert_same_reduced(prob, ref, info)
+    assert info.counts[11] == ref.counts["tightened"]
+    if ref.reduced.m == 0 or ref.status != PS.REDUCED:
+        return
+    _, xr, yr = highs_solve(ref.reduced)
+    rng = np.random.default_rng(1)
+    for scale in (0.0, 1e-3):
+        xp = xr + scale * rng.standard_normal(xr.shape[0])
+        yp = yr + scale * rng.standard_normal(yr.shape[0])
+        xo, yo, zo = PS.postsolve(ref, xp, yp)
+        xc, yc, zc = prob.postsolve_from(xp, yp)
+        tol = 1e-12 * (1 + max(np.max(np.abs(xo)), np.max(np.abs(yo)), np.max(np.abs(zo))))
+        assert np.max(np.abs(xc - xo)) <= tol
+        assert np.max(np.abs(yc - yo)) <= tol
+        assert np.max(np.abs(zc - zo)) <= tol
+
+
+def test_primal_propagation_infeasible_matches_oracle():
+    _lib_or_skip()
+    lp = SimpleLP([[1.0, 1.0], [1.0, -1.0]], [1.0, 1.0], [3.0, -5.0], [INF, 5.0],
+                  [0.0, 0.0], [1.0, 1.0])
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PRIMAL_PROPAGATION)
+    assert info.status == PS.INFEASIBLE == PS.presolve(lp, propagation=True).status
