@@ -50,6 +50,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <limits>
 #include <thread>
 #include <vector>
@@ -94,6 +95,28 @@ constexpr int kPropSweeps = 2;  // propagation sweeps per presolve
 // compared with at most this many earlier unmerged rows of its column pattern.
 constexpr double kParTol = 1e-12;
 constexpr int kParCandidates = 32;
+
+// Worker threads that are always joined, also when an exception unwinds the
+// caller; work whose thread cannot be started runs on the calling thread.
+class ThreadGroup {
+ public:
+  template <class F>
+  void run(const F &f, size_t a, size_t b) {
+    try {
+      ts_.emplace_back(f, a, b);
+    } catch (const std::exception &) {
+      f(a, b);
+    }
+  }
+  void join() {
+    for (std::thread &t : ts_)
+      if (t.joinable()) t.join();
+  }
+  ~ThreadGroup() { join(); }
+
+ private:
+  std::vector<std::thread> ts_;
+};
 
 // Sorted sparse vectors in one pool, each with spare capacity.  A vector that
 // outgrows its capacity moves to the end of the pool with twice the room.
@@ -215,11 +238,11 @@ struct Presolver {
     const int64_t nnz_in = in.row_ptr.empty() ? 0 : in.row_ptr.back();
     const unsigned ncb =
         nnz_in >= 1000000 ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
-    auto fill_cols = [&](int32_t j0, int32_t j1) {
+    auto fill_cols = [&](size_t j0, size_t j1) {
       for (int32_t i = 0; i < m; ++i)
         for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
           const int32_t j = in.col_idx[k];
-          if (j < j0 || j >= j1) continue;
+          if ((size_t)j < j0 || (size_t)j >= j1) continue;
           const double v = in.val[k];
           if (v == 0.0) continue;
           cols.idx[cols.start[j] + cols.len[j]] = i;
@@ -227,10 +250,9 @@ struct Presolver {
           ++cols.len[j];
         }
     };
-    std::vector<std::thread> col_builders;
+    ThreadGroup col_builders;
     for (unsigned t = 0; t < ncb; ++t)
-      col_builders.emplace_back(fill_cols, (int32_t)((int64_t)n * t / ncb),
-                                (int32_t)((int64_t)n * (t + 1) / ncb));
+      col_builders.run(fill_cols, (size_t)n * t / ncb, (size_t)n * (t + 1) / ncb);
     rows.init(m, rl);
     for (int32_t i = 0; i < m; ++i) {
       for (int64_t k = in.row_ptr[i]; k < in.row_ptr[i + 1]; ++k) {
@@ -241,7 +263,7 @@ struct Presolver {
         ++rows.len[i];
       }
     }
-    for (std::thread &th : col_builders) th.join();
+    col_builders.join();
     c = in.c;
     {
       double cmax = 1.0;
@@ -271,10 +293,8 @@ struct Presolver {
       f((size_t)0, count);
       return;
     }
-    std::vector<std::thread> pool;
-    for (unsigned t = 0; t < nt; ++t)
-      pool.emplace_back(f, count * t / nt, count * (t + 1) / nt);
-    for (std::thread &th : pool) th.join();
+    ThreadGroup pool;
+    for (unsigned t = 0; t < nt; ++t) pool.run(f, count * t / nt, count * (t + 1) / nt);
   }
 
   void dirty_row(int32_t i) {
@@ -909,18 +929,9 @@ struct Presolver {
           if (row_on[i] && rows.len[i] >= 1 && lo[i] != hi[i]) cand.push_back(i);
         std::vector<double> amin(cand.size()), amax(cand.size());
         const size_t nc = cand.size();
-        const unsigned nt = nc >= 20000 ? std::min(16u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
-        auto work = [&](size_t a, size_t b) {
+        parallel_for(nc, 20000, [&](size_t a, size_t b) {
           for (size_t q = a; q < b; ++q) activity(cand[q], -1, amin[q], amax[q]);
-        };
-        if (nt <= 1) {
-          work(0, nc);
-        } else {
-          std::vector<std::thread> pool;
-          for (unsigned t = 0; t < nt; ++t)
-            pool.emplace_back(work, nc * t / nt, nc * (t + 1) / nt);
-          for (std::thread &th : pool) th.join();
-        }
+        });
         for (size_t q = 0; q < nc; ++q) redundant_row_with(cand[q], amin[q], amax[q]);
       }
       if (mask & LP_RULE_DOUBLETON)
