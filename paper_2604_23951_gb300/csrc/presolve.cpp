@@ -214,6 +214,7 @@ struct Presolver {
   std::vector<uint8_t> row_on, col_on;
   std::vector<uint8_t> dmark_r, dmark_c;
   std::vector<uint8_t> fixmark, rmark;  // scratch of the batched fixed-column pass
+  std::vector<double> prop_lo, prop_hi;   // scratch of primal propagation (one row)
   std::vector<int32_t> dlist_r, dlist_c;
   bool changed = false;
   int32_t status = LP_PRESOLVE_REDUCED;
@@ -835,7 +836,11 @@ struct Presolver {
       if (std::isinf(bl)) ++nmin; else smin += a * bl;
       if (std::isinf(bu)) ++nmax; else smax += a * bu;
     }
-    std::vector<double> nls(len), nus(len);
+    if ((int32_t)prop_lo.size() < len) {
+      prop_lo.resize(len);
+      prop_hi.resize(len);
+    }
+    double *nls = prop_lo.data(), *nus = prop_hi.data();
     for (int32_t q = 0; q < len; ++q) {
       const int32_t j = rows.idx[s + q];
       const double a = rows.val[s + q];
