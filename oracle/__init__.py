@@ -8,9 +8,11 @@ no code with the CUDA path.
 Contents
 --------
 ``pdhg``      rel-KKT of eq. (2), Ruiz + Pock-Chambolle scaling, power
-              iteration, the PDHG operator, restarted reflected Halpern PDHG.
+              iteration, the PDHG operator, restarted reflected Halpern PDHG,
+              infeasibility / unboundedness certificates.
 ``vertex``    brute-force vertex enumeration for tiny bounded LPs (a pin).
-``presolve``  the simple presolve rules of Sec. 2-3 and their postsolve.
+``presolve``  the presolve rules of Sec. 2-3 (fast explorers, parallel rows,
+              opt-in primal propagation) and their postsolve.
 
 Problems are passed as any object with the attributes ``m, n, row_ptr,
 col_idx, val, c, obj_offset, row_lo, row_hi, col_lo, col_hi`` (the CSR form of

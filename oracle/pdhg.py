@@ -16,8 +16,10 @@ fixed point of the operator T for any step sizes; vertex enumeration and
 and small LPs; with rho = 0 and no anchor the iteration reproduces a textbook
 equality-form PDHG written independently; a 1 x 1 LP has a closed-form
 solution; rel-KKT takes hand-computed values on 1-D examples; the power
-iteration matches numpy's 2-norm; scaling leaves a signed permutation matrix
-unchanged.
+iteration matches numpy's 2-norm (and finds the norm of matrices whose rows
+sum to zero); scaling leaves a signed permutation matrix unchanged; the
+infeasibility certificates accept hand-made Farkas rays and reject
+near-misses, and LPs without an optimum get the status HiGHS reports.
 """
 from __future__ import annotations
 
