@@ -177,6 +177,9 @@ typedef struct {
                           * All in the LP's own units; the returned x, y
                           * are T(z) of that check.                         */
   double eps_infeas;     /* 1e-8                                            */
+  double primal_weight_clamp; /* 10: after each primal-weight update omega
+                          * stays within [omega_0 / c, omega_0 * c], omega_0
+                          * the initial weight (0: no bound; else >= 1)     */
 } lp_solve_opts;
 
 typedef struct {

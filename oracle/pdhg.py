@@ -45,6 +45,7 @@ class Opts:
     beta_nec: float = 0.8
     beta_art: float = 0.36
     theta: float = 0.5  # primal-weight smoothing
+    omega_clamp: float = 10.0  # READING: omega kept within [omega0 / c, omega0 * c] (0: none)
     ruiz_iters: int = 10
     pock_chambolle: bool = True
     power_iters: int = 100
@@ -337,7 +338,10 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
             r > r_prev, or (iii) k >= beta_art t.  On restart: new anchor
             z0' = T(z); primal weight omega <- exp(theta log(dy/dx) +
             (1 - theta) log omega) with dx = ||x0' - x0||, dy = ||y0' - y0||
-            when both exceed 1e-10; z = z0 = T(z); k = 0; r0 = r_prev = r;
+            when both exceed 1e-10, then kept within [omega0 / omega_clamp,
+            omega0 * omega_clamp] (READING, omega_clamp = 10; a weight that
+            drifts by orders of magnitude stalled some planted LPs for
+            100k+ iterations); z = z0 = T(z); k = 0; r0 = r_prev = r;
             skip step 3.  Otherwise r_prev = r.
       3. z <- lam_k ((1 + rho) T(z) - rho z) + (1 - lam_k) z0,  lam_k = (k+1)/(k+2);
          k <- k + 1.   (halpern=False: z <- (1 + rho) T(z) - rho z.)
@@ -412,6 +416,8 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                 if dx > 1e-10 and dy > 1e-10:
                     omega = math.exp(opts.theta * math.log(dy / dx)
                                      + (1.0 - opts.theta) * math.log(omega))
+                if opts.omega_clamp > 0:
+                    omega = min(max(omega, omega0 / opts.omega_clamp), omega0 * opts.omega_clamp)
                 x, y = xh.copy(), yh.copy()
                 x0, y0 = xh.copy(), yh.copy()
                 k = 0

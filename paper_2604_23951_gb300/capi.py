@@ -55,7 +55,7 @@ class lp_solve_opts(C.Structure):
                 ("primal_weight", C.c_double), ("x_init", C.POINTER(C.c_double)),
                 ("y_init", C.POINTER(C.c_double)), ("engine", C.c_int32),
                 ("verbose", C.c_int32), ("infeas_every", C.c_int32),
-                ("eps_infeas", C.c_double)]
+                ("eps_infeas", C.c_double), ("primal_weight_clamp", C.c_double)]
 
 
 class lp_result(C.Structure):

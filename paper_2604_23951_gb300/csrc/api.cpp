@@ -102,6 +102,7 @@ void lp_solve_opts_default(lp_solve_opts *o) {
   std::memset(o, 0, sizeof(*o));
   o->infeas_every = 4;
   o->eps_infeas = 1e-8;
+  o->primal_weight_clamp = 10.0;
   o->eps_rel = 1e-6;
   o->max_iter = 200000;
   o->time_limit_s = 3600.0;
@@ -261,6 +262,7 @@ int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res) {
   if (opts) o = *opts;
   if (!(o.eps_rel >= 0) || o.max_iter < 1 || o.check_every < 1 || o.rho < 0 || o.rho > 1 ||
       o.infeas_every < 0 || !(o.eps_infeas >= 0) ||
+      !(o.primal_weight_clamp == 0.0 || o.primal_weight_clamp >= 1.0) ||
       (o.precision != LP_FP64 && o.precision != LP_MIXED) || o.engine < LP_ENGINE_AUTO ||
       o.engine > LP_ENGINE_CLUSTER)
     return fail(LP_ERR_INVALID, "invalid solve options");

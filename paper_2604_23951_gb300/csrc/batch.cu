@@ -359,6 +359,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
     const double om = C.primal_weight > 0 ? C.primal_weight : ((cn > 0 && bn > 0) ? cn / bn : 1.0);
     st->eta = eta;
     st->omega = om;
+    st->omega0 = om;
     st->tau = eta / om;
     st->sigma = eta * om;
     st->t = 0;
@@ -949,6 +950,7 @@ void state_init(const lp_solve_opts &o, State &st, const Packed &pk) {
   st.eps_rel = o.eps_rel;
   st.eps_infeas = o.eps_infeas;
   st.infeas_every = o.infeas_every;
+  st.omega_clamp = o.primal_weight_clamp;
   st.bnorm = pk.bnorm;
   st.cnorm = pk.cnorm;
   st.off = pk.off;

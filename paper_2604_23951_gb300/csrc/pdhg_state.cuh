@@ -7,7 +7,8 @@
 // record r0 = r_prev = r at the first check, otherwise restart when
 // r <= beta_suff r0, or r <= beta_nec r0 and r > r_prev, or k >= beta_art t;
 // a restart moves the anchor and the iterate to T(z) and smooths the primal
-// weight omega <- exp(theta log(dy / dx) + (1 - theta) log omega).  At every
+// weight omega <- exp(theta log(dy / dx) + (1 - theta) log omega), kept
+// within [omega_0 / clamp, omega_0 * clamp] when omega_clamp > 0.  At every
 // infeas_every-th check that does not stop, the direction T(z) - z0 is
 // tested for a dual ray (LP_INFEASIBLE) and then a primal ray
 // (LP_UNBOUNDED), from the Q_I* quantities.
@@ -24,6 +25,7 @@ struct State {
   double rho, beta_suff, beta_nec, beta_art, theta, eps_rel;
   double eps_infeas;
   int infeas_every;  // 0: no infeasibility test
+  double omega0, omega_clamp;  // initial primal weight; band factor (0: none)
   double r0, r_prev, last_r;
   double bnorm, cnorm, off;
   double rel_kkt, rel_p, rel_d, rel_gap, r_p, r_d, gap, pobj, dobj;
@@ -155,6 +157,8 @@ __device__ __forceinline__ void check_update(State *st, const double *q, bool ev
               (double)kb >= st->beta_art * (double)st->t)) {
     double dx = sqrt(q[Q_XD]), dy = sqrt(q[Q_YD]);
     if (dx > 1e-10 && dy > 1e-10) om = exp(st->theta * log(dy / dx) + (1.0 - st->theta) * log(om));
+    if (st->omega_clamp > 0.0)
+      om = fmin(fmax(om, st->omega0 / st->omega_clamp), st->omega0 * st->omega_clamp);
     st->omega = om;
     st->tau = st->eta / om;
     st->sigma = st->eta * om;

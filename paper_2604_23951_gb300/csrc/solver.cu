@@ -241,6 +241,7 @@ __global__ void k_setup_final(State *st, const double *partials, int G, double e
     double om = omega_given > 0 ? omega_given : ((cn > 0 && bn > 0) ? cn / bn : 1.0);
     st->eta = eta;
     st->omega = om;
+    st->omega0 = om;
     st->tau = eta / om;
     st->sigma = eta * om;
     st->t = 0;
@@ -904,6 +905,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     init.eps_rel = o.eps_rel;
     init.eps_infeas = o.eps_infeas;
     init.infeas_every = o.infeas_every;
+    init.omega_clamp = o.primal_weight_clamp;
     d->infeas_every = o.infeas_every;
     init.bnorm = d->bnorm;
     init.cnorm = d->cnorm;

@@ -358,3 +358,16 @@ def test_feasible_lps_are_never_flagged():
         lp = lpgen.general_structure(300, 700, 100 + s, nnz_target=4000, one_sided=0.3)
         r = oracle.pdhg_solve(lp, oracle.Opts(max_iter=50000, infeas_every=1))
         assert r.status == P.OPTIMAL
+
+
+def test_primal_weight_stays_in_its_band():
+    # item 236 of the C4 batch: unbounded weight updates drift omega down by
+    # 400x and the solve needs 138k iterations; kept within 10x of omega_0 it
+    # reaches 1e-6 in under 3k (the band is the READING of the update)
+    lp = lpgen.c4_batch(count=1, first=236)[0]
+    r = oracle.pdhg_solve(lp, oracle.Opts(max_iter=6000), record_checks=True)
+    w0 = r.omega0
+    assert all(w0 / 10 * (1 - 1e-12) <= c["omega"] <= w0 * 10 * (1 + 1e-12) for c in r.checks)
+    assert r.status == P.OPTIMAL and r.iterations < 6000
+    free = oracle.pdhg_solve(lp, oracle.Opts(max_iter=6000, omega_clamp=0.0), record_checks=True)
+    assert min(c["omega"] for c in free.checks) < w0 / 10  # the band was needed
