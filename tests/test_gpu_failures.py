@@ -134,3 +134,13 @@ def test_server_answers_presolve_infeasible_at_once(pkg, dev):
     got = srv.poll(t)  # no pump needed: decided at submission
     assert got is not None and got[0].termination == pkg.LP_INFEASIBLE
     srv.close()
+
+
+@pytest.mark.parametrize("bad", [{"infeas_every": -1}, {"eps_infeas": -1.0},
+                                 {"primal_weight_clamp": 0.5}, {"primal_weight_clamp": -2.0}])
+def test_invalid_solver_options_are_rejected(pkg, dev, bad):
+    prob = pkg.Problem(lpgen.c1_small(), dev)
+    with pytest.raises(pkg.LPError) as ei:
+        prob.solve(**bad)
+    assert ei.value.code == -1  # LP_ERR_INVALID, before any device work
+    prob.close()
