@@ -1010,29 +1010,36 @@ bool start_solo(lp_server *srv, Request &rq) {
     const double t_admit = now_s();
     Done d;
     d.lp = lp;
-    std::string err;
-    int rc = LP_OK;
-    cudaSetDevice(srv->device);
-    lp_device_ctx ctx{};
-    ctx.alloc = arena_alloc;
-    ctx.free = arena_free;
-    ctx.user = srv;
-    ctx.stream = nullptr;
-    ctx.device = srv->device;
-    DeviceLP *dl = dev_create(&ctx, err);
-    if (!dl) rc = LP_ERR_CUDA;
-    const HostLP &h = problem_current(lp);
-    DeviceSolution sol;
-    if (rc == LP_OK) rc = dev_upload(dl, h, err);
-    if (rc == LP_OK) rc = dev_solve(dl, h, srv->opts, &d.res, sol, err);
-    if (dl) dev_destroy(dl);
-    if (rc == LP_OK) {
-      d.x = std::move(sol.x);
-      d.y = std::move(sol.y);
-      d.z = std::move(sol.z);
-    } else {
+    DeviceLP *dl = nullptr;
+    // no exception may leave a thread: a failure becomes the request's
+    // LP_NUMERICAL answer
+    try {
+      std::string err;
+      int rc = LP_OK;
+      cudaSetDevice(srv->device);
+      lp_device_ctx ctx{};
+      ctx.alloc = arena_alloc;
+      ctx.free = arena_free;
+      ctx.user = srv;
+      ctx.stream = nullptr;
+      ctx.device = srv->device;
+      dl = dev_create(&ctx, err);
+      if (!dl) rc = LP_ERR_CUDA;
+      const HostLP &h = problem_current(lp);
+      DeviceSolution sol;
+      if (rc == LP_OK) rc = dev_upload(dl, h, err);
+      if (rc == LP_OK) rc = dev_solve(dl, h, srv->opts, &d.res, sol, err);
+      if (rc == LP_OK) {
+        d.x = std::move(sol.x);
+        d.y = std::move(sol.y);
+        d.z = std::move(sol.z);
+      } else {
+        d.res.termination = LP_NUMERICAL;
+      }
+    } catch (const std::exception &) {
       d.res.termination = LP_NUMERICAL;
     }
+    if (dl) dev_destroy(dl);
     const double tnow = now_s();
     d.res.t_setup_s = t_admit - t_submit;
     d.res.t_solve_s = tnow - t_admit;
