@@ -110,6 +110,10 @@ typedef struct {
 #define LP_RULE_PARALLEL_ROWS 512  /* medium explorer (Table 1): run when a
                                       round of the others changed nothing  */
 #define LP_RULE_ALL 1023
+#define LP_RULE_PARALLEL_COLS 2048 /* medium explorer (Table 1), not in
+                                      LP_RULE_ALL: columns with a_k = s a_j
+                                      and c_k = s c_j become one variable
+                                      x_j + s x_k (split again in postsolve) */
 #define LP_RULE_PRIMAL_PROPAGATION 1024 /* medium explorer (Table 1), not in
                                            LP_RULE_ALL: bounds implied by the
                                            rows' activities (a tightened bound
@@ -123,12 +127,13 @@ typedef struct {
   int64_t nnz;
   int32_t m0, n0;          /* original sizes                                */
   int64_t nnz0;
-  int64_t counts[12];      /* reductions per rule: empty_row, empty_col,
+  int64_t counts[16];      /* reductions per rule: empty_row, empty_col,
                               fixed_col, singleton_row, redundant_row,
                               dropped_side, doubleton, free_col_singleton,
                               variable locks (dual fixing), inequality
                               rows made equalities, parallel rows merged,
-                              bounds tightened by primal propagation       */
+                              bounds tightened by primal propagation,
+                              parallel columns merged; 13-15 unused        */
   double seconds;
 } lp_presolve_info;
 

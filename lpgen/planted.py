@@ -523,7 +523,8 @@ def tiny_box(m: int, n: int, seed: int, density: float = 0.7) -> PlantedLP:
 
 
 def medium_structure(m: int, n: int, seed: int, nnz_target: int | None = None,
-                     frac_parallel: float = 0.08, frac_slack: float = 0.05) -> PlantedLP:
+                     frac_parallel: float = 0.08, frac_slack: float = 0.05,
+                     frac_parallel_cols: float = 0.0) -> PlantedLP:
     """general_structure (with one-sided rows) plus two planted structures:
 
     * parallel copies: frac_parallel * m extra rows, each a copy of a random
@@ -534,6 +535,11 @@ def medium_structure(m: int, n: int, seed: int, nnz_target: int | None = None,
       inequality row whose y*_i is nonzero, with x* = 0 and either x >= 0 or
       x free; for x >= 0 the coefficient's sign and z* = |a y*_i| / 2 make
       c_j = a y*_i + z*_j of the sign that pushes x_j against the row.
+
+    * parallel columns (frac_parallel_cols * n extra columns, 0 by default):
+      copies s a_j of random columns with two or more entries, cost s c_j, so
+      z*_k = s z*_j; x*_k = 0 with bounds [0, u] when z*_k > 0, [l, 0] when
+      z*_k < 0 and [-w, w] when z*_k = 0.
 
     The planted optimum (x*, y*, z*) stays optimal, so p* is unchanged.
     """
@@ -576,15 +582,33 @@ def medium_structure(m: int, n: int, seed: int, nnz_target: int | None = None,
     top = sp.hstack([A, S])
     bot = sp.hstack([B, sp.csr_matrix((src.shape[0], k))])
     M = sp.vstack([top, bot]).tocsr()
-    M.sort_indices()
-    M.eliminate_zeros()
-    mm, nn = M.shape
     x = np.concatenate([base.x_star, np.zeros(k)])
     z = np.concatenate([base.z_star, z_s])
     y = np.concatenate([base.y_star, np.zeros(src.shape[0])])
     c = np.concatenate([base.c, c_s])
     col_lo = np.concatenate([base.col_lo, np.where(free, -np.inf, 0.0)])
     col_hi = np.concatenate([base.col_hi, np.full(k, np.inf)])
+    npc = int(round(frac_parallel_cols * n))
+    if npc > 0:
+        clen = np.diff(base.csr().tocsc().indptr)
+        srcc = rng.choice(np.nonzero(clen >= 2)[0], npc)
+        sc = rng.choice(np.array([-2.0, -0.5, 0.5, 3.0]), npc)
+        P = (M.tocsc()[:, srcc] @ sp.diags(sc)).tocsr()
+        M = sp.hstack([M, P]).tocsr()
+        zp = sc * z[srcc]
+        w = np.exp(rng.standard_normal(npc)) + 0.1
+        lo_p = np.where(zp > 0, 0.0, -w)
+        hi_p = np.where(zp < 0, 0.0, w)
+        hi_p = np.where(zp > 0, w, hi_p)
+        lo_p = np.where(zp < 0, -w, lo_p)
+        x = np.concatenate([x, np.zeros(npc)])
+        z = np.concatenate([z, zp])
+        c = np.concatenate([c, sc * c[srcc]])
+        col_lo = np.concatenate([col_lo, lo_p])
+        col_hi = np.concatenate([col_hi, hi_p])
+    M.sort_indices()
+    M.eliminate_zeros()
+    mm, nn = M.shape
     return PlantedLP(m=mm, n=nn, row_ptr=M.indptr.astype(np.int64),
                      col_idx=M.indices.astype(np.int32), val=M.data.astype(np.float64), c=c,
                      obj_offset=0.0, row_lo=np.concatenate([base.row_lo, blo]),

@@ -72,6 +72,19 @@ whose sign points at a tightened bound (z_j > 0 lower, z_j < 0 upper) belongs
 to row i: y_i += z_j / a_ij and z_k -= a_ik z_j / a_ij over the row's entries
 at that time (z_j becomes 0).
 
+Parallel columns (Table 1, medium; off unless asked for): after parallel
+rows, columns with two or more entries are grouped by row pattern and, in
+increasing index, column k is compared with at most 32 earlier unmerged
+columns of its pattern; it is parallel to j when a_ik = s a_ij for every row
+(1e-12 relative, s taken at the first row) and c_k = s c_j (1e-12 relative to
+the larger of |c_k|, |s c_j|; columns whose costs are not parallel are left
+alone).  Then a_j x_j + a_k x_k = a_j (x_j + s x_k): column k is removed and
+x_j stands for x_j + s x_k, with bounds [l_j, u_j] + s [l_k, u_k].
+Postsolve splits the merged value v: x_k = proj_[l_k,u_k](0), x_j = v - s x_k,
+and if x_j leaves [l_j, u_j] it is put on the violated bound and
+x_k = proj_[l_k,u_k]((v - x_j) / s); z_k = s z_j.  At an optimum where v sits
+on a merged bound this puts both columns on the bounds that z's sign needs.
+
 Parallel rows (Table 1, medium): rows k and i with the same columns and
 a_k = s a_i.  Rows with two or more entries are grouped by column pattern; in
 increasing index, row k is compared with the earlier rows of its pattern that
@@ -191,7 +204,7 @@ class Presolver:
         self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
                                       "redundant_row", "dropped_side", "doubleton",
                                       "free_col_singleton", "dual_fix", "ineq_to_eq",
-                                      "parallel_row", "tightened")}
+                                      "parallel_row", "tightened", "parallel_col")}
 
     # -- primitive edits with dirty marking --------------------------------
     def _mark_col_bounds(self, j):
@@ -624,8 +637,50 @@ class Presolver:
             else:
                 lst.append(k)
 
+    def _parallel_col_scale(self, j, k):
+        """s with a_k = s a_j and c_k = s c_j (to PAR_TOL), or None"""
+        cj, ck = self.cols[j], self.cols[k]
+        f = min(cj)
+        s = ck[f] / cj[f]
+        for i, a in cj.items():
+            if abs(ck[i] - s * a) > PAR_TOL * abs(ck[i]):
+                return None
+        sc = s * self.c[j]
+        if abs(self.c[k] - sc) > PAR_TOL * max(abs(self.c[k]), abs(sc)):
+            return None
+        return s
+
+    def merge_parallel_col(self, j, k, s):
+        lj, uj, lk, uk = self.lx[j], self.ux[j], self.lx[k], self.ux[k]
+        if s > 0:
+            nl, nu = lj + s * lk, uj + s * uk
+        else:
+            nl, nu = lj + s * uk, uj + s * lk
+        self.records.append(("parallel_col", j, k, s, lj, uj, lk, uk))
+        self._remove_col(k)
+        self.lx[j] = nl
+        self.ux[j] = nu
+        self._mark_col_bounds(j)
+        self.counts["parallel_col"] += 1
+        self.changed = True
+
+    def parallel_cols(self):
+        reps = {}  # row pattern -> columns not merged, increasing index
+        for k in range(self.n):
+            if not self.col_on[k] or len(self.cols[k]) < 2:
+                continue
+            key = tuple(sorted(self.cols[k]))
+            lst = reps.setdefault(key, [])
+            for j in lst[:PAR_CANDIDATES]:
+                s = self._parallel_col_scale(j, k)
+                if s is not None:
+                    self.merge_parallel_col(j, k, s)
+                    break
+            else:
+                lst.append(k)
+
     # -- driver ----------------------------------------------------------------
-    def run(self, max_rounds=MAX_ROUNDS, propagation=False):
+    def run(self, max_rounds=MAX_ROUNDS, propagation=False, parallel_cols=False):
         sweeps = 0
         rows_c = list(range(self.m))
         cols_c = list(range(self.n))
@@ -680,6 +735,8 @@ class Presolver:
                     if self.status != REDUCED:
                         return rounds
                 self.parallel_rows()
+                if parallel_cols and self.status == REDUCED:
+                    self.parallel_cols()
                 if self.status != REDUCED:
                     return rounds
                 if not self.changed:
@@ -711,10 +768,11 @@ class Presolver:
         return lp, rmap, cmap
 
 
-def presolve(lp, max_rounds: int = MAX_ROUNDS, propagation: bool = False) -> PresolveResult:
+def presolve(lp, max_rounds: int = MAX_ROUNDS, propagation: bool = False,
+             parallel_cols: bool = False) -> PresolveResult:
     t0 = time.perf_counter()
     ps = Presolver(lp)
-    rounds = ps.run(max_rounds, propagation)
+    rounds = ps.run(max_rounds, propagation, parallel_cols)
     red, rmap, cmap = ps.reduced()
     status = ps.status
     if status == REDUCED and red.m == 0 and red.n == 0:
@@ -785,6 +843,20 @@ def postsolve(res: PresolveResult, x_red, y_red, z_red=None):
                 for k, ak in entries:
                     z[k] -= ak * d
                 z[j] = 0.0
+        elif kind == "parallel_col":
+            _, j, k, s, lj, uj, lk, uk = rec
+            v = x[j]
+            xk = min(max(0.0, lk), uk)
+            xj = v - s * xk
+            if xj < lj:
+                xj = lj
+                xk = min(max((v - xj) / s, lk), uk)
+            elif xj > uj:
+                xj = uj
+                xk = min(max((v - xj) / s, lk), uk)
+            x[j] = xj
+            x[k] = xk
+            z[k] = s * z[j]
         elif kind == "parallel_row":
             _, i, k, s, lo_from, hi_from = rec
             if (y[i] > 0 and lo_from) or (y[i] < 0 and hi_from):

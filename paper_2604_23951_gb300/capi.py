@@ -25,6 +25,7 @@ LP_ENGINE_AUTO, LP_ENGINE_GRID, LP_ENGINE_CLUSTER = 0, 1, 2
 LP_RULE_VARIABLE_LOCKS, LP_RULE_COL_SINGLETON_INEQ, LP_RULE_PARALLEL_ROWS = 128, 256, 512
 LP_RULE_ALL = 1023
 LP_RULE_PRIMAL_PROPAGATION = 1024  # opt-in, not in LP_RULE_ALL
+LP_RULE_PARALLEL_COLS = 2048  # opt-in, not in LP_RULE_ALL
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -42,7 +43,7 @@ class lp_presolve_opts(C.Structure):
 class lp_presolve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("rounds", C.c_int32), ("m", C.c_int32),
                 ("n", C.c_int32), ("nnz", C.c_int64), ("m0", C.c_int32), ("n0", C.c_int32),
-                ("nnz0", C.c_int64), ("counts", C.c_int64 * 12), ("seconds", C.c_double)]
+                ("nnz0", C.c_int64), ("counts", C.c_int64 * 16), ("seconds", C.c_double)]
 
 
 class lp_solve_opts(C.Structure):

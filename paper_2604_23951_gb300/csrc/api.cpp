@@ -223,7 +223,7 @@ int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *
     info->m0 = lp->orig.m;
     info->n0 = lp->orig.n;
     info->nnz0 = lp->orig.nnz();
-    for (int q = 0; q < 12; ++q) info->counts[q] = lp->po.counts[q];
+    for (int q = 0; q < 16; ++q) info->counts[q] = lp->po.counts[q];
     info->seconds = secs;
   }
   return LP_OK;

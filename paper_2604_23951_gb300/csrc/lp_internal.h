@@ -40,7 +40,7 @@ struct PostsolveRecord {
 struct PresolveOutcome {
   int32_t status = LP_PRESOLVE_REDUCED;
   int32_t rounds = 0;
-  int64_t counts[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t counts[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<PostsolveRecord> records;
   std::vector<int32_t> ent_idx;
   std::vector<double> ent_val;

@@ -44,6 +44,10 @@
 //   bound of x_j tightened from row i:  z_j of the sign that points at the
 //                            tightened bound moves to the row: y_i += z_j /
 //                            a_ij, z_r -= a_ir z_j / a_ij over its entries
+//   parallel column k (a_k = s a_j, c_k = s c_j) merged into x_j + s x_k = v:
+//                            x_k = proj_[l_k,u_k](0), x_j = v - s x_k; if x_j
+//                            leaves its bounds it takes the violated one and
+//                            x_k = proj((v - x_j) / s); z_k = s z_j
 //   parallel row k (a_k = s a_i) merged into row i:  y_k = y_i / s, y_i = 0
 //                            when y_i's sign points at a side that came
 //                            strictly from row k; else y_k = 0
@@ -76,12 +80,13 @@ enum RecKind {
   REC_ROW_TO_EQ = 7,
   REC_PARALLEL_ROW = 8,
   REC_TIGHTEN = 9,
+  REC_PARALLEL_COL = 10,
 };
 
 enum CountIdx {
   C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
   C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX, C_INEQ_TO_EQ, C_PARALLEL_ROW,
-  C_TIGHTENED,
+  C_TIGHTENED, C_PARALLEL_COL,
 };
 
 // Primal propagation: an implied bound replaces a finite one when tighter by
@@ -892,6 +897,84 @@ struct Presolver {
       }
   }
 
+  // Parallel columns (Table 1, medium; enabled by LP_RULE_PARALLEL_COLS):
+  // the column analogue of parallel_rows, with the costs parallel as well.
+  bool same_col_pattern(int32_t j, int32_t k) const {
+    if (cols.len[j] != cols.len[k]) return false;
+    return std::memcmp(&cols.idx[cols.start[j]], &cols.idx[cols.start[k]],
+                       sizeof(int32_t) * cols.len[j]) == 0;
+  }
+  bool parallel_col_scale(int32_t j, int32_t k, double &s) const {
+    const double *vj = &cols.val[cols.start[j]];
+    const double *vk = &cols.val[cols.start[k]];
+    s = vk[0] / vj[0];
+    for (int32_t q = 0; q < cols.len[j]; ++q)
+      if (std::fabs(vk[q] - s * vj[q]) > kParTol * std::fabs(vk[q])) return false;
+    const double sc = s * c[j];
+    return !(std::fabs(c[k] - sc) > kParTol * std::max(std::fabs(c[k]), std::fabs(sc)));
+  }
+  void merge_parallel_col(int32_t j, int32_t k, double s) {
+    const double lj = lx[j], uj = ux[j], lk = lx[k], uk = ux[k];
+    double nl, nu;
+    if (s > 0) { nl = lj + s * lk; nu = uj + s * uk; }
+    else { nl = lj + s * uk; nu = uj + s * lk; }
+    {
+      // the record's b, cj, v, ak hold l_j, u_j, l_k, u_k
+      PostsolveRecord &r = push(REC_PARALLEL_COL);
+      r.j = j; r.k = k; r.a = s; r.b = lj; r.cj = uj; r.v = lk; r.ak = uk;
+    }
+    remove_col(k);
+    lx[j] = nl;
+    ux[j] = nu;
+    mark_col_bounds(j);
+    po->counts[C_PARALLEL_COL]++;
+    changed = true;
+  }
+  void parallel_cols() {
+    std::vector<std::pair<uint64_t, int32_t>> key;
+    for (int32_t j = 0; j < n; ++j)
+      if (col_on[j] && cols.len[j] >= 2) key.emplace_back(0, j);
+    parallel_for(key.size(), 20000, [&](size_t a, size_t b) {
+      for (size_t t = a; t < b; ++t) {
+        const int32_t j = key[t].second;
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)cols.len[j];
+        const int64_t s = cols.start[j];
+        for (int32_t q = 0; q < cols.len[j]; ++q) {
+          h ^= (uint64_t)(uint32_t)cols.idx[s + q];
+          h *= 1099511628211ull;
+        }
+        key[t].first = h;
+      }
+    });
+    std::sort(key.begin(), key.end());
+    struct Merge { int32_t k, j; double s; };
+    std::vector<Merge> merges;
+    std::vector<int32_t> reps;
+    for (size_t a = 0; a < key.size();) {
+      size_t b = a + 1;
+      while (b < key.size() && key[b].first == key[a].first) ++b;
+      if (b - a > 1) {
+        reps.clear();
+        for (size_t t = a; t < b; ++t) {
+          const int32_t k = key[t].second;
+          int found = -1, checked = 0;
+          double s = 0.0;
+          for (int32_t j : reps) {
+            if (!same_col_pattern(j, k)) continue;
+            if (checked++ >= kParCandidates) break;
+            if (parallel_col_scale(j, k, s)) { found = j; break; }
+          }
+          if (found >= 0) merges.push_back({k, found, s});
+          else reps.push_back(k);
+        }
+      }
+      a = b;
+    }
+    std::sort(merges.begin(), merges.end(),
+              [](const Merge &x, const Merge &y) { return x.k < y.k; });
+    for (const Merge &g : merges) merge_parallel_col(g.j, g.k, g.s);
+  }
+
   int run(int max_rounds, int mask) {
     int prop_sweeps = 0;
     std::vector<int32_t> rc(m), cc(n);
@@ -967,6 +1050,7 @@ struct Presolver {
           parallel_rows();
           if (status != LP_PRESOLVE_REDUCED) return rounds;
         }
+        if (mask & LP_RULE_PARALLEL_COLS) parallel_cols();
         if (!changed) break;
       }
       rc.clear();
@@ -1108,6 +1192,23 @@ void postsolve_run(const PresolveOutcome &po, const HostLP &red, const double *x
           for (int64_t e = r.ent_begin; e < r.ent_end; ++e) z[po.ent_idx[e]] -= po.ent_val[e] * d;
           z[r.j] = 0.0;
         }
+        break;
+      }
+      case REC_PARALLEL_COL: {
+        const double s = r.a, lj = r.b, uj = r.cj, lk = r.v, uk = r.ak;
+        const double v = x[r.j];
+        double xk = std::min(std::max(0.0, lk), uk);
+        double xj = v - s * xk;
+        if (xj < lj) {
+          xj = lj;
+          xk = std::min(std::max((v - xj) / s, lk), uk);
+        } else if (xj > uj) {
+          xj = uj;
+          xk = std::min(std::max((v - xj) / s, lk), uk);
+        }
+        x[r.j] = xj;
+        x[r.k] = xk;
+        z[r.k] = s * z[r.j];
         break;
       }
       case REC_PARALLEL_ROW: {

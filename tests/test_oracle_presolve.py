@@ -444,3 +444,50 @@ def test_propagation_keeps_the_planted_optimum(make):
     assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
     g = lp.c - lp.csr().T @ y
     assert np.max(np.abs(g - z)) <= 1e-8 * (1 + np.max(np.abs(lp.c)))
+
+
+# ---------------------------------------------------------------------------
+# parallel columns (opt-in medium explorer)
+
+def test_parallel_columns_worked_example():
+    # column 2 is 2 x column 1 in every row and in the cost: x1 + 2 x2 acts as
+    # one variable x' in [0, 1] + 2 [0, 2] = [0, 5], capped at 4 by row 0
+    A = [[1.0, 2.0, 0.0], [1.0, 2.0, 1.0]]
+    lp = SimpleLP(A, [-1.0, -2.0, 1.0], [-np.inf, 4.0], [4.0, np.inf], [0.0, 0.0, 0.0],
+                  [1.0, 2.0, 10.0])
+    res = PS.presolve(lp, parallel_cols=True)
+    assert res.counts["parallel_col"] == 1
+    rec = [r for r in res.records if r[0] == "parallel_col"][0]
+    assert rec[1:4] == (0, 1, 2.0)
+    red = res.reduced
+    _, xr, yr = highs_solve(red) if red.m else (None, np.zeros(red.n), np.zeros(0))
+    if red.m == 0:
+        xr = np.where(red.c > 0, red.col_lo, np.where(red.c < 0, red.col_hi, 0.0))
+    x, y, z = PS.postsolve(res, xr, yr)
+    p, _, _ = highs_solve(lp)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9 and abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+    assert 0.0 <= x[0] <= 1.0 and 0.0 <= x[1] <= 2.0
+
+
+@pytest.mark.parametrize("seed", [13, 21])
+def test_parallel_columns_keep_the_planted_optimum(seed):
+    lp = lpgen.medium_structure(600, 1500, seed, nnz_target=9000, frac_parallel_cols=0.05)
+    res = PS.presolve(lp, parallel_cols=True)
+    assert res.counts["parallel_col"] >= 30
+    red = res.reduced
+    _, xr, yr = highs_solve(red)
+    x, y, z = PS.postsolve(res, xr, yr)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))
+    g = lp.c - lp.csr().T @ y
+    assert np.max(np.abs(g - z)) <= 1e-8 * (1 + np.max(np.abs(lp.c)))
+    assert np.all(x >= lp.col_lo - 1e-9) and np.all(x <= lp.col_hi + 1e-9)
+
+
+def test_parallel_columns_need_parallel_costs():
+    # same columns but c_2 != 2 c_1: not merged
+    lp = SimpleLP([[1.0, 2.0], [1.0, 2.0]], [1.0, 3.0], [1.0, -5.0], [5.0, 5.0], [0.0, 0.0],
+                  [4.0, 4.0])
+    assert PS.presolve(lp, parallel_cols=True).counts["parallel_col"] == 0

@@ -98,7 +98,7 @@ def test_reduced_problem_identical(name, make):
     assert list(info.counts) == [ref.counts[k] for k in (
         "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
         "dropped_side", "doubleton", "free_col_singleton", "dual_fix", "ineq_to_eq",
-        "parallel_row", "tightened")]
+        "parallel_row", "tightened", "parallel_col")] + [0, 0, 0]
     np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
     np.testing.assert_array_equal(red.col_idx, r.col_idx)
     np.testing.assert_array_equal(red.val, r.val)
@@ -280,3 +280,36 @@ def test_primal_propagation_infeasible_matches_oracle():
     prob = pkg.Problem(lp, None)
     info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PRIMAL_PROPAGATION)
     assert info.status == PS.INFEASIBLE == PS.presolve(lp, propagation=True).status
+
+
+@pytest.mark.parametrize("seed", [13, 21])
+def test_parallel_columns_match_oracle(seed):
+    _lib_or_skip()
+    lp = lpgen.medium_structure(600, 1500, seed, nnz_target=9000, frac_parallel_cols=0.05)
+    ref = PS.presolve(lp, parallel_cols=True)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PARALLEL_COLS)
+    _assert_same_reduced(prob, ref, info)
+    assert info.counts[12] == ref.counts["parallel_col"] > 0
+    _, xr, yr = highs_solve(ref.reduced)
+    rng = np.random.default_rng(2)
+    for scale in (0.0, 1e-3):
+        xp = xr + scale * rng.standard_normal(xr.shape[0])
+        yp = yr + scale * rng.standard_normal(yr.shape[0])
+        xo, yo, zo = PS.postsolve(ref, xp, yp)
+        xc, yc, zc = prob.postsolve_from(xp, yp)
+        tol = 1e-12 * (1 + max(np.max(np.abs(xo)), np.max(np.abs(yo)), np.max(np.abs(zo))))
+        assert np.max(np.abs(xc - xo)) <= tol
+        assert np.max(np.abs(yc - yo)) <= tol
+        assert np.max(np.abs(zc - zo)) <= tol
+
+
+def test_all_medium_explorers_together_match_oracle():
+    _lib_or_skip()
+    lp = lpgen.medium_structure(900, 2000, 29, nnz_target=15000, frac_parallel=0.2,
+                                frac_slack=0.1, frac_parallel_cols=0.05)
+    ref = PS.presolve(lp, propagation=True, parallel_cols=True)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PARALLEL_COLS
+                         | pkg.LP_RULE_PRIMAL_PROPAGATION)
+    _assert_same_reduced(prob, ref, info)
