@@ -228,8 +228,9 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
  * doubleton equalities, column singletons in inequality rows, free column
  * singletons, variable locks; round 1 scans everything, later rounds what
  * the previous round changed.  A round in which these change nothing runs
- * the parallel-row explorer over every row; the rounds end when that finds
- * nothing either (or after max_rounds).  Parts run on several host threads;
+ * the medium explorers over every row / column: primal propagation (if
+ * enabled), parallel rows, parallel columns (if enabled); the rounds end
+ * when they find nothing either (or after max_rounds).  Parts run on several host threads;
  * the result does not depend on the thread count. */
 int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *info);
 

@@ -18,8 +18,10 @@ Schedule (READING): each round runs the passes
 each pass scanning its candidates in increasing index order.  Round 1 scans
 every row and column; later rounds scan the rows and columns marked dirty in
 the previous round.  A round in which these fast passes change nothing runs
-the medium explorer of Table 1 implemented here, parallel rows, over every
-row; the rounds stop when that finds nothing either, or after 20 rounds.
+the medium explorers of Table 1 implemented here -- primal propagation (if
+asked for), parallel rows, parallel columns (if asked for) -- over every row
+or column; the rounds stop when they find nothing either, or after 20
+rounds.
 
 Dirty marking: removing, adding or changing an entry (i, j) dirties row i and
 column j; changing row bounds dirties the row; changing column bounds dirties
