@@ -110,6 +110,12 @@ typedef struct {
 #define LP_RULE_PARALLEL_ROWS 512  /* medium explorer (Table 1): run when a
                                       round of the others changed nothing  */
 #define LP_RULE_ALL 1023
+#define LP_RULE_DUAL_PROPAGATION 4096 /* medium explorer (Table 1), not in
+                                         LP_RULE_ALL: one sweep of dual
+                                         bounds from the columns' dual
+                                         constraints; rows with a signed dual
+                                         become equalities, columns with a
+                                         signed reduced cost are fixed       */
 #define LP_RULE_PARALLEL_COLS 2048 /* medium explorer (Table 1), not in
                                       LP_RULE_ALL: columns with a_k = s a_j
                                       and c_k = s c_j become one variable
@@ -133,7 +139,9 @@ typedef struct {
                               variable locks (dual fixing), inequality
                               rows made equalities, parallel rows merged,
                               bounds tightened by primal propagation,
-                              parallel columns merged; 13-15 unused        */
+                              parallel columns merged, dual propagation
+                              (rows made equalities + columns fixed);
+                              14-15 unused                                 */
   double seconds;
 } lp_presolve_info;
 
@@ -229,7 +237,8 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
  * singletons, variable locks; round 1 scans everything, later rounds what
  * the previous round changed.  A round in which these change nothing runs
  * the medium explorers over every row / column: primal propagation (if
- * enabled), parallel rows, parallel columns (if enabled); the rounds end
+ * enabled), dual propagation (if enabled, once), parallel rows, parallel
+ * columns (if enabled); the rounds end
  * when they find nothing either (or after max_rounds).  Parts run on several host threads;
  * the result does not depend on the thread count. */
 int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *info);

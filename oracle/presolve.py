@@ -19,7 +19,8 @@ each pass scanning its candidates in increasing index order.  Round 1 scans
 every row and column; later rounds scan the rows and columns marked dirty in
 the previous round.  A round in which these fast passes change nothing runs
 the medium explorers of Table 1 implemented here -- primal propagation (if
-asked for), parallel rows, parallel columns (if asked for) -- over every row
+asked for), dual propagation (if asked for, once), parallel rows, parallel
+columns (if asked for) -- over every row
 or column; the rounds stop when they find nothing either, or after 20
 rounds.
 
@@ -73,6 +74,24 @@ one above it by less is set to the upper.  Postsolve: a reduced cost z_j
 whose sign points at a tightened bound (z_j > 0 lower, z_j < 0 upper) belongs
 to row i: y_i += z_j / a_ij and z_k -= a_ik z_j / a_ij over the row's entries
 at that time (z_j becomes 0).
+
+Dual propagation (Table 1, medium; off unless asked for): at a fixpoint,
+after primal propagation, one sweep bounds the duals.  Every row starts with
+the sign domain eq. (2) gives y_i (y_i >= 0 when only l_i is finite, <= 0 when
+only u_i is, free otherwise); every column j with x_j not boxed bounds
+S_j = sum_i a_ij y_i by c_j - z_j with z_j's sign domain (S_j <= c_j when only
+l_j is finite, >= c_j when only u_j is, = c_j when x_j is free), and in
+increasing column order each of its rows gets the bound S_j minus the other
+rows' dual activity implies (activities as in primal propagation, from the
+bounds at the start of the column).  Then, in increasing index, an
+inequality row whose dual is at least 1e-9 becomes the equality at its
+(finite) lower side, at most -1e-9 at its upper side (the reduction and
+postsolve of a column singleton in an inequality row), and a column whose
+reduced cost c_j - S_j is, over the final dual box, above 1e-9 max(1, |c_j|)
+is fixed at its (finite) lower bound, below minus that at its upper bound
+(the fixed-column reduction).  Every optimal dual lies in the box, so these
+are dual reductions like variable locks (READING: one sweep, tolerance
+1e-9).
 
 Parallel columns (Table 1, medium; off unless asked for): after parallel
 rows, columns with two or more entries are grouped by row pattern and, in
@@ -141,6 +160,7 @@ PAR_CANDIDATES = 32
 PROP_STEP = 1e-3
 PROP_MAX_BOUND = 1e6
 PROP_SWEEPS = 2
+DPROP_TOL = 1e-9
 MAX_ROUNDS = 20
 
 REDUCED, INFEASIBLE, UNBOUNDED, SOLVED = 0, 1, 2, 3
@@ -206,7 +226,8 @@ class Presolver:
         self.counts = {k: 0 for k in ("empty_row", "empty_col", "fixed_col", "singleton_row",
                                       "redundant_row", "dropped_side", "doubleton",
                                       "free_col_singleton", "dual_fix", "ineq_to_eq",
-                                      "parallel_row", "tightened", "parallel_col")}
+                                      "parallel_row", "tightened", "parallel_col",
+                                      "dual_prop")}
 
     # -- primitive edits with dirty marking --------------------------------
     def _mark_col_bounds(self, j):
@@ -622,6 +643,109 @@ class Presolver:
                 if self.status != REDUCED:
                     return
 
+    @staticmethod
+    def _range_sums(terms):
+        """finite sums of the lower / upper ends of a list of (lo, hi)
+        contributions and the counts of infinite ones"""
+        slo = shi = 0.0
+        nlo = nhi = 0
+        for lo, hi in terms:
+            if math.isinf(lo):
+                nlo += 1
+            else:
+                slo += lo
+            if math.isinf(hi):
+                nhi += 1
+            else:
+                shi += hi
+        return slo, nlo, shi, nhi
+
+    @staticmethod
+    def _scaled_range(a, lo, hi):
+        """range of a * y for y in [lo, hi]"""
+        if a > 0:
+            return (a * lo if not math.isinf(lo) else -INF, a * hi if not math.isinf(hi) else INF)
+        return (a * hi if not math.isinf(hi) else -INF, a * lo if not math.isinf(lo) else INF)
+
+    def dual_propagate(self):
+        yl, yu = {}, {}
+        for i in range(self.m):
+            if self.row_on[i]:
+                yl[i] = 0.0 if math.isinf(self.hi[i]) else -INF
+                yu[i] = 0.0 if math.isinf(self.lo[i]) else INF
+        for j in range(self.n):
+            if not self.col_on[j] or not self.cols[j]:
+                continue
+            lf, uf = not math.isinf(self.lx[j]), not math.isinf(self.ux[j])
+            if lf and uf:
+                continue
+            cj = self.c[j]
+            dl = -INF if lf else cj
+            du = INF if uf else cj
+            ents = sorted(self.cols[j].items())
+            terms = [self._scaled_range(a, yl[i], yu[i]) for i, a in ents]
+            slo, nlo, shi, nhi = self._range_sums(terms)
+            found = []
+            for (i, a), (tlo, thi) in zip(ents, terms):
+                if math.isinf(thi):
+                    omax = shi if nhi == 1 else INF
+                else:
+                    omax = shi - thi if nhi == 0 else INF
+                if math.isinf(tlo):
+                    omin = slo if nlo == 1 else -INF
+                else:
+                    omin = slo - tlo if nlo == 0 else -INF
+                # a y_i in [dl - omax, du - omin]
+                t_lo = dl - omax if not (math.isinf(dl) or math.isinf(omax)) else -INF
+                t_hi = du - omin if not (math.isinf(du) or math.isinf(omin)) else INF
+                if a > 0:
+                    nl = t_lo / a if not math.isinf(t_lo) else -INF
+                    nu = t_hi / a if not math.isinf(t_hi) else INF
+                else:
+                    nl = t_hi / a if not math.isinf(t_hi) else -INF
+                    nu = t_lo / a if not math.isinf(t_lo) else INF
+                found.append((i, nl, nu))
+            for i, nl, nu in found:
+                if nl > yl[i]:
+                    yl[i] = nl
+                if nu < yu[i]:
+                    yu[i] = nu
+        for i in range(self.m):
+            if not self.row_on[i] or self.lo[i] == self.hi[i] or not self.rows[i]:
+                continue
+            if yl[i] >= DPROP_TOL and not math.isinf(self.lo[i]):
+                side = 1
+                self.hi[i] = self.lo[i]
+            elif yu[i] <= -DPROP_TOL and not math.isinf(self.hi[i]):
+                side = -1
+                self.lo[i] = self.hi[i]
+            else:
+                continue
+            self.records.append(("row_to_eq", i, side, sorted(self.rows[i].items())))
+            self.dirty_r.add(i)
+            self.counts["dual_prop"] += 1
+            self.changed = True
+        for j in range(self.n):
+            if not self.col_on[j] or not self.cols[j] or self.lx[j] == self.ux[j]:
+                continue
+            terms = [self._scaled_range(a, yl[i], yu[i]) for i, a in sorted(self.cols[j].items())]
+            slo, nlo, shi, nhi = self._range_sums(terms)
+            cj = self.c[j]
+            tol = DPROP_TOL * max(1.0, abs(cj))
+            zmin = cj - shi if nhi == 0 else -INF
+            zmax = cj - slo if nlo == 0 else INF
+            if zmin > tol and not math.isinf(self.lx[j]):
+                v = self.lx[j]
+            elif zmax < -tol and not math.isinf(self.ux[j]):
+                v = self.ux[j]
+            else:
+                continue
+            self.lx[j] = v
+            self.ux[j] = v
+            self.fixed_col(j)
+            self.counts["fixed_col"] -= 1
+            self.counts["dual_prop"] += 1
+
     def parallel_rows(self):
         reps = {}  # column pattern -> rows not merged, increasing index
         for k in range(self.m):
@@ -682,8 +806,10 @@ class Presolver:
                 lst.append(k)
 
     # -- driver ----------------------------------------------------------------
-    def run(self, max_rounds=MAX_ROUNDS, propagation=False, parallel_cols=False):
+    def run(self, max_rounds=MAX_ROUNDS, propagation=False, parallel_cols=False,
+            dual_propagation=False):
         sweeps = 0
+        dsweeps = 0
         rows_c = list(range(self.m))
         cols_c = list(range(self.n))
         rounds = 0
@@ -736,6 +862,9 @@ class Presolver:
                     self.propagate()
                     if self.status != REDUCED:
                         return rounds
+                if dual_propagation and dsweeps < 1:
+                    dsweeps += 1
+                    self.dual_propagate()
                 self.parallel_rows()
                 if parallel_cols and self.status == REDUCED:
                     self.parallel_cols()
@@ -771,10 +900,10 @@ class Presolver:
 
 
 def presolve(lp, max_rounds: int = MAX_ROUNDS, propagation: bool = False,
-             parallel_cols: bool = False) -> PresolveResult:
+             parallel_cols: bool = False, dual_propagation: bool = False) -> PresolveResult:
     t0 = time.perf_counter()
     ps = Presolver(lp)
-    rounds = ps.run(max_rounds, propagation, parallel_cols)
+    rounds = ps.run(max_rounds, propagation, parallel_cols, dual_propagation)
     red, rmap, cmap = ps.reduced()
     status = ps.status
     if status == REDUCED and red.m == 0 and red.n == 0:

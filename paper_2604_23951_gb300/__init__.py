@@ -14,6 +14,7 @@ from .capi import (  # noqa: F401
     LP_RULE_ALL,
     LP_RULE_COL_SINGLETON_INEQ,
     LP_RULE_PARALLEL_ROWS,
+    LP_RULE_DUAL_PROPAGATION,
     LP_RULE_PARALLEL_COLS,
     LP_RULE_PRIMAL_PROPAGATION,
     LP_RULE_VARIABLE_LOCKS,

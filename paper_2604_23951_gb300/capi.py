@@ -26,6 +26,7 @@ LP_RULE_VARIABLE_LOCKS, LP_RULE_COL_SINGLETON_INEQ, LP_RULE_PARALLEL_ROWS = 128,
 LP_RULE_ALL = 1023
 LP_RULE_PRIMAL_PROPAGATION = 1024  # opt-in, not in LP_RULE_ALL
 LP_RULE_PARALLEL_COLS = 2048  # opt-in, not in LP_RULE_ALL
+LP_RULE_DUAL_PROPAGATION = 4096  # opt-in, not in LP_RULE_ALL
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

@@ -86,8 +86,10 @@ enum RecKind {
 enum CountIdx {
   C_EMPTY_ROW = 0, C_EMPTY_COL, C_FIXED_COL, C_SINGLETON_ROW, C_REDUNDANT_ROW,
   C_DROPPED_SIDE, C_DOUBLETON, C_FREE_COL, C_DUAL_FIX, C_INEQ_TO_EQ, C_PARALLEL_ROW,
-  C_TIGHTENED, C_PARALLEL_COL,
+  C_TIGHTENED, C_PARALLEL_COL, C_DUAL_PROP,
 };
+
+constexpr double kDualPropTol = 1e-9;  // a dual / reduced cost this far from 0 has a sign
 
 // Primal propagation: an implied bound replaces a finite one when tighter by
 // more than kPropStep * max(1, |bound|), an infinite one when its magnitude
@@ -897,6 +899,125 @@ struct Presolver {
       }
   }
 
+  // Dual propagation (Table 1, medium; enabled by LP_RULE_DUAL_PROPAGATION):
+  // one sweep of dual bounds.  Rows start from the sign domain of y_i; each
+  // column j with x_j not boxed bounds S_j = sum_i a_ij y_i by c_j - z_j with
+  // z_j's sign domain, and its rows (ascending) get the bounds S_j minus the
+  // others' dual activity implies (from the bounds at the start of the
+  // column).  Rows whose dual is bounded away from 0 become equalities, then
+  // columns whose reduced cost is are fixed (dual reductions).
+  static void scaled_range(double a, double lo, double hi, double &rlo, double &rhi) {
+    if (a > 0) {
+      rlo = std::isinf(lo) ? -kInf : a * lo;
+      rhi = std::isinf(hi) ? kInf : a * hi;
+    } else {
+      rlo = std::isinf(hi) ? -kInf : a * hi;
+      rhi = std::isinf(lo) ? kInf : a * lo;
+    }
+  }
+  void dual_propagate() {
+    std::vector<double> yl(m, -kInf), yu(m, kInf);
+    for (int32_t i = 0; i < m; ++i)
+      if (row_on[i]) {
+        yl[i] = std::isinf(hi[i]) ? 0.0 : -kInf;
+        yu[i] = std::isinf(lo[i]) ? 0.0 : kInf;
+      }
+    std::vector<double> tlo, thi, nls, nus;
+    for (int32_t j = 0; j < n; ++j) {
+      if (!col_on[j] || cols.len[j] == 0) continue;
+      const bool lf = !std::isinf(lx[j]), uf = !std::isinf(ux[j]);
+      if (lf && uf) continue;
+      const double cj = c[j];
+      const double dl = lf ? -kInf : cj, du = uf ? kInf : cj;
+      const int64_t s0 = cols.start[j];
+      const int32_t len = cols.len[j];
+      tlo.resize(len);
+      thi.resize(len);
+      nls.resize(len);
+      nus.resize(len);
+      double slo = 0.0, shi = 0.0;
+      int nlo = 0, nhi = 0;
+      for (int32_t q = 0; q < len; ++q) {
+        const int32_t i = cols.idx[s0 + q];
+        scaled_range(cols.val[s0 + q], yl[i], yu[i], tlo[q], thi[q]);
+        if (std::isinf(tlo[q])) ++nlo; else slo += tlo[q];
+        if (std::isinf(thi[q])) ++nhi; else shi += thi[q];
+      }
+      for (int32_t q = 0; q < len; ++q) {
+        const double a = cols.val[s0 + q];
+        const double omax = std::isinf(thi[q]) ? (nhi == 1 ? shi : kInf)
+                                               : (nhi == 0 ? shi - thi[q] : kInf);
+        const double omin = std::isinf(tlo[q]) ? (nlo == 1 ? slo : -kInf)
+                                               : (nlo == 0 ? slo - tlo[q] : -kInf);
+        const double t_lo = (!std::isinf(dl) && !std::isinf(omax)) ? dl - omax : -kInf;
+        const double t_hi = (!std::isinf(du) && !std::isinf(omin)) ? du - omin : kInf;
+        if (a > 0) {
+          nls[q] = std::isinf(t_lo) ? -kInf : t_lo / a;
+          nus[q] = std::isinf(t_hi) ? kInf : t_hi / a;
+        } else {
+          nls[q] = std::isinf(t_hi) ? -kInf : t_hi / a;
+          nus[q] = std::isinf(t_lo) ? kInf : t_lo / a;
+        }
+      }
+      for (int32_t q = 0; q < len; ++q) {
+        const int32_t i = cols.idx[s0 + q];
+        if (nls[q] > yl[i]) yl[i] = nls[q];
+        if (nus[q] < yu[i]) yu[i] = nus[q];
+      }
+    }
+    for (int32_t i = 0; i < m; ++i) {
+      if (!row_on[i] || lo[i] == hi[i] || rows.len[i] == 0) continue;
+      int side;
+      if (yl[i] >= kDualPropTol && !std::isinf(lo[i])) {
+        side = 1;
+        hi[i] = lo[i];
+      } else if (yu[i] <= -kDualPropTol && !std::isinf(hi[i])) {
+        side = -1;
+        lo[i] = hi[i];
+      } else {
+        continue;
+      }
+      {
+        PostsolveRecord &r = push(REC_ROW_TO_EQ);
+        r.i = i;
+        r.flags = side > 0 ? 1 : 2;
+      }
+      const size_t ri = po->records.size() - 1;
+      const int64_t s = rows.start[i];
+      for (int32_t q = 0; q < rows.len[i]; ++q)
+        push_entry(po->records[ri], rows.idx[s + q], rows.val[s + q]);
+      dirty_row(i);
+      po->counts[C_DUAL_PROP]++;
+      changed = true;
+    }
+    for (int32_t j = 0; j < n; ++j) {
+      if (!col_on[j] || cols.len[j] == 0 || lx[j] == ux[j]) continue;
+      const int64_t s0 = cols.start[j];
+      double slo = 0.0, shi = 0.0;
+      int nlo = 0, nhi = 0;
+      for (int32_t q = 0; q < cols.len[j]; ++q) {
+        const int32_t i = cols.idx[s0 + q];
+        double rlo, rhi;
+        scaled_range(cols.val[s0 + q], yl[i], yu[i], rlo, rhi);
+        if (std::isinf(rlo)) ++nlo; else slo += rlo;
+        if (std::isinf(rhi)) ++nhi; else shi += rhi;
+      }
+      const double cj = c[j];
+      const double tol = kDualPropTol * std::max(1.0, std::fabs(cj));
+      const double zmin = nhi == 0 ? cj - shi : -kInf;
+      const double zmax = nlo == 0 ? cj - slo : kInf;
+      double v;
+      if (zmin > tol && !std::isinf(lx[j])) v = lx[j];
+      else if (zmax < -tol && !std::isinf(ux[j])) v = ux[j];
+      else continue;
+      lx[j] = v;
+      ux[j] = v;
+      fixed_col(j);
+      po->counts[C_FIXED_COL]--;
+      po->counts[C_DUAL_PROP]++;
+    }
+  }
+
   // Parallel columns (Table 1, medium; enabled by LP_RULE_PARALLEL_COLS):
   // the column analogue of parallel_rows, with the costs parallel as well.
   bool same_col_pattern(int32_t j, int32_t k) const {
@@ -976,7 +1097,7 @@ struct Presolver {
   }
 
   int run(int max_rounds, int mask) {
-    int prop_sweeps = 0;
+    int prop_sweeps = 0, dual_sweeps = 0;
     std::vector<int32_t> rc(m), cc(n);
     for (int32_t i = 0; i < m; ++i) rc[i] = i;
     for (int32_t j = 0; j < n; ++j) cc[j] = j;
@@ -1045,6 +1166,10 @@ struct Presolver {
           ++prop_sweeps;
           propagate();
           if (status != LP_PRESOLVE_REDUCED) return rounds;
+        }
+        if ((mask & LP_RULE_DUAL_PROPAGATION) && dual_sweeps < 1) {
+          ++dual_sweeps;
+          dual_propagate();
         }
         if (mask & LP_RULE_PARALLEL_ROWS) {
           parallel_rows();

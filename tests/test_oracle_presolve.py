@@ -491,3 +491,49 @@ def test_parallel_columns_need_parallel_costs():
     lp = SimpleLP([[1.0, 2.0], [1.0, 2.0]], [1.0, 3.0], [1.0, -5.0], [5.0, 5.0], [0.0, 0.0],
                   [4.0, 4.0])
     assert PS.presolve(lp, parallel_cols=True).counts["parallel_col"] == 0
+
+
+# ---------------------------------------------------------------------------
+# dual propagation (opt-in medium explorer)
+
+def _dual_prop_example():
+    # x1 >= 0 with c1 = -3 in x1 + x2 >= 1 (y0 >= 0) and x1 - x3 <= 5 (y1 <= 0):
+    # its dual constraint y0 + y1 <= -3 forces y1 <= -3, so row 1 is active at
+    # its upper side in every optimum (variable locks and column singletons
+    # see nothing here)
+    return SimpleLP([[1.0, 1.0, 0.0], [1.0, 0.0, -1.0]], [-3.0, 1.0, 0.0], [1.0, -np.inf],
+                    [np.inf, 5.0], [0.0, 0.0, 0.0], [np.inf, np.inf, 10.0])
+
+
+def test_dual_propagation_worked_example():
+    lp = _dual_prop_example()
+    assert PS.presolve(lp).counts["ineq_to_eq"] == 0
+    res = PS.presolve(lp, dual_propagation=True)
+    assert res.counts["dual_prop"] >= 1
+    assert ("row_to_eq", 1, -1) == [r for r in res.records if r[0] == "row_to_eq"][0][:3]
+    p, xh, yh = highs_solve(lp)
+    assert abs(xh[0] - xh[2] - 5.0) <= 1e-9 and yh[1] <= -3.0 + 1e-9
+    red = res.reduced
+    if red.m:
+        _, xr, yr = highs_solve(red)
+    else:
+        xr = np.where(red.c > 0, red.col_lo, np.where(red.c < 0, red.col_hi, 0.0))
+        yr = np.zeros(0)
+    x, y, z = PS.postsolve(res, xr, yr)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-9 and abs(k["p"] - p) <= 1e-9 * (1 + abs(p))
+
+
+@pytest.mark.parametrize("make", [
+    lambda: lpgen.general_structure(600, 1500, 31, nnz_target=9000, one_sided=0.2),
+    lambda: lpgen.medium_structure(600, 1500, 13, nnz_target=9000),
+    lambda: lpgen.c2_presolvable(scale=0.005),
+])
+def test_dual_propagation_keeps_the_planted_optimum(make):
+    lp = make()
+    res = PS.presolve(lp, dual_propagation=True)
+    _, xr, yr = highs_solve(res.reduced)
+    x, y, z = PS.postsolve(res, xr, yr)
+    k = oracle.rel_kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    assert abs(k["p"] - lp.p_star) <= 1e-8 * (1 + abs(lp.p_star))

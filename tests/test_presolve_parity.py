@@ -98,7 +98,7 @@ def test_reduced_problem_identical(name, make):
     assert list(info.counts) == [ref.counts[k] for k in (
         "empty_row", "empty_col", "fixed_col", "singleton_row", "redundant_row",
         "dropped_side", "doubleton", "free_col_singleton", "dual_fix", "ineq_to_eq",
-        "parallel_row", "tightened", "parallel_col")] + [0, 0, 0]
+        "parallel_row", "tightened", "parallel_col", "dual_prop")] + [0, 0]
     np.testing.assert_array_equal(red.row_ptr, r.row_ptr)
     np.testing.assert_array_equal(red.col_idx, r.col_idx)
     np.testing.assert_array_equal(red.val, r.val)
@@ -308,8 +308,34 @@ def test_all_medium_explorers_together_match_oracle():
     _lib_or_skip()
     lp = lpgen.medium_structure(900, 2000, 29, nnz_target=15000, frac_parallel=0.2,
                                 frac_slack=0.1, frac_parallel_cols=0.05)
-    ref = PS.presolve(lp, propagation=True, parallel_cols=True)
+    ref = PS.presolve(lp, propagation=True, parallel_cols=True, dual_propagation=True)
     prob = pkg.Problem(lp, None)
     info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_PARALLEL_COLS
-                         | pkg.LP_RULE_PRIMAL_PROPAGATION)
+                         | pkg.LP_RULE_PRIMAL_PROPAGATION | pkg.LP_RULE_DUAL_PROPAGATION)
     _assert_same_reduced(prob, ref, info)
+
+
+def _dual_prop_example():
+    return SimpleLP([[1.0, 1.0, 0.0], [1.0, 0.0, -1.0]], [-3.0, 1.0, 0.0], [1.0, -INF],
+                    [INF, 5.0], [0.0, 0.0, 0.0], [INF, INF, 10.0])
+
+
+@pytest.mark.parametrize("name,make", [("example", _dual_prop_example)] +
+                         [c for c in _cases() if c[0] in ("general_small", "medium", "c2_scaled",
+                                                          "variable_locks", "ineq_singletons")])
+def test_dual_propagation_matches_oracle(name, make):
+    _lib_or_skip()
+    lp = make()
+    ref = PS.presolve(lp, dual_propagation=True)
+    prob = pkg.Problem(lp, None)
+    info = prob.presolve(enable=pkg.LP_RULE_ALL | pkg.LP_RULE_DUAL_PROPAGATION)
+    _assert_same_reduced(prob, ref, info)
+    assert info.counts[13] == ref.counts["dual_prop"]
+    if ref.reduced.m == 0 or ref.status != PS.REDUCED:
+        return
+    _, xr, yr = highs_solve(ref.reduced)
+    xo, yo, zo = PS.postsolve(ref, xr, yr)
+    xc, yc, zc = prob.postsolve_from(xr, yr)
+    tol = 1e-12 * (1 + max(np.max(np.abs(xo)), np.max(np.abs(yo)), np.max(np.abs(zo))))
+    assert np.max(np.abs(xc - xo)) <= tol and np.max(np.abs(yc - yo)) <= tol
+    assert np.max(np.abs(zc - zo)) <= tol
