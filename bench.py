@@ -187,6 +187,16 @@ def solver_kw(args):
     return {"infeas_every": args.infeas_every} if args.infeas_every >= 0 else {}
 
 
+def fifo_latencies(arrivals, services):
+    """arrival-to-completion times when requests are served one at a time in
+    arrival order with the given service times"""
+    out, free_at = [], 0.0
+    for a, sv in zip(arrivals, services):
+        free_at = max(free_at, a) + sv
+        out.append(free_at - a)
+    return out
+
+
 def term_hist(codes):
     """{termination code: count} (0 optimal, 1 iteration limit, 2 time limit,
     3 numerical, 4 infeasible, 5 unbounded, 6 cancelled)"""
@@ -653,10 +663,7 @@ def run_batch(args):
         single.append(time.perf_counter() - ts)
     t_single = time.perf_counter() - t0
     offered = len(lps) / max(reqs[-1].arrival_s, 1e-9)
-    fifo, free_at = [], 0.0
-    for rq, sv in zip(reqs, single):
-        free_at = max(free_at, rq.arrival_s) + sv
-        fifo.append(free_at - rq.arrival_s)
+    fifo = fifo_latencies([rq.arrival_s for rq in reqs], single)
     line = {
         "metric": METRIC, "value": world * len(lps) / el, "unit": "requests/s", "n_gpus": world,
         "steps": 1, "warmup": max(1, args.warmup // 3), "ms_per_step": el * 1e3,
