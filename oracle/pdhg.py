@@ -19,7 +19,12 @@ solution; rel-KKT takes hand-computed values on 1-D examples; the power
 iteration matches numpy's 2-norm (and finds the norm of matrices whose rows
 sum to zero); scaling leaves a signed permutation matrix unchanged; the
 infeasibility certificates accept hand-made Farkas rays and reject
-near-misses, and LPs without an optimum get the status HiGHS reports.
+near-misses, and LPs without an optimum get the status HiGHS reports; on an
+LP whose operator T is constant (fixed columns, free rows) the iterates have
+a closed form, which fixes the restart residual ||z - T(z)||_omega at every
+check, the check at which criterion (i) and criterion (ii) each first fire,
+and the primal weight after the restart for two values of theta (and its
+band).
 """
 from __future__ import annotations
 
@@ -404,6 +409,8 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                 break
             r = math.sqrt(omega * float(np.sum((x - xh) ** 2))
                           + float(np.sum((y - yh) ** 2)) / omega)
+            if record_checks:
+                checks[-1]["r"] = r
             if k == 0:
                 r0 = r_prev = r
             elif opts.restarts and (
@@ -423,6 +430,9 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                 k = 0
                 r0 = r_prev = r
                 restarts += 1
+                if record_checks:
+                    checks[-1]["restart"] = True
+                    checks[-1]["omega_after"] = omega
                 t += 1
                 if record_iterates and t <= record_iterates:
                     iterates.append((sc.dc * x, sc.dr * y))

@@ -371,3 +371,101 @@ def test_primal_weight_stays_in_its_band():
     assert r.status == P.OPTIMAL and r.iterations < 6000
     free = oracle.pdhg_solve(lp, oracle.Opts(max_iter=6000, omega_clamp=0.0), record_checks=True)
     assert min(c["omega"] for c in free.checks) < w0 / 10  # the band was needed
+
+
+# ---------------------------------------------------------------------------
+# restart criteria (i), (ii) and the primal-weight update, on an LP whose
+# operator T is constant, so every iterate has a closed form
+#
+# Two fixed columns (l = u = 0) and two free rows (l = -inf, u = +inf), no
+# scaling.  Whatever z = (x, y) is, T(z) = (0, 0): x^ = proj_[0,0](.) = 0,
+# and for a free row y^ = v + sigma proj_R(-v / sigma) = 0.  With omega_0 = 16
+# and eta = 1/16 (tau = 1/256, sigma = 1) both are exact in floating point.
+# Start at x = u0 with ||u0|| = 3 and y = w0 with ||w0|| = 12, so
+# d_k = z_k - T(z_k) = z_k and R = ||d_0||_omega = sqrt(16 * 9 + 144 / 16)
+# = sqrt(153).
+#
+# Halpern, rho = 0:  z_{k+1} = lam_k z* + (1 - lam_k) z_0  =>  d_k = d_0 / (k + 1).
+# Halpern, rho = 1:  d_{k+1} = -lam_k d_k + (1 - lam_k) d_0  =>  d_1 = 0,
+#                    d_2 = d_0 / 3, d_3 = 0, d_4 = d_0 / 5, ...
+# On a restart at T(z) = z* the primal weight moves with dx = ||x^ - x0|| = 3,
+# dy = ||y^ - y0|| = 12: omega = (dy / dx)^theta * omega_prev^(1 - theta).
+
+_U0 = np.array([3 * 0.6, 3 * 0.8])
+_W0 = np.array([12 * 0.6, -12 * 0.8])
+_R = math.sqrt(153.0)
+
+
+def _constant_T_lp():
+    A = np.array([[1.0, 2.0], [3.0, 4.0]])
+    inf = np.inf
+    return SimpleLP(A, [1.0, -2.0], [-inf, -inf], [inf, inf], [0.0, 0.0], [0.0, 0.0])
+
+
+def _constant_T_run(rho, K, beta_suff, beta_nec, max_iter, theta=0.25):
+    opts = P.Opts(eps_rel=-1.0, max_iter=max_iter, check_every=K, rho=rho, beta_suff=beta_suff,
+                  beta_nec=beta_nec, beta_art=2.0, theta=theta, ruiz_iters=0,
+                  pock_chambolle=False, infeas_every=0)
+    return oracle.pdhg_solve(_constant_T_lp(), opts, eta=1.0 / 16.0, omega0=16.0,
+                             x_init=_U0, y_init=_W0, record_checks=True)
+
+
+def test_restart_criterion_sufficient_decay_hand_derived():
+    # rho = 0, checks at t = 0, 2, 4: r = R, R / 3, R / 5.  (ii) and (iii) are
+    # off (beta_nec < 0, beta_art = 2 > k / t).  (i) r <= 0.21 r0 first holds
+    # at k = 4 (1/5 <= 0.21 < 1/3).
+    r = _constant_T_run(rho=0.0, K=2, beta_suff=0.21, beta_nec=-1.0, max_iter=5)
+    ch = {c["t"]: c for c in r.checks}
+    assert sorted(ch) == [0, 2, 4]
+    for t, div in ((0, 1), (2, 3), (4, 5)):
+        assert abs(ch[t]["r"] - _R / div) <= 1e-14 * _R, (t, ch[t]["r"])
+    assert not ch[0].get("restart") and not ch[2].get("restart")
+    assert ch[4].get("restart") and r.restarts == 1
+    # just above the threshold (0.19 < 1/5) the check at t = 4 does not restart
+    r = _constant_T_run(rho=0.0, K=2, beta_suff=0.19, beta_nec=-1.0, max_iter=5)
+    assert r.restarts == 0
+
+
+def test_restart_criterion_necessary_decay_and_growth_hand_derived():
+    # rho = 1, a check every iteration: r = R, 0, R / 3, 0, R / 5.  (i) is off
+    # (beta_suff < 0) until r0 becomes 0 after the first restart.
+    # beta_nec = 0.8: at t = 1 r = 0 does not exceed r_prev = R; at t = 2
+    # r = R / 3 <= 0.8 R and R / 3 > r_prev = 0: restart.
+    r = _constant_T_run(rho=1.0, K=1, beta_suff=-1.0, beta_nec=0.8, max_iter=3)
+    ch = {c["t"]: c for c in r.checks}
+    assert abs(ch[0]["r"] - _R) <= 1e-14 * _R
+    assert ch[1]["r"] == 0.0 and not ch[1].get("restart")
+    assert abs(ch[2]["r"] - _R / 3) <= 1e-14 * _R and ch[2].get("restart")
+    assert r.restarts == 1
+    # beta_nec = 0.3: R / 3 > 0.3 R keeps t = 2 going; t = 3 has r ~ 0 < r_prev;
+    # t = 4 has r = R / 5 <= 0.3 R and R / 5 > r_prev: the first restart is at t = 4
+    r = _constant_T_run(rho=1.0, K=1, beta_suff=-1.0, beta_nec=0.3, max_iter=5)
+    ch = {c["t"]: c for c in r.checks}
+    assert [t for t in sorted(ch) if ch[t].get("restart")] == [4]
+    assert abs(ch[4]["r"] - _R / 5) <= 1e-14 * _R
+
+
+def test_primal_weight_update_hand_derived():
+    # the restart of the test above at t = 2, with dx = 3, dy = 12, omega = 16:
+    # theta = 1/4: (12/3)^(1/4) * 16^(3/4) = sqrt(2) * 8
+    r = _constant_T_run(rho=1.0, K=1, beta_suff=-1.0, beta_nec=0.8, max_iter=3, theta=0.25)
+    assert abs(r.omega - 8.0 * math.sqrt(2.0)) <= 1e-13
+    # theta = 3/4: 4^(3/4) * 16^(1/4) = 2 sqrt(2) * 2
+    r = _constant_T_run(rho=1.0, K=1, beta_suff=-1.0, beta_nec=0.8, max_iter=3, theta=0.75)
+    assert abs(r.omega - 4.0 * math.sqrt(2.0)) <= 1e-13
+    # no restart yet: the weight is still omega_0
+    r = _constant_T_run(rho=1.0, K=1, beta_suff=-1.0, beta_nec=0.8, max_iter=2)
+    assert r.omega == 16.0 and r.restarts == 0
+
+
+def test_primal_weight_band_clamps_the_update():
+    # dy / dx = 12 / 3e-6 = 4e6: (4e6)^(1/4) * 8 = 357.8 > 10 * omega_0 = 160
+    lp = _constant_T_lp()
+    opts = P.Opts(eps_rel=-1.0, max_iter=3, check_every=1, rho=1.0, beta_suff=-1.0,
+                  beta_nec=0.8, beta_art=2.0, theta=0.25, ruiz_iters=0, pock_chambolle=False,
+                  infeas_every=0)
+    r = oracle.pdhg_solve(lp, opts, eta=1.0 / 16.0, omega0=16.0, x_init=_U0 * 1e-6, y_init=_W0)
+    assert r.restarts == 1 and r.omega == 160.0
+    opts.omega_clamp = 0.0
+    r = oracle.pdhg_solve(lp, opts, eta=1.0 / 16.0, omega0=16.0, x_init=_U0 * 1e-6, y_init=_W0)
+    assert abs(r.omega - 8.0 * (4e6) ** 0.25) <= 1e-9 * r.omega
