@@ -328,7 +328,10 @@ void lp_destroy(lp_problem *lp);
  * All work vectors live in one file-scope device array of 2^20 doubles
  * (8 MiB) that every GPU loading the library holds until the process exits.
  * The first call on a device looks up that array's device address (a
- * one-time set-up per device): make it before any stream capture.  Every
+ * one-time set-up per device, repeated only if the device's context has
+ * been replaced, e.g. after cudaDeviceReset): make the first call before
+ * any stream capture.  m + 2 n must be at most 1,047,551 (else
+ * LP_ERR_INVALID); m = 0 or n = 0 gives 0 without touching the GPU.  Every
  * call shares the array and it keeps the last call's contents; calls that
  * overlap on the GPU (other streams, other threads) race on it.  The call
  * returns after synchronizing `stream`. */

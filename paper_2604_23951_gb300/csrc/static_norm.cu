@@ -35,7 +35,31 @@ static __device__ __align__(256) double g_norm_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+// per device: the context the address was looked up in, and the address
+struct ScratchAddr {
+  void *ctx = nullptr;
+  double *ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+// the calling thread's current CUDA context (through the driver entry point,
+// so the library needs no link against the driver library), or nullptr when
+// it cannot be queried
+void *current_context() {
+  using CtxGetCurrent = int (*)(void **);
+  static CtxGetCurrent fn = []() -> CtxGetCurrent {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<CtxGetCurrent>(f);
+  }();
+  void *ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 // out[r] = sum_k val[k] * vec[col[k]] (one warp per row); with `partials`,
 // each CTA also stores its sum of out[r]^2 in partials[blockIdx.x]
@@ -104,24 +128,32 @@ __global__ void k_sn_final(const double *partials, int nparts, double *result) {
   if (threadIdx.x == 0) *result = sqrt(s);
 }
 
-// the device address of g_norm_scratch for the current device (set-up on the
-// first call per device)
+// The device address of g_norm_scratch for the current device.  It is
+// looked up (cudaGetSymbolAddress, with that device current) on the first
+// call per device and again whenever the device's current context has
+// changed since (after a cudaDeviceReset the module, and so the array, is
+// loaded afresh in a new context and the old address is stale).  If the
+// context cannot be queried, it is looked up on every call.
 double *scratch_for_device(int dev, std::string &err) {
   if (dev < 0 || dev >= kMaxDevices) {
     err = "device index out of range";
     return nullptr;
   }
+  void *ctx = current_context();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchAddr &a = g_scratch[dev];
+  if (!a.ptr || !ctx || a.ctx != ctx) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
     if (e != cudaSuccess) {
       err = std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
       return nullptr;
     }
-    g_scratch_ptr[dev] = static_cast<double *>(p);
+    a.ptr = static_cast<double *>(p);
+    // the lookup may have created the primary context: record the one in use
+    a.ctx = ctx ? current_context() : nullptr;
   }
-  return g_scratch_ptr[dev];
+  return a.ptr;
 }
 
 }  // namespace
