@@ -193,6 +193,15 @@ typedef struct {
   double primal_weight_clamp; /* 10: after each primal-weight update omega
                           * stays within [omega_0 / c, omega_0 * c], omega_0
                           * the initial weight (0: no bound; else >= 1)     */
+  int32_t refine_original; /* 3: for a presolved problem, after an optimal
+                          * solve the reduced solution is postsolved and its
+                          * rel-KKT measured on the ORIGINAL LP (host, FP64);
+                          * while that exceeds eps_rel (postsolve can amplify
+                          * the reduced LP's error), the reduced LP is solved
+                          * again with a tolerance ten times tighter, warm-
+                          * started from the last solution, at most this many
+                          * times (0: no check).  Applies to lp_solve and to
+                          * served requests (lp_batch_poll).                 */
 } lp_solve_opts;
 
 typedef struct {
@@ -209,6 +218,14 @@ typedef struct {
   int64_t kernel_launches; /* kernels launched by this call                 */
   int64_t fp32_iterations; /* LP_MIXED: iterations run with the FP32 SpMV
                               before the switch to FP64 (see lp_solve)      */
+  double rel_kkt_original; /* rel-KKT of the postsolved point on the original
+                              LP (host, FP64) when the problem was presolved
+                              and refine_original > 0; otherwise the same as
+                              rel_kkt (the current LP is the original)      */
+  int32_t refinements;     /* re-solves at a tighter tolerance that the
+                              original-LP check asked for (iterations and
+                              times above include them)                     */
+  int32_t pad_;
 } lp_result;
 
 /* Defaults above; always call before filling in a field. */

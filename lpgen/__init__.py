@@ -16,6 +16,7 @@ c = A^T y* + z*.  Hence p* = c^T x* equals the dual objective at (y*, z*).
 from .planted import (  # noqa: F401
     BASE_SEED,
     PlantedLP,
+    amplified_postsolve,
     c1_small,
     c2_presolvable,
     c3_powerlaw,

@@ -616,3 +616,39 @@ def medium_structure(m: int, n: int, seed: int, nnz_target: int | None = None,
                      x_star=x, y_star=y, z_star=z, p_star=float(c @ x),
                      name=f"medium_{mm}x{nn}",
                      meta={"parallel": int(src.shape[0]), "slack": int(k)})
+
+
+def amplified_postsolve(m: int = 300, n: int = 700, seed: int = BASE_SEED + 41,
+                        shrink: float = 30.0, fixed_value: float = 1.0,
+                        fixed_cost: float = 0.7) -> PlantedLP:
+    """An LP whose presolve shrinks nothing but the row norm it is measured by.
+
+    Start from equality_nonneg(m, n, seed) (rows A x = b, x >= 0) and append
+    one fixed column (l = u = fixed_value) with entry a_i = -(1 - 1/shrink)
+    b_i / fixed_value in every row; the original rows become A x + a x_f =
+    b / shrink.  Removing the fixed column gives back rows with right-hand
+    side b, so the reduced LP's bhat is `shrink` times the original's while
+    every row residual is the same: a point at relative KKT error eps on the
+    reduced LP can be up to shrink * eps off on the original.  The planted
+    optimum (x*, fixed_value), y*, z* (z_f free on a fixed column) stays
+    optimal; p* = c^T x* + fixed_cost * fixed_value.
+    """
+    import scipy.sparse as sp
+
+    base = equality_nonneg(m, n, seed)
+    b = base.row_lo
+    a = -(1.0 - 1.0 / shrink) * b / fixed_value
+    A = sp.hstack([base.csr(), sp.csr_matrix(a.reshape(-1, 1))]).tocsr()
+    A.sort_indices()
+    rhs = b + a * fixed_value
+    x = np.concatenate([base.x_star, [fixed_value]])
+    y = base.y_star
+    c = np.concatenate([base.c, [fixed_cost]])
+    z = np.concatenate([base.z_star, [fixed_cost - float(a @ y)]])
+    return PlantedLP(m=m, n=n + 1, row_ptr=A.indptr.astype(np.int64),
+                     col_idx=A.indices.astype(np.int32), val=A.data.astype(np.float64), c=c,
+                     obj_offset=0.0, row_lo=rhs.copy(), row_hi=rhs.copy(),
+                     col_lo=np.concatenate([base.col_lo, [fixed_value]]),
+                     col_hi=np.concatenate([base.col_hi, [fixed_value]]), x_star=x, y_star=y,
+                     z_star=z, p_star=float(c @ x), name="amplified_postsolve",
+                     meta={"shrink": shrink})

@@ -57,7 +57,8 @@ class lp_solve_opts(C.Structure):
                 ("primal_weight", C.c_double), ("x_init", C.POINTER(C.c_double)),
                 ("y_init", C.POINTER(C.c_double)), ("engine", C.c_int32),
                 ("verbose", C.c_int32), ("infeas_every", C.c_int32),
-                ("eps_infeas", C.c_double), ("primal_weight_clamp", C.c_double)]
+                ("eps_infeas", C.c_double), ("primal_weight_clamp", C.c_double),
+                ("refine_original", C.c_int32)]
 
 
 class lp_result(C.Structure):
@@ -67,7 +68,9 @@ class lp_result(C.Structure):
                 ("gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("eta", C.c_double), ("omega", C.c_double), ("t_setup_s", C.c_double),
                 ("t_solve_s", C.c_double), ("t_total_s", C.c_double),
-                ("kernel_launches", C.c_int64), ("fp32_iterations", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("fp32_iterations", C.c_int64),
+                ("rel_kkt_original", C.c_double), ("refinements", C.c_int32),
+                ("pad_", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

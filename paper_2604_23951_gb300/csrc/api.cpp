@@ -71,6 +71,18 @@ int problem_proven_status(const lp_problem *lp) {
   if (lp->po.status == LP_PRESOLVE_UNBOUNDED) return LP_UNBOUNDED;
   return -1;
 }
+// rel-KKT on the original LP of the postsolved reduced solution (x, y, z of
+// the current LP), or -1 when the problem was not presolved (the current LP
+// is the original and the device measure already applies to it)
+double problem_original_kkt(const lp_problem *lp, const double *x, const double *y,
+                            const double *z) {
+  if (!lp->presolved) return -1.0;
+  std::vector<double> X(lp->orig.n), Y(lp->orig.m), Z(lp->orig.n);
+  postsolve_run(lp->po, lp->cur, x, y, z, X.data(), Y.data(), Z.data());
+  double k[9];
+  host_rel_kkt(lp->orig, X.data(), Y.data(), k);
+  return k[0];
+}
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z) {
   lp->sol.x = x;
@@ -79,6 +91,16 @@ void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
   lp->sol.xi = x;
   lp->sol.yi = y;
   lp->sol.valid = true;
+}
+}  // namespace gb300lp
+
+namespace gb300lp {
+bool valid_solve_opts(const lp_solve_opts &o) {
+  return o.eps_rel >= 0 && o.max_iter >= 1 && o.check_every >= 1 && o.rho >= 0 && o.rho <= 1 &&
+         o.infeas_every >= 0 && o.eps_infeas >= 0 &&
+         (o.primal_weight_clamp == 0.0 || o.primal_weight_clamp >= 1.0) &&
+         (o.precision == LP_FP64 || o.precision == LP_MIXED) && o.engine >= LP_ENGINE_AUTO &&
+         o.engine <= LP_ENGINE_CLUSTER && o.refine_original >= 0 && o.refine_original <= 8;
 }
 }  // namespace gb300lp
 
@@ -103,6 +125,7 @@ void lp_solve_opts_default(lp_solve_opts *o) {
   o->infeas_every = 4;
   o->eps_infeas = 1e-8;
   o->primal_weight_clamp = 10.0;
+  o->refine_original = 3;
   o->eps_rel = 1e-6;
   o->max_iter = 200000;
   o->time_limit_s = 3600.0;
@@ -260,36 +283,60 @@ int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res) {
   lp_solve_opts o;
   lp_solve_opts_default(&o);
   if (opts) o = *opts;
-  if (!(o.eps_rel >= 0) || o.max_iter < 1 || o.check_every < 1 || o.rho < 0 || o.rho > 1 ||
-      o.infeas_every < 0 || !(o.eps_infeas >= 0) ||
-      !(o.primal_weight_clamp == 0.0 || o.primal_weight_clamp >= 1.0) ||
-      (o.precision != LP_FP64 && o.precision != LP_MIXED) || o.engine < LP_ENGINE_AUTO ||
-      o.engine > LP_ENGINE_CLUSTER)
-    return fail(LP_ERR_INVALID, "invalid solve options");
+  if (!valid_solve_opts(o)) return fail(LP_ERR_INVALID, "invalid solve options");
   std::string err;
-  const bool cluster = o.engine == LP_ENGINE_CLUSTER ||
-                       (o.engine == LP_ENGINE_AUTO && lp->cur.nnz() < kClusterEngineNnz);
-  if (cluster) {
-    lp_result r;
+  auto solve_once = [&](const lp_solve_opts &oo, lp_result &r) -> int {
     std::memset(&r, 0, sizeof(r));
-    int rc = cluster_solve(lp->cur, o, &lp->dev, &r, lp->sol, err);
-    if (rc != LP_OK) return fail(rc, err);
-    lp->last_termination = r.termination;
-    if (res) *res = r;
-    return LP_OK;
-  }
-  if (!lp->dlp) {
-    lp->dlp = dev_create(&lp->dev, err);
-    if (!lp->dlp) return fail(LP_ERR_CUDA, err);
-  }
-  if (!dev_uploaded(lp->dlp)) {
-    int rc = dev_upload(lp->dlp, lp->cur, err);
-    if (rc != LP_OK) return fail(rc, err);
-  }
+    const bool cluster = oo.engine == LP_ENGINE_CLUSTER ||
+                         (oo.engine == LP_ENGINE_AUTO && lp->cur.nnz() < kClusterEngineNnz);
+    if (cluster) return cluster_solve(lp->cur, oo, &lp->dev, &r, lp->sol, err);
+    if (!lp->dlp) {
+      lp->dlp = dev_create(&lp->dev, err);
+      if (!lp->dlp) return LP_ERR_CUDA;
+    }
+    if (!dev_uploaded(lp->dlp)) {
+      int rc = dev_upload(lp->dlp, lp->cur, err);
+      if (rc != LP_OK) return rc;
+    }
+    return dev_solve(lp->dlp, lp->cur, oo, &r, lp->sol, err);
+  };
+  const auto t0 = std::chrono::steady_clock::now();
   lp_result r;
-  std::memset(&r, 0, sizeof(r));
-  int rc = dev_solve(lp->dlp, lp->cur, o, &r, lp->sol, err);
+  int rc = solve_once(o, r);
   if (rc != LP_OK) return fail(rc, err);
+  r.rel_kkt_original = r.rel_kkt;
+  r.refinements = 0;
+  // postsolve amplification: the reduced LP's rel-KKT bounds the original
+  // LP's only up to the postsolve's conditioning; while the postsolved point
+  // misses eps_rel on the original LP, solve the reduced LP again ten times
+  // tighter, warm-started from the last solution
+  if (lp->presolved && o.refine_original > 0 && r.termination == LP_OPTIMAL) {
+    double eps = o.eps_rel;
+    for (int q = 0;; ++q) {
+      const double k = problem_original_kkt(lp, lp->sol.x.data(), lp->sol.y.data(),
+                                            lp->sol.z.data());
+      r.rel_kkt_original = k;
+      if (!(k > o.eps_rel) || q == o.refine_original || r.termination != LP_OPTIMAL) break;
+      eps *= 0.1;
+      const std::vector<double> xw = lp->sol.x, yw = lp->sol.y;
+      lp_solve_opts o2 = o;
+      o2.eps_rel = eps;
+      o2.x_init = xw.data();
+      o2.y_init = yw.data();
+      lp_result r2;
+      rc = solve_once(o2, r2);
+      if (rc != LP_OK) return fail(rc, err);
+      r2.iterations += r.iterations;
+      r2.restarts += r.restarts;
+      r2.t_setup_s += r.t_setup_s;
+      r2.t_solve_s += r.t_solve_s;
+      r2.kernel_launches += r.kernel_launches;
+      r2.fp32_iterations += r.fp32_iterations;
+      r2.refinements = r.refinements + 1;
+      r = r2;
+    }
+    r.t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
   lp->last_termination = r.termination;
   if (res) *res = r;
   return LP_OK;

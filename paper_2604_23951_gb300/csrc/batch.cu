@@ -58,6 +58,8 @@ int problem_proven_status(const lp_problem *lp);
 constexpr long long kSoloNnz = 500000;  // larger requests run on the single-LP grid path
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
                             const std::vector<double> &y, const std::vector<double> &z);
+double problem_original_kkt(const lp_problem *lp, const double *x, const double *y,
+                            const double *z);
 
 constexpr int ST_SETUP = -2;
 constexpr int kMaxCluster = 8;
@@ -705,7 +707,10 @@ struct Packed {
 
 static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-static void pack_request(const HostLP &h, Packed &p) {
+// xw / yw: NULL, or a warm start (x: n, y: m, unscaled, the request's own
+// order) stored with the inputs in the slot's device order
+static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
+                         const double *yw = nullptr) {
   Layout L;
   build_layout(h, L);
   p.m = h.m;
@@ -730,6 +735,8 @@ static void pack_request(const HostLP &h, Packed &p) {
   size_t o_avf = take(4 * nzA), o_tvf = take(4 * nzT);
   size_t o_c0 = take(8 * n), o_lx0 = take(8 * n), o_ux0 = take(8 * n);
   size_t o_lc0 = take(8 * m), o_uc0 = take(8 * m), o_pv0 = take(8 * n);
+  const bool warm = xw || yw;
+  size_t o_xi = warm ? take(8 * n) : 0, o_yi = warm ? take(8 * m) : 0;
   r.m = m;
   r.n = n;
   r.nnz = nnz;
@@ -755,6 +762,8 @@ static void pack_request(const HostLP &h, Packed &p) {
   r.lc0 = (const double *)P(o_lc0);
   r.uc0 = (const double *)P(o_uc0);
   r.pv0 = (const double *)P(o_pv0);
+  r.xinit = warm ? (const double *)P(o_xi) : nullptr;
+  r.yinit = warm ? (const double *)P(o_yi) : nullptr;
   const size_t input_end = cur;
   double **colv[] = {&r.c, &r.lx, &r.ux, &r.dc, &r.dc2, &r.idc, &r.x, &r.x0, &r.xbar, &r.xhat,
                      &r.xout, &r.zout};
@@ -785,6 +794,12 @@ static void pack_request(const HostLP &h, Packed &p) {
   put(o_lc0, L.lc0.data(), 8 * m);
   put(o_uc0, L.uc0.data(), 8 * m);
   put(o_pv0, L.pv0.data(), 8 * n);
+  if (warm) {
+    double *xi = reinterpret_cast<double *>(b + o_xi);
+    double *yi = reinterpret_cast<double *>(b + o_yi);
+    for (int j = 0; j < n; ++j) xi[j] = xw ? xw[L.cperm[j]] : 0.0;
+    for (int i = 0; i < m; ++i) yi[i] = yw ? yw[L.rperm[i]] : 0.0;
+  }
   p.bnorm = L.bnorm;
   p.cnorm = L.cnorm;
   p.off = L.off;
@@ -815,6 +830,8 @@ static SlotDesc relocate(const SlotDesc &rel, unsigned char *base) {
   d.lc0 = R(rel.lc0);
   d.uc0 = R(rel.uc0);
   d.pv0 = R(rel.pv0);
+  d.xinit = rel.xinit ? R(rel.xinit) : nullptr;
+  d.yinit = rel.yinit ? R(rel.yinit) : nullptr;
   d.c = R(rel.c);
   d.lx = R(rel.lx);
   d.ux = R(rel.ux);
@@ -846,8 +863,15 @@ struct Request {
   Packed pk;
   bool solo = false;
   size_t solo_bytes = 0;  // arena estimate of a solo request
-  double t_submit = 0;
+  double t_submit = 0;    // first submission (a re-solve keeps it)
   bool cancelled = false;
+  // a re-solve asked for by the original-LP check: tighter tolerance and a
+  // warm start (solo requests; batched ones carry it in pk), the work done
+  double eps_rel = -1.0;  // < 0: the server's
+  std::vector<double> xw, yw;
+  int refinements = 0;
+  long long iters_before = 0;
+  double solve_s_before = 0;
 };
 
 // device bytes the single-LP path allocates for an LP (upper estimate)
@@ -877,6 +901,9 @@ struct Slot {
   bool cancel = false;
   long long last_t = 0;   // iteration count after the last launch
   long long launches = 0; // launches the slot took part in
+  int refinements = 0;    // re-solves before this one (original-LP check)
+  long long iters_before = 0;
+  double solve_s_before = 0;
 };
 
 // one size bucket: its launch loop runs independently of the others
@@ -1006,7 +1033,15 @@ bool start_solo(lp_server *srv, Request &rq) {
   const uint64_t ticket = rq.ticket;
   lp_problem *lp = rq.lp;
   const double t_submit = rq.t_submit;
-  srv->solo_threads.emplace_back([srv, ticket, lp, t_submit]() {
+  lp_solve_opts o = srv->opts;
+  if (rq.eps_rel >= 0) o.eps_rel = rq.eps_rel;
+  const int refinements = rq.refinements;
+  const long long iters_before = rq.iters_before;
+  const double solve_s_before = rq.solve_s_before;
+  std::vector<double> xw = std::move(rq.xw), yw = std::move(rq.yw);
+  srv->solo_threads.emplace_back([srv, ticket, lp, t_submit, o, refinements, iters_before,
+                                  solve_s_before, xw = std::move(xw),
+                                  yw = std::move(yw)]() mutable {
     const double t_admit = now_s();
     Done d;
     d.lp = lp;
@@ -1028,7 +1063,9 @@ bool start_solo(lp_server *srv, Request &rq) {
       const HostLP &h = problem_current(lp);
       DeviceSolution sol;
       if (rc == LP_OK) rc = dev_upload(dl, h, err);
-      if (rc == LP_OK) rc = dev_solve(dl, h, srv->opts, &d.res, sol, err);
+      if (!xw.empty()) o.x_init = xw.data();
+      if (!yw.empty()) o.y_init = yw.data();
+      if (rc == LP_OK) rc = dev_solve(dl, h, o, &d.res, sol, err);
       if (rc == LP_OK) {
         d.x = std::move(sol.x);
         d.y = std::move(sol.y);
@@ -1042,8 +1079,11 @@ bool start_solo(lp_server *srv, Request &rq) {
     if (dl) dev_destroy(dl);
     const double tnow = now_s();
     d.res.t_setup_s = t_admit - t_submit;
-    d.res.t_solve_s = tnow - t_admit;
+    d.res.t_solve_s = tnow - t_admit + solve_s_before;
     d.res.t_total_s = tnow - t_submit;
+    d.res.iterations += iters_before;
+    d.res.refinements = refinements;
+    d.res.rel_kkt_original = d.res.rel_kkt;
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->done[ticket] = std::move(d);
     srv->where[ticket] = 2;
@@ -1101,11 +1141,15 @@ void admit(lp_server *srv) {
     sl.desc = relocate(rq.pk.rel, srv->arena + off);
     sl.rperm = std::move(rq.pk.rperm);
     sl.cperm = std::move(rq.pk.cperm);
+    sl.refinements = rq.refinements;
+    sl.iters_before = rq.iters_before;
+    sl.solve_s_before = rq.solve_s_before;
     CK(cudaMemcpyAsync(srv->arena + off, rq.pk.blob.data(), rq.pk.blob.size(),
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaMemcpyAsync(srv->d_desc + sid, &sl.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice,
                        srv->s));
     state_init(srv->opts, srv->h_state[sid], rq.pk);
+    if (rq.eps_rel >= 0) srv->h_state[sid].eps_rel = rq.eps_rel;
     CK(cudaMemcpyAsync(srv->d_state + sid, &srv->h_state[sid], sizeof(State),
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaStreamSynchronize(srv->s));  // the pageable blob may be freed next
@@ -1195,9 +1239,12 @@ void retire(lp_server *srv, int q, const State *S, double tnow) {
                             ? (S->t_switch >= 0 ? S->t_switch : r.iterations) : 0;
   }
   r.t_setup_s = sl.t_admit - sl.t_submit;  // queueing delay
-  r.t_solve_s = tnow - sl.t_admit;
+  r.t_solve_s = tnow - sl.t_admit + sl.solve_s_before;
   r.t_total_s = tnow - sl.t_submit;
   r.kernel_launches = sl.launches;
+  r.iterations += sl.iters_before;
+  r.refinements = sl.refinements;
+  r.rel_kkt_original = r.rel_kkt;
   srv->done[sl.ticket] = std::move(d);
   srv->where[sl.ticket] = 2;
   {
@@ -1360,6 +1407,11 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
     if (opts) srv->opts = *opts;
     srv->opts.x_init = nullptr;
     srv->opts.y_init = nullptr;
+    if (!valid_solve_opts(srv->opts)) {
+      delete srv;
+      set_last_error("invalid solve options");
+      return LP_ERR_INVALID;
+    }
     CK(cudaSetDevice(srv->device));
     CK(cudaDeviceGetAttribute(&srv->sm_count, cudaDevAttrMultiProcessorCount, srv->device));
     if (srv->ctx.stream) {
@@ -1506,7 +1558,7 @@ int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, do
     set_last_error("server is NULL");
     return LP_ERR_INVALID;
   }
-  std::lock_guard<std::mutex> lk(srv->mu);
+  std::unique_lock<std::mutex> lk(srv->mu);
   if (!srv->worker_err.empty()) {
     set_last_error("server worker failed: " + srv->worker_err);
     return LP_ERR_CUDA;
@@ -1518,12 +1570,68 @@ int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, do
   }
   if (w->second != 2) return LP_PENDING;
   Done &d = srv->done[ticket];
-  if (res) *res = d.res;
-  if (x && !d.x.empty()) std::memcpy(x, d.x.data(), 8 * d.x.size());
-  if (y && !d.y.empty()) std::memcpy(y, d.y.data(), 8 * d.y.size());
+  // the original-LP check of a presolved request (postsolve + host rel-KKT,
+  // O(nnz) host work) runs on this polling thread without the server lock;
+  // meanwhile the ticket reads as pending
+  if (d.lp && d.res.termination == LP_OPTIMAL && srv->opts.refine_original > 0) {
+    Done dd = std::move(d);
+    srv->done.erase(ticket);
+    w->second = 3;
+    lk.unlock();
+    try {
+      const double k = problem_original_kkt(dd.lp, dd.x.data(), dd.y.data(), dd.z.data());
+      if (k >= 0) dd.res.rel_kkt_original = k;
+      if (k > srv->opts.eps_rel && dd.res.refinements < srv->opts.refine_original) {
+        // solve the reduced LP again ten times tighter, warm-started
+        Request rq;
+        rq.lp = dd.lp;
+        rq.ticket = ticket;
+        rq.refinements = dd.res.refinements + 1;
+        rq.eps_rel = srv->opts.eps_rel * std::pow(0.1, rq.refinements);
+        rq.iters_before = dd.res.iterations;
+        rq.solve_s_before = dd.res.t_solve_s;
+        rq.t_submit = now_s() - dd.res.t_total_s;
+        const HostLP &h = problem_current(dd.lp);
+        if (h.nnz() >= srv->solo_nnz) {
+          rq.solo = true;
+          rq.solo_bytes = solo_estimate(h);
+          rq.pk.m = h.m;
+          rq.pk.n = h.n;
+          rq.pk.nnz = h.nnz();
+          rq.pk.bytes = rq.solo_bytes;
+          rq.xw = std::move(dd.x);
+          rq.yw = std::move(dd.y);
+        } else {
+          pack_request(h, rq.pk, dd.x.data(), dd.y.data());
+        }
+        lk.lock();
+        // a packed re-solve also carries its warm start; if that no longer
+        // fits the budget the answer stands as it is (dd is intact then)
+        if (rq.pk.bytes <= srv->arena_bytes) {
+          srv->where[ticket] = 0;
+          srv->queue.push_back(std::move(rq));
+          srv->cv.notify_all();
+          return LP_PENDING;
+        }
+      } else {
+        lk.lock();
+      }
+    } catch (const std::exception &e) {
+      if (!lk.owns_lock()) lk.lock();
+      srv->where.erase(ticket);
+      set_last_error(std::string("original-LP check failed: ") + e.what());
+      return LP_ERR_INVALID;
+    }
+    srv->done[ticket] = std::move(dd);
+    w = srv->where.find(ticket);
+  }
+  Done &dn = srv->done[ticket];
+  if (res) *res = dn.res;
+  if (x && !dn.x.empty()) std::memcpy(x, dn.x.data(), 8 * dn.x.size());
+  if (y && !dn.y.empty()) std::memcpy(y, dn.y.data(), 8 * dn.y.size());
   // hand the answer to the problem so lp_postsolve can map it back
-  if (d.lp && d.res.termination >= 0 && d.res.termination <= LP_NUMERICAL)
-    problem_store_solution(d.lp, d.x, d.y, d.z);
+  if (dn.lp && dn.res.termination >= 0 && dn.res.termination <= LP_NUMERICAL)
+    problem_store_solution(dn.lp, dn.x, dn.y, dn.z);
   srv->where.erase(w);
   srv->done.erase(ticket);
   return LP_OK;

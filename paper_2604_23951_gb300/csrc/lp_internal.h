@@ -27,6 +27,9 @@ struct HostLP {
 // r_p, r_d, gap.
 void host_rel_kkt(const HostLP &lp, const double *x, const double *y, double out[9]);
 
+// lp_solve_opts within their documented ranges (api.cpp)
+bool valid_solve_opts(const lp_solve_opts &o);
+
 // ---- presolve (presolve.cpp) -------------------------------------------
 struct PostsolveRecord {
   int32_t kind;  // see presolve.cpp

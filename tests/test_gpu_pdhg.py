@@ -9,6 +9,7 @@ import pytest
 
 import lpgen
 import oracle
+from oracle import pipeline as oracle_pipeline
 from oracle import presolve as PS
 from lp_helpers import SimpleLP
 
@@ -125,7 +126,10 @@ def test_presolve_solve_postsolve_is_kkt(pkg, dev, engine):
     assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
     x, y, z = prob.postsolve()
     k = oracle.rel_kkt(lp, x, y)
-    assert k["rel_kkt"] <= 1e-5
+    # the original-LP check holds the postsolved point to eps_rel = 1e-6
+    assert r.rel_kkt_original <= 1e-6
+    assert k["rel_kkt"] <= 1e-6 * (1 + 1e-6)
+    assert abs(k["rel_kkt"] - r.rel_kkt_original) <= 1e-6 * r.rel_kkt_original
     assert rel_obj(k["p"], lp.p_star) <= 1e-6
     # the oracle on the same reduced problem reaches the same objective
     ref = oracle.pdhg_solve(PS.presolve(lp).reduced)
@@ -228,3 +232,30 @@ def test_rows_summing_to_zero_get_a_real_step(pkg, dev, engine):
     r = prob.solve(engine=engine)
     assert r.termination == pkg.LP_OPTIMAL
     assert abs(r.primal_obj - 0.5) <= 1e-5
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_original_lp_check_re_solves_an_amplified_postsolve(pkg, dev, engine):
+    # a fixed column shrinks every right-hand side 30x in the original LP:
+    # the reduced solve at 1e-6 misses 1e-6 on the original, the check
+    # re-solves at 1e-7 (warm-started) and the postsolved point meets it
+    lp = lpgen.amplified_postsolve(seed=43)
+    prob = pkg.Problem(lp, dev)
+    prob.presolve()
+    r0 = prob.solve(engine=engine, refine_original=0)
+    assert r0.termination == pkg.LP_OPTIMAL and r0.refinements == 0
+    x, y, _ = prob.postsolve()
+    assert oracle.rel_kkt(lp, x, y)["rel_kkt"] > 2e-6
+    r = prob.solve(engine=engine)
+    assert r.termination == pkg.LP_OPTIMAL
+    assert r.refinements >= 1 and r.iterations > r0.iterations
+    x, y, _ = prob.postsolve()
+    k = oracle.rel_kkt(lp, x, y)
+    assert r.rel_kkt_original <= 1e-6 and k["rel_kkt"] <= 1e-6 * (1 + 1e-6)
+    assert abs(k["rel_kkt"] - r.rel_kkt_original) <= 1e-6 * r.rel_kkt_original
+    assert rel_obj(k["p"], lp.p_star) <= 1e-6
+    # the oracle's pipeline (same reading) also needs a re-solve here
+    ref = oracle_pipeline.solve_original(lp)
+    assert ref.refinements >= 1 and ref.kkt["rel_kkt"] <= 1e-6
+    assert rel_obj(k["p"], ref.kkt["p"]) <= 1e-6
+    prob.close()
