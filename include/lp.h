@@ -202,6 +202,15 @@ typedef struct {
                           * started from the last solution, at most this many
                           * times (0: no check).  Applies to lp_solve and to
                           * served requests (lp_batch_poll).                 */
+  int32_t tile_run_max;  /* grid engine tile shape: most entries one lane
+                          * owns in a row (8, 16 or 32) ...                 */
+  int32_t tile_nnz;      /* ... and nonzeros per warp tile (512 or 2048);
+                          * either 0 (default): the autotuner's choice for
+                          * each matrix (A and A^T separately), measured on
+                          * the first solve of a size class and kept for the
+                          * process.  Results are bitwise reproducible for a
+                          * fixed shape; different shapes sum in a different
+                          * order.                                          */
 } lp_solve_opts;
 
 typedef struct {
@@ -304,8 +313,8 @@ int lp_get_data(const lp_problem *lp, int64_t *row_ptr, int32_t *col_idx,
 int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, double *out);
 
 /* The row plan of the device layout, for `rows` rows of lengths len[]:
- * perm[new] = old row (rows longer than 512 entries first, then rows longer
- * than 256, then the rest by length, longest first; stable within a class);
+ * perm[new] = old row (longest first; equal lengths in their original
+ * order -- the same order for every tile shape);
  * *nlong = the number of rows longer than 512 (each reduced by one CTA);
  * tiles[2 t], tiles[2 t + 1] = first row and packed word (nrows | lanes_log2
  * << 8 | entries_per_lane << 12) of warp tile t, for t < *ntiles.  tiles
@@ -313,6 +322,23 @@ int lp_host_rel_kkt(const lp_problem *lp, const double *x, const double *y, doub
  * that is too few.  Host only; no device needed. */
 int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles,
                  int32_t tile_cap, int32_t *ntiles, int32_t *nlong);
+
+/* The same under a given tile shape: run_max (1..64) most entries a lane owns
+ * in a row (2^v lanes per row, v the least with 2^v * run_max >= the tile's
+ * longest row L; a lane walks its share in c = ceil(L / (2^v * 8)) chunks of
+ * nit = ceil(L / (2^v c)) entries), tile_nnz (>= 32) nonzeros a tile aims at
+ * (min(32, tile_nnz / L) rows).  segmented != 0: rows longer than
+ * 32 * run_max come first and are cut into segments of 32 * run_max entries,
+ * one tile each: tiles[2 t] = the row, tiles[2 t + 1] = INT_MIN | segment
+ * index, and seg_base (seg_cap ints, may be NULL) receives *nsegrows + 1
+ * offsets: row r's segments are seg_base[r] .. seg_base[r + 1] - 1; *nlong is
+ * then 0.  segmented == 0: rows longer than 512 are CTA rows (*nlong) and
+ * rows in (32 * run_max, 512] single-row tiles, as lp_plan_rows (which is
+ * run_max 8, tile_nnz 512, unsegmented). */
+int lp_plan_rows_shape(int32_t rows, const int64_t *len, int32_t run_max, int32_t tile_nnz,
+                       int32_t segmented, int32_t *perm, int32_t *tiles, int32_t tile_cap,
+                       int32_t *ntiles, int32_t *nlong, int32_t *seg_base, int32_t seg_cap,
+                       int32_t *nsegrows);
 
 /* Measurement hook (no counterpart in the paper): time the PDHG iteration
  * kernels of the last lp_solve one launch at a time with CUDA events on the
@@ -323,6 +349,21 @@ int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles
  * Fails LP_ERR_STATE without a prior solve.  Changes the internal iterate
  * (not the stored solution). */
 int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out);
+
+/* The grid engine's tile shapes after the last lp_solve (no counterpart in
+ * the paper: the autotuner of the warp-tile layout).  out[0], out[1]: the
+ * candidate index used for the rows of A (the dual kernel) and of A^T (the
+ * primal kernel); out[2]: 1 if that solve measured the candidates, 0 if the
+ * shapes came from the cache, the default or the options; then per
+ * candidate c: out[3 + 4c] run_max, out[4 + 4c] tile_nnz, out[5 + 4c] and
+ * out[6 + 4c] the mean ms of the dual and the primal kernel under it (0 when
+ * not measured).  cap: doubles available (LP_ERR_INVALID if too few);
+ * *count: doubles written.  LP_ERR_STATE without a grid-engine solve. */
+int lp_get_tile_tuning(const lp_problem *lp, double *out, int32_t cap, int32_t *count);
+
+/* Forget the autotuner's cached tile shapes (the next solve of each size
+ * class measures again). */
+void lp_tile_cache_clear(void);
 
 void lp_destroy(lp_problem *lp);
 

@@ -31,5 +31,7 @@ from .capi import (  # noqa: F401
     TorchDevice,
     load,
     plan_rows,
+    plan_rows_shape,
+    tile_cache_clear,
     solve_opts,
 )

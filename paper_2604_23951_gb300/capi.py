@@ -58,7 +58,8 @@ class lp_solve_opts(C.Structure):
                 ("y_init", C.POINTER(C.c_double)), ("engine", C.c_int32),
                 ("verbose", C.c_int32), ("infeas_every", C.c_int32),
                 ("eps_infeas", C.c_double), ("primal_weight_clamp", C.c_double),
-                ("refine_original", C.c_int32)]
+                ("refine_original", C.c_int32), ("tile_run_max", C.c_int32),
+                ("tile_nnz", C.c_int32)]
 
 
 class lp_result(C.Structure):
@@ -108,6 +109,10 @@ SIGNATURES = [
     ("lp_batch_poll", C.c_int, [_P, C.c_uint64, C.POINTER(lp_result), _D, _D]),
     ("lp_server_pump", C.c_int, [_P, C.c_int32]),
     ("lp_plan_rows", C.c_int, [C.c_int32, _I64, _I32, _I32, C.c_int32, _I32, _I32]),
+    ("lp_plan_rows_shape", C.c_int, [C.c_int32, _I64, C.c_int32, C.c_int32, C.c_int32, _I32,
+                                     _I32, C.c_int32, _I32, _I32, _I32, C.c_int32, _I32]),
+    ("lp_get_tile_tuning", C.c_int, [_P, _D, C.c_int32, _I32]),
+    ("lp_tile_cache_clear", None, []),
     ("lp_server_tune", C.c_int, [_P, C.c_int64, C.c_int32, C.c_double]),
     ("lp_batch_cancel", C.c_int, [_P, C.c_uint64]),
     ("lp_server_stats", C.c_int, [_P, _I64]),
@@ -170,6 +175,29 @@ def plan_rows(lengths):
     check(lib.lp_plan_rows(rows, L.ctypes.data_as(_I64), perm.ctypes.data_as(_I32),
                            tiles.ctypes.data_as(_I32), cap, C.byref(nt), C.byref(nl)))
     return perm[:rows], tiles[: 2 * nt.value].reshape(-1, 2), nl.value
+
+
+def plan_rows_shape(lengths, run_max: int, tile_nnz: int, segmented: bool):
+    """lp_plan_rows_shape: (perm, tiles (ntiles, 2), nlong, seg_base)."""
+    lib = load()
+    L = np.ascontiguousarray(lengths, dtype=np.int64)
+    rows = int(L.size)
+    perm = np.zeros(max(rows, 1), dtype=np.int32)
+    nt, nl, ns = C.c_int32(), C.c_int32(), C.c_int32()
+    seg_total = int(np.sum(-(-L // (32 * max(int(run_max), 1))))) if rows else 0
+    cap = rows + seg_total + 1
+    tiles = np.zeros(2 * cap, dtype=np.int32)
+    sb = np.zeros(rows + 1, dtype=np.int32)
+    check(lib.lp_plan_rows_shape(rows, L.ctypes.data_as(_I64), int(run_max), int(tile_nnz),
+                                 1 if segmented else 0, perm.ctypes.data_as(_I32),
+                                 tiles.ctypes.data_as(_I32), cap, C.byref(nt), C.byref(nl),
+                                 sb.ctypes.data_as(_I32), rows + 1, C.byref(ns)))
+    return (perm[:rows], tiles[: 2 * nt.value].reshape(-1, 2), nl.value,
+            sb[: ns.value + 1])
+
+
+def tile_cache_clear():
+    load().lp_tile_cache_clear()
 
 
 # --------------------------------------------------------------------------
@@ -327,6 +355,19 @@ class Problem:
         keys = ("primal_ms", "dual_ms", "primal_bytes", "dual_bytes", "kkt_rows_ms",
                 "kkt_cols_ms", "kkt_rows_bytes", "kkt_cols_bytes")
         return dict(zip(keys, out))
+
+    def tile_tuning(self):
+        """The grid engine's tile shapes of the last solve (lp_get_tile_tuning):
+        {"A": index, "T": index, "measured": bool, "shapes": [(run_max,
+        tile_nnz)], "ms_A": [...], "ms_T": [...]}"""
+        out = np.zeros(128)
+        k = C.c_int32()
+        check(self.lib.lp_get_tile_tuning(self.h, dptr(out), 128, C.byref(k)))
+        nc = (k.value - 3) // 4
+        q = out[3:3 + 4 * nc].reshape(nc, 4)
+        return {"A": int(out[0]), "T": int(out[1]), "measured": bool(out[2]),
+                "shapes": [(int(a), int(b)) for a, b in q[:, :2]],
+                "ms_A": q[:, 2].tolist(), "ms_T": q[:, 3].tolist()}
 
     def rel_kkt(self, x, y):
         out = np.zeros(6)

@@ -100,7 +100,10 @@ bool valid_solve_opts(const lp_solve_opts &o) {
          o.infeas_every >= 0 && o.eps_infeas >= 0 &&
          (o.primal_weight_clamp == 0.0 || o.primal_weight_clamp >= 1.0) &&
          (o.precision == LP_FP64 || o.precision == LP_MIXED) && o.engine >= LP_ENGINE_AUTO &&
-         o.engine <= LP_ENGINE_CLUSTER && o.refine_original >= 0 && o.refine_original <= 8;
+         o.engine <= LP_ENGINE_CLUSTER && o.refine_original >= 0 && o.refine_original <= 8 &&
+         (o.tile_run_max == 0 || o.tile_run_max == 8 || o.tile_run_max == 16 ||
+          o.tile_run_max == 32) &&
+         (o.tile_nnz == 0 || o.tile_nnz == 512 || o.tile_nnz == 2048);
 }
 }  // namespace gb300lp
 
@@ -454,6 +457,20 @@ int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out) {
   return LP_OK;
   API_GUARD_END
 }
+
+int lp_get_tile_tuning(const lp_problem *lp, double *out, int32_t cap, int32_t *count) {
+  API_GUARD_BEGIN
+  if (!lp || !out || !count) return fail(LP_ERR_INVALID, "NULL argument");
+  if (!lp->dlp || !dev_uploaded(lp->dlp))
+    return fail(LP_ERR_STATE, "no grid-engine solve on this problem");
+  const int k = dev_tile_tuning(lp->dlp, out, cap);
+  if (k < 0) return fail(LP_ERR_INVALID, "cap too small");
+  *count = k;
+  return LP_OK;
+  API_GUARD_END
+}
+
+void lp_tile_cache_clear(void) { dev_tile_cache_clear(); }
 
 void lp_destroy(lp_problem *lp) {
   if (!lp) return;

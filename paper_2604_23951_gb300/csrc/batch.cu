@@ -712,7 +712,7 @@ static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
                          const double *yw = nullptr) {
   Layout L;
-  build_layout(h, L);
+  build_layout(h, L, TileShape{});  // run_max 8, 512 nonzeros, CTA rows: no segments
   p.m = h.m;
   p.n = h.n;
   p.nnz = h.nnz();
@@ -726,7 +726,7 @@ static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
   };
   SlotDesc &r = p.rel;
   auto P = [](size_t o) { return reinterpret_cast<void *>(o); };
-  const size_t ntA = L.tA.size(), ntT = L.tT.size();
+  const size_t ntA = L.pA.tiles.size(), ntT = L.pT.tiles.size();
   const size_t nzA = (size_t)nnz, nzT = (size_t)nnz;
   size_t o_tA = take(sizeof(int2) * ntA), o_tT = take(sizeof(int2) * ntT);
   size_t o_arp = take(sizeof(int) * (m + 1)), o_aci = take(sizeof(int) * nzA);
@@ -742,8 +742,8 @@ static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
   r.nnz = nnz;
   r.a_ntiles = (int)ntA;
   r.t_ntiles = (int)ntT;
-  r.a_nlong = L.nlongA;
-  r.t_nlong = L.nlongT;
+  r.a_nlong = L.pA.nlong;
+  r.t_nlong = L.pT.nlong;
   r.a_tiles = (const int2 *)P(o_tA);
   r.t_tiles = (const int2 *)P(o_tT);
   r.a_rp = (const int *)P(o_arp);
@@ -780,8 +780,8 @@ static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
   auto put = [b](size_t o, const void *src, size_t bytes) {
     if (bytes) std::memcpy(b + o, src, bytes);
   };
-  put(o_tA, L.tA.data(), sizeof(int2) * ntA);
-  put(o_tT, L.tT.data(), sizeof(int2) * ntT);
+  put(o_tA, L.pA.tiles.data(), sizeof(int2) * ntA);
+  put(o_tT, L.pT.tiles.data(), sizeof(int2) * ntT);
   put(o_arp, L.arp.data(), sizeof(int) * (m + 1));
   put(o_aci, L.aci.data(), sizeof(int) * nzA);
   put(o_trp, L.trp.data(), sizeof(int) * (n + 1));

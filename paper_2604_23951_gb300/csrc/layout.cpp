@@ -3,65 +3,101 @@
 
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <string>
 
 #include "spmv_warp.cuh"
 
 namespace gb300lp {
 
-// Order rows for the warp engine (stable within a class): rows longer than
-// kCtaRow first (nlong of them, one whole CTA each), then rows longer than
-// kLongRow (a single-row warp tile each), then the rest by length, longest
-// first, cut into warp tiles of at most 32 rows and about kWarpTileNnz
-// nonzeros.  A tile's lanes per row 2^v is the least with 2^v * kWarpItems
-// >= its longest row L, and its entries per lane nit = ceil(L / 2^v).
-void plan_tiles(const std::vector<int64_t> &len, std::vector<int> &perm,
-                std::vector<int2> &tiles, int &nlong) {
+// Rows longest first, stable (counting sort on the length when the longest
+// row allows it, a stable comparison sort otherwise).
+void sort_rows(const std::vector<int64_t> &len, std::vector<int> &perm) {
   const int rows = (int)len.size();
-  // key: the length for rows up to kLongRow, kLongRow + 1 for warp-long
-  // rows, kLongRow + 2 for CTA rows; counting sort by descending key
-  auto key = [](int64_t L) -> int {
-    if (L > kCtaRow) return kLongRow + 2;
-    if (L > kLongRow) return kLongRow + 1;
-    return (int)L;
-  };
-  const int nkeys = kLongRow + 3;
-  std::vector<int> cnt(nkeys, 0);
-  for (int64_t L : len) cnt[key(L)]++;
-  std::vector<int> start(nkeys, 0);
-  int acc = 0;
-  for (int k = nkeys - 1; k >= 0; --k) {
-    start[k] = acc;
-    acc += cnt[k];
-  }
   perm.assign(rows, 0);
-  for (int r = 0; r < rows; ++r) perm[start[key(len[r])]++] = r;
-  tiles.clear();
-  int i = 0;
-  while (i < rows && len[perm[i]] > kCtaRow) ++i;
-  nlong = i;
-  while (i < rows && len[perm[i]] > kLongRow) {
-    tiles.push_back(pack_wtile(i, 1, 5, kWarpItems));
-    ++i;
+  int64_t lmax = 0;
+  for (int64_t L : len) lmax = std::max(lmax, L);
+  if (lmax <= (int64_t(1) << 22)) {
+    std::vector<int> cnt(lmax + 2, 0);
+    for (int64_t L : len) cnt[L]++;
+    // start of each length, longest first
+    std::vector<int> start(lmax + 2, 0);
+    int acc = 0;
+    for (int64_t L = lmax; L >= 0; --L) {
+      start[L] = acc;
+      acc += cnt[L];
+    }
+    for (int r = 0; r < rows; ++r) perm[start[len[r]]++] = r;
+  } else {
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(),
+                     [&](int a, int b) { return len[a] > len[b]; });
   }
+}
+
+// Tiles over rows in length order (sorted[r] = length of row r).  Rows
+// longer than 32 * run_max come first: segmented (one tile per segment,
+// {row, INT_MIN | segment index}) or, unsegmented, rows longer than kCtaRow
+// as CTA rows and the others as single-row tiles.  The rest is cut into
+// tiles of up to 32 rows and about tile_nnz nonzeros (a tile whose first
+// row is longer than 8 ends before a row of less than half its length); in
+// a tile whose longest row has L entries each row gets 2^v lanes (least v with 2^v * run_max >= L)
+// and a lane walks its share in c = ceil(L / (2^v * 8)) chunks of
+// nit = ceil(L / (2^v * c)) <= 8 entries (balanced chunks: no lane pads more
+// than one chunk step).
+void plan_tiles(const std::vector<int64_t> &sorted, const TileShape &shape, TilePlan &plan) {
+  const int rows = (int)sorted.size();
+  const int rmax = std::max(1, std::min(shape.run_max, 64));
+  const int64_t llong = 32LL * rmax;
+  plan.tiles.clear();
+  plan.seg_base.assign(1, 0);
+  plan.nlong = 0;
+  plan.nsegrows = 0;
+  plan.seg_len = 0;
+  int i = 0;
+  if (shape.segmented) {
+    plan.seg_len = (int)llong;
+    int g = 0;
+    while (i < rows && sorted[i] > llong) {
+      const int nseg = (int)((sorted[i] + llong - 1) / llong);
+      for (int s = 0; s < nseg; ++s)
+        plan.tiles.push_back(make_int2(i, (int)(0x80000000u | (unsigned)(g + s))));
+      g += nseg;
+      plan.seg_base.push_back(g);
+      ++i;
+    }
+    plan.nsegrows = i;
+  } else {
+    while (i < rows && sorted[i] > kCtaRow) ++i;
+    plan.nlong = i;
+    while (i < rows && sorted[i] > llong) {
+      const int nit = (int)std::min<int64_t>(kWarpItems, (sorted[i] + 31) / 32);
+      plan.tiles.push_back(pack_wtile(i, 1, 5, std::max(1, nit)));
+      ++i;
+    }
+  }
+  const int64_t tnnz = std::max(32, shape.tile_nnz);
   while (i < rows) {
-    const int64_t L = len[perm[i]];
-#ifndef GB300_MIN_VLOG
-#define GB300_MIN_VLOG 0
-#endif
-    int vlog = GB300_MIN_VLOG;
-    while ((int64_t(1) << vlog) * kWarpItems < L) ++vlog;
-    const int vl = 1 << vlog;
-    const int nit = (int)std::max<int64_t>(1, (L + vl - 1) / vl);
-    int nr = (int)std::max<int64_t>(
-        1, std::min<int64_t>(32, kWarpTileNnz / std::max<int64_t>(L, 1)));
+    const int64_t L = sorted[i];
+    int vlog = 0;
+    while ((int64_t(1) << vlog) * rmax < L && vlog < 5) ++vlog;
+    const int64_t vl = int64_t(1) << vlog;
+    const int64_t chunks = std::max<int64_t>(1, (L + vl * kWarpItems - 1) / (vl * kWarpItems));
+    const int nit = (int)std::max<int64_t>(1, (L + vl * chunks - 1) / (vl * chunks));
+    int nr = (int)std::max<int64_t>(1, std::min<int64_t>(32, tnnz / std::max<int64_t>(L, 1)));
     nr = std::min(nr, rows - i);
-    tiles.push_back(pack_wtile(i, nr, vlog, nit));
+    // rows much shorter than the first would idle most of their lanes
+    for (int k = 1; k < nr; ++k)
+      if (L > kWarpItems && 2 * sorted[i + k] < L) {
+        nr = k;
+        break;
+      }
+    plan.tiles.push_back(pack_wtile(i, nr, vlog, nit));
     i += nr;
   }
 }
 
-void build_layout(const HostLP &h, Layout &L) {
+void build_layout(const HostLP &h, Layout &L, const TileShape &shape) {
   const int m = h.m, n = h.n;
   const long long nnz = h.nnz();
   L.m = m;
@@ -70,8 +106,15 @@ void build_layout(const HostLP &h, Layout &L) {
   std::vector<int64_t> rlen(m), clen(n, 0);
   for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
   for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
-  plan_tiles(rlen, L.rperm, L.tA, L.nlongA);
-  plan_tiles(clen, L.cperm, L.tT, L.nlongT);
+  sort_rows(rlen, L.rperm);
+  sort_rows(clen, L.cperm);
+  {
+    std::vector<int64_t> sr(m), sc(n);
+    for (int i = 0; i < m; ++i) sr[i] = rlen[L.rperm[i]];
+    for (int j = 0; j < n; ++j) sc[j] = clen[L.cperm[j]];
+    plan_tiles(sr, shape, L.pA);
+    plan_tiles(sc, shape, L.pT);
+  }
   std::vector<int> cinv(n);
   for (int j = 0; j < n; ++j) cinv[L.cperm[j]] = j;
   L.arp.assign(m + 1, 0);
@@ -139,8 +182,11 @@ namespace gb300lp {
 void set_last_error(const std::string &m);
 }
 
-extern "C" int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles,
-                            int32_t tile_cap, int32_t *ntiles, int32_t *nlong) {
+// the row plan of one matrix under a shape (shared by the two C entry points)
+static int plan_rows_common(int32_t rows, const int64_t *len, const gb300lp::TileShape &shape,
+                            int32_t *perm, int32_t *tiles, int32_t tile_cap, int32_t *ntiles,
+                            int32_t *nlong, int32_t *seg_base, int32_t seg_cap,
+                            int32_t *nsegrows) {
   using namespace gb300lp;
   if (rows < 0 || (rows > 0 && (!len || !perm)) || !ntiles || !nlong || tile_cap < 0 ||
       (tile_cap > 0 && !tiles)) {
@@ -154,19 +200,53 @@ extern "C" int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int
       return LP_ERR_INVALID;
     }
   std::vector<int> p;
-  std::vector<int2> t;
-  int nl = 0;
-  plan_tiles(L, p, t, nl);
-  *ntiles = (int32_t)t.size();
-  *nlong = nl;
-  if ((int64_t)t.size() > tile_cap) {
+  sort_rows(L, p);
+  std::vector<int64_t> sl(rows);
+  for (int r = 0; r < rows; ++r) sl[r] = L[p[r]];
+  TilePlan plan;
+  plan_tiles(sl, shape, plan);
+  *ntiles = (int32_t)plan.tiles.size();
+  *nlong = plan.nlong;
+  if (nsegrows) *nsegrows = plan.nsegrows;
+  if ((int64_t)plan.tiles.size() > tile_cap) {
     set_last_error("lp_plan_rows: tile_cap too small");
     return LP_ERR_INVALID;
   }
+  if (seg_base) {
+    if ((int64_t)plan.seg_base.size() > seg_cap) {
+      set_last_error("lp_plan_rows: seg_cap too small");
+      return LP_ERR_INVALID;
+    }
+    std::copy(plan.seg_base.begin(), plan.seg_base.end(), seg_base);
+  }
   std::copy(p.begin(), p.end(), perm);
-  for (size_t k = 0; k < t.size(); ++k) {
-    tiles[2 * k] = t[k].x;
-    tiles[2 * k + 1] = t[k].y;
+  for (size_t k = 0; k < plan.tiles.size(); ++k) {
+    tiles[2 * k] = plan.tiles[k].x;
+    tiles[2 * k + 1] = plan.tiles[k].y;
   }
   return LP_OK;
+}
+
+extern "C" int lp_plan_rows(int32_t rows, const int64_t *len, int32_t *perm, int32_t *tiles,
+                            int32_t tile_cap, int32_t *ntiles, int32_t *nlong) {
+  gb300lp::TileShape shape;  // the batch path's shape: run_max 8, 512 nonzeros, CTA rows
+  return plan_rows_common(rows, len, shape, perm, tiles, tile_cap, ntiles, nlong, nullptr, 0,
+                          nullptr);
+}
+
+extern "C" int lp_plan_rows_shape(int32_t rows, const int64_t *len, int32_t run_max,
+                                  int32_t tile_nnz, int32_t segmented, int32_t *perm,
+                                  int32_t *tiles, int32_t tile_cap, int32_t *ntiles,
+                                  int32_t *nlong, int32_t *seg_base, int32_t seg_cap,
+                                  int32_t *nsegrows) {
+  if (run_max < 1 || run_max > 64 || tile_nnz < 32) {
+    gb300lp::set_last_error("lp_plan_rows_shape: run_max must be 1..64, tile_nnz >= 32");
+    return LP_ERR_INVALID;
+  }
+  gb300lp::TileShape shape;
+  shape.run_max = run_max;
+  shape.tile_nnz = tile_nnz;
+  shape.segmented = segmented != 0;
+  return plan_rows_common(rows, len, shape, perm, tiles, tile_cap, ntiles, nlong, seg_base,
+                          seg_cap, nsegrows);
 }

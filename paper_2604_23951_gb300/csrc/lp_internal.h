@@ -75,6 +75,11 @@ int dev_solve(DeviceLP *d, const HostLP &lp, const lp_solve_opts &opts, lp_resul
               DeviceSolution &sol, std::string &err);
 void dev_destroy(DeviceLP *d);
 int dev_profile(DeviceLP *d, int reps, double *out, std::string &err);
+// the grid engine's tile-shape autotuner: forget every cached choice; report
+// the last solve's shapes and measurement (lp_get_tile_tuning's layout;
+// -1 if cap is too small)
+void dev_tile_cache_clear();
+int dev_tile_tuning(const DeviceLP *d, double *out, int cap);
 
 // Per-check trace: when the environment variable LP_TRACE names a file, one
 // JSON line per state read-back of a solve is appended to it (api.cpp).

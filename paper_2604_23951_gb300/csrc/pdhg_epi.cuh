@@ -4,16 +4,20 @@
 // Every epilogue gets pre(r) (prefetch of the row's own vector entries, so
 // those loads overlap the row's gathers) and then row(r, s) with
 // s = (row r of the matrix) . vec, on the same thread.  Vectors are in the
-// renumbered (length-sorted) order of the device layout.
+// renumbered (length-sorted) order of the device layout.  clear() zeroes the
+// accumulators and sink(k, r) stores them into slot r of their quantities
+// (segmented rows: the warp that finishes the row runs the epilogue on a
+// copy, so its contribution lands in a slot of the row's own).
 #pragma once
 
 #include "device_common.cuh"
 #include "pdhg_state.cuh"
+#include "spmv_warp.cuh"
 
 namespace gb300lp {
 
 // out[r] = s (power iteration); acc collects sum s^2
-template <typename O>
+template <typename O, int QI = Q_PW>
 struct StoreSqEpi {
   O *out;
   double acc;
@@ -21,6 +25,10 @@ struct StoreSqEpi {
   __device__ __forceinline__ void row(int r, double s) {
     out[r] = (O)s;
     acc += s * s;
+  }
+  __device__ __forceinline__ void clear() { acc = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (k.p) k.p[QI * k.stride + k.base + r] = acc;
   }
 };
 
@@ -52,6 +60,13 @@ struct PrimalEpi {
       xhat[j] = xh;
       acc0 += (xk - xh) * (xk - xh);
       acc1 += (xh - a0) * (xh - a0);
+    }
+  }
+  __device__ __forceinline__ void clear() { acc0 = acc1 = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (CHECK && k.p) {
+      k.p[Q_XRES * k.stride + k.base + r] = acc0;
+      k.p[Q_XD * k.stride + k.base + r] = acc1;
     }
   }
 };
@@ -86,6 +101,13 @@ struct DualEpi {
       acc1 += (yh - a0) * (yh - a0);
     }
   }
+  __device__ __forceinline__ void clear() { acc0 = acc1 = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (CHECK && k.p) {
+      k.p[Q_YRES * k.stride + k.base + r] = acc0;
+      k.p[Q_YD * k.stride + k.base + r] = acc1;
+    }
+  }
 };
 
 // K3a: rows of A at xh: primal residual of the unscaled A x against
@@ -105,6 +127,13 @@ struct KktRowEpi {
     if (!isfinite(hi)) yp = fmax(yp, 0.0);
     rdy2 += (yv - yp) * (yv - yp);
     dy += support_term(yp, lo, hi);
+  }
+  __device__ __forceinline__ void clear() { rp2 = rdy2 = dy = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (!k.p) return;
+    k.p[Q_RP * k.stride + k.base + r] = rp2;
+    k.p[Q_RDY * k.stride + k.base + r] = rdy2;
+    k.p[Q_DY * k.stride + k.base + r] = dy;
   }
 };
 
@@ -128,6 +157,13 @@ struct KktColEpi {
     dl += support_term(lam, lo, hi);
     p += c0[j] * (d * xhat[j]);
     zbuf[j] = g;
+  }
+  __device__ __forceinline__ void clear() { rd2 = dl = p = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (!k.p) return;
+    k.p[Q_RD * k.stride + k.base + r] = rd2;
+    k.p[Q_DL * k.stride + k.base + r] = dl;
+    k.p[Q_P * k.stride + k.base + r] = p;
   }
 };
 
@@ -155,6 +191,12 @@ struct InfRowEpi {
     wbuf[i] = w;
     dobj += support_term(dr[i] * w, lo, hi);
   }
+  __device__ __forceinline__ void clear() { v2 = dobj = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (!k.p) return;
+    k.p[Q_IPVR * k.stride + k.base + r] = v2;
+    k.p[Q_IDOR * k.stride + k.base + r] = dobj;
+  }
 };
 
 // Infeasibility test, rows of A^T at the projected w~: g = A^T w (unscaled),
@@ -174,6 +216,12 @@ struct InfColEpi {
     else if (!lf && uf) lam = fmin(lam, 0.0);
     r2 += (g + lam) * (g + lam);
     dobj += support_term(lam, lo, hi);
+  }
+  __device__ __forceinline__ void clear() { r2 = dobj = 0.0; }
+  __device__ __forceinline__ void sink(const AccSink &k, int r) const {
+    if (!k.p) return;
+    k.p[Q_IDR * k.stride + k.base + r] = r2;
+    k.p[Q_IDOC * k.stride + k.base + r] = dobj;
   }
 };
 

@@ -61,8 +61,11 @@ constexpr int kPolishStall = 256;
 enum {
   Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P,
   Q_ICD, Q_IPVC, Q_IPVR, Q_IDR, Q_IDOR, Q_IDOC,
-  Q_CN, Q_BN, Q_PW, NQ
+  Q_CN, Q_BN, Q_PW, Q_PWA, NQ
 };
+// (Q_PW: ||A^T A v||^2 of the power iteration's A^T passes; Q_PWA: ||A v||^2
+// of its final pass over A.  Every quantity is summed from one matrix's
+// kernels only, so the per-row slots of segmented rows never mix matrices.)
 
 // whether the check at iteration t tests for infeasibility
 __host__ __device__ __forceinline__ bool infeas_due(long long t, int K, int every) {

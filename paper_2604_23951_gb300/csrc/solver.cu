@@ -37,6 +37,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -58,10 +60,12 @@ constexpr int kBlock = GB300_BLOCK;
 #endif
 constexpr int kMinBlocks = GB300_MIN_BLOCKS;
 
-// deterministic block reduction of NQL accumulators into partials[q * G + block]
+// deterministic block reduction of NQL accumulators into partials[q * GP + block]
+// (GP: the stride of a quantity, the grid's G slots followed by one slot per
+// segmented row)
 template <int NQL>
 __device__ __forceinline__ void store_partials(double (&acc)[NQL], const int (&qidx)[NQL],
-                                               double *partials, int G) {
+                                               double *partials, int GP) {
   __shared__ double sh[NQL][kBlock / 32];
 #pragma unroll
   for (int q = 0; q < NQL; ++q) {
@@ -72,16 +76,16 @@ __device__ __forceinline__ void store_partials(double (&acc)[NQL], const int (&q
   if (threadIdx.x < NQL) {
     double s = 0;
     for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
-    partials[qidx[threadIdx.x] * G + blockIdx.x] = s;
+    partials[qidx[threadIdx.x] * GP + blockIdx.x] = s;
   }
 }
 
-// fixed-order sum of one quantity's partials by a whole CTA; result in all threads
-__device__ double reduce_partials(const double *partials, int q, int G) {
+// fixed-order sum of one quantity's GP partials by a whole CTA; result in all threads
+__device__ double reduce_partials(const double *partials, int q, int GP) {
   __shared__ double sh[kBlock / 32];
   __shared__ double out;
   double s = 0;
-  for (int b = threadIdx.x; b < G; b += blockDim.x) s += partials[q * G + b];
+  for (int b = threadIdx.x; b < GP; b += blockDim.x) s += partials[q * GP + b];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -142,7 +146,7 @@ __global__ void k_apply_matrix(int rows, const int *__restrict__ rp, const int *
 __global__ void k_apply_cols(int n, const double *__restrict__ c0, const double *__restrict__ lx0,
                              const double *__restrict__ ux0, const double *__restrict__ dc,
                              double *__restrict__ c, double *__restrict__ lx,
-                             double *__restrict__ ux, double *partials, int G) {
+                             double *__restrict__ ux, double *partials, int GP) {
   double acc[1] = {0.0};
   const int qi[1] = {Q_CN};
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -153,13 +157,13 @@ __global__ void k_apply_cols(int n, const double *__restrict__ c0, const double 
     ux[j] = ux0[j] / d;
     acc[0] += cj * cj;
   }
-  store_partials<1>(acc, qi, partials, G);
+  store_partials<1>(acc, qi, partials, GP);
 }
 
 // lc~ = dr lc, uc~ = dr uc; partial ||bhat~||^2 (finite sides, equality once)
 __global__ void k_apply_rows(int m, const double *__restrict__ lc0, const double *__restrict__ uc0,
                              const double *__restrict__ dr, double *__restrict__ lc,
-                             double *__restrict__ uc, double *partials, int G) {
+                             double *__restrict__ uc, double *partials, int GP) {
   double acc[1] = {0.0};
   const int qi[1] = {Q_BN};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -171,7 +175,7 @@ __global__ void k_apply_rows(int m, const double *__restrict__ lc0, const double
     if (lf) acc[0] += l * l;
     if (uf && !(lf && l == u)) acc[0] += u * u;
   }
-  store_partials<1>(acc, qi, partials, G);
+  store_partials<1>(acc, qi, partials, GP);
 }
 
 __global__ void k_fill(double *p, double v, int n) {
@@ -187,7 +191,15 @@ struct MatDev {
   int ntiles;
   int nlong;  // rows [0, nlong) are long rows reduced by a whole CTA
   const int *rp, *ci;
+  SegCtx seg;  // segmented rows (sink: the partials of the launching kernel)
 };
+
+// the matrix with its segment sums' per-row slots in `partials` (stride GP,
+// after the G per-CTA slots)
+__host__ __device__ __forceinline__ SegCtx seg_sink(SegCtx s, double *partials, int GP, int G) {
+  s.sink = AccSink{partials, GP, G};
+  return s;
+}
 
 // kBlock / 32 accumulators of shared memory for the whole-CTA rows
 template <typename T, typename V, typename Acc>
@@ -200,30 +212,34 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, con
                                                        const double *__restrict__ vec, double *out,
                                                        int *err) {
   StoreSqEpi<double> e{out, 0.0};
+  SegCtx sc = M.seg;
+  sc.sink = AccSink{nullptr, 0, 0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
-                                    red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    sc);
 }
 
+// QI: Q_PW for the A^T passes, Q_PWA for the final pass over A
+template <int QI>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
                                                           const double *__restrict__ vec,
-                                                          double *out, double *partials, int G,
+                                                          double *out, double *partials, int GP,
                                                           int *err) {
-  StoreSqEpi<double> e{out, 0.0};
+  StoreSqEpi<double, QI> e{out, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
-                                    red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    seg_sink(M.seg, partials, GP, gridDim.x));
   double acc[1] = {e.acc};
-  const int qi[1] = {Q_PW};
-  store_partials<1>(acc, qi, partials, G);
+  const int qi[1] = {QI};
+  store_partials<1>(acc, qi, partials, GP);
 }
 
 // v = w / ||w|| (every CTA reduces the partials in the same fixed order)
 // v = w / ||w||; a zero w (the start was orthogonal to A's row space)
 // continues from the fallback start vector
 __global__ void k_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
-                            const double *__restrict__ fallback, const double *partials, int G) {
-  double nw = sqrt(reduce_partials(partials, Q_PW, G));
+                            const double *__restrict__ fallback, const double *partials, int GP) {
+  double nw = sqrt(reduce_partials(partials, Q_PW, GP));
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
     v[j] = nw > 0.0 ? w[j] / nw : fallback[j];
 }
@@ -231,11 +247,11 @@ __global__ void k_normalize(int n, const double *__restrict__ w, double *__restr
 // ---------------------------------------------------------------------------
 // state set-up
 
-__global__ void k_setup_final(State *st, const double *partials, int G, double eta_given,
+__global__ void k_setup_final(State *st, const double *partials, int GP, double eta_given,
                               double omega_given, int power_done) {
-  double cn = sqrt(reduce_partials(partials, Q_CN, G));
-  double bn = sqrt(reduce_partials(partials, Q_BN, G));
-  double pw = power_done ? sqrt(reduce_partials(partials, Q_PW, G)) : 0.0;
+  double cn = sqrt(reduce_partials(partials, Q_CN, GP));
+  double bn = sqrt(reduce_partials(partials, Q_BN, GP));
+  double pw = power_done ? sqrt(reduce_partials(partials, Q_PWA, GP)) : 0.0;
   if (threadIdx.x == 0) {
     double eta = eta_given > 0 ? eta_given : (pw > 0 ? 0.998 / pw : 1.0);
     double om = omega_given > 0 ? omega_given : ((cn > 0 && bn > 0) ? cn / bn : 1.0);
@@ -294,30 +310,30 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
     const double *__restrict__ y, const float *__restrict__ yf, const double *__restrict__ c,
     const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
     double *xbar, float *xbar_f, double *xhat, const State *__restrict__ st, int j,
-    double *partials, int G, int *err) {
+    double *partials, int GP, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
   double acc[2];
+  const SegCtx sc = seg_sink(M.seg, CHECK ? partials : nullptr, GP, gridDim.x);
   if (MIXED && st->mixed_active) {
     PrimalEpi<CHECK, true> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                              halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
-                                       red_smem<T, float, float>(),
-                          blockIdx.x, gridDim.x);
+                               red_smem<T, float, float>(), blockIdx.x, gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     PrimalEpi<CHECK, false> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                               halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y,
-                                              e, red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, y, e,
+                                      red_smem<double, double, double>(), blockIdx.x,
+                                      gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
   if (CHECK) {
     const int qi[2] = {Q_XRES, Q_XD};
-    store_partials<2>(acc, qi, partials, G);
+    store_partials<2>(acc, qi, partials, GP);
   }
 }
 
@@ -326,31 +342,31 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
     const double *__restrict__ xbar, const float *__restrict__ xbar_f,
     const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
-    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int G,
+    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int GP,
     int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
   double acc[2];
+  const SegCtx sc = seg_sink(M.seg, CHECK ? partials : nullptr, GP, gridDim.x);
   if (MIXED && st->mixed_active) {
     DualEpi<CHECK, true> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                            0.0, 0.0, 0.0, 0.0};
     warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
-                                       red_smem<T, float, float>(),
-                          blockIdx.x, gridDim.x);
+                               red_smem<T, float, float>(), blockIdx.x, gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
     DualEpi<CHECK, false> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                             0.0, 0.0, 0.0, 0.0};
-    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64,
-                                              xbar, e, red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+    warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va64, xbar, e,
+                                      red_smem<double, double, double>(), blockIdx.x,
+                                      gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   }
   if (CHECK) {
     const int qi[2] = {Q_YRES, Q_YD};
-    store_partials<2>(acc, qi, partials, G);
+    store_partials<2>(acc, qi, partials, GP);
   }
 }
 
@@ -359,14 +375,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     const double *__restrict__ dr, const double *__restrict__ idr,
     const double *__restrict__ lc0, const double *__restrict__ uc0,
     const double *__restrict__ yhat, const State *__restrict__ st, int force, double *partials,
-    int G, int *err) {
+    int GP, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
-  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e, red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    seg_sink(M.seg, partials, GP, gridDim.x));
   double acc[3] = {e.rp2, e.rdy2, e.dy};
   const int qi[3] = {Q_RP, Q_RDY, Q_DY};
-  store_partials<3>(acc, qi, partials, G);
+  store_partials<3>(acc, qi, partials, GP);
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
@@ -374,14 +391,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     const double *__restrict__ c, const double *__restrict__ dc, const double *__restrict__ idc,
     const double *__restrict__ c0, const double *__restrict__ lx0, const double *__restrict__ ux0,
     const double *__restrict__ xhat, double *zbuf, const State *__restrict__ st, int force,
-    double *partials, int G, int *err) {
+    double *partials, int GP, int *err) {
   if (!force && st->status != ST_RUNNING) return;
   KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
-  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e, red_smem<double, double, double>(),
-                          blockIdx.x, gridDim.x);
+  warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e,
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    seg_sink(M.seg, partials, GP, gridDim.x));
   double acc[3] = {e.rd2, e.dl, e.p};
   const int qi[3] = {Q_RD, Q_DL, Q_P};
-  store_partials<3>(acc, qi, partials, G);
+  store_partials<3>(acc, qi, partials, GP);
 }
 
 // Infeasibility test of a check (skipped unless due): the direction
@@ -392,13 +410,13 @@ __global__ void k_inf_prep(const State *__restrict__ st, int n, const double *__
                            const double *__restrict__ x0, const double *__restrict__ dc,
                            const double *__restrict__ c0, const double *__restrict__ lx0,
                            const double *__restrict__ ux0, double *dbuf, double *partials,
-                           int G) {
+                           int GP) {
   if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
   double acc[2] = {0.0, 0.0};
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
     inf_col_prep(j, xhat, x0, dc, c0, lx0, ux0, dbuf, acc[0], acc[1]);
   const int qi[2] = {Q_ICD, Q_IPVC};
-  store_partials<2>(acc, qi, partials, G);
+  store_partials<2>(acc, qi, partials, GP);
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_rows(
@@ -406,41 +424,43 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_rows(
     const double *__restrict__ dr, const double *__restrict__ idr,
     const double *__restrict__ lc0, const double *__restrict__ uc0,
     const double *__restrict__ yhat, const double *__restrict__ y0, double *wbuf,
-    const State *__restrict__ st, double *partials, int G) {
+    const State *__restrict__ st, double *partials, int GP) {
   if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
   InfRowEpi e{dr, idr, lc0, uc0, yhat, y0, wbuf, 0.0, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, dbuf, e,
-                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    seg_sink(M.seg, partials, GP, gridDim.x));
   double acc[2] = {e.v2, e.dobj};
   const int qi[2] = {Q_IPVR, Q_IDOR};
-  store_partials<2>(acc, qi, partials, G);
+  store_partials<2>(acc, qi, partials, GP);
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_inf_cols(
     MatDev M, const double *__restrict__ va, const double *__restrict__ wbuf,
     const double *__restrict__ idc, const double *__restrict__ lx0,
-    const double *__restrict__ ux0, const State *__restrict__ st, double *partials, int G) {
+    const double *__restrict__ ux0, const State *__restrict__ st, double *partials, int GP) {
   if (st->status != ST_RUNNING || !infeas_due(st->t, st->K, st->infeas_every)) return;
   InfColEpi e{idc, lx0, ux0, 0.0, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, wbuf, e,
-                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x);
+                                    red_smem<double, double, double>(), blockIdx.x, gridDim.x,
+                                    seg_sink(M.seg, partials, GP, gridDim.x));
   double acc[2] = {e.r2, e.dobj};
   const int qi[2] = {Q_IDR, Q_IDOC};
-  store_partials<2>(acc, qi, partials, G);
+  store_partials<2>(acc, qi, partials, GP);
 }
 
 // K4: the check.  eval_only: fill in the KKT fields and mark ITER_LIMIT.
 // One warp per quantity (fixed lane stride over the G partials, fixed
 // shuffle tree: deterministic), all quantities' loads in flight at once; the
 // infeasibility quantities only on the checks that test for it.
-__global__ void k_check(State *st, const double *partials, int G, int eval_only) {
+__global__ void k_check(State *st, const double *partials, int GP, int eval_only) {
   if (!eval_only && st->status != ST_RUNNING) return;
   __shared__ double q[NQ];
   const int nq = (!eval_only && infeas_due(st->t, st->K, st->infeas_every)) ? Q_CN : Q_ICD;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < nq; i += nw) {
     double s = 0.0;
-    for (int b = lane; b < G; b += 32) s += partials[i * G + b];
+    for (int b = lane; b < GP; b += 32) s += partials[i * GP + b];
     s = warp_sum(s);
     if (lane == 0) q[i] = s;
   }
@@ -488,6 +508,7 @@ __global__ void k_unscale(int n, int m, const double *__restrict__ dc, const dou
 
 constexpr size_t kSmem64 = 0;  // the warp engine needs no dynamic shared memory
 constexpr size_t kSmem32 = 0;
+constexpr int kDefaultShape = 3;  // tile_candidates()[3]: run_max 16, 2048 nonzeros
 
 struct DeviceLP {
   lp_device_ctx ctx{};
@@ -501,7 +522,15 @@ struct DeviceLP {
   std::vector<int> rperm, cperm;  // new -> old
   int ntilesA = 0, ntilesT = 0, nlongA = 0, nlongT = 0;
   int2 *tilesA = nullptr, *tilesT = nullptr;
-  int G = 1;
+  // segmented rows of A and A^T (see spmv_warp.cuh)
+  int *segbaseA = nullptr, *segbaseT = nullptr, *segcntA = nullptr, *segcntT = nullptr;
+  double *segpartA = nullptr, *segpartT = nullptr;
+  int seglenA = 0, seglenT = 0, nsegrowsA = 0, nsegrowsT = 0;
+  // every candidate shape's tile table (host), and which one is on the device
+  std::vector<TilePlan> plansA, plansT;
+  int planA = -1, planT = -1;
+  int G = 1;   // CTAs of the grid-wide kernels
+  int GP = 1;  // stride of a quantity in `partials`: G + the most segmented rows
   int *A_rp = nullptr, *A_ci = nullptr, *T_rp = nullptr, *T_ci = nullptr;
   double *A_v0 = nullptr, *T_v0 = nullptr, *A_v = nullptr, *T_v = nullptr;
   float *A_vf = nullptr, *T_vf = nullptr;
@@ -514,6 +543,9 @@ struct DeviceLP {
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
   double *pv = nullptr, *pv0 = nullptr, *pw = nullptr, *pu = nullptr;
   int infeas_every = 0;  // of the current solve (host copy of the state's)
+  // last tile-shape measurement: mean ms of K1 (rows of A^T) and K2 (rows of
+  // A) per candidate, or empty when the choice came from the cache / opts
+  std::vector<double> tune_msT, tune_msA;
   double *ox = nullptr, *oy = nullptr, *oxi = nullptr, *oyi = nullptr;
   float *xbar_f = nullptr, *yf = nullptr;
   double *partials = nullptr;
@@ -530,8 +562,14 @@ struct DeviceLP {
   void *flush = nullptr;
   size_t flush_bytes = 0;
 
-  MatDev matA() const { return MatDev{tilesA, ntilesA, nlongA, A_rp, A_ci}; }
-  MatDev matT() const { return MatDev{tilesT, ntilesT, nlongT, T_rp, T_ci}; }
+  MatDev matA() const {
+    return MatDev{tilesA, ntilesA, nlongA, A_rp, A_ci,
+                  SegCtx{segbaseA, segpartA, segcntA, seglenA, AccSink{nullptr, 0, 0}}};
+  }
+  MatDev matT() const {
+    return MatDev{tilesT, ntilesT, nlongT, T_rp, T_ci,
+                  SegCtx{segbaseT, segpartT, segcntT, seglenT, AccSink{nullptr, 0, 0}}};
+  }
   int *errp() const { return &st->err; }
 
   void *dalloc(size_t bytes) {
@@ -580,6 +618,54 @@ struct DeviceLP {
     return (int)g;
   }
 };
+
+// Tile shapes of the single-LP path (segmented long rows): run_max 8, 16, 32
+// entries per lane, times 512 or 2048 nonzeros per tile.
+const std::vector<TileShape> &tile_candidates() {
+  static const std::vector<TileShape> c = [] {
+    std::vector<TileShape> v;
+    for (int r : {8, 16, 32})
+      for (int t : {512, 2048}) v.push_back(TileShape{r, t, true});
+    return v;
+  }();
+  return c;
+}
+
+// index of a candidate shape, or -1
+int tile_candidate_index(int run_max, int tile_nnz) {
+  const std::vector<TileShape> &c = tile_candidates();
+  for (size_t i = 0; i < c.size(); ++i)
+    if (c[i].run_max == run_max && c[i].tile_nnz == tile_nnz) return (int)i;
+  return -1;
+}
+
+// Put candidate plans ca (rows of A) and ct (rows of A^T) on the device,
+// in stream order on the library stream.  A change drops the captured
+// iteration graphs (their kernel arguments hold the tile counts).
+void install_plan(DeviceLP *d, int ca, int ct) {
+  if (ca == d->planA && ct == d->planT) return;
+  auto put = [d](const TilePlan &p, int2 *tiles, int *segbase, int &ntiles, int &nlong,
+                 int &nsegrows, int &seglen) {
+    ntiles = (int)p.tiles.size();
+    nlong = p.nlong;
+    nsegrows = p.nsegrows;
+    seglen = p.seg_len;
+    if (ntiles)
+      CK(cudaMemcpyAsync(tiles, p.tiles.data(), sizeof(int2) * ntiles, cudaMemcpyHostToDevice,
+                         d->s));
+    CK(cudaMemcpyAsync(segbase, p.seg_base.data(), sizeof(int) * p.seg_base.size(),
+                       cudaMemcpyHostToDevice, d->s));
+  };
+  put(d->plansA[ca], d->tilesA, d->segbaseA, d->ntilesA, d->nlongA, d->nsegrowsA, d->seglenA);
+  put(d->plansT[ct], d->tilesT, d->segbaseT, d->ntilesT, d->nlongT, d->nsegrowsT, d->seglenT);
+  d->planA = ca;
+  d->planT = ct;
+  for (int q = 0; q < 2; ++q)
+    if (d->graph[q]) {
+      CK(cudaGraphExecDestroy(d->graph[q]));
+      d->graph[q] = nullptr;
+    }
+}
 
 DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
   DeviceLP *d = new DeviceLP();
@@ -630,14 +716,41 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     d->n = n;
     d->nnz = nnz;
     Layout L;
-    build_layout(h, L);
+    const std::vector<TileShape> &cands = tile_candidates();
+    build_layout(h, L, cands[kDefaultShape]);
     d->rperm = std::move(L.rperm);
     d->cperm = std::move(L.cperm);
-    d->nlongA = L.nlongA;
-    d->nlongT = L.nlongT;
-    const std::vector<int2> &tA = L.tA, &tT = L.tT;
-    d->ntilesA = (int)tA.size();
-    d->ntilesT = (int)tT.size();
+    // the tile tables of every candidate shape (same row order, so one
+    // stored matrix serves them all); the device buffers hold the largest
+    {
+      std::vector<int64_t> sa(m), st(n);
+      for (int i = 0; i < m; ++i) sa[i] = L.arp[i + 1] - L.arp[i];
+      for (int j = 0; j < n; ++j) st[j] = L.trp[j + 1] - L.trp[j];
+      d->plansA.assign(cands.size(), TilePlan());
+      d->plansT.assign(cands.size(), TilePlan());
+      for (size_t c = 0; c < cands.size(); ++c) {
+        if ((int)c == kDefaultShape) {
+          d->plansA[c] = std::move(L.pA);
+          d->plansT[c] = std::move(L.pT);
+        } else {
+          plan_tiles(sa, cands[c], d->plansA[c]);
+          plan_tiles(st, cands[c], d->plansT[c]);
+        }
+      }
+    }
+    size_t capTA = 1, capTT = 1, capSA = 1, capST = 1, capRA = 0, capRT = 0;
+    int maxtiles = 0;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const TilePlan &a = d->plansA[c], &t = d->plansT[c];
+      capTA = std::max(capTA, a.tiles.size());
+      capTT = std::max(capTT, t.tiles.size());
+      capSA = std::max(capSA, (size_t)a.seg_base.back());
+      capST = std::max(capST, (size_t)t.seg_base.back());
+      capRA = std::max(capRA, (size_t)a.nsegrows);
+      capRT = std::max(capRT, (size_t)t.nsegrows);
+      maxtiles = std::max(maxtiles, (int)std::max(a.tiles.size(), t.tiles.size()));
+    }
+    d->planA = d->planT = -1;
     d->bnorm = L.bnorm;
     d->cnorm = L.cnorm;
     d->off = L.off;
@@ -653,8 +766,14 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     d->T_v = d->dalloc_n<double>(nzT);
     d->A_vf = d->dalloc_n<float>(nzA);
     d->T_vf = d->dalloc_n<float>(nzT);
-    d->tilesA = d->dalloc_n<int2>(std::max<size_t>(tA.size(), 1));
-    d->tilesT = d->dalloc_n<int2>(std::max<size_t>(tT.size(), 1));
+    d->tilesA = d->dalloc_n<int2>(capTA);
+    d->tilesT = d->dalloc_n<int2>(capTT);
+    d->segbaseA = d->dalloc_n<int>(capRA + 1);
+    d->segbaseT = d->dalloc_n<int>(capRT + 1);
+    d->segcntA = d->dalloc_n<int>(std::max<size_t>(capRA, 1));
+    d->segcntT = d->dalloc_n<int>(std::max<size_t>(capRT, 1));
+    d->segpartA = d->dalloc_n<double>(capSA);
+    d->segpartT = d->dalloc_n<double>(capST);
     double **cols_[] = {&d->c0, &d->lx0, &d->ux0, &d->c, &d->lx, &d->ux, &d->dc, &d->dc2,
                         &d->idc, &d->x, &d->x0, &d->xbar, &d->xhat, &d->zbuf, &d->pv,
                         &d->pv0, &d->pw, &d->ox, &d->oxi};
@@ -670,10 +789,12 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_primal<double, true>, kBlock, kSmem64));
     occ = std::max(occ, 1);
     const int wpb = kBlock / 32;
-    int need = std::max(std::max((d->ntilesA + wpb - 1) / wpb, d->nlongA),
-                        std::max((d->ntilesT + wpb - 1) / wpb, d->nlongT));
+    int need = (maxtiles + wpb - 1) / wpb;
     d->G = std::max(1, std::min(need, d->sm_count * occ));
-    d->partials = d->dalloc_n<double>((size_t)NQ * d->G);
+    // a quantity's partials: one per CTA, then one per segmented row (those
+    // of the other matrix stay zero)
+    d->GP = d->G + (int)std::max(capRA, capRT);
+    d->partials = d->dalloc_n<double>((size_t)NQ * d->GP);
     d->st = d->dalloc_n<State>(1);
     CK(cudaMemcpyAsync(d->A_rp, L.arp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->A_ci, L.aci.data(), sizeof(int) * nzA, cudaMemcpyHostToDevice, d->s));
@@ -681,10 +802,10 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     CK(cudaMemcpyAsync(d->T_rp, L.trp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->T_ci, L.tci.data(), sizeof(int) * nzT, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->T_v0, L.tv.data(), sizeof(double) * nzT, cudaMemcpyHostToDevice, d->s));
-    if (!tA.empty())
-      CK(cudaMemcpyAsync(d->tilesA, tA.data(), sizeof(int2) * tA.size(), cudaMemcpyHostToDevice, d->s));
-    if (!tT.empty())
-      CK(cudaMemcpyAsync(d->tilesT, tT.data(), sizeof(int2) * tT.size(), cudaMemcpyHostToDevice, d->s));
+    CK(cudaMemsetAsync(d->partials, 0, sizeof(double) * NQ * d->GP, d->s));
+    CK(cudaMemsetAsync(d->segcntA, 0, sizeof(int) * std::max<size_t>(capRA, 1), d->s));
+    CK(cudaMemsetAsync(d->segcntT, 0, sizeof(int) * std::max<size_t>(capRT, 1), d->s));
+    install_plan(d, kDefaultShape, kDefaultShape);
     CK(cudaMemcpyAsync(d->c0, L.c0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->lx0, L.lx0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
     CK(cudaMemcpyAsync(d->ux0, L.ux0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, d->s));
@@ -725,12 +846,12 @@ void launch_primal(DeviceLP *d, bool wr, int grid, int j) {
   if (wr)
     k_primal<T, true><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                     d->ux, d->x, d->x0, d->xbar, d->xbar_f,
-                                                    d->xhat, d->st, j, d->partials, d->G,
+                                                    d->xhat, d->st, j, d->partials, d->GP,
                                                     d->errp());
   else
     k_primal<T, false><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                      d->ux, d->x, d->x0, d->xbar, d->xbar_f,
-                                                     d->xhat, d->st, j, d->partials, d->G,
+                                                     d->xhat, d->st, j, d->partials, d->GP,
                                                      d->errp());
 }
 
@@ -751,20 +872,20 @@ void launch_dual(DeviceLP *d, bool wr, int grid, int j) {
   if (wr)
     k_dual<T, true><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                   d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
-                                                  d->partials, d->G, d->errp());
+                                                  d->partials, d->GP, d->errp());
   else
     k_dual<T, false><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                    d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
-                                                   d->partials, d->G, d->errp());
+                                                   d->partials, d->GP, d->errp());
 }
 
 void launch_kkt(DeviceLP *d, int force) {
   k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr, d->lc0,
-                                              d->uc0, d->yhat, d->st, force, d->partials, d->G,
+                                              d->uc0, d->yhat, d->st, force, d->partials, d->GP,
                                               d->errp());
   k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc, d->idc,
                                               d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st,
-                                              force, d->partials, d->G, d->errp());
+                                              force, d->partials, d->GP, d->errp());
 }
 
 // one PDHG iteration (position j in its chunk); check adds K3, K4, K5
@@ -788,15 +909,15 @@ void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only)
     if (d->infeas_every > 0) {
       // pw (n) and pu (m) are the power iteration's vectors, free after set-up
       k_inf_prep<<<d->G, kBlock, 0, d->s>>>(d->st, d->n, d->xhat, d->x0, d->dc, d->c0, d->lx0,
-                                            d->ux0, d->pw, d->partials, d->G);
+                                            d->ux0, d->pw, d->partials, d->GP);
       k_inf_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pw, d->dr, d->idr,
                                                   d->lc0, d->uc0, d->yhat, d->y0, d->pu, d->st,
-                                                  d->partials, d->G);
+                                                  d->partials, d->GP);
       k_inf_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->idc, d->lx0,
-                                                  d->ux0, d->st, d->partials, d->G);
+                                                  d->ux0, d->st, d->partials, d->GP);
       d->launches += 3;
     }
-    k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 0);
+    k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->GP, 0);
     k_restart<<<d->grid_for(std::max(d->m, d->n)), kBlock, 0, d->s>>>(
         d->st, d->n, d->m, d->x, d->x0, d->xhat, d->y, d->y0, d->yhat, mixed ? d->yf : nullptr);
     d->launches += 4;
@@ -805,12 +926,96 @@ void launch_iteration(DeviceLP *d, bool mixed, int j, bool check, bool hat_only)
 
 void final_eval(DeviceLP *d) {
   launch_kkt(d, 1);
-  k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, 1);
+  k_check<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->GP, 1);
   d->launches += 3;
 }
 
+// ---- tile-shape autotuner of the grid engine -------------------------------
+//
+// Per matrix (rows of A for K2, rows of A^T for K1) the candidate shapes are
+// timed on the first solve of a size class -- (log2 rows, 2 log2 mean row
+// length, precision) -- with CUDA events around each kernel, 2 warm-up and
+// 4 timed iterations per candidate, after the scaling and before the power
+// iteration; the fastest is kept for the process.  The measured launches
+// run the real iteration kernels on the scaled matrices from the start
+// point; the set-up initialises the iterate and the state afterwards, so
+// the solve itself is the same as with the chosen shape given in the options.
+
+std::mutex g_tune_mu;
+std::map<long long, int> g_tune_cache;
+
+long long tune_key(int mat, long long rows, long long nnz, bool mixed) {
+  const int rb = rows > 0 ? (int)std::floor(std::log2((double)rows)) : 0;
+  const int lb =
+      rows > 0 ? (int)std::floor(2.0 * std::log2(std::max(1.0, (double)nnz / (double)rows))) : 0;
+  return ((long long)mat << 40) | ((long long)(mixed ? 1 : 0) << 32) | ((long long)rb << 16) |
+         (long long)lb;
+}
+
+// measure: 0 = the cached choice or the default shape, 1 = measure on a miss
+void tune_tiles(DeviceLP *d, bool mixed, bool measure) {
+  const std::vector<TileShape> &cands = tile_candidates();
+  const int nc = (int)cands.size();
+  const long long kA = tune_key(0, d->m, d->nnz, mixed), kT = tune_key(1, d->n, d->nnz, mixed);
+  d->tune_msA.clear();
+  d->tune_msT.clear();
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto a = g_tune_cache.find(kA), t = g_tune_cache.find(kT);
+    if (a != g_tune_cache.end() && t != g_tune_cache.end()) {
+      install_plan(d, a->second, t->second);
+      return;
+    }
+  }
+  if (!measure) {
+    install_plan(d, kDefaultShape, kDefaultShape);
+    return;
+  }
+  cudaEvent_t ev[3];
+  for (cudaEvent_t &e : ev) CK(cudaEventCreate(&e));
+  constexpr int kWarm = 2, kTimed = 4;
+  d->tune_msA.assign(nc, 0.0);
+  d->tune_msT.assign(nc, 0.0);
+  for (int c = 0; c < nc; ++c) {
+    install_plan(d, c, c);
+    const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
+    const int gT = d->grid_tiles(d->ntilesT, d->nlongT);
+    for (int r = 0; r < kWarm + kTimed; ++r) {
+      CK(cudaEventRecord(ev[0], d->s));
+      if (mixed) launch_primal<float>(d, false, gT, 1);
+      else launch_primal<double>(d, false, gT, 1);
+      CK(cudaEventRecord(ev[1], d->s));
+      if (mixed) launch_dual<float>(d, false, gA, 1);
+      else launch_dual<double>(d, false, gA, 1);
+      CK(cudaEventRecord(ev[2], d->s));
+      CK(cudaEventSynchronize(ev[2]));
+      if (r >= kWarm) {
+        float t1 = 0, t2 = 0;
+        CK(cudaEventElapsedTime(&t1, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&t2, ev[1], ev[2]));
+        d->tune_msT[c] += t1 / kTimed;
+        d->tune_msA[c] += t2 / kTimed;
+      }
+    }
+  }
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  const int bA = (int)(std::min_element(d->tune_msA.begin(), d->tune_msA.end()) -
+                       d->tune_msA.begin());
+  const int bT = (int)(std::min_element(d->tune_msT.begin(), d->tune_msT.end()) -
+                       d->tune_msT.begin());
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[kA] = bA;
+    g_tune_cache[kT] = bT;
+  }
+  install_plan(d, bA, bT);
+  d->launches += 2LL * (kWarm + kTimed) * nc;
+}
+
+// tune: 0 = keep the installed tile shapes, 1 = the cached choice or the
+// default, 2 = also measure the candidates on a cache miss
 void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double *xinit_perm,
-                  const double *yinit_perm) {
+                  const double *yinit_perm, int tune) {
   const int m = d->m, n = d->n;
   const int gm = d->grid_for(std::max(m, 1)), gn = d->grid_for(std::max(n, 1));
   const int gwm = d->grid_for((long long)std::max(m, 1) * 32);
@@ -854,12 +1059,20 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
   k_apply_matrix<true><<<gwn, kBlock, 0, d->s>>>(n, d->T_rp, d->T_ci, d->T_v0, d->dc, d->dr,
                                                  d->T_v, mixed ? d->T_vf : nullptr);
   k_apply_cols<<<d->G, kBlock, 0, d->s>>>(n, d->c0, d->lx0, d->ux0, d->dc, d->c, d->lx, d->ux,
-                                          d->partials, d->G);
+                                          d->partials, d->GP);
   k_apply_rows<<<d->G, kBlock, 0, d->s>>>(m, d->lc0, d->uc0, d->dr, d->lc, d->uc, d->partials,
-                                          d->G);
+                                          d->GP);
   k_reciprocal<<<gm, kBlock, 0, d->s>>>(m, d->dr, d->idr);
   k_reciprocal<<<gn, kBlock, 0, d->s>>>(n, d->dc, d->idc);
   d->launches += 6;
+  if (tune > 0) {
+    // the measurement's iterations start from the initial point (set again
+    // below); the state is still the host's initial copy (running, zero steps)
+    k_init_x<<<gn, kBlock, 0, d->s>>>(n, d->lx, d->ux, d->dc, xinit_perm, d->x, d->x0);
+    k_init_y<<<gm, kBlock, 0, d->s>>>(m, d->dr, yinit_perm, d->y, d->y0, mixed ? d->yf : nullptr);
+    d->launches += 2;
+    tune_tiles(d, mixed, tune == 2);
+  }
   bool power = !(o.step_size > 0) && n > 0 && m > 0;
   if (power) {
     k_fill<<<gn, kBlock, 0, d->s>>>(d->pv, 1.0 / std::sqrt((double)n), n);
@@ -867,23 +1080,45 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
     const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     for (int it = 0; it < o.power_iters; ++it) {
       k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());
-      k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
-                                                       d->partials, d->G, d->errp());
-      k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->pv0, d->partials, d->G);
+      k_spmv_store_sq<Q_PW><<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
+                                                       d->partials, d->GP, d->errp());
+      k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->pv0, d->partials, d->GP);
       d->launches += 3;
     }
-    k_spmv_store_sq<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu,
-                                                     d->partials, d->G, d->errp());
+    k_spmv_store_sq<Q_PWA><<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu,
+                                                     d->partials, d->GP, d->errp());
     d->launches += 1;
   }
   k_init_x<<<gn, kBlock, 0, d->s>>>(n, d->lx, d->ux, d->dc, xinit_perm, d->x, d->x0);
   k_init_y<<<gm, kBlock, 0, d->s>>>(m, d->dr, yinit_perm, d->y, d->y0, mixed ? d->yf : nullptr);
-  k_setup_final<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->G, o.step_size, o.primal_weight,
+  k_setup_final<<<1, kBlock, 0, d->s>>>(d->st, d->partials, d->GP, o.step_size, o.primal_weight,
                                         power ? 1 : 0);
   d->launches += 3;
 }
 
 }  // namespace
+
+void dev_tile_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
+}
+
+// the last solve's tile shapes and measurement (see lp_get_tile_tuning)
+int dev_tile_tuning(const DeviceLP *d, double *out, int cap) {
+  const std::vector<TileShape> &cands = tile_candidates();
+  const int nc = (int)cands.size();
+  if (cap < 3 + 4 * nc) return -1;
+  out[0] = d->planA;
+  out[1] = d->planT;
+  out[2] = d->tune_msA.empty() ? 0.0 : 1.0;
+  for (int c = 0; c < nc; ++c) {
+    out[3 + 4 * c] = cands[c].run_max;
+    out[4 + 4 * c] = cands[c].tile_nnz;
+    out[5 + 4 * c] = d->tune_msA.empty() ? 0.0 : d->tune_msA[c];
+    out[6 + 4 * c] = d->tune_msT.empty() ? 0.0 : d->tune_msT[c];
+  }
+  return 3 + 4 * nc;
+}
 
 int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *res,
               DeviceSolution &sol, std::string &err) {
@@ -941,8 +1176,20 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     CK(cudaEventCreate(&e1));
     CK(cudaEventCreate(&e2));
     CK(cudaEventRecord(e0, d->s));
+    // tile shapes: given, or the autotuner's (measured after the set-up)
+    const bool fixed_shape = o.tile_run_max > 0 && o.tile_nnz > 0;
+    if (fixed_shape) {
+      const int ci = tile_candidate_index(o.tile_run_max, o.tile_nnz);
+      if (ci < 0) {
+        err = "tile_run_max / tile_nnz is not a candidate shape";
+        return LP_ERR_INVALID;
+      }
+      install_plan(d, ci, ci);
+      d->tune_msA.clear();
+      d->tune_msT.clear();
+    }
     // k_setup_final overwrites the state's running fields; constants stay
-    setup_device(d, o, mixed, xin, yin);
+    setup_device(d, o, mixed, xin, yin, fixed_shape ? 0 : (o.max_iter > 64 ? 2 : 1));
     CK(cudaGetLastError());
     CK(cudaEventRecord(e1, d->s));
     // iteration driver
@@ -1180,11 +1427,11 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
         } else if (which == 2) {
           k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr,
                                                       d->lc0, d->uc0, d->yhat, d->st, 1,
-                                                      d->partials, d->G, d->errp());
+                                                      d->partials, d->GP, d->errp());
         } else {
           k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc,
                                                       d->idc, d->c0, d->lx0, d->ux0, d->xhat,
-                                                      d->zbuf, d->st, 1, d->partials, d->G,
+                                                      d->zbuf, d->st, 1, d->partials, d->GP,
                                                       d->errp());
         }
         CK(cudaEventRecord(b, d->s));

@@ -4,20 +4,21 @@
 // at most 32 consecutive rows.  Every warp of a persistent grid walks its
 // tiles independently -- no CTA barrier inside the loop -- so the warps of an
 // SM hide each other's memory latency.  In a tile each row is reduced by
-// 2^v lanes, and each lane owns `nit` entries of its row per chunk (v and
-// nit from the tile's longest row, so padding is bounded by the length
-// spread inside one tile); a lane issues all its coalesced value / index
-// loads and all its gathers before its first multiply-add.  Group sums are
-// combined with xor shuffles and moved to lane = row, so the epilogue runs
-// with one lane per row and all lanes active.  A warp tile holds about
-// kWarpTileNnz nonzeros so the tiles balance across warps.  Rows longer than
-// kLongRow get a tile of their own (one warp, 32 lanes, chunks of 256
-// entries); rows longer than kCtaRow come first and are each reduced by a
-// whole CTA, so no warp walks a long chain of chunks.
+// 2^v lanes, and each lane owns up to `nit` entries of its row per chunk (v
+// and nit from the tile's longest row and the tile shape, so padding is
+// bounded by the length spread inside one tile); a lane issues all its
+// coalesced value / index loads and all its gathers of a chunk before its
+// first multiply-add.  Group sums are combined with xor shuffles and moved
+// to lane = row, so the epilogue runs with one lane per row.
 //
-// FP64 issue is scarce on GB300 (2 FP64 lanes per clock per SM): every
-// multiply-add a warp issues has (up to the in-tile length spread) all 32
-// lanes on real entries, and the epilogue never runs with idle lanes.
+// Rows too long for one warp's tile are either cut into segments (one warp
+// each; the warp that completes a row's last segment adds the segments'
+// partial sums in segment order and runs the row's epilogue) or, in the
+// batched kernel, reduced by a whole CTA each.
+//
+// FP64 issue is scarce on GB300 (2 FP64 lanes per clock per SM), so the tile
+// shape trades lanes per row (each costs a shuffle-add per pass) against
+// chunks per lane (latency); the autotuner picks it per matrix.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,10 +29,29 @@
 
 namespace gb300lp {
 
-constexpr int kWarpItems = 8;                 // most entries one lane owns per chunk
-constexpr int kLongRow = 32 * kWarpItems;      // longer rows: single-row warp tiles
-constexpr int kCtaRow = 512;                   // longer rows: one whole CTA each
-constexpr int kWarpTileNnz = 512;              // nonzeros a warp tile aims at
+constexpr int kWarpItems = 8;  // most entries one lane owns per chunk
+constexpr int kCtaRow = 512;   // unsegmented plans: longer rows take one whole CTA each
+
+// Where the epilogue of a segmented row leaves its accumulators: the check
+// quantity q of long row r goes to p[q * stride + base + r] (a slot of its
+// own, so the sums do not depend on which warp finished the row).
+struct AccSink {
+  double *p;
+  int stride, base;
+};
+
+// Segmented rows of a matrix (tiles {r, INT_MIN | g}): row r's segments are
+// seg_base[r] .. seg_base[r + 1] - 1, each of seg_len entries (the last one
+// shorter); seg_part holds one partial sum per segment, seg_cnt one arrival
+// counter per segmented row (zero between launches: the finishing warp
+// resets it).  All NULL when the matrix has no segmented rows.
+struct SegCtx {
+  const int *seg_base;
+  double *seg_part;
+  int *seg_cnt;
+  int seg_len;
+  AccSink sink;
+};
 
 // A warp tile: rows [r0, r0 + nrows) with 2^vlog lanes per row and nit
 // entries per lane per chunk, packed as int2 {r0, nrows | vlog << 8 |
@@ -44,8 +64,7 @@ __host__ __device__ __forceinline__ int2 pack_wtile(int r0, int nrows, int vlog,
   return make_int2(r0, nrows | (vlog << 8) | (nit << 12));
 }
 
-__device__ __forceinline__ WarpTile load_wtile(const int2 *__restrict__ tiles, int t) {
-  int2 v = tiles[t];
+__device__ __forceinline__ WarpTile decode_wtile(int2 v) {
   WarpTile w;
   w.r0 = v.x;
   w.nrows = v.y & 0xff;
@@ -127,11 +146,54 @@ __device__ __forceinline__ void cta_rows(int nlong, const int *__restrict__ rp,
 // whole CTA; then each warp walks its warp tiles (wid, wid + wstride, ...).  For
 // every row r: epi.pre(r) then epi.row(r, sum_k va[k] * vec[ci[k]]), both on
 // the same thread.  red: blockDim.x / 32 Acc of shared memory.
+// One segment g of segmented row r (a whole warp): its partial sum goes to
+// seg_part[g]; the warp whose arrival completes the row adds the row's
+// partials in segment order (a fixed shuffle tree: the result does not depend
+// on the arrival order), resets the row's counter and runs the epilogue on a
+// copy of `epi` whose accumulators go to the row's own slots in sc.sink.
+// No warp waits for another.
+template <typename T, typename V, typename Acc, class Epi>
+__device__ __forceinline__ void segment_tile(int r, int g, const int *__restrict__ rp,
+                                             const int *__restrict__ ci,
+                                             const T *__restrict__ va,
+                                             const V *__restrict__ vec, const Epi &epi,
+                                             const SegCtx &sc) {
+  const int lane = threadIdx.x & 31;
+  const int sb = sc.seg_base[r];
+  const int nseg = sc.seg_base[r + 1] - sb;
+  const int lo = rp[r] + (g - sb) * sc.seg_len;
+  const int hi = min(lo + sc.seg_len, rp[r + 1]);
+  Acc s = group_dot<kWarpItems, T, V, Acc>(lo, hi, lane, 32, ci, va, vec);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  int last = 0;
+  if (lane == 0) {
+    sc.seg_part[g] = (double)s;
+    __threadfence();
+    last = atomicAdd(&sc.seg_cnt[r], 1) == nseg - 1;
+  }
+  last = __shfl_sync(kFull, last, 0);
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int q = lane; q < nseg; q += 32) t += __ldcg(&sc.seg_part[sb + q]);
+  t = warp_sum(t);
+  if (lane == 0) {
+    sc.seg_cnt[r] = 0;
+    Epi e = epi;
+    e.clear();
+    e.pre(r);
+    e.row(r, t);
+    e.sink(sc.sink, r);
+  }
+}
+
 template <typename T, typename V, typename Acc, class Epi>
 __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ tiles, int ntiles,
                                           const int *__restrict__ rp, const int *__restrict__ ci,
                                           const T *__restrict__ va, const V *__restrict__ vec,
-                                          Epi &epi, Acc *red, int cta, int ncta) {
+                                          Epi &epi, Acc *red, int cta, int ncta,
+                                          const SegCtx &sc = SegCtx{}) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nthr = blockDim.x;
@@ -141,7 +203,12 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
   const int wid = cta * nwarp + warp;
   const int wstride = ncta * nwarp;
   for (int t = wid; t < ntiles; t += wstride) {
-    const WarpTile w = load_wtile(tiles, t);
+    const int2 raw = tiles[t];
+    if (raw.y < 0) {
+      segment_tile<T, V, Acc>(raw.x, raw.y & 0x7fffffff, rp, ci, va, vec, epi, sc);
+      continue;
+    }
+    const WarpTile w = decode_wtile(raw);
     const bool has = lane < w.nrows;
     if (has) epi.pre(w.r0 + lane);
     // row offsets of the tile, one row per lane

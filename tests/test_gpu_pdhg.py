@@ -259,3 +259,79 @@ def test_original_lp_check_re_solves_an_amplified_postsolve(pkg, dev, engine):
     assert ref.refinements >= 1 and ref.kkt["rel_kkt"] <= 1e-6
     assert rel_obj(k["p"], ref.kkt["p"]) <= 1e-6
     prob.close()
+
+
+SHAPES = [(8, 512), (8, 2048), (16, 512), (16, 2048), (32, 512), (32, 2048)]
+
+
+@pytest.fixture(scope="module")
+def powerlaw_lp():
+    # row lengths from 1 to thousands and 20 columns of 2,500 entries: rows
+    # of A and of A^T longer than 32 * run_max are segmented under every shape
+    return lpgen.c3_powerlaw(seed=7, m=3000, n=8000, row_nnz_target=60000, n_dense=20,
+                             dense_len=2500, kmax=6000)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_tile_shape_matches_oracle(pkg, dev, powerlaw_lp, shape):
+    # 130 iterations straddle the checks at 64 and 128, whose restart test and
+    # primal-weight update read the segmented rows' own partial slots
+    lp = powerlaw_lp
+    eta, om = 0.02, 0.7
+    prob = pkg.Problem(lp, dev)
+    for iters in (40, 130):
+        ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta,
+                                omega0=om)
+        r = prob.solve(max_iter=iters, eps_rel=0.0, step_size=eta, primal_weight=om, engine=1,
+                       tile_run_max=shape[0], tile_nnz=shape[1])
+        assert r.restarts == ref.restarts
+        xi, yi = prob.iterate()
+        assert relerr(xi, ref.x_iter) <= 1e-10 and relerr(yi, ref.y_iter) <= 1e-10
+        assert abs(r.rel_kkt - ref.kkt["rel_kkt"]) <= 1e-9 * (1 + ref.kkt["rel_kkt"])
+        tt = prob.tile_tuning()
+        assert tt["shapes"][tt["A"]] == shape and tt["shapes"][tt["T"]] == shape
+    # the step size (power iteration through the segmented rows) and omega_0
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=1, eps_rel=0.0))
+    r = prob.solve(max_iter=1, eps_rel=0.0, engine=1, tile_run_max=shape[0], tile_nnz=shape[1])
+    assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
+    assert abs(r.omega - ref.omega0) <= 1e-12 * ref.omega0
+    prob.close()
+
+
+def test_autotuner_keeps_the_fastest_shape_and_caches_it(pkg, dev, powerlaw_lp):
+    pkg.tile_cache_clear()
+    prob = pkg.Problem(powerlaw_lp, dev)
+    r1 = prob.solve(max_iter=300, eps_rel=0.0, engine=1)
+    t1 = prob.tile_tuning()
+    assert t1["measured"]
+    assert len(t1["shapes"]) == len(SHAPES) and set(t1["shapes"]) == set(SHAPES)
+    assert all(v > 0 for v in t1["ms_A"] + t1["ms_T"])
+    assert t1["ms_A"][t1["A"]] == min(t1["ms_A"])
+    assert t1["ms_T"][t1["T"]] == min(t1["ms_T"])
+    x1, y1 = prob.iterate()
+    # the same size class again: the cached choice, no measurement, and the
+    # same iterates bit for bit (the measurement does not touch the solve)
+    r2 = prob.solve(max_iter=300, eps_rel=0.0, engine=1)
+    t2 = prob.tile_tuning()
+    assert not t2["measured"] and (t2["A"], t2["T"]) == (t1["A"], t1["T"])
+    x2, y2 = prob.iterate()
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(y1, y2)
+    assert r1.restarts == r2.restarts
+    # and the same as a solve given those shapes (A and A^T each its own)
+    if t1["A"] == t1["T"]:
+        sh = t1["shapes"][t1["A"]]
+        prob.solve(max_iter=300, eps_rel=0.0, engine=1, tile_run_max=sh[0], tile_nnz=sh[1])
+        x3, y3 = prob.iterate()
+        np.testing.assert_array_equal(x1, x3)
+        np.testing.assert_array_equal(y1, y3)
+    prob.close()
+
+
+def test_tile_shape_options_are_validated(pkg, dev):
+    prob = pkg.Problem(lpgen.c1_small(), dev)
+    with pytest.raises(pkg.LPError):
+        prob.solve(max_iter=5, engine=1, tile_run_max=12, tile_nnz=512)
+    with pytest.raises(pkg.LPError):
+        prob.solve(max_iter=5, engine=1, tile_run_max=8, tile_nnz=1000)
+    prob.close()
