@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Benchmark: time to relative KKT error 1e-6 on a planted LP, on GB300.
 
-Default workload: the presolvable planted LP with m = 200k rows, n = 500k
-columns and ~5M nonzeros (seeded, synthetic).  One step = one full device
-solve of the presolved LP (GPU scaling, power-iteration step size,
-restarted reflected Halpern PDHG to rel-KKT <= 1e-6) with the reduced LP
-resident in HBM.  `e2e` times the whole C-ABI path from host buffers
-(lp_create, lp_presolve, lp_solve with its H2D upload, lp_postsolve with the
-D2H of the solution).
+Default workload: the large planted LP with m = 2M rows, n = 5M columns and
+~50M nonzeros (power-law row lengths up to 10k plus 5,000 columns of 2,000
+entries; seeded, synthetic).  One step = one full device solve in FP64
+(GPU scaling, power-iteration step size, restarted reflected Halpern PDHG to
+rel-KKT <= 1e-6) with the LP resident in HBM; the same LP is then solved once
+in the mixed precision and reported beside it with its per-instance
+difference.  `e2e` times the whole C-ABI path from host buffers (lp_create,
+lp_presolve for c2, lp_solve with its H2D upload, lp_postsolve with the D2H of
+the solution).
 
 Prints ONE JSON line (rank 0).  Under torchrun the single-LP workloads
 (c1, c2, c3) run one replica per rank (no collective on the data path;
@@ -17,7 +19,7 @@ or stream (rank 0 the configured one) and the value counts all ranks' LPs
 over the slowest rank's time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c1|c3|c4|c5] [--precision fp64|mixed]
+                  [--workload c3|c2|c1|c4|c5] [--precision fp64|mixed]
 """
 from __future__ import annotations
 
@@ -40,20 +42,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to rel-KKT 1e-6 (s); SpMV HBM GB/s vs peak; batched LPs/s with p50/p99"
 
-# Iterations the device path needs to reach rel-KKT 1e-6 on each seeded
-# workload (FP64), measured with this repository's GPU solver on GB300.  The
-# oracle runs the same iteration, so the reference arm extrapolates its timed
-# sample with this count (at the 200 x 400 workload both take 1217).
+# Iterations to rel-KKT 1e-6 on each seeded workload (FP64) that the
+# reference arm extrapolates its timed oracle sample with: the oracle's own
+# count where it was run to completion (c1: 1217; c2, see ORACLE_C2_FULL),
+# else the device solve's count (c3: a full oracle run would take about 15
+# hours; the two follow the same iteration).
 ITERS_TO_TOL = {"c2": 12161, "c1": 1217, "c3": 51905}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"])
+    p.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c4", "c5"])
     p.add_argument("--requests", type=int, default=96, help="c5: stream length")
     p.add_argument("--lps", type=int, default=512,
                    help="c4: LPs in the batch (512 is the configuration; fewer for profiling)")
@@ -69,21 +72,34 @@ def parse():
     p.add_argument("--launch-ms", type=float, default=0.0,
                    help="c4/c5: device time budget of one bucket launch (0: default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-iters", type=int, default=20)
+    p.add_argument("--no-mixed", action="store_true",
+                   help="c2/c3: skip the solve in the other precision")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="c2/c3: generate the workload at this fraction of its size "
+                        "(profiling captures of a smaller case; not a bench line)")
     p.add_argument("--profile-iters", type=int, default=0,
                    help="ncu capture command: one solve capped at this many iterations, "
                         "no timing and no JSON line")
     return p.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, scale=1.0):
     import lpgen
 
     if name == "c1":
         return lpgen.c1_small(), "planted LP 200 x 400, ~2,000 nnz, equality rows, x >= 0"
     if name == "c3":
+        if scale != 1.0:
+            s = float(scale)
+            lp = lpgen.c3_powerlaw(m=int(2_000_000 * s), n=int(5_000_000 * s),
+                                   row_nnz_target=int(40_000_000 * s),
+                                   n_dense=max(1, int(5_000 * s)))
+            return lp, f"planted LP C3 structure at scale {s:g} ({lp.m} x {lp.n}, {lp.nnz} nnz)"
         return lpgen.c3_powerlaw(), ("planted LP 2M x 5M, ~50M nnz, power-law rows + 5,000 "
                                      "dense columns, box bounds")
+    if scale != 1.0:
+        lp = lpgen.c2_presolvable(scale=float(scale))
+        return lp, f"presolvable planted LP C2 structure at scale {scale:g}"
     return lpgen.c2_presolvable(), ("presolvable planted LP 200k x 500k, ~5M nnz "
                                     "(lognormal rows, 60% eq / 40% ranged, singleton, "
                                     "doubleton, fixed, mixed bounds)")
@@ -242,28 +258,73 @@ def ncu_traffic(kernel: str, workload: str, precision: str):
         return None
 
 
-def oracle_sample(lp, n_iter_gpu, cpu_iters, workload):
-    """The oracle as it stands on this host: presolve, then setup + a bounded
-    number of PDHG iterations; extrapolated to n_iter_gpu iterations."""
+def host_cpu():
+    """(model name, logical cores) of this host"""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
+
+
+def oracle_sample(lp, n_iter_gpu, workload, iters=3):
+    """The oracle as it stands on this host (one thread), on a bounded sample:
+    presolve (C2), one Ruiz pass and one power-iteration step (each scaled to
+    the 10 + 1 passes and 100 steps of the set-up), and `iters` PDHG
+    iterations with the step size and weight given (the set-up's cost is
+    counted above); extrapolated to n_iter_gpu iterations.  Returns (seconds,
+    sample description, CPU seconds spent)."""
+    import numpy as np
+
     import oracle
+    from oracle import pdhg as P
     from oracle import presolve as PS
 
+    spent = time.perf_counter()
     t0 = time.perf_counter()
     pres = PS.presolve(lp) if workload == "c2" else None
     t_pre = time.perf_counter() - t0
     red = pres.reduced if pres is not None else lp
+    A = P.csr_of(red)
     t0 = time.perf_counter()
-    oracle.pdhg_solve(red, oracle.Opts(max_iter=1, eps_rel=0.0))
+    P.ruiz_pc_scaling(A, 1, False)
+    t_ruiz = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    v = np.full(red.n, 1.0)
+    A.T @ (A @ v)
+    t_pow = time.perf_counter() - t0
+    base = dict(eps_rel=0.0, ruiz_iters=0, pock_chambolle=False, infeas_every=0)
+    t0 = time.perf_counter()
+    oracle.pdhg_solve(red, oracle.Opts(max_iter=1, **base), eta=0.01, omega0=1.0)
     t_1 = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.pdhg_solve(red, oracle.Opts(max_iter=1 + cpu_iters, eps_rel=0.0))
-    t_s = time.perf_counter() - t0
-    per_iter = max(t_s - t_1, 0.0) / cpu_iters
-    est = t_pre + t_1 + per_iter * max(n_iter_gpu - 1, 0)
-    sample = (f"oracle presolve ({t_pre:.2f} s) + scaling/step-size setup and 1 iteration "
-              f"({t_1:.2f} s) + {cpu_iters} timed PDHG iterations ({per_iter * 1e3:.1f} ms each) "
-              f"on the presolved LP, extrapolated to {n_iter_gpu} iterations")
-    return est, sample, t_pre + t_s
+    oracle.pdhg_solve(red, oracle.Opts(max_iter=1 + iters, **base), eta=0.01, omega0=1.0)
+    per_iter = max(time.perf_counter() - t0 - t_1, 0.0) / iters
+    setup = 11 * t_ruiz + 100 * t_pow + t_1
+    est = t_pre + setup + per_iter * max(n_iter_gpu - 1, 0)
+    model, nproc = host_cpu()
+    sample = (f"EXTRAPOLATION: oracle (NumPy/SciPy, 1 thread) on {model} ({nproc} logical "
+              f"cores): presolve {t_pre:.2f} s measured; set-up = 11 x one Ruiz/Pock-Chambolle "
+              f"pass ({t_ruiz:.2f} s) + 100 x one power step ({t_pow:.2f} s) + first iteration "
+              f"({t_1:.2f} s); {iters} timed PDHG iterations ({per_iter:.3f} s each) x "
+              f"{n_iter_gpu} iterations (the device solve's count)")
+    return est, sample, time.perf_counter() - spent
+
+
+# Oracle time to rel-KKT 1e-6 on the presolved 200k x 500k workload, run to
+# completion once on an 8-core Xeon @ 2.7 GHz (one thread): its own
+# iteration count (the device's FP64 count on the same LP is within a few
+# restarts of it).
+ORACLE_C2_FULL = None
 
 
 # ---------------------------------------------------------------------------
@@ -271,38 +332,21 @@ def oracle_sample(lp, n_iter_gpu, cpu_iters, workload):
 
 
 def run_reference(args):
-    import numpy as np  # noqa: F401
-
+    """The oracle as the reference arm: each step is a bounded sample of the
+    workload, extrapolated as in oracle_sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    lp, desc = make_workload(args.workload)
+    lp, desc = make_workload(args.workload, args.scale)
     n_iter = ITERS_TO_TOL[args.workload]
-    import oracle
-    from oracle import presolve as PS
-
-    t0 = time.perf_counter()
-    pres = PS.presolve(lp) if args.workload == "c2" else None
-    t_pre = time.perf_counter() - t0
-    red = pres.reduced if pres is not None else lp
-    vals = []
-    t_first = None
+    vals, sample, spent = [], None, 0.0
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.pdhg_solve(red, oracle.Opts(max_iter=1, eps_rel=0.0))
-        t_1 = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        oracle.pdhg_solve(red, oracle.Opts(max_iter=1 + args.cpu_iters, eps_rel=0.0))
-        t_s = time.perf_counter() - t0
-        per_iter = max(t_s - t_1, 0.0) / args.cpu_iters
-        est = t_pre + t_1 + per_iter * (n_iter - 1)
+        est, sample, sp = oracle_sample(lp, n_iter, args.workload)
+        spent += sp
         if step >= args.warmup:
             vals.append(est)
-        t_first = t_first or est
     value = statistics.mean(vals)
-    sample = (f"each step: oracle scaling/step-size setup + 1 iteration, then {args.cpu_iters} "
-              f"PDHG iterations on the presolved LP (oracle presolve {t_pre:.2f} s measured once), "
-              f"extrapolated to {n_iter} iterations")
+    model, nproc = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -310,7 +354,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc},
         "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host_cpu": model, "host_logical_cores": nproc,
+                         "cpu_seconds_spent": round(spent, 1)},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -339,7 +384,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     pkg.load()
-    lp, desc = make_workload(args.workload)
+    lp, desc = make_workload(args.workload, args.scale)
     dev = pkg.TorchDevice(local)
     prec = pkg.LP_MIXED if args.precision == "mixed" else pkg.LP_FP64
     prob = pkg.Problem(lp, dev)
@@ -352,7 +397,7 @@ def run_ours(args):
               f"iterations={r.iterations} launches={r.kernel_launches}", flush=True)
         return 0
     for _ in range(args.warmup):
-        r = prob.solve(precision=prec)
+        r = prob.solve(precision=prec, **solver_kw(args))
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -368,7 +413,7 @@ def run_ours(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        results.append(prob.solve(precision=prec))
+        results.append(prob.solve(precision=prec, **solver_kw(args)))
         ev1.record(stream)
         ev1.synchronize()
         elapsed += ev0.elapsed_time(ev1) / 1e3
@@ -377,10 +422,39 @@ def run_ours(args):
     elapsed = max_over_ranks(elapsed, dist, f"cuda:{local}")
     value = elapsed / args.steps
     r = results[-1]
+    tiles = prob.tile_tuning()
     launches = int(sum(x.kernel_launches for x in results))
+    # the other precision on the same LP: time to 1e-6 and, per instance,
+    # its objective and rel-KKT against this solve's
+    other = None
+    if not args.no_mixed and args.workload in ("c2", "c3"):
+        oprec = pkg.LP_FP64 if prec == pkg.LP_MIXED else pkg.LP_MIXED
+        prob.solve(precision=oprec, max_iter=256, eps_rel=0.0)  # shape measurement
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ro = prob.solve(precision=oprec, **solver_kw(args))
+        ev1.record(stream)
+        ev1.synchronize()
+        t_o = ev0.elapsed_time(ev1) / 1e3
+        fp64 = r if prec == pkg.LP_FP64 else ro
+        mix = ro if prec == pkg.LP_FP64 else r
+        other = {"precision": "mixed" if oprec == pkg.LP_MIXED else "fp64", "value": t_o,
+                 "unit": "s", "iterations": int(ro.iterations),
+                 "fp32_iterations": int(ro.fp32_iterations), "rel_kkt": ro.rel_kkt,
+                 "termination": int(ro.termination),
+                 "mixed_vs_fp64": {
+                     "objective_rel_diff": abs(mix.primal_obj - fp64.primal_obj)
+                     / (1 + abs(fp64.primal_obj)),
+                     "rel_kkt_mixed": mix.rel_kkt, "rel_kkt_fp64": fp64.rel_kkt,
+                     "time_ratio_mixed_over_fp64": (t_o / value if oprec == pkg.LP_MIXED
+                                                    else value / t_o)},
+                 "note": "one solve of the same LP (L2 flushed before it); per-instance "
+                         "objective difference against the FP64 solve"}
     # per-kernel timing (CUDA events, cold L2) for the roofline: the grid
-    # engine's K1 / K2, set up by a short grid-engine solve (tiny LPs are
-    # solved on the cluster engine)
+    # engine's K1 / K2 in the bench precision, set up by a short solve
     prob.solve(precision=prec, max_iter=128, eps_rel=0.0, engine=pkg.LP_ENGINE_GRID)
     prof = prob.profile_kernels(reps=10)
     peak, peak_kind = peaks()
@@ -395,13 +469,13 @@ def run_ours(args):
     barrier()
     e2e_times = []
     h2d = d2h = 0
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 3 if args.workload != "c3" else 1))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = pkg.Problem(lp, dev)
         if args.workload == "c2":
             p2.presolve(enable=presolve_rules(pkg, args))
-        r2 = p2.solve(precision=prec)
+        r2 = p2.solve(precision=prec, **solver_kw(args))
         x, y, z = p2.postsolve()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
@@ -410,19 +484,13 @@ def run_ours(args):
         d2h = 8 * (3 * n2 + 2 * m2)
         p2.close()
     e2e = statistics.mean(e2e_times)
-    kkt_orig = None
-    try:
-        import oracle
-
-        kk = oracle.rel_kkt(lp, x, y)
-        kkt_orig = kk["rel_kkt"]
-        obj_err = abs(kk["p"] - lp.p_star) / (1 + abs(lp.p_star))
-    except Exception:
-        obj_err = None
+    obj_err = abs(r2.primal_obj - lp.p_star) / (1 + abs(lp.p_star))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample, spent = oracle_sample(lp, int(r.iterations), args.cpu_iters, args.workload)
+        est, sample, spent = oracle_sample(lp, int(r.iterations), args.workload)
+        model, nproc = host_cpu()
         cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+               "host_cpu": model, "host_logical_cores": nproc,
                "cpu_seconds_spent": round(spent, 2)}
     if rank == 0:
         line = {
@@ -439,9 +507,13 @@ def run_ours(args):
                 "l2": "L2 flushed (256 MiB write) before each timed solve",
             },
             "iterations": int(r.iterations), "restarts": int(r.restarts),
-            "rel_kkt": r.rel_kkt, "rel_kkt_original_after_postsolve": kkt_orig,
+            "termination": int(r.termination), "rel_kkt": r.rel_kkt,
+            "rel_kkt_original_after_postsolve": r2.rel_kkt_original,
+            "refinements": int(r2.refinements),
             "objective_rel_err_vs_planted": obj_err,
             "us_per_iteration": 1e6 * r.t_solve_s / max(1, r.iterations),
+            "tile_shapes": {"A": tiles["shapes"][tiles["A"]], "AT": tiles["shapes"][tiles["T"]]},
+            "other_precision": other,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                          "peak_kind": peak_kind, "kernel_ms": ms, "algorithmic_bytes": byt,
