@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--lps", type=int, default=512,
                    help="c4: LPs in the batch (512 is the configuration; fewer for profiling)")
     p.add_argument("--rate", type=float, default=200.0, help="c5: arrivals per second")
+    p.add_argument("--sweep", default="2,4,8",
+                   help="c5: arrival rates (req/s) at which the first --sweep-count requests "
+                        "are served again ('' for none)")
+    p.add_argument("--sweep-count", type=int, default=24)
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     p.add_argument("--solo-nnz", type=int, default=0,
                    help="c4/c5: nonzeros from which a request runs the single-LP path (0: default)")
@@ -203,6 +207,18 @@ def solver_kw(args):
     return {"infeas_every": args.infeas_every} if args.infeas_every >= 0 else {}
 
 
+def iter_bytes(m, n, nnz, fp32):
+    """Algorithmic bytes of one PDHG iteration (K1 + K2): both matrices'
+    values and indices once, row offsets, each gathered vector once, and the
+    epilogues' vectors (K1 reads x, x0, c, l, u and writes x and xbar; K2
+    reads y, y0, l, u and writes y; the FP32 SpMV gathers and writes FP32
+    shadows)."""
+    sv = 4 if fp32 else 8
+    k1 = nnz * (sv + 4) + 4 * (n + 1) + sv * m + 8 * 6 * n + sv * n
+    k2 = nnz * (sv + 4) + 4 * (m + 1) + sv * n + 8 * 5 * m + (4 * m if fp32 else 0)
+    return k1 + k2
+
+
 def fifo_latencies(arrivals, services):
     """arrival-to-completion times when requests are served one at a time in
     arrival order with the given service times"""
@@ -269,6 +285,15 @@ def host_cpu():
                     break
     except OSError:
         pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.startswith(("Model name", "Vendor ID")) and ":" in ln:
+                    v = ln.split(":", 1)[1].strip()
+                    model = v if model is None else f"{model} {v}"
+        except Exception:
+            pass
     if model is None:
         import platform
 
@@ -609,7 +634,9 @@ def run_batch(args):
             st["submit_s"] = t_sub
             st["submit_threads"] = nsub
             srv.close()
-            return el, lat, errs, opt, st
+            per = [(int(res[t][0].iterations), int(res[t][0].fp32_iterations),
+                    res[t][0].primal_obj, res[t][0].rel_kkt) for t in tickets]
+            return el, lat, errs, opt, st, per
 
         for _ in range(args.warmup):
             one_step()
@@ -622,27 +649,57 @@ def run_batch(args):
         el = max_over_ranks(statistics.mean(s_[0] for s_ in steps), dist, f"cuda:{local}")
         lat = steps[-1][1]
         value = world * len(lps) / el
+        per = steps[-1][5]
+        # the batch as a roofline: the algorithmic bytes of every slot
+        # iteration (each LP's FP32-SpMV iterations and FP64 ones) over the
+        # batch's wall time, against the measured copy bandwidth
+        peak, peak_kind = peaks()
+        tot_bytes = sum(iter_bytes(lp.m, lp.n, lp.nnz, True) * f32
+                        + iter_bytes(lp.m, lp.n, lp.nnz, False) * (its - f32)
+                        for lp, (its, f32, _, _) in zip(lps, per))
+        achieved = tot_bytes / statistics.mean(s_[0] for s_ in steps) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_batch",
+                "peak_kind": peak_kind,
+                "note": "algorithmic bytes of every slot-iteration of the batch (K1 + K2 bytes "
+                        "at each iteration's SpMV precision) / the batch's wall time, which also "
+                        "holds submission, set-up, checks and the host loop"}
         # comparator: the same LPs solved singly in plain FP64 (lp_solve, one
-        # after another), on every 16th LP of the batch
-        sub = lps[::16] if len(lps) >= 16 else lps[:1]
+        # after another), on every 16th LP of the batch; per instance the
+        # batch's (mixed) objective against that FP64 solve
+        idx = list(range(0, len(lps), 16)) if len(lps) >= 16 else [0]
         t0 = time.perf_counter()
-        for lp in sub:
-            p = pkg.Problem(lp, dev)
-            p.solve(precision=pkg.LP_FP64)
+        diffs = []
+        for j in idx:
+            p = pkg.Problem(lps[j], dev)
+            rs = p.solve(precision=pkg.LP_FP64)
             p.close()
+            diffs.append({"item": j, "m": int(lps[j].m),
+                          "objective_rel_diff": abs(per[j][2] - rs.primal_obj)
+                          / (1 + abs(rs.primal_obj)),
+                          "rel_kkt_batch": per[j][3], "rel_kkt_fp64": rs.rel_kkt})
         ts = time.perf_counter() - t0
-        single = {"LPs_per_s": len(sub) / ts, "sample": f"{len(sub)} of the 512 LPs (every 16th), "
+        single = {"LPs_per_s": len(idx) / ts, "sample": f"{len(idx)} of the 512 LPs (every 16th), "
                   f"each lp_create + lp_solve (FP64) + lp_destroy, one after another ({ts:.1f} s)"}
+        od = [d["objective_rel_diff"] for d in diffs]
+        vs_fp64 = {"instances": len(diffs), "objective_rel_diff_max": max(od),
+                   "objective_rel_diff_median": float(np.median(od)), "per_instance": diffs}
         cpu = None
+        vs_oracle = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            sample = lps[:: max(1, len(lps) // 8)][:8]
+            pick = list(range(0, len(lps), max(1, len(lps) // 8)))[:8]
             t0 = time.perf_counter()
-            for lp in sample:
-                oracle.pdhg_solve(lp)
+            vs_oracle = []
+            for j in pick:
+                ro = oracle.pdhg_solve(lps[j])
+                vs_oracle.append({"item": j, "objective_rel_diff": abs(per[j][2] - ro.kkt["p"])
+                                  / (1 + abs(ro.kkt["p"])), "rel_kkt_oracle": ro.kkt["rel_kkt"]})
             tc = time.perf_counter() - t0
-            cpu = {"value": len(sample) / tc, "unit": "LPs/s", "cores": 1, "kind": "oracle",
-                   "sample": f"oracle solves of {len(sample)} of the 512 LPs (every 64th) to "
-                             f"rel-KKT 1e-6, sequential ({tc:.1f} s)"}
+            model, nproc = host_cpu()
+            cpu = {"value": len(pick) / tc, "unit": "LPs/s", "cores": 1, "kind": "oracle",
+                   "sample": f"oracle solves of {len(pick)} of the 512 LPs (every 64th) to "
+                             f"rel-KKT 1e-6, sequential ({tc:.1f} s)",
+                   "host_cpu": model, "host_logical_cores": nproc}
         line = {
             "metric": METRIC, "value": value, "unit": "LPs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3,
@@ -655,6 +712,8 @@ def run_batch(args):
             "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)),
             "optimal": steps[-1][3], "max_objective_rel_err_vs_planted": max(steps[-1][2]),
+            "vs_fp64_per_instance": vs_fp64, "vs_oracle_per_instance": vs_oracle,
+            "roofline": roof,
             "single_fp64": single,
             "server_stats": steps[-1][4], "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "LPs/s",
@@ -678,21 +737,23 @@ def run_batch(args):
     desc = (f"Poisson stream: {len(reqs)} planted LPs at {args.rate:g} req/s, nnz log-uniform "
             f"[1e3, 1e7], presolvable structure, 150 GB HBM budget")
 
-    def serve():
+    def serve(arrivals, lps_):
+        """Serve lps_ arriving at the given times (s from the start); returns
+        (elapsed, {j: (latency, result)}, server stats)."""
         srv = pkg.Server(int(150e9), dev, worker=True, precision=prec, **solver_kw(args))
         srv.tune(args.solo_nnz, args.solo_max, args.launch_ms)
-        probs = [None] * len(lps)
-        tickets = [None] * len(lps)
-        arrivals = [None] * len(lps)
+        probs = [None] * len(lps_)
+        tickets = [None] * len(lps_)
+        arr = [None] * len(lps_)
         t0 = time.perf_counter()
         done = {}
         import threading as th
 
         def submitter():
-            for j, (rq, lp) in enumerate(zip(reqs, lps)):
-                while time.perf_counter() - t0 < rq.arrival_s:
+            for j, (a, lp) in enumerate(zip(arrivals, lps_)):
+                while time.perf_counter() - t0 < a:
                     time.sleep(0.0005)
-                arrivals[j] = time.perf_counter()
+                arr[j] = time.perf_counter()
                 p = pkg.Problem(lp, dev)
                 p.presolve(enable=presolve_rules(pkg, args))
                 probs[j] = p
@@ -700,14 +761,14 @@ def run_batch(args):
 
         sub = th.Thread(target=submitter)
         sub.start()
-        while len(done) < len(lps):
-            for j in range(len(lps)):
+        while len(done) < len(lps_):
+            for j in range(len(lps_)):
                 if j in done or tickets[j] is None:
                     continue
                 got = srv.poll(tickets[j])
                 if got is not None:
                     probs[j].postsolve()
-                    done[j] = (time.perf_counter() - arrivals[j], got[0])
+                    done[j] = (time.perf_counter() - arr[j], got[0])
             time.sleep(0.001)
         sub.join()
         el = time.perf_counter() - t0
@@ -715,30 +776,70 @@ def run_batch(args):
         srv.close()
         return el, done, st
 
+    arrivals = [rq.arrival_s for rq in reqs]
     for _ in range(max(1, args.warmup // 3)):
-        serve()
+        serve(arrivals, lps)
     clocks = ClockSampler(local)
     clocks.start()
-    el, done, st = serve()
+    el, done, st = serve(arrivals, lps)
     el = max_over_ranks(el, dist, f"cuda:{local}")
     clk = clocks.stop()
     lat = [done[j][0] for j in range(len(lps))]
     opt = sum(1 for j in range(len(lps)) if done[j][1].termination == 0)
     st["terminations"] = term_hist(done[j][1].termination for j in range(len(lps)))
+    orig_kkt = [done[j][1].rel_kkt_original for j in range(len(lps))
+                if done[j][1].termination == 0]
+    # the same requests at arrival rates the server keeps up with: the first
+    # sweep_count requests, their arrival times rescaled to each rate
+    sweep = []
+    if args.sweep:
+        k = min(args.sweep_count, len(lps))
+        for lam in (float(v) for v in args.sweep.split(",")):
+            arr_l = [a * args.rate / lam for a in arrivals[:k]]
+            el_l, done_l, _ = serve(arr_l, lps[:k])
+            lat_l = [done_l[j][0] for j in range(k)]
+            sweep.append({"rate": lam, "requests": k, "offered_req_per_s": k / max(arr_l[-1], 1e-9),
+                          "served_req_per_s": k / el_l,
+                          "latency_p50_s": float(np.percentile(lat_l, 50)),
+                          "latency_p99_s": float(np.percentile(lat_l, 99)),
+                          "optimal": sum(1 for j in range(k) if done_l[j][1].termination == 0)})
     # comparator: each request solved singly, FP64, one after another
     t0 = time.perf_counter()
     single = []
+    single_iters = []
     for lp in lps:
         ts = time.perf_counter()
         p = pkg.Problem(lp, dev)
         p.presolve(enable=presolve_rules(pkg, args))
-        p.solve(precision=pkg.LP_FP64)
+        rs = p.solve(precision=pkg.LP_FP64)
         p.postsolve()
         p.close()
         single.append(time.perf_counter() - ts)
+        single_iters.append(int(rs.iterations))
     t_single = time.perf_counter() - t0
     offered = len(lps) / max(reqs[-1].arrival_s, 1e-9)
     fifo = fifo_latencies([rq.arrival_s for rq in reqs], single)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on 8 requests spread over the size range: each presolved
+        # and timed for a few PDHG iterations, extrapolated to the iteration
+        # count the device's FP64 solve of that request needed
+        idx = sorted(range(len(lps)), key=lambda j: lps[j].nnz)
+        pick = [idx[int(q * (len(idx) - 1) / 7)] for q in range(8)] if len(idx) >= 8 else idx
+        tot, spent = 0.0, 0.0
+        for j in pick:
+            est, _, sp = oracle_sample(lps[j], max(single_iters[j], 1), "c2", iters=2)
+            tot += est
+            spent += sp
+        model, nproc = host_cpu()
+        cpu = {"value": len(pick) / tot, "unit": "requests/s", "cores": 1, "kind": "oracle",
+               "sample": f"EXTRAPOLATION: {len(pick)} requests spread over the size range "
+                         f"(nnz {min(lps[j].nnz for j in pick)}-{max(lps[j].nnz for j in pick)}), "
+                         "each: oracle presolve, set-up passes and 2 PDHG iterations timed, "
+                         "extrapolated to the device FP64 solve's iteration count of that "
+                         "request; served one after another",
+               "host_cpu": model, "host_logical_cores": nproc,
+               "cpu_seconds_spent": round(spent, 1)}
     line = {
         "metric": METRIC, "value": world * len(lps) / el, "unit": "requests/s", "n_gpus": world,
         "steps": 1, "warmup": max(1, args.warmup // 3), "ms_per_step": el * 1e3,
@@ -751,6 +852,9 @@ def run_batch(args):
         "latency_p50_s": float(np.percentile(lat, 50)),
         "latency_p99_s": float(np.percentile(lat, 99)),
         "optimal": opt,
+        "rel_kkt_original_after_postsolve_max": max(orig_kkt) if orig_kkt else None,
+        "refinements": int(sum(done[j][1].refinements for j in range(len(lps)))),
+        "rate_sweep": sweep,
         "single_fp64": {"requests_per_s": len(lps) / t_single,
                         "latency_p50_s": float(np.percentile(single, 50)),
                         "latency_p99_s": float(np.percentile(single, 99)),
@@ -764,7 +868,7 @@ def run_batch(args):
         "e2e": {"value": world * len(lps) / el, "unit": "requests/s",
                 "h2d_bytes_per_step": int(sum(lp.nnz * 24 for lp in lps)),
                 "d2h_bytes_per_step": int(sum((2 * lp.n + lp.m) * 8 for lp in lps))},
-        "cpu_baseline": None, "clocks": clk, "gpu_launches": st["launches"],
+        "cpu_baseline": cpu, "clocks": clk, "gpu_launches": st["launches"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -449,10 +449,12 @@ int lp_server_tune(lp_server *srv, int64_t solo_nnz, int32_t solo_max, double la
  * termination LP_CANCELLED. */
 int lp_batch_cancel(lp_server *srv, uint64_t ticket);
 
-/* Statistics (10 int64): out[0] admitted, out[1] finished, out[2] bucket
+/* Statistics (12 int64): out[0] admitted, out[1] finished, out[2] bucket
  * launches, out[3] peak resident bytes, out[4] kernel launches, out[5] queue
  * length, out[6..9] shape index the autotuner uses for each size bucket
- * (nonzeros < 16Ki, < 128Ki, < 1Mi, larger). */
+ * (nonzeros < 16Ki, < 128Ki, < 1Mi, larger), out[10] host nanoseconds spent
+ * issuing bucket launches (order copy, events, the launch, the state
+ * read-back), out[11] device nanoseconds of the completed bucket launches. */
 int lp_server_stats(const lp_server *srv, int64_t *out);
 
 void lp_server_destroy(lp_server *srv);

@@ -420,10 +420,11 @@ class Server:
         check(self.lib.lp_batch_cancel(self.h, C.c_uint64(ticket)))
 
     def stats(self):
-        out = np.zeros(10, dtype=np.int64)
+        out = np.zeros(12, dtype=np.int64)
         check(self.lib.lp_server_stats(self.h, out.ctypes.data_as(_I64)))
         keys = ("admitted", "finished", "periods", "peak_resident_bytes", "launches",
-                "queued", "shape_b0", "shape_b1", "shape_b2", "shape_b3")
+                "queued", "shape_b0", "shape_b1", "shape_b2", "shape_b3", "host_launch_ns",
+                "device_launch_ns")
         return dict(zip(keys, (int(v) for v in out)))
 
     def run_all(self, tickets, max_periods: int = 1_000_000):

@@ -952,6 +952,9 @@ struct lp_server {
   std::map<uint64_t, int> where;  // ticket -> 0 queued, 1 running, 2 done
   uint64_t next_ticket = 1;
   long long n_admitted = 0, n_finished = 0, n_periods = 0, launches = 0;
+  // host time spent issuing bucket launches (order copy, events, the launch,
+  // the state read-back) and the device time of the completed launches
+  long long host_launch_ns = 0, device_launch_ns = 0;
   size_t resident = 0, peak_resident = 0;
   std::mutex mu;
   std::mutex arena_mu;  // guards ralloc, resident, solo_blocks
@@ -1263,6 +1266,7 @@ void complete_bucket(lp_server *srv, int b) {
   B.inflight = false;
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, B.ev0, B.ev1));
+  srv->device_launch_ns += (long long)(ms * 1e6);
   const State *out = srv->h_sout + (size_t)b * srv->max_slots;
   const double tnow = now_s();
   double work = 0;
@@ -1311,6 +1315,7 @@ void launch_idle(lp_server *srv) {
     B.tail = nord * shp.cl * 4 < srv->sm_count && B.tuner.chosen >= 0;
     if (B.tail) shp = Shape{8, 256};
     cudaStream_t st = srv->bs[b];
+    const auto th0 = std::chrono::steady_clock::now();
     CK(cudaMemcpyAsync(srv->d_order + (size_t)b * srv->max_slots, h_order, sizeof(int) * nord,
                        cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(B.ev0, st));
@@ -1320,6 +1325,9 @@ void launch_idle(lp_server *srv) {
                        srv->d_sout + (size_t)b * srv->max_slots, sizeof(State) * nord,
                        cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(B.ev_done, st));
+    srv->host_launch_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(
+                               std::chrono::steady_clock::now() - th0)
+                               .count();
     B.inflight = true;
     ++srv->n_periods;
   }
@@ -1715,6 +1723,8 @@ int lp_server_stats(const lp_server *srv, int64_t *out) {
   out[4] = s->launches;
   out[5] = (int64_t)s->queue.size();
   for (int b = 0; b < kNumBuckets; ++b) out[6 + b] = s->buckets[b].tuner.current();
+  out[10] = s->host_launch_ns;
+  out[11] = s->device_launch_ns;
   return LP_OK;
 }
 

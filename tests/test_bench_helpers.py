@@ -38,3 +38,14 @@ def test_fifo_latencies(bench):
     # idle server: latency = service time; a burst queues behind earlier work
     assert bench.fifo_latencies([0.0, 10.0], [1.0, 2.0]) == [1.0, 2.0]
     assert bench.fifo_latencies([0.0, 0.5, 0.6], [1.0, 1.0, 1.0]) == [1.0, 1.5, 2.4]
+
+
+def test_iteration_bytes_follow_the_per_iteration_formula():
+    # FP64: B = 2 nnz (8 + 4) + 4 (m + n) + 8 (8 n + 6 m), plus the two
+    # trailing row offsets; the FP32 SpMV halves values and gathered vectors
+    import bench
+
+    m, n, nnz = 1000, 2500, 30000
+    assert bench.iter_bytes(m, n, nnz, False) == 2 * nnz * 12 + 4 * (m + n) + 8 * (8 * n + 6 * m) + 8
+    b32 = bench.iter_bytes(m, n, nnz, True)
+    assert b32 == 2 * nnz * 8 + 4 * (m + n) + 8 + 4 * m + 48 * n + 4 * n + 4 * n + 40 * m + 4 * m

@@ -225,3 +225,35 @@ def test_served_request_is_re_solved_when_postsolve_amplifies(pkg, dev, lane):
     assert abs(k["rel_kkt"] - r.rel_kkt_original) <= 1e-6 * r.rel_kkt_original
     assert rel_obj(k["p"], lp.p_star) <= 1e-6
     srv.close()
+
+
+def test_batch_iterates_match_oracle_elementwise(pkg, dev):
+    # 20 LPs from 30 to 20,000 rows (three size buckets) run together, with
+    # the step size and weight fixed: after 50 and 130 iterations each
+    # returned point T(z) matches the oracle's entry by entry.  A 10 us launch
+    # budget gives every slot one block of K iterations per launch, so a
+    # slot's iterations run across several launches and the autotuner's
+    # cluster x CTA shapes (it tries one per launch while tuning).
+    ms = np.exp(np.linspace(np.log(30), np.log(20000), 20)).astype(int)
+    lps = [lpgen.equality_nonneg(int(m), 2 * int(m), 5100 + j, 4, 30) for j, m in enumerate(ms)]
+    eta, om = 0.05, 1.3
+    for iters in (50, 130):
+        srv = pkg.Server(1 << 31, dev, precision=0, max_iter=iters, eps_rel=0.0, step_size=eta,
+                         primal_weight=om)
+        srv.tune(launch_ms=0.01)
+        probs = [pkg.Problem(lp, dev) for lp in lps]
+        tickets = [srv.submit(p) for p in probs]
+        res = srv.run_all(tickets)
+        st = srv.stats()
+        # three buckets, each slot over at least ceil(iters / 64) launches
+        assert st["launches"] >= 3 * ((iters + 63) // 64)
+        for lp, t in zip(lps, tickets):
+            r, x, y = res[t]
+            ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta,
+                                    omega0=om)
+            assert r.termination == pkg.LP_ITER_LIMIT and r.iterations == iters
+            assert r.restarts == ref.restarts
+            ex = np.max(np.abs(x - ref.x)) / max(1.0, np.max(np.abs(ref.x)))
+            ey = np.max(np.abs(y - ref.y)) / max(1.0, np.max(np.abs(ref.y)))
+            assert ex <= 1e-10 and ey <= 1e-10, (lp.m, iters, ex, ey)
+        srv.close()

@@ -1,5 +1,6 @@
-"""Parity at the benchmark's full size (the presolved C2 workload, grid
-engine, the launch configuration bench.py times).
+"""Parity at full size: the presolved 200k x 500k workload and the 2M x 5M,
+50M-nonzero workload the benchmark times (grid engine, autotuned tile
+shapes: the launch configuration bench.py times).
 
 The oracle runs a few FP64 iterations of the same presolved LP (each takes a
 fraction of a second at this size); the GPU iterates must agree to 1e-10
@@ -73,4 +74,43 @@ def test_c2_solves_to_tolerance_and_postsolves(pkg, c2, precision):
     x, y, _ = prob.postsolve()
     k = oracle.rel_kkt(c2, x, y)
     assert abs(k["p"] - c2.p_star) / (1 + abs(c2.p_star)) <= 1e-6
+    prob.close()
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return lpgen.c3_powerlaw()
+
+
+def test_c3_first_iterates_match_oracle(pkg, c3):
+    # rows up to 10k entries and 5,000 columns of 2,000: every tile class and
+    # the segmented rows of A and A^T at the benchmark's size; three FP64
+    # iterations of the oracle (after its scaling) take about a minute
+    dev = pkg.TorchDevice(0)
+    eta, om = 0.5, 1.0
+    ref = oracle.pdhg_solve(c3, oracle.Opts(max_iter=3, eps_rel=0.0, infeas_every=0), eta=eta,
+                            omega0=om)
+    prob = pkg.Problem(c3, dev)
+    r = prob.solve(max_iter=3, eps_rel=0.0, step_size=eta, primal_weight=om,
+                   engine=pkg.LP_ENGINE_GRID)
+    assert r.iterations == 3
+    xi, yi = prob.iterate()
+    assert relerr(xi, ref.x_iter) <= 1e-10
+    assert relerr(yi, ref.y_iter) <= 1e-10
+    x, y, _ = prob.solution()
+    assert relerr(x, ref.x) <= 1e-10 and relerr(y, ref.y) <= 1e-10
+    prob.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c3_solves_to_tolerance(pkg, c3, precision):
+    dev = pkg.TorchDevice(0)
+    prob = pkg.Problem(c3, dev)
+    r = prob.solve(precision=precision, engine=pkg.LP_ENGINE_GRID)
+    assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+    x, y, _ = prob.solution()
+    host = prob.rel_kkt(x, y)
+    assert host["rel_kkt"] <= 1e-6 * (1 + 1e-6)
+    assert abs(host["p"] - r.primal_obj) <= 1e-9 * (1 + abs(r.primal_obj))
+    assert abs(host["p"] - c3.p_star) / (1 + abs(c3.p_star)) <= 1e-6
     prob.close()
