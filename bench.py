@@ -211,11 +211,11 @@ def iter_bytes(m, n, nnz, fp32):
     """Algorithmic bytes of one PDHG iteration (K1 + K2): both matrices'
     values and indices once, row offsets, each gathered vector once, and the
     epilogues' vectors (K1 reads x, x0, c, l, u and writes x and xbar; K2
-    reads y, y0, l, u and writes y; the FP32 SpMV gathers and writes FP32
-    shadows)."""
+    reads y, y0, l, u and writes y).  The mixed SpMV streams FP32 values and
+    gathers x-bar and y as 8-byte float pairs, which K2 also writes for y."""
     sv = 4 if fp32 else 8
-    k1 = nnz * (sv + 4) + 4 * (n + 1) + sv * m + 8 * 6 * n + sv * n
-    k2 = nnz * (sv + 4) + 4 * (m + 1) + sv * n + 8 * 5 * m + (4 * m if fp32 else 0)
+    k1 = nnz * (sv + 4) + 4 * (n + 1) + 8 * m + 8 * 6 * n + 8 * n
+    k2 = nnz * (sv + 4) + 4 * (m + 1) + 8 * n + 8 * 5 * m + (8 * m if fp32 else 0)
     return k1 + k2
 
 

@@ -80,7 +80,7 @@ struct SlotDesc {
   double *c, *lx, *ux, *lc, *uc;
   double *dr, *dc, *dr2, *dc2, *idr, *idc;
   double *x, *x0, *xbar, *xhat, *y, *y0, *yhat;
-  float *xbarf, *yf, *pwf;
+  float2 *xbarf, *yf;  // mixed: x-bar and y as float pairs (split_f2)
   double *xout, *yout, *zout;
   const double *xinit, *yinit;  // warm start (unscaled, device order) or NULL
 };
@@ -108,7 +108,7 @@ struct Ctl {
 
 struct BatchShared {
   double redd[kMaxWarps];  // whole-CTA rows of the warp engine
-  float redf[kMaxWarps];
+  F2 red2[kMaxWarps];  // the same for the compensated FP32 SpMV
   double wsum[kMaxWarps][NQ];
   double part[kMaxCluster][NQ];  // used on rank 0
   double total[NQ];
@@ -193,31 +193,32 @@ __device__ __forceinline__ void cluster_sum(const double (&acc)[NQL], const int 
 }
 
 // one Ruiz / Pock-Chambolle pass over the rows of a matrix: dnew[r] =
-// dself[r] / sqrt(max or sum_k (dr |a|) dc); S is the arithmetic type
-template <typename S, bool TRANSPOSED, bool SUM>
+// dself[r] / sqrt(max or sum_k (dr |a|) dc)
+template <bool TRANSPOSED, bool SUM>
 __device__ __forceinline__ void scale_rows(int rows, const int *rp, const int *ci,
                                            const double *a0, const double *dself,
                                            const double *dother, double *dnew, int gt,
                                            int gs) {
   for (int r = gt; r < rows; r += gs) {
-    const S ds = (S)dself[r];
-    S acc = 0;
+    const double ds = dself[r];
+    double acc = 0.0;
     for (int k = rp[r]; k < rp[r + 1]; ++k) {
-      const S v = TRANSPOSED ? ((S)dother[ci[k]] * (S)fabs(a0[k])) * ds
-                             : (ds * (S)fabs(a0[k])) * (S)dother[ci[k]];
+      const double v = TRANSPOSED ? (dother[ci[k]] * fabs(a0[k])) * ds
+                                  : (ds * fabs(a0[k])) * dother[ci[k]];
       acc = SUM ? acc + v : (v > acc ? v : acc);
     }
-    dnew[r] = acc > (S)0 ? (double)(ds / sqrt(acc)) : (double)ds;
+    dnew[r] = acc > 0.0 ? ds / sqrt(acc) : ds;
   }
 }
 
 // ---------------------------------------------------------------------------
 // set-up of one slot (scaling, step size, primal weight, initial point)
 
+// Both precisions set up in FP64 (scaling, power iteration): the mixed mode
+// differs only in its iteration SpMV, as on the grid engine.
 template <bool MIXED>
 __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, BatchShared &sh,
                            cg::cluster_group &cl) {
-  using S = typename std::conditional<MIXED, float, double>::type;
   const int m = D.m, n = D.n;
   const int gt = cl.block_rank() * blockDim.x + threadIdx.x;
   const int gs = cl.num_blocks() * blockDim.x;
@@ -226,15 +227,15 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
   for (int j = gt; j < n; j += gs) dc[j] = 1.0;
   cl.sync();
   for (int it = 0; it < C.ruiz_iters; ++it) {
-    scale_rows<S, false, false>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
-    scale_rows<S, true, false>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
+    scale_rows<false, false>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
+    scale_rows<true, false>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
     cl.sync();
     double *t = dr; dr = dr2; dr2 = t;
     t = dc; dc = dc2; dc2 = t;
   }
   if (C.pock_chambolle) {
-    scale_rows<S, false, true>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
-    scale_rows<S, true, true>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
+    scale_rows<false, true>(m, D.a_rp, D.a_ci, D.a_v0, dr, dc, dr2, gt, gs);
+    scale_rows<true, true>(n, D.t_rp, D.t_ci, D.t_v0, dc, dr, dc2, gt, gs);
     cl.sync();
     double *t = dr; dr = dr2; dr2 = t;
     t = dc; dc = dc2; dc2 = t;
@@ -281,26 +282,21 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
     const int qid[2] = {Q_CN, Q_BN};
     cluster_sum<2>(acc, qid, sh, cl);
   }
-  // power iteration on A~^T A~ (v in pwf / xhat, u in yf / yhat, w in xbarf / xbar)
+  // power iteration on A~^T A~ (v in xhat, u in yhat, w in xbar)
   double eta = C.step_size;
   if (!(eta > 0.0)) {
     double pw = 0.0;
     if (m > 0 && n > 0) {
       const double v0 = 1.0 / sqrt((double)n);
       for (int j = gt; j < n; j += gs) {
-        if (MIXED) D.pwf[j] = (float)v0; else D.xhat[j] = v0;
+        D.xhat[j] = v0;
       }
       cl.sync();
       const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
       for (int it = 0; it <= C.power_iters; ++it) {
         // u = A~ v
         double a2[1] = {0.0};
-        if (MIXED) {
-          StoreSqEpi<float> e{D.yf, 0.0};
-          warp_spmv<float, float, float>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_vf,
-                                         D.pwf, e, sh.redf, rank, CL);
-          a2[0] = e.acc;
-        } else {
+        {
           StoreSqEpi<double> e{D.yhat, 0.0};
           warp_spmv<double, double, double>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci,
                                             D.a_v, D.xhat, e, sh.redd, rank, CL);
@@ -314,12 +310,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
         }
         cl.sync();
         // w = A~^T u
-        if (MIXED) {
-          StoreSqEpi<float> e{D.xbarf, 0.0};
-          warp_spmv<float, float, float>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_vf,
-                                         D.yf, e, sh.redf, rank, CL);
-          a2[0] = e.acc;
-        } else {
+        {
           StoreSqEpi<double> e{D.xbar, 0.0};
           warp_spmv<double, double, double>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci,
                                             D.t_v, D.yhat, e, sh.redd, rank, CL);
@@ -336,8 +327,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
         const double nw = sh.bcast;
         // a zero w continues from the fallback start vector
         for (int j = gt; j < n; j += gs) {
-          if (MIXED) D.pwf[j] = nw > 0.0 ? (float)((double)D.xbarf[j] / nw) : (float)D.pv0[j];
-          else D.xhat[j] = nw > 0.0 ? D.xbar[j] / nw : D.pv0[j];
+          D.xhat[j] = nw > 0.0 ? D.xbar[j] / nw : D.pv0[j];
         }
         cl.sync();
       }
@@ -354,7 +344,7 @@ __device__ void slot_setup(const SlotDesc &D, State *st, const BatchConst &C, Ba
     const double v = D.yinit ? D.yinit[i] / dr[i] : 0.0;
     D.y[i] = v;
     D.y0[i] = v;
-    if (MIXED) D.yf[i] = (float)v;
+    if (MIXED) D.yf[i] = split_f2(v);
   }
   if (cl.block_rank() == 0 && threadIdx.x == 0) {
     const double cn = sqrt(sh.total[Q_CN]), bn = sqrt(sh.total[Q_BN]);
@@ -390,8 +380,8 @@ __device__ __forceinline__ void phase_primal(const SlotDesc &D, bool f32, double
   if (f32) {
     PrimalEpi<CHECK, true> e{D.c, D.lx, D.ux, D.x, D.x0, D.xbar, D.xhat, D.xbarf, tau, hc,
                              0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<float, float, float>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_vf, D.yf,
-                                   e, sh.redf, rank, CL);
+    warp_spmv<float, float2, F2>(D.t_nlong, D.t_tiles, D.t_ntiles, D.t_rp, D.t_ci, D.t_vf, D.yf,
+                                 e, sh.red2, rank, CL);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
@@ -411,8 +401,8 @@ __device__ __forceinline__ void phase_dual(const SlotDesc &D, bool f32, double s
   if (f32) {
     DualEpi<CHECK, true> e{D.lc, D.uc, D.y, D.y0, D.yhat, D.yf, sigma, hc,
                            0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<float, float, float>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_vf,
-                                   D.xbarf, e, sh.redf, rank, CL);
+    warp_spmv<float, float2, F2>(D.a_nlong, D.a_tiles, D.a_ntiles, D.a_rp, D.a_ci, D.a_vf,
+                                 D.xbarf, e, sh.red2, rank, CL);
     acc[2] = e.acc0;
     acc[3] = e.acc1;
   } else {
@@ -536,7 +526,7 @@ __device__ void slot_iterate(const SlotDesc &D, State *st, const BatchConst &C, 
           const double v = D.yhat[r];
           D.y[r] = v;
           D.y0[r] = v;
-          if (MIXED) D.yf[r] = (float)v;
+          if (MIXED) D.yf[r] = split_f2(v);
         }
         cl.sync();
       }
@@ -770,9 +760,8 @@ static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
   for (double **q : colv) *q = (double *)P(take(8 * n));
   double **rowv[] = {&r.lc, &r.uc, &r.dr, &r.dr2, &r.idr, &r.y, &r.y0, &r.yhat, &r.yout};
   for (double **q : rowv) *q = (double *)P(take(8 * m));
-  r.xbarf = (float *)P(take(4 * n));
-  r.pwf = (float *)P(take(4 * n));
-  r.yf = (float *)P(take(4 * m));
+  r.xbarf = (float2 *)P(take(8 * n));
+  r.yf = (float2 *)P(take(8 * m));
   p.bytes = align16(cur);
   // the host blob covers the inputs; the rest of the block is device work space
   p.blob.assign(input_end, 0);
@@ -850,7 +839,6 @@ static SlotDesc relocate(const SlotDesc &rel, unsigned char *base) {
   d.yhat = R(rel.yhat);
   d.xbarf = R(rel.xbarf);
   d.yf = R(rel.yf);
-  d.pwf = R(rel.pwf);
   d.xout = R(rel.xout);
   d.yout = R(rel.yout);
   d.zout = R(rel.zout);

@@ -39,7 +39,7 @@ template <bool CHECK, bool MIXED>
 struct PrimalEpi {
   const double *c, *lx, *ux;
   double *x, *x0, *xbar, *xhat;
-  float *xbar_f;
+  float2 *xbar_f;  // mixed: xbar as a float pair (split_f2) for the FP32 SpMV
   double tau;
   Halpern hc;
   double acc0, acc1;
@@ -55,7 +55,7 @@ struct PrimalEpi {
     const double xh = clampd(fma(-tau, cj - g, xk), lo, hi);
     const double xb = fma(2.0, xh, -xk);
     x[j] = fma(hc.a, xh, fma(hc.b, xk, hc.g * a0));
-    if (MIXED) xbar_f[j] = (float)xb; else xbar[j] = xb;
+    if (MIXED) xbar_f[j] = split_f2(xb); else xbar[j] = xb;
     if (CHECK) {
       xhat[j] = xh;
       acc0 += (xk - xh) * (xk - xh);
@@ -78,7 +78,7 @@ template <bool CHECK, bool MIXED>
 struct DualEpi {
   const double *lc, *uc;
   double *y, *y0, *yhat;
-  float *yf;
+  float2 *yf;  // mixed: y as a float pair
   double sigma;
   Halpern hc;
   double acc0, acc1;
@@ -94,7 +94,7 @@ struct DualEpi {
     const double yh = v + clampd(-v, sigma * lo, sigma * hi);
     const double yn = fma(hc.a, yh, fma(hc.b, yk, hc.g * a0));
     y[i] = yn;
-    if (MIXED) yf[i] = (float)yn;
+    if (MIXED) yf[i] = split_f2(yn);
     if (CHECK) {
       yhat[i] = yh;
       acc0 += (yk - yh) * (yk - yh);

@@ -284,12 +284,12 @@ __global__ void k_init_x(int n, const double *__restrict__ lx, const double *__r
 }
 
 __global__ void k_init_y(int m, const double *__restrict__ dr, const double *__restrict__ yinit,
-                         double *y, double *y0, float *yf) {
+                         double *y, double *y0, float2 *yf) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     double v = yinit ? yinit[i] / dr[i] : 0.0;
     y[i] = v;
     y0[i] = v;
-    if (yf) yf[i] = (float)v;
+    if (yf) yf[i] = split_f2(v);
   }
 }
 
@@ -307,9 +307,9 @@ __global__ void k_reciprocal(int n, const double *__restrict__ d, double *__rest
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
-    const double *__restrict__ y, const float *__restrict__ yf, const double *__restrict__ c,
+    const double *__restrict__ y, const float2 *__restrict__ yf, const double *__restrict__ c,
     const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
-    double *xbar, float *xbar_f, double *xhat, const State *__restrict__ st, int j,
+    double *xbar, float2 *xbar_f, double *xhat, const State *__restrict__ st, int j,
     double *partials, int GP, int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
   if (MIXED && st->mixed_active) {
     PrimalEpi<CHECK, true> e{c, lx, ux, x, x0, xbar, xhat, xbar_f, st->tau,
                              halpern_coeffs(st, j), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
-                               red_smem<T, float, float>(), blockIdx.x, gridDim.x, sc);
+    warp_spmv<T, float2, F2>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yf, e,
+                             red_smem<T, float2, F2>(), blockIdx.x, gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
@@ -340,9 +340,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
-    const double *__restrict__ xbar, const float *__restrict__ xbar_f,
+    const double *__restrict__ xbar, const float2 *__restrict__ xbar_f,
     const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
-    float *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int GP,
+    float2 *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int GP,
     int *err) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
   if (MIXED && st->mixed_active) {
     DualEpi<CHECK, true> e{lc, uc, y, y0, yhat, yf, st->sigma, halpern_coeffs(st, j), 0.0, 0.0,
                            0.0, 0.0, 0.0, 0.0};
-    warp_spmv<T, float, float>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
-                               red_smem<T, float, float>(), blockIdx.x, gridDim.x, sc);
+    warp_spmv<T, float2, F2>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xbar_f, e,
+                             red_smem<T, float2, F2>(), blockIdx.x, gridDim.x, sc);
     acc[0] = e.acc0;
     acc[1] = e.acc1;
   } else {
@@ -473,7 +473,7 @@ __global__ void k_check(State *st, const double *partials, int GP, int eval_only
 // K5: on restart, x = x0 = xh and y = y0 = yh
 __global__ void k_restart(const State *__restrict__ st, int n, int m, double *x, double *x0,
                           const double *__restrict__ xhat, double *y, double *y0,
-                          const double *__restrict__ yhat, float *yf) {
+                          const double *__restrict__ yhat, float2 *yf) {
   if (st->status != ST_RUNNING || !st->restart_flag) return;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double v = xhat[j];
@@ -484,7 +484,7 @@ __global__ void k_restart(const State *__restrict__ st, int n, int m, double *x,
     double v = yhat[i];
     y[i] = v;
     y0[i] = v;
-    if (yf) yf[i] = (float)v;
+    if (yf) yf[i] = split_f2(v);
   }
 }
 
@@ -547,7 +547,7 @@ struct DeviceLP {
   // A) per candidate, or empty when the choice came from the cache / opts
   std::vector<double> tune_msT, tune_msA;
   double *ox = nullptr, *oy = nullptr, *oxi = nullptr, *oyi = nullptr;
-  float *xbar_f = nullptr, *yf = nullptr;
+  float2 *xbar_f = nullptr, *yf = nullptr;  // mixed: x-bar and y as float pairs
   double *partials = nullptr;
   State *st = nullptr;
   State *hst = nullptr;
@@ -660,6 +660,13 @@ void install_plan(DeviceLP *d, int ca, int ct) {
   put(d->plansT[ct], d->tilesT, d->segbaseT, d->ntilesT, d->nlongT, d->nsegrowsT, d->seglenT);
   d->planA = ca;
   d->planT = ct;
+  // the per-row slots of segmented rows (after the G per-CTA slots of every
+  // quantity) are summed by every reduction: drop what the previous plan's
+  // segmented rows left there
+  if (d->GP > d->G)
+    for (int q = 0; q < NQ; ++q)
+      CK(cudaMemsetAsync(d->partials + (size_t)q * d->GP + d->G, 0,
+                         sizeof(double) * (d->GP - d->G), d->s));
   for (int q = 0; q < 2; ++q)
     if (d->graph[q]) {
       CK(cudaGraphExecDestroy(d->graph[q]));
@@ -783,8 +790,8 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     for (double **p : rows_) *p = d->dalloc_n<double>(m);
     d->dr_main = d->dr;
     d->dc_main = d->dc;
-    d->xbar_f = d->dalloc_n<float>(n);
-    d->yf = d->dalloc_n<float>(m);
+    d->xbar_f = d->dalloc_n<float2>(n);
+    d->yf = d->dalloc_n<float2>(m);
     int occ = 1;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_primal<double, true>, kBlock, kSmem64));
     occ = std::max(occ, 1);
@@ -859,7 +866,7 @@ template <typename T>
 void launch_dual(DeviceLP *d, bool wr, int grid, int j) {
   const T *va;
   size_t smem;
-  float *yf;
+  float2 *yf;
   if constexpr (sizeof(T) == 4) {
     va = reinterpret_cast<const T *>(d->A_vf);
     smem = kSmem32;

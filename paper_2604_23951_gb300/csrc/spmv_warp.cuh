@@ -53,6 +53,77 @@ struct SegCtx {
   AccSink sink;
 };
 
+// ---- accumulators ---------------------------------------------------------
+// Acc = double / float: plain multiply-adds.  Acc = F2: the mixed-precision
+// SpMV, FP32 matrix values times a gathered vector held as a float pair
+// hi + lo (split_f2: about 2^-48 relative), accumulated after the
+// dot-product algorithm Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005): each product is split into its
+// rounded value and its error (TwoProduct with an FMA; the lo part of the
+// vector joins the error term), the running sum takes the rounded product
+// through Knuth's TwoSum, and the error terms are summed on the side, so the
+// result is about as accurate as a sum in twice FP32's precision of the
+// products of the float-rounded matrix and the exact vector.  All of it runs
+// on the FP32 pipe; the _rn intrinsics keep the compiler from fusing steps.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ float2 split_f2(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+template <typename Acc, typename T, typename V>
+__device__ __forceinline__ void acc_mad(Acc &s, T a, V g) {
+  s += (Acc)a * (Acc)g;
+}
+template <typename T>
+__device__ __forceinline__ void acc_mad(F2 &s, T a_, float2 g) {
+  const float a = (float)a_;
+  const float p = __fmul_rn(a, g.x);
+  // a * (g.x + g.y) - p: the FMA gives a * g.x - p exactly, plus a * g.y
+  const float e = __fmaf_rn(a, g.y, __fmaf_rn(a, g.x, -p));
+  const float t = __fadd_rn(s.hi, p);  // TwoSum: s.hi + p == t + q exactly
+  const float z = __fsub_rn(t, s.hi);
+  const float q = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(q, e));
+}
+
+template <typename Acc>
+__device__ __forceinline__ void acc_add(Acc &s, Acc t) {
+  s += t;
+}
+__device__ __forceinline__ void acc_add(F2 &s, F2 u) {
+  const float t = __fadd_rn(s.hi, u.hi);
+  const float z = __fsub_rn(t, s.hi);
+  const float q = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(u.hi, z));
+  s.hi = t;
+  s.lo = __fadd_rn(__fadd_rn(s.lo, u.lo), q);
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc acc_shfl_xor(Acc s, int o) {
+  return __shfl_xor_sync(kFull, s, o);
+}
+__device__ __forceinline__ F2 acc_shfl_xor(F2 s, int o) {
+  return F2{__shfl_xor_sync(kFull, s.hi, o), __shfl_xor_sync(kFull, s.lo, o)};
+}
+template <typename Acc>
+__device__ __forceinline__ Acc acc_shfl(Acc s, int src) {
+  return __shfl_sync(kFull, s, src);
+}
+__device__ __forceinline__ F2 acc_shfl(F2 s, int src) {
+  return F2{__shfl_sync(kFull, s.hi, src), __shfl_sync(kFull, s.lo, src)};
+}
+
+template <typename Acc>
+__device__ __forceinline__ double acc_value(Acc s) {
+  return (double)s;
+}
+__device__ __forceinline__ double acc_value(F2 s) { return (double)s.hi + (double)s.lo; }
+
 // A warp tile: rows [r0, r0 + nrows) with 2^vlog lanes per row and nit
 // entries per lane per chunk, packed as int2 {r0, nrows | vlog << 8 |
 // nit << 12}.
@@ -79,7 +150,7 @@ template <int NIT, typename T, typename V, typename Acc>
 __device__ __forceinline__ Acc group_dot(int lo, int hi, int gl, int vl,
                                          const int *__restrict__ ci, const T *__restrict__ va,
                                          const V *__restrict__ vec) {
-  Acc s = 0;
+  Acc s{};
   const int span = vl * NIT;
   for (int k0 = lo + gl; k0 < hi; k0 += span) {
     int j[NIT];
@@ -94,7 +165,7 @@ __device__ __forceinline__ Acc group_dot(int lo, int hi, int gl, int vl,
 #pragma unroll
     for (int u = 0; u < NIT; ++u) g[u] = vec[j[u]];
 #pragma unroll
-    for (int u = 0; u < NIT; ++u) s += (Acc)a[u] * (Acc)g[u];
+    for (int u = 0; u < NIT; ++u) acc_mad(s, a[u], g[u]);
   }
   return s;
 }
@@ -117,7 +188,7 @@ __device__ __forceinline__ void cta_rows(int nlong, const int *__restrict__ rp,
     // entries per thread per chunk: just enough for one chunk, at most
     // kWarpItems (CTA-uniform)
     const int nit = min(kWarpItems, max(1, (hi - lo + nthr - 1) / nthr));
-    Acc s = 0;
+    Acc s{};
     switch (nit) {
       case 1: s = group_dot<1, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
       case 2: s = group_dot<2, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
@@ -129,13 +200,13 @@ __device__ __forceinline__ void cta_rows(int nlong, const int *__restrict__ rp,
       default: s = group_dot<8, T, V, Acc>(lo, hi, threadIdx.x, nthr, ci, va, vec); break;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    for (int o = 16; o > 0; o >>= 1) acc_add(s, acc_shfl_xor(s, o));
     if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-      Acc t = 0;
-      for (int w = 0; w < nwarp; ++w) t += red[w];
-      epi.row(r, (double)t);
+      Acc t{};
+      for (int w = 0; w < nwarp; ++w) acc_add(t, red[w]);
+      epi.row(r, acc_value(t));
     }
     __syncthreads();
   }
@@ -165,10 +236,10 @@ __device__ __forceinline__ void segment_tile(int r, int g, const int *__restrict
   const int hi = min(lo + sc.seg_len, rp[r + 1]);
   Acc s = group_dot<kWarpItems, T, V, Acc>(lo, hi, lane, 32, ci, va, vec);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  for (int o = 16; o > 0; o >>= 1) acc_add(s, acc_shfl_xor(s, o));
   int last = 0;
   if (lane == 0) {
-    sc.seg_part[g] = (double)s;
+    sc.seg_part[g] = acc_value(s);
     __threadfence();
     last = atomicAdd(&sc.seg_cnt[r], 1) == nseg - 1;
   }
@@ -214,7 +285,7 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
     // row offsets of the tile, one row per lane
     const int my_lo = has ? rp[w.r0 + lane] : 0;
     const int my_hi = has ? rp[w.r0 + lane + 1] : 0;
-    Acc mine = 0;
+    Acc mine{};
     const int vlog = w.vlog;
     const int vl = 1 << vlog;
     const int rpp = 32 >> vlog;  // rows per pass
@@ -223,7 +294,7 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
       const int q = p0 + g;  // row of this lane's group (may be past the tile)
       const int lo = __shfl_sync(kFull, my_lo, q & 31);
       const int hi = __shfl_sync(kFull, my_hi, q & 31);
-      Acc s = 0;
+      Acc s{};
       if (q < w.nrows) {
         switch (w.nit) {
           case 1: s = group_dot<1, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
@@ -236,13 +307,13 @@ __device__ __forceinline__ void warp_spmv(int nlong, const int2 *__restrict__ ti
           default: s = group_dot<8, T, V, Acc>(lo, hi, gl, vl, ci, va, vec); break;
         }
       }
-      for (int o = vl >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+      for (int o = vl >> 1; o > 0; o >>= 1) acc_add(s, acc_shfl_xor(s, o));
       // lane L keeps the sum of row L when row L was reduced in this pass
       const int src = ((lane - p0) & (rpp - 1)) << vlog;
-      const Acc got = __shfl_sync(kFull, s, src);
+      const Acc got = acc_shfl(s, src);
       if (lane >= p0 && lane < p0 + rpp) mine = got;
     }
-    if (has) epi.row(w.r0 + lane, (double)mine);
+    if (has) epi.row(w.r0 + lane, acc_value(mine));
   }
 }
 

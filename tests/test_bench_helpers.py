@@ -42,10 +42,11 @@ def test_fifo_latencies(bench):
 
 def test_iteration_bytes_follow_the_per_iteration_formula():
     # FP64: B = 2 nnz (8 + 4) + 4 (m + n) + 8 (8 n + 6 m), plus the two
-    # trailing row offsets; the FP32 SpMV halves values and gathered vectors
+    # trailing row offsets; the mixed SpMV halves the values and K2 also
+    # writes y as a float pair
     import bench
 
     m, n, nnz = 1000, 2500, 30000
     assert bench.iter_bytes(m, n, nnz, False) == 2 * nnz * 12 + 4 * (m + n) + 8 * (8 * n + 6 * m) + 8
     b32 = bench.iter_bytes(m, n, nnz, True)
-    assert b32 == 2 * nnz * 8 + 4 * (m + n) + 8 + 4 * m + 48 * n + 4 * n + 4 * n + 40 * m + 4 * m
+    assert b32 == 2 * nnz * 8 + 4 * (m + n) + 8 + 8 * m + 48 * n + 8 * n + 8 * n + 40 * m + 8 * m

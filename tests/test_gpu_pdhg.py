@@ -145,6 +145,66 @@ def test_mixed_precision_reaches_tolerance(pkg, dev, engine):
     assert rel_obj(r.primal_obj, lp.p_star) <= 1e-5
 
 
+def _one_mixed_iteration(pkg, dev, lp, engine, eta, om, scaled, y_init=None):
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(max_iter=1, eps_rel=0.0, step_size=eta, primal_weight=om, engine=engine,
+                   precision=pkg.LP_MIXED, y_init=y_init, ruiz_iters=10 if scaled else 0,
+                   pock_chambolle=int(scaled))
+    assert r.iterations == 1 and r.fp32_iterations == 1
+    xi, yi = prob.iterate()
+    prob.close()
+    return xi, yi
+
+
+@pytest.mark.parametrize("scaled", [False, True])
+@pytest.mark.parametrize("engine", ENGINES)
+def test_mixed_spmv_error_is_the_matrix_rounding_only(pkg, dev, engine, scaled):
+    # One iteration of the mixed mode against the FP64 oracle on rows of
+    # 3,000 positive terms.  The mixed SpMV multiplies FP32 matrix values by
+    # the gathered vector held as a float pair and accumulates with Dot2, so
+    # row i of its result differs from the exact one by the matrix rounding
+    # (at most u (|A~| |v|)_i, u = 2^-24) plus the error of the side sums,
+    # about (entries per lane) u^2 (each lane adds at most 32 entries before
+    # the exact TwoSum combination).  Unscaled, the small-integer matrix is
+    # exact in float and the result must agree to 2^-38 of (|A~| |v|)_i: a
+    # float-rounded vector would be off by about 2^-31.6 of it on these rows
+    # (u / 2 per term, random signs) and a plain FP32 running sum by far more.
+    # Scaled, the bound is 2.5u.
+    # rho = 1, lambda_0 = 1/2 and a zero anchor make the first iterate T(z)
+    # itself, and the projections are 1-Lipschitz, so the SpMV bound carries
+    # over scaled by tau (x) or sigma (y).
+    rel = 2.5 * 2.0 ** -24 if scaled else 2.0 ** -38
+    rng = np.random.default_rng(21)
+    eta, om = 0.3 if scaled else 1e-4, 1.0
+    tau, sigma = eta / om, eta * om
+    opts = oracle.Opts(max_iter=1, eps_rel=0.0, ruiz_iters=10 if scaled else 0,
+                       pock_chambolle=scaled)
+    # K2 (rows of A): 24 equality rows of 3,000 entries, x_0 = 0
+    A = rng.integers(1, 4, (24, 3000)).astype(float)
+    b = A @ np.ones(3000)
+    lp = SimpleLP(A, -rng.uniform(0.5, 1.5, 3000), b, b, np.zeros(3000), np.full(3000, INF))
+    sc = oracle.pdhg.Scaled(lp, opts)
+    xh, _ = oracle.pdhg.pdhg_operator(sc.A, sc.c, sc.lx, sc.ux, sc.lc, sc.uc, np.zeros(3000),
+                                      np.zeros(24), tau, sigma)
+    bound = sigma * rel * (abs(sc.A) @ np.abs(2.0 * xh))
+    ref = oracle.pdhg_solve(lp, opts, eta=eta, omega0=om)
+    _, yi = _one_mixed_iteration(pkg, dev, lp, engine, eta, om, scaled)
+    err = np.abs(yi - ref.y_iter) / sc.dr
+    assert np.all(err <= bound + 1e-15 * np.max(np.abs(ref.y_iter / sc.dr)))
+    # K1 (rows of A^T): 24 columns of 3,000 entries, warm-started y > 0
+    A = rng.integers(1, 4, (3000, 24)).astype(float)
+    b = A @ np.ones(24)
+    lp = SimpleLP(A, rng.uniform(0.5, 1.5, 24), b, b, np.zeros(24), np.full(24, INF))
+    sc = oracle.pdhg.Scaled(lp, opts)
+    y0 = rng.uniform(0.5, 1.5, 3000)
+    ref = oracle.pdhg_solve(lp, opts, eta=eta, omega0=om, y_init=y0)
+    bound = tau * rel * (abs(sc.A).T @ np.abs(y0 / sc.dr))
+    xi, _ = _one_mixed_iteration(pkg, dev, lp, engine, eta, om, scaled, y_init=y0)
+    err = np.abs(xi - ref.x_iter) / sc.dc
+    assert np.all(err <= bound + 1e-15 * np.max(np.abs(ref.x_iter / sc.dc)))
+    assert np.max(np.abs(xi)) > 0 and np.max(np.abs(yi)) > 0
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_deterministic_reruns(pkg, dev, engine):
     lp = lpgen.general_structure(600, 1500, 4, nnz_target=9000)
@@ -295,6 +355,22 @@ def test_every_tile_shape_matches_oracle(pkg, dev, powerlaw_lp, shape):
     r = prob.solve(max_iter=1, eps_rel=0.0, engine=1, tile_run_max=shape[0], tile_nnz=shape[1])
     assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
     assert abs(r.omega - ref.omega0) <= 1e-12 * ref.omega0
+    prob.close()
+
+
+def test_shape_change_between_solves_matches_oracle(pkg, dev, powerlaw_lp):
+    # run_max 8 segments every row over 256 entries, run_max 32 only those
+    # over 1024: the second solve on the same upload must not sum the slots
+    # the first plan's extra segmented rows left (step size, restart tests)
+    lp = powerlaw_lp
+    prob = pkg.Problem(lp, dev)
+    prob.solve(max_iter=130, eps_rel=0.0, engine=1, tile_run_max=8, tile_nnz=512)
+    ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=130, eps_rel=0.0))
+    r = prob.solve(max_iter=130, eps_rel=0.0, engine=1, tile_run_max=32, tile_nnz=2048)
+    assert abs(r.eta - ref.eta) <= 1e-12 * ref.eta
+    assert r.restarts == ref.restarts
+    xi, yi = prob.iterate()
+    assert relerr(xi, ref.x_iter) <= 1e-10 and relerr(yi, ref.y_iter) <= 1e-10
     prob.close()
 
 
