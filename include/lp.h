@@ -49,7 +49,8 @@ extern "C" {
 #define LP_ERR_TIMEOUT (-6) /* a bounded wait ran out                        */
 
 /* ---- termination codes (lp_result.termination) ------------------------ */
-#define LP_OPTIMAL 0    /* relative KKT error <= eps_rel                     */
+#define LP_OPTIMAL 0    /* the stopping test holds: rel_p, rel_d <= eps_rel and
+                         * rel_gap <= eps_gap_rel (default: rel-KKT <= eps_rel) */
 #define LP_ITER_LIMIT 1 /* max_iter iterations done                          */
 #define LP_TIME_LIMIT 2 /* time_limit_s elapsed                              */
 #define LP_NUMERICAL 3  /* a non-finite value appeared                       */
@@ -211,6 +212,31 @@ typedef struct {
                           * process.  Results are bitwise reproducible for a
                           * fixed shape; different shapes sum in a different
                           * order.                                          */
+  double eps_gap_rel;    /* 0 (= eps_rel): the stopping test is rel_p <=
+                          * eps_rel, rel_d <= eps_rel and rel_gap <= this
+                          * (with 0 exactly relative KKT error <= eps_rel)  */
+  int32_t polish;        /* 0; 1: feasibility polishing (grid engine only;
+                          * LP_ENGINE_AUTO then picks the grid engine).  At
+                          * a check at t >= the next allowed attempt where
+                          * rel_gap <= eps_gap_rel but rel_p or rel_d >
+                          * eps_rel, two PDHG phases start from that check's
+                          * T(z) = (x^, y^): the LP with c = 0 from (x^, 0)
+                          * until rel_p <= eps_rel, then the LP with every
+                          * finite bound set to 0 from (0, y^) until rel_d <=
+                          * eps_rel (the original LP's rel_p / rel_d), each
+                          * a fresh restarted Halpern PDHG with the solve's
+                          * step size and omega_0 = the current weight, no
+                          * infeasibility test, at most max(K, polish_fraction
+                          * t) iterations rounded up to a multiple of K.
+                          * If both succeed and their pair (x, y) meets the
+                          * stopping test on the original LP, it is returned
+                          * (LP_OPTIMAL); otherwise the solve resumes at that
+                          * check and the next attempt waits until 2 t.
+                          * Meant for eps_gap_rel well above eps_rel: the
+                          * phases move the objective values.  The phases'
+                          * iterations count in lp_result.iterations.       */
+  int32_t pad_polish_;
+  double polish_fraction; /* 0.125 (0 < f <= 8)                             */
 } lp_solve_opts;
 
 typedef struct {
@@ -234,7 +260,10 @@ typedef struct {
   int32_t refinements;     /* re-solves at a tighter tolerance that the
                               original-LP check asked for (iterations and
                               times above include them)                     */
+  int32_t polish_attempts; /* feasibility-polishing attempts (opts.polish)  */
+  int32_t polished;        /* 1: the returned point is a polished pair      */
   int32_t pad_;
+  int64_t polish_iterations; /* iterations of the polishing phases         */
 } lp_result;
 
 /* Defaults above; always call before filling in a field. */
@@ -275,9 +304,10 @@ int lp_upload(lp_problem *lp);
 
 /* Solve the current (reduced) LP on the GPU.  May be called repeatedly;
  * every call starts from the initial (or warm-start) point.  LP_MIXED runs
- * the SpMV in FP32 until the relative KKT error is within 10 x eps_rel, or
- * its best value has not halved over 256 checks; then it finishes with the
- * FP64 SpMV, and the iterates, anchor and weights carry over.  When the
+ * the SpMV on FP32 matrix values (the gathered vectors as float pairs,
+ * compensated FP32 sums; everything else FP64) and switches to the FP64
+ * SpMV for good only if the best relative KKT error has not halved over 256
+ * checks; the iterates, anchor and weights carry over.  When the
  * environment variable LP_TRACE names a file, every state read-back (each
  * check period of the grid engine, each launch of the cluster engine)
  * appends one JSON line: engine, t, rel_kkt, rel_p, rel_d, rel_gap, omega,

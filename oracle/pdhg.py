@@ -24,7 +24,13 @@ LP whose operator T is constant (fixed columns, free rows) the iterates have
 a closed form, which fixes the restart residual ||z - T(z)||_omega at every
 check, the check at which criterion (i) and criterion (ii) each first fire,
 and the primal weight after the restart for two values of theta (and its
-band).
+band).  Feasibility polishing and the separate gap tolerance
+(tests/test_oracle_polish.py): zeroing c leaves every primal residual and
+zeroing the finite bounds every dual residual unchanged; the phases' points
+are feasible by a direct evaluation of eq. (1) and of eq. (2)'s sign rules;
+a polished solve meets the test with the objective HiGHS finds, within the
+gap tolerance; failed attempts leave the main iterates bit for bit those of
+a solve without polishing; the phase budget rounds up to a check period.
 """
 from __future__ import annotations
 
@@ -58,6 +64,9 @@ class Opts:
     restarts: bool = True
     infeas_every: int = 4  # READING: infeasibility test every 4th check (0: never)
     eps_infeas: float = 1e-8  # READING: PDLP's infeasibility tolerances
+    eps_gap: float | None = None  # relative gap tolerance (None: eps_rel; see pdhg_solve)
+    polish: bool = False  # READING: feasibility polishing (see feasibility_polish), off
+    polish_fraction: float = 0.125  # a polishing phase runs at most max(K, fraction * t) iterations
 
 
 @dataclass
@@ -76,6 +85,7 @@ class Result:
     omega0: float
     iterates: list = field(default_factory=list)
     checks: list = field(default_factory=list)
+    polish: dict = field(default_factory=dict)  # attempts, successes, phase iterations
 
 
 # ----------------------------------------------------------------------------
@@ -326,7 +336,8 @@ def default_omega(sc: Scaled) -> float:
 
 def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                omega0: float | None = None, x_init=None, y_init=None,
-               record_iterates: int = 0, record_checks: bool = False) -> Result:
+               record_iterates: int = 0, record_checks: bool = False,
+               check_lp=None, stop_on: str = "kkt") -> Result:
     """Restarted reflected Halpern PDHG (READING of the solver the paper times).
 
     State z = (x, y) in the scaled space, anchor z0, Halpern counter k.
@@ -352,8 +363,20 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
          k <- k + 1.   (halpern=False: z <- (1 + rho) T(z) - rho z.)
     tau = eta / omega, sigma = eta * omega; eta = 0.998 / ||A~||_2 unless given.
     Initial point (READING): x = proj_[lx~,ux~](0), y = 0, or the given warm start.
+
+    The checks evaluate rel-KKT of `check_lp` (default: lp itself, which must
+    have the same matrix).  stop_on="kkt" stops when rel_p <= eps_rel,
+    rel_d <= eps_rel and rel_gap <= eps_gap (eps_gap = eps_rel unless set:
+    then this is rel-KKT <= eps_rel); "primal" / "dual" stop on rel_p / rel_d
+    alone (the phases of feasibility_polish).  With opts.polish, a check that
+    does not stop and finds rel_gap <= eps_gap while max(rel_p, rel_d) >
+    eps_rel, at t at or past the next allowed attempt, runs
+    feasibility_polish from T(z); when the polished pair meets the stopping
+    test the solve stops OPTIMAL with it, else the next attempt waits until
+    t >= 2 t (READING).  `iterations` then also counts the phases'.
     """
     opts = opts or Opts()
+    check_lp = lp if check_lp is None else check_lp
     sc = Scaled(lp, opts)
     A = sc.A
     m, n = A.shape
@@ -380,6 +403,9 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
     yh = y
     iterates = []
     checks = []
+    polish = {"attempts": 0, "successes": 0, "phase_iterations": 0}
+    next_polish = 0
+    polished = None
     start = time.perf_counter()
     if record_iterates:
         iterates.append((sc.dc * x, sc.dr * y))
@@ -388,13 +414,17 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
         sigma = eta * omega
         xh, yh = pdhg_operator(A, sc.c, sc.lx, sc.ux, sc.lc, sc.uc, x, y, tau, sigma)
         if t % K == 0:
-            kkt = rel_kkt(lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
+            kkt = rel_kkt(check_lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
+            if stop_on == "kkt":
+                done = kkt_met(kkt, opts)
+            else:
+                done = kkt["rel_p" if stop_on == "primal" else "rel_d"] <= opts.eps_rel
             if record_checks:
                 checks.append({"t": t, "rel_kkt": kkt["rel_kkt"], "omega": omega, "k": k})
             if not (np.all(np.isfinite(xh)) and np.all(np.isfinite(yh))
                     and math.isfinite(kkt["rel_kkt"])):
                 status = NUMERICAL
-            elif kkt["rel_kkt"] <= opts.eps_rel:
+            elif done:
                 status = OPTIMAL
             elif time.perf_counter() - start > opts.time_limit_s:
                 status = TIME_LIMIT
@@ -404,6 +434,18 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
                                                  opts.eps_infeas)
                 if cert is not None:
                     status = cert
+            if (status == ITER_LIMIT and opts.polish and stop_on == "kkt" and t >= next_polish
+                    and kkt["rel_gap"] <= gap_tol(opts)
+                    and max(kkt["rel_p"], kkt["rel_d"]) > opts.eps_rel):
+                got = feasibility_polish(lp, opts, sc.dc * xh, sc.dr * yh, eta, omega, t)
+                polish["attempts"] += 1
+                polish["phase_iterations"] += got["iterations"]
+                if got["kkt"] is not None and kkt_met(got["kkt"], opts):
+                    polish["successes"] += 1
+                    polished = got
+                    status = OPTIMAL
+                else:
+                    next_polish = 2 * t
             if status != ITER_LIMIT:
                 t += 1  # count this evaluation of T
                 break
@@ -451,10 +493,80 @@ def pdhg_solve(lp, opts: Opts | None = None, eta: float | None = None,
         if record_iterates and t <= record_iterates:
             iterates.append((sc.dc * x, sc.dr * y))
     if kkt is None or status == ITER_LIMIT:
-        kkt = rel_kkt(lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
+        kkt = rel_kkt(check_lp, sc.dc * xh, sc.dr * yh, A=sc.A0)
     xs = sc.dc * xh
     ys = sc.dr * yh
+    if polished is not None:
+        xs, ys, kkt = polished["x"], polished["y"], polished["kkt"]
     zs = np.asarray(lp.c, np.float64) - sc.A0.T @ ys
     return Result(status=status, x=xs, y=ys, z=zs, x_iter=sc.dc * x, y_iter=sc.dr * y,
-                  iterations=t, restarts=restarts, kkt=kkt, eta=float(eta), omega=omega,
-                  omega0=float(omega0), iterates=iterates, checks=checks)
+                  iterations=t + polish["phase_iterations"], restarts=restarts, kkt=kkt,
+                  eta=float(eta), omega=omega, omega0=float(omega0), iterates=iterates,
+                  checks=checks, polish=polish)
+
+
+def gap_tol(opts: Opts) -> float:
+    return opts.eps_rel if opts.eps_gap is None else opts.eps_gap
+
+
+def kkt_met(kkt: dict, opts: Opts) -> bool:
+    """The stopping test: rel_p, rel_d <= eps_rel and rel_gap <= eps_gap."""
+    return (kkt["rel_p"] <= opts.eps_rel and kkt["rel_d"] <= opts.eps_rel
+            and kkt["rel_gap"] <= gap_tol(opts))
+
+
+class _Modified:
+    """lp with its cost vector and / or its finite bounds replaced (the same
+    matrix, so the same scaling)."""
+
+    def __init__(self, lp, zero_cost=False, zero_bounds=False):
+        for a in ("m", "n", "row_ptr", "col_idx", "val"):
+            setattr(self, a, getattr(lp, a))
+        self.c = np.zeros(lp.n) if zero_cost else np.asarray(lp.c, np.float64)
+        self.obj_offset = 0.0 if zero_cost else float(lp.obj_offset)
+
+        def z(v):
+            v = np.asarray(v, np.float64)
+            return np.where(np.isfinite(v), 0.0, v) if zero_bounds else v
+
+        self.row_lo, self.row_hi = z(lp.row_lo), z(lp.row_hi)
+        self.col_lo, self.col_hi = z(lp.col_lo), z(lp.col_hi)
+
+
+def feasibility_polish(lp, opts: Opts, x_hat, y_hat, eta: float, omega: float, t: int) -> dict:
+    """Feasibility polishing (READING; the PDLP family's variant, which the
+    paper does not specify).  From a point whose duality gap already meets
+    eps_rel, two PDHG runs on feasibility problems of the same matrix:
+      primal phase: the LP with c = 0 (any feasible x is optimal), from
+        (x_hat, 0), stopped when rel_p of the ORIGINAL LP is <= eps_rel;
+      dual phase: the LP with every finite bound set to 0 (its dual has the
+        same feasible set as the original's, with objective 0), from
+        (0, y_hat), stopped when rel_d of the original LP is <= eps_rel;
+    each a fresh restarted Halpern PDHG (same options, no infeasibility test,
+    no polishing) with the solve's eta and omega_0 = the current omega, at
+    most max(K, polish_fraction * t) iterations rounded up to a multiple of
+    K.  The candidate is (x of the primal phase, y of the dual phase): both
+    moved little from (x_hat, y_hat), so their gap stays near the gap of
+    (x_hat, y_hat); the caller accepts it when it meets the stopping test
+    (kkt_met) on the original LP.  The phases stay near (x_hat, y_hat) in
+    norm, but the gap of the pair grows with the moves (measured: 2e-4 to
+    1e-3 relative from points at 1e-5 feasibility), so polishing pays only
+    with eps_gap well above eps_rel, the regime it is meant for.
+    Returns {"x", "y", "kkt" (None if a phase failed), "iterations"}.
+    """
+    K = max(int(opts.check_every), 1)
+    budget = K * max(1, math.ceil(opts.polish_fraction * t / K))
+    sub = Opts(**{**opts.__dict__, "max_iter": budget, "infeas_every": 0, "polish": False})
+    rp = pdhg_solve(_Modified(lp, zero_cost=True), sub, eta=eta, omega0=omega,
+                    x_init=x_hat, y_init=np.zeros(lp.m), check_lp=lp, stop_on="primal")
+    out = {"x": None, "y": None, "kkt": None, "iterations": rp.iterations}
+    if rp.status != OPTIMAL:
+        return out
+    rd = pdhg_solve(_Modified(lp, zero_bounds=True), sub, eta=eta, omega0=omega,
+                    x_init=np.zeros(lp.n), y_init=y_hat, check_lp=lp, stop_on="dual")
+    out["iterations"] += rd.iterations
+    if rd.status != OPTIMAL:
+        return out
+    out["x"], out["y"] = rp.x, rd.y
+    out["kkt"] = rel_kkt(lp, rp.x, rd.y)
+    return out

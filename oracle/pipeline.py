@@ -7,8 +7,9 @@ READING (the paper states that presolve returns an approximate solution of
 the original LP, Sec. 2.1 and Sec. 3.3, without a rule for when that
 approximation is not good enough): the reduced LP is solved to eps_rel; the
 postsolved point's relative KKT error (eq. (2), the measure of
-``pdhg.rel_kkt``) is then measured on the ORIGINAL LP, and while it exceeds
-eps_rel the reduced LP is solved again with a tolerance ten times tighter,
+``pdhg.rel_kkt``) is then measured on the ORIGINAL LP, and while it fails the
+stopping test (``pdhg.kkt_met``: rel-KKT <= eps_rel unless a separate gap
+tolerance is set) the reduced LP is solved again with tolerances ten times tighter,
 warm-started from the previous solution, at most ``refine`` times.  The
 reduction can amplify the error because the relative measure normalises by
 the problem's own ||bhat|| and ||c||, which presolve changes (a fixed column
@@ -57,10 +58,11 @@ def solve_original(lp, opts: P.Opts | None = None, refine: int = 3) -> PipelineR
     while True:
         x, y, z = PS.postsolve(pres, r.x, r.y, r.z)
         k = P.rel_kkt(lp, x, y)
-        if not (k["rel_kkt"] > opts.eps_rel) or refinements == refine or r.status != P.OPTIMAL:
+        if P.kkt_met(k, opts) or refinements == refine or r.status != P.OPTIMAL:
             break
         eps *= 0.1
-        o2 = P.Opts(**{**opts.__dict__, "eps_rel": eps})
+        gap = None if opts.eps_gap is None else opts.eps_gap * 0.1 ** (refinements + 1)
+        o2 = P.Opts(**{**opts.__dict__, "eps_rel": eps, "eps_gap": gap})
         r = P.pdhg_solve(red, o2, x_init=r.x, y_init=r.y)
         iters += r.iterations
         refinements += 1

@@ -59,7 +59,8 @@ class lp_solve_opts(C.Structure):
                 ("verbose", C.c_int32), ("infeas_every", C.c_int32),
                 ("eps_infeas", C.c_double), ("primal_weight_clamp", C.c_double),
                 ("refine_original", C.c_int32), ("tile_run_max", C.c_int32),
-                ("tile_nnz", C.c_int32)]
+                ("tile_nnz", C.c_int32), ("eps_gap_rel", C.c_double), ("polish", C.c_int32),
+                ("pad_polish_", C.c_int32), ("polish_fraction", C.c_double)]
 
 
 class lp_result(C.Structure):
@@ -71,7 +72,8 @@ class lp_result(C.Structure):
                 ("t_solve_s", C.c_double), ("t_total_s", C.c_double),
                 ("kernel_launches", C.c_int64), ("fp32_iterations", C.c_int64),
                 ("rel_kkt_original", C.c_double), ("refinements", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("polish_attempts", C.c_int32), ("polished", C.c_int32), ("pad_", C.c_int32),
+                ("polish_iterations", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

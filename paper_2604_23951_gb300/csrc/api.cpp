@@ -74,13 +74,20 @@ int problem_proven_status(const lp_problem *lp) {
 // rel-KKT on the original LP of the postsolved reduced solution (x, y, z of
 // the current LP), or -1 when the problem was not presolved (the current LP
 // is the original and the device measure already applies to it)
-double problem_original_kkt(const lp_problem *lp, const double *x, const double *y,
-                            const double *z) {
-  if (!lp->presolved) return -1.0;
+// the measures of host_rel_kkt for the postsolved point on the original LP
+// (k[0] = rel-KKT; -1 when the problem was not presolved)
+void problem_original_measures(const lp_problem *lp, const double *x, const double *y,
+                               const double *z, double k[9]) {
+  k[0] = -1.0;
+  if (!lp->presolved) return;
   std::vector<double> X(lp->orig.n), Y(lp->orig.m), Z(lp->orig.n);
   postsolve_run(lp->po, lp->cur, x, y, z, X.data(), Y.data(), Z.data());
-  double k[9];
   host_rel_kkt(lp->orig, X.data(), Y.data(), k);
+}
+double problem_original_kkt(const lp_problem *lp, const double *x, const double *y,
+                            const double *z) {
+  double k[9];
+  problem_original_measures(lp, x, y, z, k);
   return k[0];
 }
 void problem_store_solution(lp_problem *lp, const std::vector<double> &x,
@@ -103,7 +110,9 @@ bool valid_solve_opts(const lp_solve_opts &o) {
          o.engine <= LP_ENGINE_CLUSTER && o.refine_original >= 0 && o.refine_original <= 8 &&
          (o.tile_run_max == 0 || o.tile_run_max == 8 || o.tile_run_max == 16 ||
           o.tile_run_max == 32) &&
-         (o.tile_nnz == 0 || o.tile_nnz == 512 || o.tile_nnz == 2048);
+         (o.tile_nnz == 0 || o.tile_nnz == 512 || o.tile_nnz == 2048) && o.eps_gap_rel >= 0 &&
+         (o.polish == 0 || o.polish == 1) && o.polish_fraction > 0 && o.polish_fraction <= 8 &&
+         !(o.polish && o.engine == LP_ENGINE_CLUSTER);
 }
 }  // namespace gb300lp
 
@@ -129,6 +138,7 @@ void lp_solve_opts_default(lp_solve_opts *o) {
   o->eps_infeas = 1e-8;
   o->primal_weight_clamp = 10.0;
   o->refine_original = 3;
+  o->polish_fraction = 0.125;
   o->eps_rel = 1e-6;
   o->max_iter = 200000;
   o->time_limit_s = 3600.0;
@@ -291,7 +301,8 @@ int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res) {
   auto solve_once = [&](const lp_solve_opts &oo, lp_result &r) -> int {
     std::memset(&r, 0, sizeof(r));
     const bool cluster = oo.engine == LP_ENGINE_CLUSTER ||
-                         (oo.engine == LP_ENGINE_AUTO && lp->cur.nnz() < kClusterEngineNnz);
+                         (oo.engine == LP_ENGINE_AUTO && !oo.polish &&
+                          lp->cur.nnz() < kClusterEngineNnz);
     if (cluster) return cluster_solve(lp->cur, oo, &lp->dev, &r, lp->sol, err);
     if (!lp->dlp) {
       lp->dlp = dev_create(&lp->dev, err);
@@ -316,14 +327,18 @@ int lp_solve(lp_problem *lp, const lp_solve_opts *opts, lp_result *res) {
   if (lp->presolved && o.refine_original > 0 && r.termination == LP_OPTIMAL) {
     double eps = o.eps_rel;
     for (int q = 0;; ++q) {
-      const double k = problem_original_kkt(lp, lp->sol.x.data(), lp->sol.y.data(),
-                                            lp->sol.z.data());
-      r.rel_kkt_original = k;
-      if (!(k > o.eps_rel) || q == o.refine_original || r.termination != LP_OPTIMAL) break;
+      double kk[9];
+      problem_original_measures(lp, lp->sol.x.data(), lp->sol.y.data(), lp->sol.z.data(), kk);
+      r.rel_kkt_original = kk[0];
+      // the stopping test on the original LP (rel_p, rel_d, rel_gap)
+      const double eg = o.eps_gap_rel > 0 ? o.eps_gap_rel : o.eps_rel;
+      const bool met = kk[1] <= o.eps_rel && kk[2] <= o.eps_rel && kk[3] <= eg;
+      if (met || q == o.refine_original || r.termination != LP_OPTIMAL) break;
       eps *= 0.1;
       const std::vector<double> xw = lp->sol.x, yw = lp->sol.y;
       lp_solve_opts o2 = o;
       o2.eps_rel = eps;
+      if (o.eps_gap_rel > 0) o2.eps_gap_rel = o.eps_gap_rel * std::pow(0.1, q + 1);
       o2.x_init = xw.data();
       o2.y_init = yw.data();
       lp_result r2;

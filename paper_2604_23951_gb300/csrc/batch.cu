@@ -966,6 +966,9 @@ void state_init(const lp_solve_opts &o, State &st, const Packed &pk) {
   st.beta_art = o.beta_art;
   st.theta = o.theta;
   st.eps_rel = o.eps_rel;
+  st.eps_gap = o.eps_gap_rel > 0 ? o.eps_gap_rel : o.eps_rel;
+  st.stop_on = 0;
+  st.polish = 0;  // the cluster engine does not polish
   st.eps_infeas = o.eps_infeas;
   st.infeas_every = o.infeas_every;
   st.omega_clamp = o.primal_weight_clamp;
@@ -1140,7 +1143,7 @@ void admit(lp_server *srv) {
     CK(cudaMemcpyAsync(srv->d_desc + sid, &sl.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice,
                        srv->s));
     state_init(srv->opts, srv->h_state[sid], rq.pk);
-    if (rq.eps_rel >= 0) srv->h_state[sid].eps_rel = rq.eps_rel;
+    if (rq.eps_rel >= 0) srv->h_state[sid].eps_rel = srv->h_state[sid].eps_gap = rq.eps_rel;
     CK(cudaMemcpyAsync(srv->d_state + sid, &srv->h_state[sid], sizeof(State),
                        cudaMemcpyHostToDevice, srv->s));
     CK(cudaStreamSynchronize(srv->s));  // the pageable blob may be freed next
@@ -1403,7 +1406,7 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
     if (opts) srv->opts = *opts;
     srv->opts.x_init = nullptr;
     srv->opts.y_init = nullptr;
-    if (!valid_solve_opts(srv->opts)) {
+    if (!valid_solve_opts(srv->opts) || srv->opts.polish || srv->opts.eps_gap_rel != 0.0) {
       delete srv;
       set_last_error("invalid solve options");
       return LP_ERR_INVALID;

@@ -2,8 +2,10 @@
 // single-LP path (solver.cu) and the batched path (batch.cu).
 //
 // The decision follows the solver reading documented with the oracle:
-// checks at t = 0, K, 2K, ...; stop when the relative KKT error of T(z) is at
-// most eps_rel (or a value is not finite); with r = ||z - T(z)||_omega,
+// checks at t = 0, K, 2K, ...; stop when T(z) passes the stopping test
+// (rel_p, rel_d <= eps_rel and rel_gap <= eps_gap: with eps_gap = eps_rel,
+// relative KKT error <= eps_rel) or a value is not finite; with
+// r = ||z - T(z)||_omega,
 // record r0 = r_prev = r at the first check, otherwise restart when
 // r <= beta_suff r0, or r <= beta_nec r0 and r > r_prev, or k >= beta_art t;
 // a restart moves the anchor and the iterate to T(z) and smooths the primal
@@ -19,6 +21,21 @@
 namespace gb300lp {
 
 constexpr int ST_RUNNING = -1;
+constexpr int ST_POLISH = -2;  // a check asked the host for feasibility polishing
+
+// reduced quantities of a check (and of the set-up)
+// Q_I*: infeasibility test of the direction (d, w) = T(z) - z0 (unscaled):
+// c^T d, squared cone violations of d (columns) and A d (rows), squared
+// residual ||A^T w + lam||^2, dual-ray objective (rows, columns)
+enum {
+  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P,
+  Q_ICD, Q_IPVC, Q_IPVR, Q_IDR, Q_IDOR, Q_IDOC,
+  Q_CN, Q_BN, Q_PW, Q_PWA, NQ
+};
+// (Q_PW: ||A^T A v||^2 of the power iteration's A^T passes; Q_PWA: ||A v||^2
+// of its final pass over A.  Every quantity is summed from one matrix's
+// kernels only, so the per-row slots of segmented rows never mix matrices.)
+
 
 struct State {
   double eta, omega, tau, sigma;
@@ -40,11 +57,24 @@ struct State {
   int err;  // set by a kernel whose bounded wait expired
   // mixed precision: 1 while the SpMV runs on FP32 matrix values; the check
   // switches the LP to the FP64 SpMV for good once the best rel-KKT so far
-  // has not halved for kPolishStall checks
+  // has not halved for kMixedStall checks
   int mixed_active;
   int stall;       // checks since the best rel-KKT halved
   double best_rel;
   long long t_switch;  // iteration of the FP64 switch (or -1)
+  // stopping test: stop_on 0: rel_p <= eps_rel, rel_d <= eps_rel and rel_gap
+  // <= eps_gap; 1: rel_p <= eps_rel only; 2: rel_d <= eps_rel only (the
+  // phases of feasibility polishing)
+  double eps_gap;
+  int stop_on;
+  // feasibility polishing: a check at t >= next_polish that does not stop,
+  // with rel_gap <= eps_gap and rel_p or rel_d > eps_rel, saves its
+  // quantities in pq and ends in ST_POLISH; the host runs the phases and
+  // either finishes or resumes the check (check_update again, next_polish
+  // = 2t)
+  int polish;
+  long long next_polish;
+  double pq[NQ];
 };
 
 // FP64 switch of the mixed mode, a guard only: the mixed SpMV (FP32 matrix
@@ -54,20 +84,7 @@ struct State {
 // little, while rounding the gathered vectors to float (an earlier form of
 // this mode) stalled it between 1e-5 and 1e-6 -- so it runs to the
 // tolerance unless its progress stops.
-constexpr int kPolishStall = 256;
-
-// reduced quantities of a check (and of the set-up)
-// Q_I*: infeasibility test of the direction (d, w) = T(z) - z0 (unscaled):
-// c^T d, squared cone violations of d (columns) and A d (rows), squared
-// residual ||A^T w + lam||^2, dual-ray objective (rows, columns)
-enum {
-  Q_XRES = 0, Q_XD, Q_YRES, Q_YD, Q_RP, Q_RDY, Q_DY, Q_RD, Q_DL, Q_P,
-  Q_ICD, Q_IPVC, Q_IPVR, Q_IDR, Q_IDOR, Q_IDOC,
-  Q_CN, Q_BN, Q_PW, Q_PWA, NQ
-};
-// (Q_PW: ||A^T A v||^2 of the power iteration's A^T passes; Q_PWA: ||A v||^2
-// of its final pass over A.  Every quantity is summed from one matrix's
-// kernels only, so the per-row slots of segmented rows never mix matrices.)
+constexpr int kMixedStall = 256;
 
 // whether the check at iteration t tests for infeasibility
 __host__ __device__ __forceinline__ bool infeas_due(long long t, int K, int every) {
@@ -118,7 +135,11 @@ __device__ __forceinline__ void check_update(State *st, const double *q, bool ev
     return;
   }
   bool finite = isfinite(rel) && isfinite(q[Q_XRES]) && isfinite(q[Q_YRES]);
-  if (!finite || rel <= st->eps_rel) {
+  const bool met = st->stop_on == 1   ? relp <= st->eps_rel
+                   : st->stop_on == 2 ? reld <= st->eps_rel
+                                      : (relp <= st->eps_rel && reld <= st->eps_rel &&
+                                         relg <= st->eps_gap);
+  if (!finite || met) {
     st->status = finite ? 0 : 3;  // LP_OPTIMAL : LP_NUMERICAL
     st->iters = st->t + 1;
     st->restart_flag = 0;
@@ -138,6 +159,13 @@ __device__ __forceinline__ void check_update(State *st, const double *q, bool ev
       return;
     }
   }
+  if (st->polish && st->stop_on == 0 && st->t >= st->next_polish && relg <= st->eps_gap &&
+      fmax(relp, reld) > st->eps_rel) {
+    for (int i = 0; i < NQ; ++i) st->pq[i] = q[i];
+    st->status = ST_POLISH;
+    st->restart_flag = 0;
+    return;
+  }
   if (st->mixed_active) {
     if (rel < 0.5 * st->best_rel) {
       st->best_rel = rel;
@@ -145,7 +173,7 @@ __device__ __forceinline__ void check_update(State *st, const double *q, bool ev
     } else {
       st->stall += 1;
     }
-    if (st->stall >= kPolishStall) {
+    if (st->stall >= kMixedStall) {
       st->mixed_active = 0;
       st->t_switch = st->t;
     }

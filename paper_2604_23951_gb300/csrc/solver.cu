@@ -470,6 +470,50 @@ __global__ void k_check(State *st, const double *partials, int GP, int eval_only
   check_update(st, q, eval_only != 0);
 }
 
+// Feasibility polishing (State::polish; the phases run on the host's
+// orders with the iteration kernels): resume the check that asked for it
+// after a failed attempt -- its quantities are in st->pq -- with the next
+// attempt allowed at 2t.
+__global__ void k_check_resume(State *st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->status = ST_RUNNING;
+  st->next_polish = 2 * st->t;
+  double q[NQ];
+  for (int i = 0; i < NQ; ++i) q[i] = st->pq[i];
+  check_update(st, q, false);
+}
+
+// the dual phase's problem: every finite entry of v set to 0
+__global__ void k_zero_finite(int n, double *v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (isfinite(v[i])) v[i] = 0.0;
+}
+
+// a phase's start (scaled): x = x0 = xs, y = y0 = ys (0 where NULL); yf the
+// float pairs of y when given
+__global__ void k_set_point(int n, int m, const double *__restrict__ xs,
+                            const double *__restrict__ ys, double *x, double *x0, double *y,
+                            double *y0, float2 *yf) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+  for (int j = i0; j < n; j += st) {
+    const double v = xs ? xs[j] : 0.0;
+    x[j] = v;
+    x0[j] = v;
+  }
+  for (int i = i0; i < m; i += st) {
+    const double v = ys ? ys[i] : 0.0;
+    y[i] = v;
+    y0[i] = v;
+    if (yf) yf[i] = split_f2(v);
+  }
+}
+
+// yf = the float pairs of y (after y is restored)
+__global__ void k_split_y(int m, const double *__restrict__ y, float2 *yf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    yf[i] = split_f2(y[i]);
+}
+
 // K5: on restart, x = x0 = xh and y = y0 = yh
 __global__ void k_restart(const State *__restrict__ st, int n, int m, double *x, double *x0,
                           const double *__restrict__ xhat, double *y, double *y0,
@@ -542,6 +586,10 @@ struct DeviceLP {
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xhat = nullptr;
   double *y = nullptr, *y0 = nullptr, *yhat = nullptr, *zbuf = nullptr;
   double *pv = nullptr, *pv0 = nullptr, *pw = nullptr, *pu = nullptr;
+  // feasibility polishing: the main iterate, anchor and T(z) kept while the
+  // phases run, and the primal phase's x (allocated on first use)
+  double *bx = nullptr, *bx0 = nullptr, *bxh = nullptr, *bxp = nullptr;
+  double *by = nullptr, *by0 = nullptr, *byh = nullptr;
   int infeas_every = 0;  // of the current solve (host copy of the state's)
   // last tile-shape measurement: mean ms of K1 (rows of A^T) and K2 (rows of
   // A) per candidate, or empty when the choice came from the cache / opts
@@ -606,6 +654,7 @@ struct DeviceLP {
     }
     allocs.clear();
     flush = nullptr;
+    bx = bx0 = bxh = bxp = by = by0 = byh = nullptr;
     uploaded = false;
   }
   // persistent grid for a warp-tile table (8 warps per CTA), at most G CTAs
@@ -1145,6 +1194,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     init.beta_art = o.beta_art;
     init.theta = o.theta;
     init.eps_rel = o.eps_rel;
+    init.eps_gap = o.eps_gap_rel > 0 ? o.eps_gap_rel : o.eps_rel;
+    init.stop_on = 0;
+    init.polish = o.polish ? 1 : 0;
+    init.next_polish = 0;
     init.eps_infeas = o.eps_infeas;
     init.infeas_every = o.infeas_every;
     init.omega_clamp = o.primal_weight_clamp;
@@ -1201,7 +1254,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     CK(cudaEventRecord(e1, d->s));
     // iteration driver
     const long long max_iter = o.max_iter;
-    long long launched = 0;
     int pi = mixed ? 1 : 0;
     bool use_graph = o.use_graph != 0;
     const int with_inf = d->infeas_every > 0 ? 1 : 0;
@@ -1224,7 +1276,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       d->launches = saved;
     }
     const long long per_graph = 2LL * K + 4 + 3LL * with_inf;
-    std::vector<cudaEvent_t> evs;
     std::vector<cudaEvent_t> pool;
     auto get_event = [&]() {
       cudaEvent_t e;
@@ -1238,54 +1289,207 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     };
     bool timed_out = false;
     const double tl = o.time_limit_s > 0 ? o.time_limit_s : 1e30;
-    size_t head = 0;
-    for (;;) {
-      // keep up to two chunks in flight
-      while (evs.size() - head < 2 && launched < max_iter) {
-        long long rem = max_iter - launched;
-        if (use_graph && rem > K) {
-          CK(cudaGraphLaunch(d->graph[pi], d->s));
-          d->launches += per_graph;
-          launched += K;
-        } else {
-          long long len = std::min<long long>(rem, K);
-          for (long long j = 0; j < len; ++j) {
-            bool last = (launched + j + 1 == max_iter);
-            launch_iteration(d, mixed, (int)j, j == 0, last && j != 0);
+    // Run the state on the device from iteration `launched` until it leaves
+    // ST_RUNNING (stops, or a check asks for polishing), `limit` iterations
+    // have been launched, a bounded wait fails or the time limit passes;
+    // then drain the stream.
+    auto drive = [&](long long limit, long long &launched) {
+      std::vector<cudaEvent_t> evs;
+      size_t head = 0;
+      for (;;) {
+        // keep up to two chunks in flight
+        while (evs.size() - head < 2 && launched < limit) {
+          long long rem = limit - launched;
+          if (use_graph && rem > K) {
+            CK(cudaGraphLaunch(d->graph[pi], d->s));
+            d->launches += per_graph;
+            launched += K;
+          } else {
+            long long len = std::min<long long>(rem, K);
+            for (long long j = 0; j < len; ++j) {
+              bool last = (launched + j + 1 == limit);
+              launch_iteration(d, mixed, (int)j, j == 0, last && j != 0);
+            }
+            CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+            launched += len;
           }
-          CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
-          launched += len;
+          cudaEvent_t e = get_event();
+          CK(cudaEventRecord(e, d->s));
+          evs.push_back(e);
         }
-        cudaEvent_t e = get_event();
-        CK(cudaEventRecord(e, d->s));
-        evs.push_back(e);
+        if (head == evs.size()) break;
+        CK(cudaEventSynchronize(evs[head]));
+        pool.push_back(evs[head]);
+        ++head;
+        volatile int status = d->hst->status;
+        volatile int kerr = d->hst->err;
+        {
+          const State &V = *d->hst;
+          trace_state("grid", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap, V.omega, V.restarts,
+                      V.mixed_active);
+        }
+        if (o.verbose) {
+          const State &V = *d->hst;
+          std::fprintf(stderr, "pdhg t=%lld rel_kkt=%.3e rel_p=%.2e rel_d=%.2e gap=%.2e "
+                       "omega=%.3e restarts=%d fp32=%d stop_on=%d\n", V.t, V.rel_kkt, V.rel_p,
+                       V.rel_d, V.rel_gap, V.omega, V.restarts, V.mixed_active, V.stop_on);
+        }
+        if (status != ST_RUNNING || kerr) break;
+        double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (el > tl) {
+          timed_out = true;
+          break;
+        }
       }
-      if (head == evs.size()) break;
-      CK(cudaEventSynchronize(evs[head]));
-      pool.push_back(evs[head]);
-      ++head;
-      volatile int status = d->hst->status;
-      volatile int kerr = d->hst->err;
-      {
+      CK(cudaStreamSynchronize(d->s));
+      for (size_t q = head; q < evs.size(); ++q) pool.push_back(evs[q]);
+      CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
+    };
+    long long launched = 0;
+    long long polish_iters = 0;
+    int polish_attempts = 0;
+    bool polished = false;
+    for (;;) {
+      drive(max_iter, launched);
+      if (d->hst->status != ST_POLISH || d->hst->err || timed_out) break;
+      // ---- feasibility polishing at the check t = S.t ----------------------
+      const State S = *d->hst;
+      const long long tc = S.t;
+      ++polish_attempts;
+      if (!d->bx) {
+        d->bx = d->dalloc_n<double>(n);
+        d->bx0 = d->dalloc_n<double>(n);
+        d->bxh = d->dalloc_n<double>(n);
+        d->bxp = d->dalloc_n<double>(n);
+        d->by = d->dalloc_n<double>(m);
+        d->by0 = d->dalloc_n<double>(m);
+        d->byh = d->dalloc_n<double>(m);
+      }
+      auto copy = [&](double *dst, const double *src, int cnt) {
+        if (cnt) CK(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, d->s));
+      };
+      copy(d->bx, d->x, n);
+      copy(d->bx0, d->x0, n);
+      copy(d->bxh, d->xhat, n);
+      copy(d->by, d->y, m);
+      copy(d->by0, d->y0, m);
+      copy(d->byh, d->yhat, m);
+      const long long budget =
+          (long long)K * std::max(1LL, (long long)std::ceil(o.polish_fraction * (double)tc / K));
+      const int gmn = d->grid_for(std::max(std::max(m, n), 1));
+      auto phase_state = [&](int stop_on) {
+        State P = S;
+        P.status = ST_RUNNING;
+        P.stop_on = stop_on;
+        P.polish = 0;
+        P.next_polish = 0;
+        P.infeas_every = 0;
+        P.omega0 = S.omega;
+        P.tau = S.eta / S.omega;
+        P.sigma = S.eta * S.omega;
+        P.r0 = P.r_prev = P.last_r = 0.0;
+        P.t = 0;
+        P.iters = 0;
+        P.k_base = 0;
+        P.k_off = 0;
+        P.restarts = 0;
+        P.restart_flag = 0;
+        P.err = 0;
+        P.stall = 0;
+        P.best_rel = INFINITY;
+        P.t_switch = -1;
+        CK(cudaMemcpyAsync(d->st, &P, sizeof(State), cudaMemcpyHostToDevice, d->s));
+      };
+      // iterations a phase took: to its stopping check, or its whole budget
+      auto phase_iters = [&](long long lim) {
+        return d->hst->status == ST_RUNNING ? lim : d->hst->iters;
+      };
+      auto restore_data = [&]() {
+        k_apply_cols<<<d->G, kBlock, 0, d->s>>>(n, d->c0, d->lx0, d->ux0, d->dc, d->c, d->lx,
+                                                d->ux, d->partials, d->GP);
+        k_apply_rows<<<d->G, kBlock, 0, d->s>>>(m, d->lc0, d->uc0, d->dr, d->lc, d->uc,
+                                                d->partials, d->GP);
+        d->launches += 2;
+      };
+      // primal phase: c = 0, from (x^, 0), until rel_p <= eps_rel
+      if (n) CK(cudaMemsetAsync(d->c, 0, sizeof(double) * n, d->s));
+      k_set_point<<<gmn, kBlock, 0, d->s>>>(n, m, d->bxh, nullptr, d->x, d->x0, d->y, d->y0,
+                                            mixed ? d->yf : nullptr);
+      phase_state(1);
+      d->launches += 1;
+      long long lp_ = 0;
+      drive(budget, lp_);
+      const bool ok_p = d->hst->status == LP_OPTIMAL && !d->hst->err;
+      polish_iters += phase_iters(budget);
+      if (ok_p) copy(d->bxp, d->xhat, n);
+      restore_data();
+      bool ok_d = false;
+      if (ok_p && !timed_out) {
+        // dual phase: finite bounds 0, from (0, y^), until rel_d <= eps_rel
+        k_zero_finite<<<d->G, kBlock, 0, d->s>>>(n, d->lx);
+        k_zero_finite<<<d->G, kBlock, 0, d->s>>>(n, d->ux);
+        k_zero_finite<<<d->G, kBlock, 0, d->s>>>(m, d->lc);
+        k_zero_finite<<<d->G, kBlock, 0, d->s>>>(m, d->uc);
+        k_set_point<<<gmn, kBlock, 0, d->s>>>(n, m, nullptr, d->byh, d->x, d->x0, d->y, d->y0,
+                                              mixed ? d->yf : nullptr);
+        d->launches += 5;
+        phase_state(2);
+        long long ld = 0;
+        drive(budget, ld);
+        ok_d = d->hst->status == LP_OPTIMAL && !d->hst->err;
+        polish_iters += phase_iters(budget);
+        restore_data();
+      }
+      if (ok_p && ok_d) {
+        // the pair (x of the primal phase, y of the dual phase) on the
+        // original LP; yhat holds the dual phase's y
+        copy(d->xhat, d->bxp, n);
+        State E = S;
+        E.status = ST_RUNNING;
+        CK(cudaMemcpyAsync(d->st, &E, sizeof(State), cudaMemcpyHostToDevice, d->s));
+        final_eval(d);
+        CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+        CK(cudaStreamSynchronize(d->s));
         const State &V = *d->hst;
-        trace_state("grid", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap, V.omega, V.restarts,
-                    V.mixed_active);
+        if (V.rel_p <= S.eps_rel && V.rel_d <= S.eps_rel && V.rel_gap <= S.eps_gap) {
+          State F = V;
+          F.status = LP_OPTIMAL;
+          F.iters = tc + 1;
+          CK(cudaMemcpyAsync(d->st, &F, sizeof(State), cudaMemcpyHostToDevice, d->s));
+          copy(d->x, d->bx, n);  // the returned iterate z^t stays the main one
+          copy(d->y, d->by, m);
+          CK(cudaStreamSynchronize(d->s));
+          *d->hst = F;
+          polished = true;
+          break;
+        }
       }
-      if (o.verbose) {
-        const State &V = *d->hst;
-        std::fprintf(stderr, "pdhg t=%lld rel_kkt=%.3e rel_p=%.2e rel_d=%.2e gap=%.2e omega=%.3e "
-                     "restarts=%d fp32=%d\n", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap,
-                     V.omega, V.restarts, V.mixed_active);
+      // failed: the main state back, then the rest of the check at tc and of
+      // its period
+      copy(d->x, d->bx, n);
+      copy(d->x0, d->bx0, n);
+      copy(d->xhat, d->bxh, n);
+      copy(d->y, d->by, m);
+      copy(d->y0, d->by0, m);
+      copy(d->yhat, d->byh, m);
+      if (mixed && m) {
+        k_split_y<<<gmn, kBlock, 0, d->s>>>(m, d->y, d->yf);
+        d->launches += 1;
       }
-      if (status != ST_RUNNING || kerr) break;
-      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-      if (el > tl) {
-        timed_out = true;
-        break;
-      }
+      CK(cudaMemcpyAsync(d->st, &S, sizeof(State), cudaMemcpyHostToDevice, d->s));
+      k_check_resume<<<1, 32, 0, d->s>>>(d->st);
+      k_restart<<<d->grid_for(std::max(m, n)), kBlock, 0, d->s>>>(
+          d->st, n, m, d->x, d->x0, d->xhat, d->y, d->y0, d->yhat, mixed ? d->yf : nullptr);
+      d->launches += 2;
+      const long long rest = std::min<long long>(K - 1, max_iter - 1 - tc);
+      for (long long j = 1; j <= rest; ++j)
+        launch_iteration(d, mixed, (int)j, false, tc + j + 1 == max_iter);
+      launched = tc + 1 + std::max(0LL, rest);
+      CK(cudaMemcpyAsync(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost, d->s));
+      CK(cudaStreamSynchronize(d->s));
+      if (d->hst->status != ST_RUNNING) break;
     }
-    CK(cudaStreamSynchronize(d->s));
-    for (size_t q = head; q < evs.size(); ++q) pool.push_back(evs[q]);
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
     if (d->hst->err) {
@@ -1297,7 +1501,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     }
     int status = d->hst->status;
     long long iters = d->hst->iters;
-    if (status == ST_RUNNING) {
+    if (status == ST_RUNNING || status == ST_POLISH) {
       if (timed_out) {
         status = LP_TIME_LIMIT;
         iters = std::min(launched, max_iter);
@@ -1377,6 +1581,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
           std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
       res->kernel_launches = d->launches;
       res->fp32_iterations = mixed ? (S.t_switch >= 0 ? S.t_switch : iters) : 0;
+      res->iterations = iters + polish_iters;
+      res->polish_attempts = polish_attempts;
+      res->polished = polished ? 1 : 0;
+      res->polish_iterations = polish_iters;
     }
   } catch (const DeviceOOM &e) {
     err = e.what();
