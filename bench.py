@@ -219,6 +219,19 @@ def iter_bytes(m, n, nnz, fp32):
     return k1 + k2
 
 
+def tile_summary(srv):
+    """The batched tile-shape autotuner's table: per (m bucket, row-length
+    bucket) the chosen shape as (entries per lane, nonzeros per tile), or
+    null while the class is still trying, and its sample count."""
+    out = []
+    for c in srv.tile_tuning():
+        ch = c["chosen"]
+        shape = None if ch < 0 else [(8, 16, 32)[ch // 2], 2048 if ch & 1 else 512]
+        out.append({"class": [c["m_bucket"], c["len_bucket"]], "shape": shape,
+                    "samples": sum(c["samples"])})
+    return out
+
+
 def fifo_latencies(arrivals, services):
     """arrival-to-completion times when requests are served one at a time in
     arrival order with the given service times"""
@@ -633,6 +646,8 @@ def run_batch(args):
             st["terminations"] = term_hist(res[t][0].termination for t in tickets)
             st["submit_s"] = t_sub
             st["submit_threads"] = nsub
+            st.update(srv.graph_stats())
+            st["tile_classes"] = tile_summary(srv)
             srv.close()
             per = [(int(res[t][0].iterations), int(res[t][0].fp32_iterations),
                     res[t][0].primal_obj, res[t][0].rel_kkt) for t in tickets]
@@ -773,6 +788,8 @@ def run_batch(args):
         sub.join()
         el = time.perf_counter() - t0
         st = srv.stats()
+        st.update(srv.graph_stats())
+        st["tile_classes"] = tile_summary(srv)
         srv.close()
         return el, done, st
 

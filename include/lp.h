@@ -162,7 +162,9 @@ typedef struct {
   int32_t power_iters;   /* 100                                             */
   int32_t halpern;       /* 1: Halpern anchoring; 0: (1+rho)T(z) - rho z    */
   int32_t restarts;      /* 1: restarts enabled                             */
-  int32_t use_graph;     /* 1: replay a CUDA graph of check_every iterations */
+  int32_t use_graph;     /* 1: replay a CUDA graph of check_every iterations
+                          * (grid engine); the server replays one graph per
+                          * bucket launch (lp_server_graph_stats)           */
   double step_size;      /* 0 = auto: 0.998 / ||A~||_2 by power iteration   */
   double primal_weight;  /* 0 = auto: ||c~|| / ||bhat~||                    */
   const double *x_init;  /* NULL or n doubles (current LP): warm start x    */
@@ -391,8 +393,9 @@ int lp_profile_kernels(lp_problem *lp, int32_t reps, double *out);
  * *count: doubles written.  LP_ERR_STATE without a grid-engine solve. */
 int lp_get_tile_tuning(const lp_problem *lp, double *out, int32_t cap, int32_t *count);
 
-/* Forget the autotuner's cached tile shapes (the next solve of each size
- * class measures again). */
+/* Forget the autotuners' cached tile shapes: the grid engine's (the next
+ * solve of each size class measures again) and the batched path's classes
+ * (lp_server_tile_tuning; later requests try the shapes again). */
 void lp_tile_cache_clear(void);
 
 void lp_destroy(lp_problem *lp);
@@ -486,6 +489,29 @@ int lp_batch_cancel(lp_server *srv, uint64_t ticket);
  * issuing bucket launches (order copy, events, the launch, the state
  * read-back), out[11] device nanoseconds of the completed bucket launches. */
 int lp_server_stats(const lp_server *srv, int64_t *out);
+
+/* CUDA-graph statistics of the bucket launches (2 int64): out[0] launches
+ * replayed from a graph, out[1] graphs instantiated.  With use_graph = 1 (the
+ * default) every bucket launch -- the order copy, events, k_batch and the
+ * state read-back -- replays a graph instantiated once per bucket and
+ * cluster x CTA shape, its copy sizes and the kernel's grid and slot count
+ * updated in place; use_graph = 0 issues the same work directly.  The paper
+ * has no counterpart (serving is this library's). */
+int lp_server_graph_stats(const lp_server *srv, int64_t *out);
+
+/* The batched path's tile-shape autotuner (the paper has no counterpart),
+ * one table per process and precision (lp_tile_cache_clear empties it).
+ * Requests are classed by m bucket = floor(log2 m / 2) and row-length bucket
+ * = floor(log2(nnz / m)); while a class is trying, its packed requests get
+ * the shapes 0..5 in turn -- entries per lane {8, 16, 32} x nonzeros per warp
+ * tile {512, 2048}, shape c = (entries index) * 2 + (2048 ? 1 : 0) -- and
+ * each finished one's device time per nonzero-iteration is recorded; when
+ * every shape has 2 samples the class keeps the least mean.  out: *nclasses
+ * rows of 15 doubles: m bucket, row-length bucket, chosen shape (-1: still
+ * trying), mean ns per nonzero-iteration of shapes 0..5 (-1: no sample),
+ * samples of shapes 0..5.  cap: rows out holds (LP_ERR_INVALID, with
+ * *nclasses set, if too small). */
+int lp_server_tile_tuning(const lp_server *srv, double *out, int32_t cap, int32_t *nclasses);
 
 void lp_server_destroy(lp_server *srv);
 

@@ -118,6 +118,8 @@ SIGNATURES = [
     ("lp_server_tune", C.c_int, [_P, C.c_int64, C.c_int32, C.c_double]),
     ("lp_batch_cancel", C.c_int, [_P, C.c_uint64]),
     ("lp_server_stats", C.c_int, [_P, _I64]),
+    ("lp_server_graph_stats", C.c_int, [_P, _I64]),
+    ("lp_server_tile_tuning", C.c_int, [_P, _D, C.c_int32, _I32]),
     ("lp_server_destroy", None, [_P]),
 ]
 
@@ -428,6 +430,26 @@ class Server:
                 "queued", "shape_b0", "shape_b1", "shape_b2", "shape_b3", "host_launch_ns",
                 "device_launch_ns")
         return dict(zip(keys, (int(v) for v in out)))
+
+    def graph_stats(self):
+        """lp_server_graph_stats: bucket launches replayed from a CUDA graph
+        and graphs instantiated."""
+        out = np.zeros(2, dtype=np.int64)
+        check(self.lib.lp_server_graph_stats(self.h, out.ctypes.data_as(_I64)))
+        return {"graph_launches": int(out[0]), "graphs": int(out[1])}
+
+    def tile_tuning(self):
+        """lp_server_tile_tuning: per request class, the chosen tile shape (or
+        -1), mean ns per nonzero-iteration and samples of each shape."""
+        cnt = C.c_int32()
+        cap = 256
+        out = np.zeros(15 * cap)
+        check(self.lib.lp_server_tile_tuning(self.h, out.ctypes.data_as(_D), cap,
+                                             C.byref(cnt)))
+        rows = out[: 15 * cnt.value].reshape(-1, 15)
+        return [{"m_bucket": int(r[0]), "len_bucket": int(r[1]), "chosen": int(r[2]),
+                 "mean_ns": [float(v) for v in r[3:9]], "samples": [int(v) for v in r[9:15]]}
+                for r in rows]
 
     def run_all(self, tickets, max_periods: int = 1_000_000):
         """Drive the device loop (non-worker servers) until every ticket is done."""

@@ -485,7 +485,10 @@ int lp_get_tile_tuning(const lp_problem *lp, double *out, int32_t cap, int32_t *
   API_GUARD_END
 }
 
-void lp_tile_cache_clear(void) { dev_tile_cache_clear(); }
+void lp_tile_cache_clear(void) {
+  dev_tile_cache_clear();
+  batch_tile_cache_clear();
+}
 
 void lp_destroy(lp_problem *lp) {
   if (!lp) return;

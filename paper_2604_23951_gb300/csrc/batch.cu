@@ -591,7 +591,10 @@ __global__ void __launch_bounds__(512, 1) k_batch(const SlotDesc *__restrict__ d
       cl.sync();
       if (!sh.cont) break;
     }
-    if (lead) sout[oi] = *st;
+    if (lead) {
+      st->dev_ns += (long long)(global_ns() - t0);
+      sout[oi] = *st;
+    }
     cl.sync();
   }
 }
@@ -648,6 +651,52 @@ struct Tuner {
   }
 };
 
+// Tile-shape autotuner of the batched path.  Requests are classed by
+// (m bucket = floor(log2 m / 2), row-length bucket = floor(log2(nnz / m)));
+// while a class is trying, its packed requests get the candidate shapes in
+// turn -- 8 / 16 / 32 entries per lane x 512 / 2048 nonzeros per warp tile,
+// the grid engine's candidates (rows over kCtaRow entries take a whole CTA
+// here) -- and each finished slot's device time per nonzero-iteration
+// (State::dev_ns, set-up included) is recorded for its shape; once every
+// shape has kTileSamples samples the class keeps the one with the least mean.
+constexpr int kTileCands = 6;
+constexpr int kTileSamples = 2;
+static TileShape tile_shape(int c) {
+  static const int rm[3] = {8, 16, 32};
+  TileShape t;
+  t.run_max = rm[c / 2];
+  t.tile_nnz = (c & 1) ? 2048 : 512;
+  t.segmented = false;
+  return t;
+}
+
+struct TileClass {
+  int next = 0;
+  int chosen = -1;
+  double sum[kTileCands] = {0, 0, 0, 0, 0, 0};
+  int cnt[kTileCands] = {0, 0, 0, 0, 0, 0};
+};
+
+// the classes of every server of the process, by precision and class key
+// (lp_tile_cache_clear forgets them)
+std::mutex g_batch_tile_mu;
+std::map<int, TileClass> g_batch_tile;
+
+void batch_tile_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_batch_tile_mu);
+  g_batch_tile.clear();
+}
+
+static int tile_class_key(int m, long long nnz) {
+  if (m <= 0) return 0;
+  const int mb = (int)std::floor(std::log2((double)m) / 2.0);
+  const int lb = (int)std::floor(std::log2(std::max(1.0, (double)nnz / (double)m)));
+  return mb * 64 + lb;
+}
+static int tile_table_key(int precision, int m, long long nnz) {
+  return (precision == LP_MIXED ? 1 << 20 : 0) + tile_class_key(m, nnz);
+}
+
 // first-fit allocator over [0, size) with coalescing of free ranges
 struct RangeAlloc {
   std::map<size_t, size_t> free_;  // offset -> bytes
@@ -693,6 +742,8 @@ struct Packed {
   SlotDesc rel{};  // pointers as offsets from the block start
   double bnorm = 0, cnorm = 0, off = 0;
   std::vector<int> rperm, cperm;  // device order -> request order
+  int tile = 0;             // tile shape candidate (tile_shape)
+  bool tile_trial = false;  // packed while its class was trying shapes
 };
 
 static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -700,9 +751,10 @@ static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 // xw / yw: NULL, or a warm start (x: n, y: m, unscaled, the request's own
 // order) stored with the inputs in the slot's device order
 static void pack_request(const HostLP &h, Packed &p, const double *xw = nullptr,
-                         const double *yw = nullptr) {
+                         const double *yw = nullptr, TileShape shape = TileShape{}) {
   Layout L;
-  build_layout(h, L, TileShape{});  // run_max 8, 512 nonzeros, CTA rows: no segments
+  shape.segmented = false;  // rows over kCtaRow entries take a whole CTA here
+  build_layout(h, L, shape);
   p.m = h.m;
   p.n = h.n;
   p.nnz = h.nnz();
@@ -892,6 +944,18 @@ struct Slot {
   int refinements = 0;    // re-solves before this one (original-LP check)
   long long iters_before = 0;
   double solve_s_before = 0;
+  int tile = 0;           // tile shape candidate of its layout
+  bool tile_trial = false;
+};
+
+// A bucket launch as a CUDA graph: the order copy, an event, k_batch (its
+// cluster shape fixed at instantiation), an event, the state read-back and
+// the completion event.  One per cluster x CTA shape; before each launch the
+// copies' sizes and the kernel's grid and slot count are updated in place.
+struct LaunchGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t h2d = nullptr, kern = nullptr, d2h = nullptr;
 };
 
 // one size bucket: its launch loop runs independently of the others
@@ -901,6 +965,7 @@ struct Bucket {
   bool inflight = false;
   bool tail = false;       // launch used the tail shape (not timed)
   std::vector<int> order;  // slots of the launch in flight
+  std::map<int, LaunchGraph> graphs;  // by cl * 4096 + block
 };
 
 static double now_s() {
@@ -919,6 +984,8 @@ struct lp_server {
   cudaStream_t bs[kNumBuckets] = {nullptr, nullptr, nullptr, nullptr};
   Bucket buckets[kNumBuckets];
   int device = 0, sm_count = 0;
+  long long graph_launches = 0;   // bucket launches replayed from a CUDA graph
+  long long graphs_built = 0;     // bucket graphs instantiated
   long long solo_nnz = kSoloNnz;  // requests at least this large run on the single-LP path
   int solo_max = 3;               // solo requests running at once
   double launch_ms = 2.0;         // device time budget of one bucket launch
@@ -1137,6 +1204,8 @@ void admit(lp_server *srv) {
     sl.cperm = std::move(rq.pk.cperm);
     sl.refinements = rq.refinements;
     sl.iters_before = rq.iters_before;
+    sl.tile = rq.pk.tile;
+    sl.tile_trial = rq.pk.tile_trial;
     sl.solve_s_before = rq.solve_s_before;
     CK(cudaMemcpyAsync(srv->arena + off, rq.pk.blob.data(), rq.pk.blob.size(),
                        cudaMemcpyHostToDevice, srv->s));
@@ -1153,7 +1222,46 @@ void admit(lp_server *srv) {
   }
 }
 
-void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
+// The shape a newly packed request gets (trial: its class is still trying).
+int tile_pick(lp_server *srv, int m, long long nnz, bool &trial) {
+  std::lock_guard<std::mutex> lk(g_batch_tile_mu);
+  TileClass &T = g_batch_tile[tile_table_key(srv->opts.precision, m, nnz)];
+  if (T.chosen >= 0) {
+    trial = false;
+    return T.chosen;
+  }
+  trial = true;
+  const int c = T.next;
+  T.next = (T.next + 1) % kTileCands;
+  return c;
+}
+
+// A trial slot finished: its cost (ns per nonzero-iteration) for shape c.
+void tile_record(lp_server *srv, int m, long long nnz, int c, double cost) {
+  std::lock_guard<std::mutex> lk(g_batch_tile_mu);
+  TileClass &T = g_batch_tile[tile_table_key(srv->opts.precision, m, nnz)];
+  if (T.chosen >= 0) return;
+  T.sum[c] += cost;
+  T.cnt[c] += 1;
+  for (int q = 0; q < kTileCands; ++q)
+    if (T.cnt[q] < kTileSamples) return;
+  int b = 0;
+  for (int q = 1; q < kTileCands; ++q)
+    if (T.sum[q] / T.cnt[q] < T.sum[b] / T.cnt[b]) b = q;
+  T.chosen = b;
+}
+
+// Pack a batched request under its class's tile shape.
+void pack_tuned(lp_server *srv, const HostLP &h, Packed &pk, const double *xw = nullptr,
+                const double *yw = nullptr) {
+  bool trial = false;
+  const int c = tile_pick(srv, h.m, h.nnz(), trial);
+  pack_request(h, pk, xw, yw, tile_shape(c));
+  pk.tile = c;
+  pk.tile_trial = trial;
+}
+
+BatchConst batch_const(const lp_server *srv) {
   BatchConst C;
   C.K = std::max(1, srv->opts.check_every);
   C.ruiz_iters = srv->opts.ruiz_iters;
@@ -1164,6 +1272,12 @@ void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
   C.step_size = srv->opts.step_size;
   C.primal_weight = srv->opts.primal_weight;
   C.budget_ns = (long long)(srv->launch_ms * 1e6);
+  return C;
+}
+
+// One bucket launch of k_batch on the bucket's stream (direct form).
+void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
+  const BatchConst C = batch_const(srv);
   const int max_clusters = std::max(1, srv->sm_count * 4 / sh.cl);
   const int nclusters = std::min(nord, max_clusters);
   cudaLaunchConfig_t cfg = {};
@@ -1189,11 +1303,75 @@ void launch_bucket(lp_server *srv, int b, int nord, const Shape &sh) {
   srv->launches++;
 }
 
+// The whole bucket step (order copy, events, k_batch, state read-back) as a
+// replay of the bucket's graph for this shape, instantiated on first use.
+void launch_bucket_graph(lp_server *srv, int b, int nord, const Shape &sh) {
+  Bucket &B = srv->buckets[b];
+  BatchConst C = batch_const(srv);
+  const int max_clusters = std::max(1, srv->sm_count * 4 / sh.cl);
+  const int nclusters = std::min(nord, max_clusters);
+  const SlotDesc *desc = srv->d_desc;
+  State *dstate = srv->d_state;
+  int *d_order = srv->d_order + (size_t)b * srv->max_slots;
+  const int *h_order = srv->h_order + (size_t)b * srv->max_slots;
+  State *d_sout = srv->d_sout + (size_t)b * srv->max_slots;
+  State *h_sout = srv->h_sout + (size_t)b * srv->max_slots;
+  int nord_arg = nord;
+  void *args[] = {(void *)&desc, (void *)&dstate, (void *)&d_order, (void *)&nord_arg,
+                  (void *)&d_sout, (void *)&C};
+  cudaKernelNodeParams kp = {};
+  kp.func = srv->opts.precision == LP_MIXED ? (void *)k_batch<true> : (void *)k_batch<false>;
+  kp.gridDim = dim3(nclusters * sh.cl);
+  kp.blockDim = dim3(sh.block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  const size_t ob = sizeof(int) * (size_t)nord, sb = sizeof(State) * (size_t)nord;
+  const int key = sh.cl * 4096 + sh.block;
+  auto it = B.graphs.find(key);
+  if (it == B.graphs.end()) {
+    LaunchGraph G;
+    cudaGraphNode_t e0, e1, e2;
+    CK(cudaGraphCreate(&G.g, 0));
+    CK(cudaGraphAddMemcpyNode1D(&G.h2d, G.g, nullptr, 0, d_order, h_order, ob,
+                                cudaMemcpyHostToDevice));
+    CK(cudaGraphAddEventRecordNode(&e0, G.g, &G.h2d, 1, B.ev0));
+    CK(cudaGraphAddKernelNode(&G.kern, G.g, &e0, 1, &kp));
+    cudaLaunchAttributeValue v = {};
+    v.clusterDim.x = sh.cl;
+    v.clusterDim.y = 1;
+    v.clusterDim.z = 1;
+    CK(cudaGraphKernelNodeSetAttribute(G.kern, cudaLaunchAttributeClusterDimension, &v));
+    CK(cudaGraphAddEventRecordNode(&e1, G.g, &G.kern, 1, B.ev1));
+    CK(cudaGraphAddMemcpyNode1D(&G.d2h, G.g, &e1, 1, h_sout, d_sout, sb,
+                                cudaMemcpyDeviceToHost));
+    CK(cudaGraphAddEventRecordNode(&e2, G.g, &G.d2h, 1, B.ev_done));
+    CK(cudaGraphInstantiate(&G.exec, G.g, 0));
+    it = B.graphs.emplace(key, G).first;
+    ++srv->graphs_built;
+  } else {
+    const LaunchGraph &G = it->second;
+    CK(cudaGraphExecMemcpyNodeSetParams1D(G.exec, G.h2d, d_order, h_order, ob,
+                                          cudaMemcpyHostToDevice));
+    CK(cudaGraphExecKernelNodeSetParams(G.exec, G.kern, &kp));
+    CK(cudaGraphExecMemcpyNodeSetParams1D(G.exec, G.d2h, h_sout, d_sout, sb,
+                                          cudaMemcpyDeviceToHost));
+  }
+  CK(cudaGraphLaunch(it->second.exec, srv->bs[b]));
+  srv->launches++;
+  ++srv->graph_launches;
+}
+
 // Hand a slot's result to its ticket and free its arena block.  The slot's
 // bucket has no launch in flight.  Caller holds mu.
 void retire(lp_server *srv, int q, const State *S, double tnow) {
   Slot &sl = srv->slots[q];
   const bool finished = S && S->status >= 0;
+  if (finished && sl.tile_trial && !sl.cancel) {
+    const long long it = std::max<long long>(std::max(S->iters, S->t), 1);
+    tile_record(srv, sl.m, sl.nnz, sl.tile,
+                (double)S->dev_ns / ((double)std::max<long long>(sl.nnz, 1) * (double)it));
+  }
   Done d;
   d.lp = sl.lp;
   d.x.assign(sl.n, 0.0);
@@ -1307,15 +1485,19 @@ void launch_idle(lp_server *srv) {
     if (B.tail) shp = Shape{8, 256};
     cudaStream_t st = srv->bs[b];
     const auto th0 = std::chrono::steady_clock::now();
-    CK(cudaMemcpyAsync(srv->d_order + (size_t)b * srv->max_slots, h_order, sizeof(int) * nord,
-                       cudaMemcpyHostToDevice, st));
-    CK(cudaEventRecord(B.ev0, st));
-    launch_bucket(srv, b, nord, shp);
-    CK(cudaEventRecord(B.ev1, st));
-    CK(cudaMemcpyAsync(srv->h_sout + (size_t)b * srv->max_slots,
-                       srv->d_sout + (size_t)b * srv->max_slots, sizeof(State) * nord,
-                       cudaMemcpyDeviceToHost, st));
-    CK(cudaEventRecord(B.ev_done, st));
+    if (srv->opts.use_graph) {
+      launch_bucket_graph(srv, b, nord, shp);
+    } else {
+      CK(cudaMemcpyAsync(srv->d_order + (size_t)b * srv->max_slots, h_order, sizeof(int) * nord,
+                         cudaMemcpyHostToDevice, st));
+      CK(cudaEventRecord(B.ev0, st));
+      launch_bucket(srv, b, nord, shp);
+      CK(cudaEventRecord(B.ev1, st));
+      CK(cudaMemcpyAsync(srv->h_sout + (size_t)b * srv->max_slots,
+                         srv->d_sout + (size_t)b * srv->max_slots, sizeof(State) * nord,
+                         cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(B.ev_done, st));
+    }
     srv->host_launch_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(
                                std::chrono::steady_clock::now() - th0)
                                .count();
@@ -1519,7 +1701,7 @@ int lp_batch_submit(lp_server *srv, lp_problem *lp, uint64_t *ticket) {
       rq.pk.nnz = h.nnz();
       rq.pk.bytes = rq.solo_bytes;
     } else {
-      pack_request(h, rq.pk);
+      pack_tuned(srv, h, rq.pk);
     }
     if (rq.pk.bytes > srv->arena_bytes) {
       set_last_error("request needs " + std::to_string(rq.pk.bytes) +
@@ -1601,7 +1783,7 @@ int lp_batch_poll(lp_server *srv, uint64_t ticket, lp_result *res, double *x, do
           rq.xw = std::move(dd.x);
           rq.yw = std::move(dd.y);
         } else {
-          pack_request(h, rq.pk, dd.x.data(), dd.y.data());
+          pack_tuned(srv, h, rq.pk, dd.x.data(), dd.y.data());
         }
         lk.lock();
         // a packed re-solve also carries its warm start; if that no longer
@@ -1719,6 +1901,49 @@ int lp_server_stats(const lp_server *srv, int64_t *out) {
   return LP_OK;
 }
 
+int lp_server_graph_stats(const lp_server *srv, int64_t *out) {
+  if (!srv || !out) {
+    set_last_error("NULL argument");
+    return LP_ERR_INVALID;
+  }
+  lp_server *s = const_cast<lp_server *>(srv);
+  std::lock_guard<std::mutex> lk(s->mu);
+  out[0] = s->graph_launches;
+  out[1] = s->graphs_built;
+  return LP_OK;
+}
+
+int lp_server_tile_tuning(const lp_server *srv, double *out, int32_t cap, int32_t *nclasses) {
+  if (!srv || !nclasses || cap < 0 || (cap > 0 && !out)) {
+    set_last_error("lp_server_tile_tuning: invalid argument");
+    return LP_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_batch_tile_mu);
+  const int mixed = srv->opts.precision == LP_MIXED ? 1 : 0;
+  int32_t cnt = 0;
+  for (const auto &kv : g_batch_tile) cnt += (kv.first >> 20) == mixed ? 1 : 0;
+  *nclasses = cnt;
+  if (cnt > cap) {
+    set_last_error("lp_server_tile_tuning: cap too small");
+    return LP_ERR_INVALID;
+  }
+  double *o = out;
+  for (const auto &kv : g_batch_tile) {
+    if ((kv.first >> 20) != mixed) continue;
+    const TileClass &T = kv.second;
+    const int key = kv.first & ((1 << 20) - 1);
+    o[0] = key / 64;
+    o[1] = key % 64;
+    o[2] = T.chosen;
+    for (int c = 0; c < kTileCands; ++c) {
+      o[3 + c] = T.cnt[c] > 0 ? T.sum[c] / T.cnt[c] : -1.0;
+      o[3 + kTileCands + c] = T.cnt[c];
+    }
+    o += 3 + 2 * kTileCands;
+  }
+  return LP_OK;
+}
+
 void lp_server_destroy(lp_server *srv) {
   if (!srv) return;
   {
@@ -1737,6 +1962,11 @@ void lp_server_destroy(lp_server *srv) {
       cudaStreamDestroy(srv->bs[b]);
     }
     Bucket &B = srv->buckets[b];
+    for (auto &kv : B.graphs) {
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+      if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
+    B.graphs.clear();
     if (B.ev0) cudaEventDestroy(B.ev0);
     if (B.ev1) cudaEventDestroy(B.ev1);
     if (B.ev_done) cudaEventDestroy(B.ev_done);

@@ -79,6 +79,8 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err);
 // the last solve's shapes and measurement (lp_get_tile_tuning's layout;
 // -1 if cap is too small)
 void dev_tile_cache_clear();
+// the batched path's tile-shape classes (batch.cu)
+void batch_tile_cache_clear();
 int dev_tile_tuning(const DeviceLP *d, double *out, int cap);
 
 // Per-check trace: when the environment variable LP_TRACE names a file, one

@@ -75,6 +75,7 @@ struct State {
   int polish;
   long long next_polish;
   double pq[NQ];
+  long long dev_ns;  // batched slots: device time the slot's cluster spent on it
 };
 
 // FP64 switch of the mixed mode, a guard only: the mixed SpMV (FP32 matrix

@@ -234,26 +234,80 @@ def test_batch_iterates_match_oracle_elementwise(pkg, dev):
     # budget gives every slot one block of K iterations per launch, so a
     # slot's iterations run across several launches and the autotuner's
     # cluster x CTA shapes (it tries one per launch while tuning).
+    # The same with every bucket launch replayed from a CUDA graph and issued
+    # directly: while the autotuner is still trying shapes (three launches
+    # per slot here) the shape sequence is fixed, so the two agree bit for bit.
     ms = np.exp(np.linspace(np.log(30), np.log(20000), 20)).astype(int)
     lps = [lpgen.equality_nonneg(int(m), 2 * int(m), 5100 + j, 4, 30) for j, m in enumerate(ms)]
     eta, om = 0.05, 1.3
     for iters in (50, 130):
-        srv = pkg.Server(1 << 31, dev, precision=0, max_iter=iters, eps_rel=0.0, step_size=eta,
-                         primal_weight=om)
-        srv.tune(launch_ms=0.01)
-        probs = [pkg.Problem(lp, dev) for lp in lps]
-        tickets = [srv.submit(p) for p in probs]
-        res = srv.run_all(tickets)
-        st = srv.stats()
-        # three buckets, each slot over at least ceil(iters / 64) launches
-        assert st["launches"] >= 3 * ((iters + 63) // 64)
-        for lp, t in zip(lps, tickets):
-            r, x, y = res[t]
-            ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta,
-                                    omega0=om)
-            assert r.termination == pkg.LP_ITER_LIMIT and r.iterations == iters
-            assert r.restarts == ref.restarts
-            ex = np.max(np.abs(x - ref.x)) / max(1.0, np.max(np.abs(ref.x)))
-            ey = np.max(np.abs(y - ref.y)) / max(1.0, np.max(np.abs(ref.y)))
-            assert ex <= 1e-10 and ey <= 1e-10, (lp.m, iters, ex, ey)
-        srv.close()
+        got = {}
+        for use_graph in (1, 0):
+            pkg.tile_cache_clear()  # the same tile shapes for the slots of both runs
+            srv = pkg.Server(1 << 31, dev, precision=0, max_iter=iters, eps_rel=0.0,
+                             step_size=eta, primal_weight=om, use_graph=use_graph)
+            srv.tune(launch_ms=0.01)
+            probs = [pkg.Problem(lp, dev) for lp in lps]
+            tickets = [srv.submit(p) for p in probs]
+            res = srv.run_all(tickets)
+            st = srv.stats()
+            gs = srv.graph_stats()
+            # three buckets, each slot over at least ceil(iters / 64) launches
+            assert st["launches"] >= 3 * ((iters + 63) // 64)
+            if use_graph:
+                assert gs["graph_launches"] == st["periods"] and 3 <= gs["graphs"] <= 3 * 6
+            else:
+                assert gs["graph_launches"] == 0 and gs["graphs"] == 0
+            got[use_graph] = [res[t] for t in tickets]
+            for lp, (r, x, y) in zip(lps, got[use_graph]):
+                ref = oracle.pdhg_solve(lp, oracle.Opts(max_iter=iters, eps_rel=0.0), eta=eta,
+                                        omega0=om)
+                assert r.termination == pkg.LP_ITER_LIMIT and r.iterations == iters
+                assert r.restarts == ref.restarts
+                ex = np.max(np.abs(x - ref.x)) / max(1.0, np.max(np.abs(ref.x)))
+                ey = np.max(np.abs(y - ref.y)) / max(1.0, np.max(np.abs(ref.y)))
+                assert ex <= 1e-10 and ey <= 1e-10, (lp.m, iters, ex, ey)
+            srv.close()
+        for (r1, x1, y1), (r0, x0, y0) in zip(got[1], got[0]):
+            np.testing.assert_array_equal(x1, x0)
+            np.testing.assert_array_equal(y1, y0)
+
+
+def test_batch_tile_tuner_keeps_the_fastest_shape(pkg, dev):
+    # two request classes of 20 LPs (m 300 and 3,000; 10-14 entries per row):
+    # all 40 are packed while their class is still trying, so each class's
+    # six tile shapes get three or four samples; then every class keeps the
+    # shape with the least mean device time per nonzero-iteration, which
+    # the next batch's requests get.  Every request solves to 1e-6 whatever
+    # its shape.
+    import math
+
+    pkg.tile_cache_clear()
+    lps = ([lpgen.equality_nonneg(300, 600, 7100 + j, 10, 14) for j in range(20)]
+           + [lpgen.equality_nonneg(3000, 6000, 7200 + j, 10, 14) for j in range(20)])
+    srv = pkg.Server(1 << 31, dev, precision=0)
+    probs = [pkg.Problem(lp, dev) for lp in lps]
+    tickets = [srv.submit(p) for p in probs]
+    res = srv.run_all(tickets)
+    for lp, t in zip(lps, tickets):
+        r, x, y = res[t]
+        assert r.termination == pkg.LP_OPTIMAL and r.rel_kkt <= 1e-6
+        assert oracle.rel_kkt(lp, x, y)["rel_kkt"] <= 1e-6 * (1 + 1e-6)
+    keys = {(int(math.floor(math.log2(lp.m) / 2)), int(math.floor(math.log2(lp.nnz / lp.m))))
+            for lp in lps}
+    tt = {(c["m_bucket"], c["len_bucket"]): c for c in srv.tile_tuning()}
+    assert keys <= set(tt)
+    assert len(keys) == 2
+    for k in keys:
+        c = tt[k]
+        assert min(c["samples"]) >= 2 and c["chosen"] >= 0
+        assert c["mean_ns"][c["chosen"]] == min(c["mean_ns"])
+    # the next batch packs each class under its chosen shape (no new samples)
+    before = {k: sum(tt[k]["samples"]) for k in keys}
+    res2 = srv.run_all([srv.submit(pkg.Problem(lp, dev)) for lp in lps[:4] + lps[-4:]])
+    assert all(r.termination == pkg.LP_OPTIMAL for r, _, _ in res2.values())
+    tt2 = {(c["m_bucket"], c["len_bucket"]): c for c in srv.tile_tuning()}
+    for k in keys:
+        if tt[k]["chosen"] >= 0:
+            assert sum(tt2[k]["samples"]) == before[k] and tt2[k]["chosen"] == tt[k]["chosen"]
+    srv.close()
