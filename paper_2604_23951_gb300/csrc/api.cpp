@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "host_parallel.h"
 #include "lp_internal.h"
 
 using namespace gb300lp;
@@ -64,6 +65,8 @@ struct lp_problem {
 namespace gb300lp {
 // used by the batch server (batch.cu) to read a problem's current LP
 const HostLP &problem_current(const lp_problem *lp) { return lp->cur; }
+// the LP as created: held in `orig` once presolved, else the current one
+const HostLP &original_lp(const lp_problem *lp) { return lp->presolved ? lp->orig : lp->cur; }
 // LP_INFEASIBLE / LP_UNBOUNDED when the presolve proved it, else -1
 int problem_proven_status(const lp_problem *lp) {
   if (!lp->presolved) return -1;
@@ -186,15 +189,29 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     return fail(LP_ERR_INVALID, "vector argument is NULL");
   if (row_ptr[0] != 0 || row_ptr[m] != nnz)
     return fail(LP_ERR_INVALID, "row_ptr must start at 0 and end at nnz");
-  for (int32_t i = 0; i < m; ++i) {
+  for (int32_t i = 0; i < m; ++i)
     if (row_ptr[i + 1] < row_ptr[i]) return fail(LP_ERR_INVALID, "row_ptr decreases");
-    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-      int32_t j = col_idx[k];
-      if (j < 0 || j >= n) return fail(LP_ERR_INVALID, "column index out of range");
-      if (k > row_ptr[i] && col_idx[k - 1] >= j)
-        return fail(LP_ERR_INVALID, "column indices not strictly increasing in a row");
-      if (!std::isfinite(val[k])) return fail(LP_ERR_INVALID, "non-finite matrix value");
-    }
+  {
+    // the rows' entries, checked in row chunks on host threads; the first
+    // failing row of the first failing chunk gives the message
+    std::vector<const char *> bad(16, nullptr);
+    host_parallel_chunks((size_t)m, nnz >= 1000000, [&](unsigned t, size_t i0, size_t i1) {
+      for (size_t i = i0; i < i1; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+          const int32_t j = col_idx[k];
+          const char *e = nullptr;
+          if (j < 0 || j >= n) e = "column index out of range";
+          else if (k > row_ptr[i] && col_idx[k - 1] >= j)
+            e = "column indices not strictly increasing in a row";
+          else if (!std::isfinite(val[k])) e = "non-finite matrix value";
+          if (e) {
+            bad[t] = e;
+            return;
+          }
+        }
+    });
+    for (const char *e : bad)
+      if (e) return fail(LP_ERR_INVALID, e);
   }
   for (int32_t j = 0; j < n; ++j) {
     if (!std::isfinite(c[j])) return fail(LP_ERR_INVALID, "non-finite cost");
@@ -209,7 +226,7 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
   }
   if (!std::isfinite(obj_offset)) return fail(LP_ERR_INVALID, "non-finite offset");
   lp_problem *lp = new lp_problem();
-  HostLP &h = lp->orig;
+  HostLP &h = lp->cur;  // the original LP is the current one until presolve
   h.m = m;
   h.n = n;
   h.row_ptr.assign(row_ptr, row_ptr + m + 1);
@@ -221,7 +238,6 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
   h.row_hi.assign(row_hi, row_hi + m);
   h.col_lo.assign(col_lo, col_lo + n);
   h.col_hi.assign(col_hi, col_hi + n);
-  lp->cur = h;
   if (dev) {
     lp->has_dev = true;
     lp->dev = *dev;
@@ -240,7 +256,14 @@ int lp_presolve(lp_problem *lp, const lp_presolve_opts *opts, lp_presolve_info *
   if (opts) o = *opts;
   auto t0 = std::chrono::steady_clock::now();
   HostLP red;
-  presolve_run(lp->orig, o.max_rounds, o.enable, red, lp->po);
+  lp->orig = std::move(lp->cur);
+  try {
+    presolve_run(lp->orig, o.max_rounds, o.enable, red, lp->po);
+  } catch (...) {
+    lp->cur = std::move(lp->orig);
+    lp->orig = HostLP();
+    throw;
+  }
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   lp->cur = std::move(red);
   lp->presolved = true;
@@ -387,7 +410,8 @@ int lp_postsolve_from(lp_problem *lp, const double *xr, const double *yr, const 
   API_GUARD_BEGIN
   if (!lp) return fail(LP_ERR_INVALID, "lp is NULL");
   if ((lp->cur.n && !xr) || (lp->cur.m && !yr)) return fail(LP_ERR_INVALID, "NULL input");
-  std::vector<double> X(lp->orig.n), Y(lp->orig.m), Z(lp->orig.n);
+  const HostLP &orig = original_lp(lp);
+  std::vector<double> X(orig.n), Y(orig.m), Z(orig.n);
   if (!lp->presolved) {
     std::copy(xr, xr + lp->cur.n, X.begin());
     std::copy(yr, yr + lp->cur.m, Y.begin());
@@ -430,8 +454,8 @@ int lp_get_dims(const lp_problem *lp, int32_t *m, int32_t *n, int64_t *nnz, int3
   if (m) *m = lp->cur.m;
   if (n) *n = lp->cur.n;
   if (nnz) *nnz = lp->cur.nnz();
-  if (m0) *m0 = lp->orig.m;
-  if (n0) *n0 = lp->orig.n;
+  if (m0) *m0 = original_lp(lp).m;
+  if (n0) *n0 = original_lp(lp).n;
   return LP_OK;
 }
 

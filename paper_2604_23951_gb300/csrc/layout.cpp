@@ -1,6 +1,8 @@
 // Host construction of the device layout (see layout.h).
 #include "layout.h"
 
+#include "host_parallel.h"
+
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -103,9 +105,19 @@ void build_layout(const HostLP &h, Layout &L, const TileShape &shape) {
   L.m = m;
   L.n = n;
   L.nnz = nnz;
+  // the O(nnz) passes run on host threads for large matrices; every pass
+  // gives the same result as in one thread (chunks own disjoint outputs)
+  const bool par = nnz >= 1000000;
   std::vector<int64_t> rlen(m), clen(n, 0);
   for (int i = 0; i < m; ++i) rlen[i] = h.row_ptr[i + 1] - h.row_ptr[i];
-  for (long long k = 0; k < nnz; ++k) clen[h.col_idx[k]]++;
+  // column counts: a chunk of columns counts its own entries in one scan
+  host_parallel_chunks((size_t)n, par, [&](unsigned, size_t j0, size_t j1) {
+    const int32_t lo = (int32_t)j0, hi = (int32_t)j1;
+    for (long long k = 0; k < nnz; ++k) {
+      const int32_t j = h.col_idx[k];
+      if (j >= lo && j < hi) clen[j]++;
+    }
+  });
   sort_rows(rlen, L.rperm);
   sort_rows(clen, L.cperm);
   {
@@ -118,31 +130,47 @@ void build_layout(const HostLP &h, Layout &L, const TileShape &shape) {
   std::vector<int> cinv(n);
   for (int j = 0; j < n; ++j) cinv[L.cperm[j]] = j;
   L.arp.assign(m + 1, 0);
-  L.aci.assign(nnz + kTilePad, 0);
-  L.av.assign(nnz + kTilePad, 0.0);
-  for (int i = 0; i < m; ++i) {
-    int o = L.rperm[i];
-    L.arp[i + 1] = L.arp[i] + (int)rlen[o];
-    int w = L.arp[i];
-    for (int64_t k = h.row_ptr[o]; k < h.row_ptr[o + 1]; ++k, ++w) {
-      L.aci[w] = cinv[h.col_idx[k]];
-      L.av[w] = h.val[k];
-    }
+  L.aci.resize(nnz + kTilePad);
+  L.av.resize(nnz + kTilePad);
+  for (int q = 0; q < kTilePad; ++q) {
+    L.aci[nnz + q] = 0;
+    L.av[nnz + q] = 0.0;
   }
-  // transpose of the permuted A: rows in new column order, entries by new row
+  for (int i = 0; i < m; ++i) L.arp[i + 1] = L.arp[i] + (int)rlen[L.rperm[i]];
+  host_parallel_chunks((size_t)m, par, [&](unsigned, size_t i0, size_t i1) {
+    for (size_t i = i0; i < i1; ++i) {
+      const int o = L.rperm[i];
+      int w = L.arp[i];
+      for (int64_t k = h.row_ptr[o]; k < h.row_ptr[o + 1]; ++k, ++w) {
+        L.aci[w] = cinv[h.col_idx[k]];
+        L.av[w] = h.val[k];
+      }
+    }
+  });
+  // transpose of the permuted A: rows in new column order, entries by new
+  // row; a chunk of new columns scans the rows in order and places its own
+  // entries
   L.trp.assign(n + 1, 0);
-  L.tci.assign(nnz + kTilePad, 0);
-  L.tv.assign(nnz + kTilePad, 0.0);
+  L.tci.resize(nnz + kTilePad);
+  L.tv.resize(nnz + kTilePad);
+  for (int q = 0; q < kTilePad; ++q) {
+    L.tci[nnz + q] = 0;
+    L.tv[nnz + q] = 0.0;
+  }
   for (int j = 0; j < n; ++j) L.trp[j + 1] = L.trp[j] + (int)clen[L.cperm[j]];
   {
     std::vector<int> cur(L.trp.begin(), L.trp.end() - 1);
-    for (int i = 0; i < m; ++i)
-      for (int k = L.arp[i]; k < L.arp[i + 1]; ++k) {
-        int j = L.aci[k];
-        L.tci[cur[j]] = i;
-        L.tv[cur[j]] = L.av[k];
-        ++cur[j];
-      }
+    host_parallel_chunks((size_t)n, par, [&](unsigned, size_t j0, size_t j1) {
+      const int lo = (int)j0, hi = (int)j1;
+      for (int i = 0; i < m; ++i)
+        for (int k = L.arp[i]; k < L.arp[i + 1]; ++k) {
+          const int j = L.aci[k];
+          if (j < lo || j >= hi) continue;
+          L.tci[cur[j]] = i;
+          L.tv[cur[j]] = L.av[k];
+          ++cur[j];
+        }
+    });
   }
   L.c0.resize(n);
   L.lx0.resize(n);
@@ -151,18 +179,22 @@ void build_layout(const HostLP &h, Layout &L, const TileShape &shape) {
   L.lc0.resize(m);
   L.uc0.resize(m);
   const double inv_sqrt_n = n > 0 ? 1.0 / std::sqrt((double)n) : 0.0;
-  for (int j = 0; j < n; ++j) {
-    int o = L.cperm[j];
-    L.c0[j] = h.c[o];
-    L.lx0[j] = h.col_lo[o];
-    L.ux0[j] = h.col_hi[o];
-    L.pv0[j] = power_start(o, inv_sqrt_n);
-  }
-  for (int i = 0; i < m; ++i) {
-    int o = L.rperm[i];
-    L.lc0[i] = h.row_lo[o];
-    L.uc0[i] = h.row_hi[o];
-  }
+  host_parallel_chunks((size_t)n, par, [&](unsigned, size_t j0, size_t j1) {
+    for (size_t j = j0; j < j1; ++j) {
+      const int o = L.cperm[j];
+      L.c0[j] = h.c[o];
+      L.lx0[j] = h.col_lo[o];
+      L.ux0[j] = h.col_hi[o];
+      L.pv0[j] = power_start(o, inv_sqrt_n);
+    }
+  });
+  host_parallel_chunks((size_t)m, par, [&](unsigned, size_t i0, size_t i1) {
+    for (size_t i = i0; i < i1; ++i) {
+      const int o = L.rperm[i];
+      L.lc0[i] = h.row_lo[o];
+      L.uc0[i] = h.row_hi[o];
+    }
+  });
   // norms of the unscaled data for the relative KKT error
   double bn2 = 0, cn2 = 0;
   for (int i = 0; i < m; ++i) {

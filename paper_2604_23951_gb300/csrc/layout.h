@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "lp_internal.h"
@@ -45,6 +47,29 @@ GB300LP_HD inline double power_start(int j, double inv_sqrt_n) {
 //             last warp to finish a row adds up (single-LP path); otherwise
 //             (batch path) rows up to kCtaRow get a single-row tile and longer
 //             rows are reduced by a whole CTA (nlong of them, first).
+// A vector whose new elements are left uninitialised (the large arrays of a
+// layout are written in full right after they are sized).
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U> &) {}
+  template <class U>
+  void construct(U *p) noexcept {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U *p, A &&...a) {
+    ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using UninitVec = std::vector<T, UninitAlloc<T>>;
+
 struct TileShape {
   int run_max = 8;
   int tile_nnz = 512;
@@ -65,8 +90,9 @@ struct Layout {
   int m = 0, n = 0;
   long long nnz = 0;
   std::vector<int> rperm, cperm;  // new -> old
-  std::vector<int> arp, aci, trp, tci;  // CSR of the permuted A and A^T (padded)
-  std::vector<double> av, tv;
+  std::vector<int> arp, trp;            // row offsets of the permuted A and A^T
+  UninitVec<int> aci, tci;              // their indices and values (padded past
+  UninitVec<double> av, tv;             // nnz with zeros)
   TilePlan pA, pT;  // tiles under the shape build_layout was given
   std::vector<double> c0, lx0, ux0, lc0, uc0;  // permuted problem vectors
   std::vector<double> pv0;  // power-iteration fallback start (power_start of cperm)
