@@ -45,6 +45,7 @@
 #include "device_common.cuh"
 #include "lp_internal.h"
 #include "pdhg_state.cuh"
+#include "host_parallel.h"
 #include "layout.h"
 #include "pdhg_epi.cuh"
 #include "spmv_warp.cuh"
@@ -784,15 +785,17 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
       for (int j = 0; j < n; ++j) st[j] = L.trp[j + 1] - L.trp[j];
       d->plansA.assign(cands.size(), TilePlan());
       d->plansT.assign(cands.size(), TilePlan());
-      for (size_t c = 0; c < cands.size(); ++c) {
-        if ((int)c == kDefaultShape) {
-          d->plansA[c] = std::move(L.pA);
-          d->plansT[c] = std::move(L.pT);
-        } else {
-          plan_tiles(sa, cands[c], d->plansA[c]);
-          plan_tiles(st, cands[c], d->plansT[c]);
+      d->plansA[kDefaultShape] = std::move(L.pA);
+      d->plansT[kDefaultShape] = std::move(L.pT);
+      // the other candidates' plans, independent of one another, on host threads
+      host_parallel_chunks(2 * cands.size(), nnz >= 1000000, [&](unsigned, size_t a, size_t b) {
+        for (size_t q = a; q < b; ++q) {
+          const size_t c = q / 2;
+          if ((int)c == kDefaultShape) continue;
+          if (q & 1) plan_tiles(st, cands[c], d->plansT[c]);
+          else plan_tiles(sa, cands[c], d->plansA[c]);
         }
-      }
+      });
     }
     size_t capTA = 1, capTT = 1, capSA = 1, capST = 1, capRA = 0, capRT = 0;
     int maxtiles = 0;
@@ -1547,17 +1550,22 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     sol.xi.assign(n, 0.0);
     sol.y.assign(m, 0.0);
     sol.yi.assign(m, 0.0);
-    for (int j = 0; j < n; ++j) {
-      int o2 = d->cperm[j];
-      sol.x[o2] = hx[j];
-      sol.xi[o2] = hxi[j];
-      sol.z[o2] = hz[j];
-    }
-    for (int i = 0; i < m; ++i) {
-      int o2 = d->rperm[i];
-      sol.y[o2] = hy[i];
-      sol.yi[o2] = hyi[i];
-    }
+    const bool par = d->nnz >= 1000000;
+    host_parallel_chunks((size_t)n, par, [&](unsigned, size_t j0, size_t j1) {
+      for (size_t j = j0; j < j1; ++j) {
+        const int o2 = d->cperm[j];
+        sol.x[o2] = hx[j];
+        sol.xi[o2] = hxi[j];
+        sol.z[o2] = hz[j];
+      }
+    });
+    host_parallel_chunks((size_t)m, par, [&](unsigned, size_t i0, size_t i1) {
+      for (size_t i = i0; i < i1; ++i) {
+        const int o2 = d->rperm[i];
+        sol.y[o2] = hy[i];
+        sol.yi[o2] = hyi[i];
+      }
+    });
     sol.valid = true;
     const State &S = *d->hst;
     if (res) {
