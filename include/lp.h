@@ -206,7 +206,7 @@ typedef struct {
                           * times (0: no check).  Applies to lp_solve and to
                           * served requests (lp_batch_poll).                 */
   int32_t tile_run_max;  /* grid engine tile shape: most entries one lane
-                          * owns in a row (8, 16 or 32) ...                 */
+                          * owns in a row (8, 16, 32 or 64) ...             */
   int32_t tile_nnz;      /* ... and nonzeros per warp tile (512 or 2048);
                           * either 0 (default): the autotuner's choice for
                           * each matrix (A and A^T separately), measured on

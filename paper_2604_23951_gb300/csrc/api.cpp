@@ -112,7 +112,7 @@ bool valid_solve_opts(const lp_solve_opts &o) {
          (o.precision == LP_FP64 || o.precision == LP_MIXED) && o.engine >= LP_ENGINE_AUTO &&
          o.engine <= LP_ENGINE_CLUSTER && o.refine_original >= 0 && o.refine_original <= 8 &&
          (o.tile_run_max == 0 || o.tile_run_max == 8 || o.tile_run_max == 16 ||
-          o.tile_run_max == 32) &&
+          o.tile_run_max == 32 || o.tile_run_max == 64) &&
          (o.tile_nnz == 0 || o.tile_nnz == 512 || o.tile_nnz == 2048) && o.eps_gap_rel >= 0 &&
          (o.polish == 0 || o.polish == 1) && o.polish_fraction > 0 && o.polish_fraction <= 8 &&
          !(o.polish && o.engine == LP_ENGINE_CLUSTER);

@@ -669,12 +669,13 @@ struct DeviceLP {
   }
 };
 
-// Tile shapes of the single-LP path (segmented long rows): run_max 8, 16, 32
-// entries per lane, times 512 or 2048 nonzeros per tile.
+// Tile shapes of the single-LP path (segmented long rows): run_max 8, 16, 32,
+// 64 entries per lane (segments of 32 run_max entries), times 512 or 2048
+// nonzeros per tile.
 const std::vector<TileShape> &tile_candidates() {
   static const std::vector<TileShape> c = [] {
     std::vector<TileShape> v;
-    for (int r : {8, 16, 32})
+    for (int r : {8, 16, 32, 64})
       for (int t : {512, 2048}) v.push_back(TileShape{r, t, true});
     return v;
   }();

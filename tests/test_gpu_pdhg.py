@@ -321,7 +321,8 @@ def test_original_lp_check_re_solves_an_amplified_postsolve(pkg, dev, engine):
     prob.close()
 
 
-SHAPES = [(8, 512), (8, 2048), (16, 512), (16, 2048), (32, 512), (32, 2048)]
+SHAPES = [(8, 512), (8, 2048), (16, 512), (16, 2048), (32, 512), (32, 2048), (64, 512),
+          (64, 2048)]
 
 
 @pytest.fixture(scope="module")
