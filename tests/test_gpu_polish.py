@@ -28,15 +28,17 @@ def gs(seed):
     return lpgen.general_structure(2000, 5000, seed, nnz_target=40_000, one_sided=0.2)
 
 
-def test_polished_solve_matches_the_oracle(pkg, dev):
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_polished_solve_matches_the_oracle(pkg, dev, use_graph):
     # eps 1e-8 with a gap tolerance of 1e-4: the oracle polishes at the
     # checks 384, 768, 1536 (failed) and 3072 (accepted), 3,715 iterations in
-    # all against 8,705 without polishing
+    # all against 8,705 without polishing; the phases run through the
+    # captured graph or as direct launches
     lp = gs(8)
     ref = P.pdhg_solve(lp, P.Opts(eps_rel=1e-8, eps_gap=1e-4, polish=True))
     assert ref.polish["successes"] == 1
     prob = pkg.Problem(lp, dev)
-    r = prob.solve(eps_rel=1e-8, eps_gap_rel=1e-4, polish=1, engine=1)
+    r = prob.solve(eps_rel=1e-8, eps_gap_rel=1e-4, polish=1, engine=1, use_graph=use_graph)
     assert r.termination == pkg.LP_OPTIMAL and r.polished == 1
     assert r.polish_attempts == ref.polish["attempts"]
     # the same checks decide; a phase's stop can move by one check period
@@ -73,6 +75,21 @@ def test_failed_attempts_resume_the_main_solve_exactly(pkg, dev):
     assert r1.restarts == r0.restarts
     assert r1.iterations == r0.iterations + r1.polish_iterations
     assert r1.polish_iterations > 0
+    prob.close()
+
+
+def test_polishing_in_mixed_precision_meets_the_test(pkg, dev):
+    # the phases run the mixed SpMV like the main solve; the accepted pair
+    # is checked on the original LP in FP64
+    lp = gs(8)
+    prob = pkg.Problem(lp, dev)
+    r = prob.solve(eps_rel=1e-7, eps_gap_rel=1e-4, polish=1, engine=1,
+                   precision=pkg.LP_MIXED)
+    assert r.termination == pkg.LP_OPTIMAL and r.polish_attempts >= 1
+    x, y, _ = prob.solution()
+    k = oracle.rel_kkt(lp, x, y)
+    tol = 1 + 1e-6
+    assert k["rel_p"] <= 1e-7 * tol and k["rel_d"] <= 1e-7 * tol and k["rel_gap"] <= 1e-4 * tol
     prob.close()
 
 
