@@ -266,7 +266,7 @@ def kernel_source_hash():
         src = fh.read()
     a = src.index("constexpr int kBlock")
     h.update(src[a:src.index("\n\n", a)].encode())
-    a = src.index("__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(")
+    a = src.index("__global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_primal(")
     b = src.index("__global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(")
     h.update(src[a:b].encode())
     return h.hexdigest()[:16]

@@ -60,6 +60,16 @@ constexpr int kBlock = GB300_BLOCK;
 #define GB300_MIN_BLOCKS (1024 / GB300_BLOCK)
 #endif
 constexpr int kMinBlocks = GB300_MIN_BLOCKS;
+// Resident CTAs per SM of the iteration kernels K1 / K2: the FP64 ones run
+// three (80 registers, no spills), the mixed ones kMinBlocks (64 registers);
+// a solve's grid follows its precision.
+#ifndef GB300_MIN_BLOCKS_FP64
+#define GB300_MIN_BLOCKS_FP64 3
+#endif
+template <typename T>
+struct IterBlocks {
+  static constexpr int value = sizeof(T) == 8 ? GB300_MIN_BLOCKS_FP64 : kMinBlocks;
+};
 
 // deterministic block reduction of NQL accumulators into partials[q * GP + block]
 // (GP: the stride of a quantity, the grid's G slots followed by one slot per
@@ -306,7 +316,7 @@ __global__ void k_reciprocal(int n, const double *__restrict__ d, double *__rest
 // T = float: the mixed-precision kernel; it runs the FP32 SpMV while
 // st->mixed_active is set and the FP64 one (va64, y) after the switch
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
+__global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_primal(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
     const double *__restrict__ y, const float2 *__restrict__ yf, const double *__restrict__ c,
     const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_primal(
 }
 
 template <typename T, bool CHECK>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) k_dual(
+__global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_dual(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
     const double *__restrict__ xbar, const float2 *__restrict__ xbar_f,
     const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
@@ -574,7 +584,8 @@ struct DeviceLP {
   // every candidate shape's tile table (host), and which one is on the device
   std::vector<TilePlan> plansA, plansT;
   int planA = -1, planT = -1;
-  int G = 1;   // CTAs of the grid-wide kernels
+  int G = 1;   // CTAs of the grid-wide kernels of the current solve
+  int G64 = 1, G32 = 1;  // ... of an FP64 / a mixed solve
   int GP = 1;  // stride of a quantity in `partials`: G + the most segmented rows
   int *A_rp = nullptr, *A_ci = nullptr, *T_rp = nullptr, *T_ci = nullptr;
   double *A_v0 = nullptr, *T_v0 = nullptr, *A_v = nullptr, *T_v = nullptr;
@@ -845,12 +856,17 @@ int dev_upload(DeviceLP *d, const HostLP &h, std::string &err) {
     d->dc_main = d->dc;
     d->xbar_f = d->dalloc_n<float2>(n);
     d->yf = d->dalloc_n<float2>(m);
-    int occ = 1;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_primal<double, true>, kBlock, kSmem64));
-    occ = std::max(occ, 1);
+    // the grid of each precision's solve: its iteration kernels' residency
+    int occ64 = 1, occ32 = 1;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_primal<double, true>, kBlock,
+                                                     kSmem64));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_primal<float, true>, kBlock,
+                                                     kSmem32));
     const int wpb = kBlock / 32;
     int need = (maxtiles + wpb - 1) / wpb;
-    d->G = std::max(1, std::min(need, d->sm_count * occ));
+    d->G64 = std::max(1, std::min(need, d->sm_count * std::max(occ64, 1)));
+    d->G32 = std::max(1, std::min(need, d->sm_count * std::max(occ32, 1)));
+    d->G = std::max(d->G64, d->G32);  // partials are sized for the larger
     // a quantity's partials: one per CTA, then one per segmented row (those
     // of the other matrix stay zero)
     d->GP = d->G + (int)std::max(capRA, capRT);
@@ -1190,6 +1206,10 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     const int K = std::max(1, o.check_every);
     d->launches = 0;
     d->last_precision = o.precision;
+    // this solve's grid (its precision's iteration-kernel residency); every
+    // per-CTA and per-row partial slot starts clean
+    d->G = mixed ? d->G32 : d->G64;
+    CK(cudaMemsetAsync(d->partials, 0, sizeof(double) * NQ * (size_t)d->GP, d->s));
     // state constants
     State init{};
     init.rho = o.rho;
