@@ -73,8 +73,9 @@ extern "C" {
 
 /* ---- precision (lp_solve_opts.precision) ------------------------------- */
 #define LP_FP64 0  /* FP64 matrix, FP64 SpMV, FP64 everything               */
-#define LP_MIXED 1 /* FP32 matrix values and SpMV with FP32 accumulation;    */
-                   /* iterates, anchor, reductions, restarts stay FP64       */
+#define LP_MIXED 1 /* FP32 matrix values times vectors gathered as float    */
+                   /* pairs, compensated FP32 sums; iterates, anchor,        */
+                   /* reductions, restarts stay FP64 (see lp_solve)          */
 
 typedef struct lp_problem lp_problem; /* opaque: host copy + device buffers */
 typedef struct lp_server lp_server;   /* opaque: continuous-batching server  */

@@ -109,7 +109,6 @@ __device__ double sn_sum(const double *partials, int nparts) {
   return total;
 }
 
-// v = w / ||w|| (0 if w = 0)
 // v = w / ||w||; a zero w continues from the fallback start vector
 __global__ void k_sn_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
                                const double *partials, int nparts) {
