@@ -16,10 +16,11 @@
 // requests that arrive while others run are admitted as memory frees up and
 // their iterations overlap on the device.
 //
-// Precision: LP_MIXED runs the set-up arithmetic and the SpMV in FP32
-// (FP32 values, FP32 accumulation) and keeps the iterates, anchor,
-// epilogues, reductions and decisions in FP64; LP_FP64 runs everything in
-// FP64.  KKT checks always use the FP64 scaled matrix.
+// Precision: LP_MIXED runs the iteration SpMV on FP32 values times the
+// float pairs of the gathered vector with compensated FP32 sums, and keeps
+// the set-up, iterates, anchor, epilogues, reductions and decisions in FP64;
+// LP_FP64 runs everything in FP64.  KKT checks always use the FP64 scaled
+// matrix.
 //
 // Autotuner: for each size bucket (by nonzeros) the server times the
 // candidate (cluster size, CTA size) shapes on its first launches and keeps

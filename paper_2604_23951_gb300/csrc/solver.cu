@@ -245,9 +245,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, 
   store_partials<1>(acc, qi, partials, GP);
 }
 
-// v = w / ||w|| (every CTA reduces the partials in the same fixed order)
-// v = w / ||w||; a zero w (the start was orthogonal to A's row space)
-// continues from the fallback start vector
+// v = w / ||w|| (every CTA reduces the partials in the same fixed order); a
+// zero w (the start was orthogonal to A's row space) continues from the
+// fallback start vector
 __global__ void k_normalize(int n, const double *__restrict__ w, double *__restrict__ v,
                             const double *__restrict__ fallback, const double *partials, int GP) {
   double nw = sqrt(reduce_partials(partials, Q_PW, GP));
@@ -313,8 +313,9 @@ __global__ void k_reciprocal(int n, const double *__restrict__ d, double *__rest
 // ---------------------------------------------------------------------------
 // the iteration kernels
 
-// T = float: the mixed-precision kernel; it runs the FP32 SpMV while
-// st->mixed_active is set and the FP64 one (va64, y) after the switch
+// T = float: the mixed-precision kernel; while st->mixed_active is set it
+// multiplies the FP32 values by the float pairs of the gathered vector with
+// compensated sums, after the switch it runs the FP64 SpMV (va64, y)
 template <typename T, bool CHECK>
 __global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_primal(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
