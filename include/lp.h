@@ -46,7 +46,7 @@ extern "C" {
 #define LP_ERR_CUDA (-3)    /* a CUDA runtime call failed                    */
 #define LP_ERR_STATE (-4)   /* call not valid in the object's current state  */
 #define LP_ERR_BUDGET (-5)  /* request larger than the server's HBM budget   */
-#define LP_ERR_TIMEOUT (-6) /* a bounded wait ran out                        */
+#define LP_ERR_TIMEOUT (-6) /* reserved: no call returns it (no device wait) */
 
 /* ---- termination codes (lp_result.termination) ------------------------ */
 #define LP_OPTIMAL 0    /* the stopping test holds: rel_p, rel_d <= eps_rel and

@@ -54,7 +54,6 @@ struct State {
   int status;
   int restart_flag;
   int halpern, restarts_on;
-  int err;  // set by a kernel whose bounded wait expired
   // mixed precision: 1 while the SpMV runs on FP32 matrix values; the check
   // switches the LP to the FP64 SpMV for good once the best rel-KKT so far
   // has not halved for kMixedStall checks

@@ -220,8 +220,7 @@ __device__ __forceinline__ Acc *red_smem() {
 }
 
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, const double *__restrict__ va,
-                                                       const double *__restrict__ vec, double *out,
-                                                       int *err) {
+                                                       const double *__restrict__ vec, double *out) {
   StoreSqEpi<double> e{out, 0.0};
   SegCtx sc = M.seg;
   sc.sink = AccSink{nullptr, 0, 0};
@@ -234,8 +233,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store(MatDev M, con
 template <int QI>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_spmv_store_sq(MatDev M, const double *__restrict__ va,
                                                           const double *__restrict__ vec,
-                                                          double *out, double *partials, int GP,
-                                                          int *err) {
+                                                          double *out, double *partials, int GP) {
   StoreSqEpi<double, QI> e{out, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, vec, e,
                                     red_smem<double, double, double>(), blockIdx.x, gridDim.x,
@@ -278,7 +276,6 @@ __global__ void k_setup_final(State *st, const double *partials, int GP, double 
     st->restarts = 0;
     st->status = ST_RUNNING;
     st->restart_flag = 0;
-    st->err = 0;
     st->r0 = st->r_prev = st->last_r = 0.0;
     st->rel_kkt = INFINITY;
   }
@@ -322,7 +319,7 @@ __global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_primal(
     const double *__restrict__ y, const float2 *__restrict__ yf, const double *__restrict__ c,
     const double *__restrict__ lx, const double *__restrict__ ux, double *x, double *x0,
     double *xbar, float2 *xbar_f, double *xhat, const State *__restrict__ st, int j,
-    double *partials, int GP, int *err) {
+    double *partials, int GP) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
   double acc[2];
@@ -354,8 +351,7 @@ __global__ void __launch_bounds__(kBlock, IterBlocks<T>::value) k_dual(
     MatDev M, const T *__restrict__ va, const double *__restrict__ va64,
     const double *__restrict__ xbar, const float2 *__restrict__ xbar_f,
     const double *__restrict__ lc, const double *__restrict__ uc, double *y, double *y0,
-    float2 *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int GP,
-    int *err) {
+    float2 *yf, double *yhat, const State *__restrict__ st, int j, double *partials, int GP) {
   if (st->status != ST_RUNNING) return;
   constexpr bool MIXED = sizeof(T) == 4;
   double acc[2];
@@ -387,7 +383,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_rows(
     const double *__restrict__ dr, const double *__restrict__ idr,
     const double *__restrict__ lc0, const double *__restrict__ uc0,
     const double *__restrict__ yhat, const State *__restrict__ st, int force, double *partials,
-    int GP, int *err) {
+    int GP) {
   if (!force && st->status != ST_RUNNING) return;
   KktRowEpi e{dr, idr, lc0, uc0, yhat, 0.0, 0.0, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, xhat, e,
@@ -403,7 +399,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_kkt_cols(
     const double *__restrict__ c, const double *__restrict__ dc, const double *__restrict__ idc,
     const double *__restrict__ c0, const double *__restrict__ lx0, const double *__restrict__ ux0,
     const double *__restrict__ xhat, double *zbuf, const State *__restrict__ st, int force,
-    double *partials, int GP, int *err) {
+    double *partials, int GP) {
   if (!force && st->status != ST_RUNNING) return;
   KktColEpi e{c, dc, idc, c0, lx0, ux0, xhat, zbuf, 0.0, 0.0, 0.0};
   warp_spmv<double, double, double>(M.nlong, M.tiles, M.ntiles, M.rp, M.ci, va, yhat, e,
@@ -631,7 +627,6 @@ struct DeviceLP {
     return MatDev{tilesT, ntilesT, nlongT, T_rp, T_ci,
                   SegCtx{segbaseT, segpartT, segcntT, seglenT, AccSink{nullptr, 0, 0}}};
   }
-  int *errp() const { return &st->err; }
 
   void *dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -923,13 +918,11 @@ void launch_primal(DeviceLP *d, bool wr, int grid, int j) {
   if (wr)
     k_primal<T, true><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                     d->ux, d->x, d->x0, d->xbar, d->xbar_f,
-                                                    d->xhat, d->st, j, d->partials, d->GP,
-                                                    d->errp());
+                                                    d->xhat, d->st, j, d->partials, d->GP);
   else
     k_primal<T, false><<<grid, kBlock, smem, d->s>>>(d->matT(), va, d->T_v, d->y, d->yf, d->c, d->lx,
                                                      d->ux, d->x, d->x0, d->xbar, d->xbar_f,
-                                                     d->xhat, d->st, j, d->partials, d->GP,
-                                                     d->errp());
+                                                     d->xhat, d->st, j, d->partials, d->GP);
 }
 
 template <typename T>
@@ -949,20 +942,19 @@ void launch_dual(DeviceLP *d, bool wr, int grid, int j) {
   if (wr)
     k_dual<T, true><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                   d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
-                                                  d->partials, d->GP, d->errp());
+                                                  d->partials, d->GP);
   else
     k_dual<T, false><<<grid, kBlock, smem, d->s>>>(d->matA(), va, d->A_v, d->xbar, d->xbar_f, d->lc,
                                                    d->uc, d->y, d->y0, yf, d->yhat, d->st, j,
-                                                   d->partials, d->GP, d->errp());
+                                                   d->partials, d->GP);
 }
 
 void launch_kkt(DeviceLP *d, int force) {
   k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr, d->lc0,
-                                              d->uc0, d->yhat, d->st, force, d->partials, d->GP,
-                                              d->errp());
+                                              d->uc0, d->yhat, d->st, force, d->partials, d->GP);
   k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc, d->idc,
                                               d->c0, d->lx0, d->ux0, d->xhat, d->zbuf, d->st,
-                                              force, d->partials, d->GP, d->errp());
+                                              force, d->partials, d->GP);
 }
 
 // one PDHG iteration (position j in its chunk); check adds K3, K4, K5
@@ -1156,14 +1148,14 @@ void setup_device(DeviceLP *d, const lp_solve_opts &o, bool mixed, const double 
     d->launches += 1;
     const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     for (int it = 0; it < o.power_iters; ++it) {
-      k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu, d->errp());
+      k_spmv_store<<<gA, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu);
       k_spmv_store_sq<Q_PW><<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->pu, d->pw,
-                                                       d->partials, d->GP, d->errp());
+                                                       d->partials, d->GP);
       k_normalize<<<gn, kBlock, 0, d->s>>>(n, d->pw, d->pv, d->pv0, d->partials, d->GP);
       d->launches += 3;
     }
     k_spmv_store_sq<Q_PWA><<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->pv, d->pu,
-                                                     d->partials, d->GP, d->errp());
+                                                     d->partials, d->GP);
     d->launches += 1;
   }
   k_init_x<<<gn, kBlock, 0, d->s>>>(n, d->lx, d->ux, d->dc, xinit_perm, d->x, d->x0);
@@ -1347,7 +1339,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
         pool.push_back(evs[head]);
         ++head;
         volatile int status = d->hst->status;
-        volatile int kerr = d->hst->err;
         {
           const State &V = *d->hst;
           trace_state("grid", V.t, V.rel_kkt, V.rel_p, V.rel_d, V.rel_gap, V.omega, V.restarts,
@@ -1359,7 +1350,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
                        "omega=%.3e restarts=%d fp32=%d stop_on=%d\n", V.t, V.rel_kkt, V.rel_p,
                        V.rel_d, V.rel_gap, V.omega, V.restarts, V.mixed_active, V.stop_on);
         }
-        if (status != ST_RUNNING || kerr) break;
+        if (status != ST_RUNNING) break;
         double el =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (el > tl) {
@@ -1377,7 +1368,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     bool polished = false;
     for (;;) {
       drive(max_iter, launched);
-      if (d->hst->status != ST_POLISH || d->hst->err || timed_out) break;
+      if (d->hst->status != ST_POLISH || timed_out) break;
       // ---- feasibility polishing at the check t = S.t ----------------------
       const State S = *d->hst;
       const long long tc = S.t;
@@ -1420,7 +1411,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
         P.k_off = 0;
         P.restarts = 0;
         P.restart_flag = 0;
-        P.err = 0;
         P.stall = 0;
         P.best_rel = INFINITY;
         P.t_switch = -1;
@@ -1445,7 +1435,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       d->launches += 1;
       long long lp_ = 0;
       drive(budget, lp_);
-      const bool ok_p = d->hst->status == LP_OPTIMAL && !d->hst->err;
+      const bool ok_p = d->hst->status == LP_OPTIMAL;
       polish_iters += phase_iters(budget);
       if (ok_p) copy(d->bxp, d->xhat, n);
       restore_data();
@@ -1462,7 +1452,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
         phase_state(2);
         long long ld = 0;
         drive(budget, ld);
-        ok_d = d->hst->status == LP_OPTIMAL && !d->hst->err;
+        ok_d = d->hst->status == LP_OPTIMAL;
         polish_iters += phase_iters(budget);
         restore_data();
       }
@@ -1517,13 +1507,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     }
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
-    if (d->hst->err) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      cudaEventDestroy(e2);
-      err = "a bounded device wait expired (tile copy did not complete)";
-      return LP_ERR_TIMEOUT;
-    }
     int status = d->hst->status;
     long long iters = d->hst->iters;
     if (status == ST_RUNNING || status == ST_POLISH) {
@@ -1672,12 +1655,11 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
         } else if (which == 2) {
           k_kkt_rows<<<d->G, kBlock, kSmem64, d->s>>>(d->matA(), d->A_v, d->xhat, d->dr, d->idr,
                                                       d->lc0, d->uc0, d->yhat, d->st, 1,
-                                                      d->partials, d->GP, d->errp());
+                                                      d->partials, d->GP);
         } else {
           k_kkt_cols<<<d->G, kBlock, kSmem64, d->s>>>(d->matT(), d->T_v, d->yhat, d->c, d->dc,
                                                       d->idc, d->c0, d->lx0, d->ux0, d->xhat,
-                                                      d->zbuf, d->st, 1, d->partials, d->GP,
-                                                      d->errp());
+                                                      d->zbuf, d->st, 1, d->partials, d->GP);
         }
         CK(cudaEventRecord(b, d->s));
         CK(cudaEventSynchronize(b));
