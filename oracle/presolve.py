@@ -3,6 +3,16 @@
 TEST INFRASTRUCTURE ONLY (see the package header).  Plain Python loops over
 dict-of-dicts row and column storage; slow, meant for small and medium LPs.
 
+Pins (tests/test_oracle_presolve.py): the worked examples of Sec. 2 (fixing
+a variable and its reduced cost, the redundant row x1 + 2 x2 >= 5 under
+x1 >= 1, x2 >= 2, the doubleton x1 + x2 = 1 with x >= 0, a variable lock of
+Sec. 2.3), each rule's postsolve on both signs or branches of its dual,
+hand-made cases for parallel rows and columns and for propagation, and the
+invariant that postsolve of an exact solution of the reduced LP (scipy's
+HiGHS, independent of the oracle's PDHG) is a KKT point of the original LP
+with the planted optimal objective; infeasible and unbounded LPs are
+detected as such.
+
 A reduction is a presolve transformation plus a postsolve transformation
 (Sec. 2.1).  The explorers used here are the fast ones of Table 1 (empty rows
 and columns, fixed columns, singleton rows, redundant rows / dominated row
