@@ -12,6 +12,13 @@ from .capi import (  # noqa: F401
     LP_ENGINE_GRID,
     LP_ENGINE_CLUSTER,
     LP_RULE_ALL,
+    LP_RULE_EMPTY_ROW,
+    LP_RULE_EMPTY_COL,
+    LP_RULE_FIXED_COL,
+    LP_RULE_SINGLETON_ROW,
+    LP_RULE_REDUNDANT_ROW,
+    LP_RULE_DOUBLETON,
+    LP_RULE_FREE_COL_SINGLETON,
     LP_RULE_COL_SINGLETON_INEQ,
     LP_RULE_PARALLEL_ROWS,
     LP_RULE_DUAL_PROPAGATION,

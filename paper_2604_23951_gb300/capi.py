@@ -22,6 +22,8 @@ LP_OPTIMAL, LP_ITER_LIMIT, LP_TIME_LIMIT, LP_NUMERICAL, LP_INFEASIBLE, LP_UNBOUN
     LP_CANCELLED = range(7)
 LP_FP64, LP_MIXED = 0, 1
 LP_ENGINE_AUTO, LP_ENGINE_GRID, LP_ENGINE_CLUSTER = 0, 1, 2
+LP_RULE_EMPTY_ROW, LP_RULE_EMPTY_COL, LP_RULE_FIXED_COL, LP_RULE_SINGLETON_ROW = 1, 2, 4, 8
+LP_RULE_REDUNDANT_ROW, LP_RULE_DOUBLETON, LP_RULE_FREE_COL_SINGLETON = 16, 32, 64
 LP_RULE_VARIABLE_LOCKS, LP_RULE_COL_SINGLETON_INEQ, LP_RULE_PARALLEL_ROWS = 128, 256, 512
 LP_RULE_ALL = 1023
 LP_RULE_PRIMAL_PROPAGATION = 1024  # opt-in, not in LP_RULE_ALL
