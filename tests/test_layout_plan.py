@@ -13,7 +13,8 @@ import pytest
 
 KWARP_ITEMS = 8
 KCTA = 512
-SHAPES = [(8, 512), (8, 2048), (16, 512), (16, 2048), (32, 512), (32, 2048)]
+SHAPES = [(8, 512), (8, 2048), (16, 512), (16, 2048), (32, 512), (32, 2048), (64, 512),
+          (64, 2048)]
 
 
 @pytest.fixture(scope="module")
@@ -116,7 +117,7 @@ def check_plan(lengths, perm, tiles, nlong, run_max=8, tile_nnz=512, seg_base=No
 def lengths_mix(rng, rows):
     parts = [rng.integers(0, 9, rows // 2), rng.integers(9, 300, rows // 3),
              rng.lognormal(2.0, 1.2, rows // 6).astype(np.int64)]
-    L = np.concatenate(parts + [np.array([0, 1, 256, 257, 512, 513, 1024, 1025, 4097, 9000])])
+    L = np.concatenate(parts + [np.array([0, 1, 256, 257, 512, 513, 1024, 1025, 2048, 2049, 4097, 9000])])
     rng.shuffle(L)
     return L
 
