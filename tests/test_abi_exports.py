@@ -50,3 +50,16 @@ def test_binding_marshals_exactly_the_declared_functions():
     capi, _ = library()
     bound = {name for name, _, _ in capi.SIGNATURES}
     assert bound == declared(), (sorted(declared() - bound), sorted(bound - declared()))
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no fallback: without the built library the package refuses to run
+    from paper_2604_23951_gb300 import capi
+
+    saved = capi._lib
+    capi._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            capi.load(str(tmp_path / "absent.so"))
+    finally:
+        capi._lib = saved
