@@ -559,6 +559,24 @@ __global__ void k_unscale(int n, int m, const double *__restrict__ dc, const dou
 // host side
 
 constexpr size_t kSmem64 = 0;  // the warp engine needs no dynamic shared memory
+
+// CUDA events owned by a scope: destroyed when it ends, also when a CUDA
+// error (an exception from CK) or an early return leaves it
+struct ScopedEvents {
+  std::vector<cudaEvent_t> ev;
+  ScopedEvents() = default;
+  ScopedEvents(const ScopedEvents &) = delete;
+  ScopedEvents &operator=(const ScopedEvents &) = delete;
+  ~ScopedEvents() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  cudaEvent_t make(unsigned flags = cudaEventDefault) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, flags));
+    ev.push_back(e);
+    return e;
+  }
+};
 constexpr size_t kSmem32 = 0;
 constexpr int kDefaultShape = 3;  // tile_candidates()[3]: run_max 16, 2048 nonzeros
 
@@ -1040,8 +1058,9 @@ void tune_tiles(DeviceLP *d, bool mixed, bool measure) {
     install_plan(d, kDefaultShape, kDefaultShape);
     return;
   }
+  ScopedEvents owned;
   cudaEvent_t ev[3];
-  for (cudaEvent_t &e : ev) CK(cudaEventCreate(&e));
+  for (cudaEvent_t &e : ev) e = owned.make();
   constexpr int kWarm = 2, kTimed = 4;
   d->tune_msA.assign(nc, 0.0);
   d->tune_msT.assign(nc, 0.0);
@@ -1067,7 +1086,6 @@ void tune_tiles(DeviceLP *d, bool mixed, bool measure) {
       }
     }
   }
-  for (cudaEvent_t e : ev) cudaEventDestroy(e);
   const int bA = (int)(std::min_element(d->tune_msA.begin(), d->tune_msA.end()) -
                        d->tune_msA.begin());
   const int bT = (int)(std::min_element(d->tune_msT.begin(), d->tune_msT.end()) -
@@ -1248,10 +1266,8 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
         CK(cudaMemcpyAsync(yin, d->hbuf + n, sizeof(double) * m, cudaMemcpyHostToDevice, d->s));
       }
     }
-    cudaEvent_t e0, e1, e2;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventCreate(&e2));
+    ScopedEvents owned;
+    const cudaEvent_t e0 = owned.make(), e1 = owned.make(), e2 = owned.make();
     CK(cudaEventRecord(e0, d->s));
     // tile shapes: given, or the autotuner's (measured after the set-up)
     const bool fixed_shape = o.tile_run_max > 0 && o.tile_nnz > 0;
@@ -1300,7 +1316,7 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
         e = pool.back();
         pool.pop_back();
       } else {
-        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        e = owned.make(cudaEventDisableTiming);
       }
       return e;
     };
@@ -1505,7 +1521,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
       CK(cudaStreamSynchronize(d->s));
       if (d->hst->status != ST_RUNNING) break;
     }
-    for (cudaEvent_t e : pool) cudaEventDestroy(e);
     CK(cudaMemcpy(d->hst, d->st, sizeof(State), cudaMemcpyDeviceToHost));
     int status = d->hst->status;
     long long iters = d->hst->iters;
@@ -1547,9 +1562,6 @@ int dev_solve(DeviceLP *d, const HostLP &h, const lp_solve_opts &o, lp_result *r
     float ms_setup = 0, ms_solve = 0;
     CK(cudaEventElapsedTime(&ms_setup, e0, e1));
     CK(cudaEventElapsedTime(&ms_solve, e1, e2));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
     sol.x.assign(n, 0.0);
     sol.z.assign(n, 0.0);
     sol.xi.assign(n, 0.0);
@@ -1636,9 +1648,8 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     run.mixed_active = mixed ? 1 : 0;  // time the FP32 SpMV of a mixed solve
     CK(cudaMemcpyAsync(d->st, &run, sizeof(State), cudaMemcpyHostToDevice, d->s));
     CK(cudaStreamSynchronize(d->s));
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
+    ScopedEvents owned;
+    const cudaEvent_t a = owned.make(), b = owned.make();
     double tot[4] = {0, 0, 0, 0};
     const int gA = d->grid_tiles(d->ntilesA, d->nlongA);
     const int gT = d->grid_tiles(d->ntilesT, d->nlongT);
@@ -1671,8 +1682,6 @@ int dev_profile(DeviceLP *d, int reps, double *out, std::string &err) {
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(d->st, &saved, sizeof(State), cudaMemcpyHostToDevice, d->s));
     CK(cudaStreamSynchronize(d->s));
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     // algorithmic bytes: matrix values + column indices + row offsets, each
     // gathered vector counted once, every epilogue vector read / written once
     const double sv = mixed ? 4.0 : 8.0;
