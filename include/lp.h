@@ -447,7 +447,11 @@ int lp_power_norm_static(int32_t m, int32_t n, const int32_t *a_row_ptr,
  * on their own stream, with device memory from the same budget, at most
  * solo_max (default 3) at once.  `opts` applies to every request
  * (precision, eps_rel, ...).  worker: 1 = a background host thread drives
- * the device loop; 0 = the caller drives it through lp_server_pump. */
+ * the device loop; 0 = the caller drives it through lp_server_pump.
+ * Errors: LP_ERR_BUDGET when the budget is below 1 MiB or cannot hold the
+ * slot tables for 4,096 slots, before any device work; LP_ERR_OOM when the
+ * budget cannot be allocated; LP_ERR_CUDA when a CUDA call fails.  On any
+ * error *out is NULL and whatever was created is released. */
 int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev,
                      const lp_solve_opts *opts, int32_t worker, lp_server **out);
 

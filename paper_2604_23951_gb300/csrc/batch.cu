@@ -1594,6 +1594,16 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
       set_last_error("invalid solve options");
       return LP_ERR_INVALID;
     }
+    // the budget covers the slot arena and the slot tables
+    srv->max_slots = 4096;
+    const size_t tables =
+        srv->max_slots * (sizeof(SlotDesc) + sizeof(State) +
+                          kNumBuckets * (sizeof(int) + sizeof(State))) + 4096;
+    if (hbm_budget_bytes <= tables + (1u << 16)) {
+      delete srv;
+      set_last_error("budget too small for the slot tables");
+      return LP_ERR_BUDGET;
+    }
     CK(cudaSetDevice(srv->device));
     CK(cudaDeviceGetAttribute(&srv->sm_count, cudaDevAttrMultiProcessorCount, srv->device));
     if (srv->ctx.stream) {
@@ -1617,20 +1627,12 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
       B.tuner.cand = candidates(b);
       B.tuner.best_ns.assign(B.tuner.cand.size(), 1e300);
     }
-    // the budget covers the slot arena and the slot tables
-    srv->max_slots = 4096;
-    const size_t tables =
-        srv->max_slots * (sizeof(SlotDesc) + sizeof(State) +
-                          kNumBuckets * (sizeof(int) + sizeof(State))) + 4096;
-    if (hbm_budget_bytes <= tables + (1u << 16)) {
-      throw std::runtime_error("budget too small for the slot tables");
-    }
     srv->arena_bytes = (hbm_budget_bytes - tables) & ~size_t(255);
     void *mem = nullptr;
     if (srv->ctx.alloc) {
       mem = srv->ctx.alloc(hbm_budget_bytes, srv->ctx.user);
       if (!mem) {
-        delete srv;
+        lp_server_destroy(srv);  // the streams and events made so far
         set_last_error("device allocation of the budget failed");
         return LP_ERR_OOM;
       }
@@ -1638,7 +1640,7 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
       cudaError_t e = cudaMalloc(&mem, hbm_budget_bytes);
       if (e != cudaSuccess) {
         cudaGetLastError();
-        delete srv;
+        lp_server_destroy(srv);
         set_last_error(std::string("device allocation of the budget failed: ") +
                        cudaGetErrorString(e));
         return LP_ERR_OOM;
@@ -1665,8 +1667,11 @@ int lp_server_create(size_t hbm_budget_bytes, const lp_device_ctx *dev, const lp
     srv->use_worker = worker != 0;
     if (srv->use_worker) srv->worker = std::thread(worker_main, srv);
   } catch (const std::exception &e) {
-    set_last_error(e.what());
-    delete srv;
+    // whatever was made before the failure (streams, events, the arena,
+    // pinned buffers) is released with the server
+    const std::string msg = e.what();
+    lp_server_destroy(srv);
+    set_last_error(msg);
     return LP_ERR_CUDA;
   }
   *out = srv;

@@ -63,3 +63,26 @@ def test_missing_library_fails_loudly(tmp_path):
             capi.load(str(tmp_path / "absent.so"))
     finally:
         capi._lib = saved
+
+
+class _NoDevice:
+    """A device context with no allocator and no stream: enough for the
+    checks lp_server_create makes before any device work."""
+
+    def __init__(self, capi):
+        self.ctx = capi.lp_device_ctx(capi.ALLOC_FN(), capi.FREE_FN(), None, None, 0)
+
+
+@pytest.mark.parametrize("budget,opts,code", [
+    (1 << 19, {}, -5),            # below 1 MiB: LP_ERR_BUDGET
+    (2 << 20, {}, -5),            # cannot hold the slot tables: LP_ERR_BUDGET
+    (1 << 30, {"polish": 1}, -1),  # the server keeps the default stopping test
+    (1 << 30, {"eps_gap_rel": 1e-4}, -1),
+])
+def test_server_checks_come_before_device_work(budget, opts, code):
+    capi, _ = library()
+    import paper_2604_23951_gb300 as pkg
+
+    with pytest.raises(pkg.LPError) as ei:
+        pkg.Server(budget, _NoDevice(capi), **opts)
+    assert ei.value.code == code
