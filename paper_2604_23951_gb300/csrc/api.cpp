@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <exception>
 #include <limits>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -225,7 +226,8 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
       return fail(LP_ERR_INVALID, "invalid row bounds");
   }
   if (!std::isfinite(obj_offset)) return fail(LP_ERR_INVALID, "non-finite offset");
-  lp_problem *lp = new lp_problem();
+  // owned here until handed out: a failed copy (bad_alloc) releases it
+  std::unique_ptr<lp_problem> lp(new lp_problem());
   HostLP &h = lp->cur;  // the original LP is the current one until presolve
   h.m = m;
   h.n = n;
@@ -242,7 +244,7 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
     lp->has_dev = true;
     lp->dev = *dev;
   }
-  *out = lp;
+  *out = lp.release();
   return LP_OK;
   API_GUARD_END
 }
