@@ -766,7 +766,7 @@ DeviceLP *dev_create(const lp_device_ctx *ctx, std::string &err) {
     CK(cudaHostAlloc(reinterpret_cast<void **>(&d->hst), sizeof(State), cudaHostAllocDefault));
   } catch (const std::exception &e) {
     err = e.what();
-    delete d;
+    dev_destroy(d);  // also the stream made before the failure
     return nullptr;
   }
   return d;
